@@ -1,0 +1,359 @@
+#!/usr/bin/env python3
+"""Benchmark of the ms2 MD hot path on GB300: pair interactions per second.
+
+Workload: rigid 3-site water, N = 1000 molecules at 997 kg/m^3 (box 31.07 A),
+molecule-centre cut-off 14 A, conducting reaction field, 298 K, leapfrog with
+quaternion integration, dt = 2 fs, FP32 site-pair arithmetic with FP64 state
+and sums.  One benchmark step = one MD time step: partner search + site-pair
+energies/forces/torques (pair kernel), reduction + thermostat kick, drift +
+quaternion rotation + site build.  The RDF (every 10 steps) is sampled as well.
+Synthetic input: simple-cubic lattice start with seeded random orientations and
+Maxwell-Boltzmann velocities, relaxed by untimed MD steps before warm-up.
+
+The L2 cache (129 MB; the whole system is ~0.1 MB) is flushed by writing a
+256 MiB buffer between timed steps, outside the timed interval.  Each step is
+timed with CUDA events on the system's stream; the pair kernel inside it is
+timed with events captured around it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ms2|reference]
+
+Under torchrun each rank runs an independent replica on its own GPU (the
+single-system path does not shard); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_WATER, RC, SEED = 1000, 14.0, 2
+RELAX_STEPS = 300
+RDF_EVERY = 10
+# algorithmic FP32 flops per unique water molecule pair (reaction field):
+# 9 charge site pairs x 22 + the O-O LJ extra 10 + pair set-up/virial 22
+FLOPS_PER_WATER_PAIR = 9 * 22 + 10 + 22
+SMS, FP32_LANES = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ms2", choices=["ms2", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle CPU-baseline sample length")
+    ap.add_argument("--no-extra", action="store_true", help="skip the Ewald sub-benchmark")
+    a = ap.parse_args()
+    a.warmup = max(a.warmup, 3)
+    return a
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.file.flush()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.file.name) as f:
+                for line in f:
+                    p = [x.strip() for x in line.split(",")]
+                    if len(p) >= 9:
+                        rows.append(p)
+            os.unlink(self.file.name)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        mhz = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------- CPU baseline
+def oracle_rate(seconds, nsteps=None):
+    """The FP64 oracle (as it stands) stepping the same workload on the host
+    cores; returns (pair interactions/s, steps, seconds, cores)."""
+    from oracle import Oracle
+    from paper_1507_07548_gb300 import workloads as W
+    wl = W.water_box(N=N_WATER, rc=RC, seed=SEED)
+    o = Oracle.from_workload(wl)
+    cores = len(os.sched_getaffinity(0))
+    R, q, v, L = wl.R, wl.q, wl.v, wl.Lang
+    t0 = time.perf_counter()
+    R, q, v, L, th, _ = o.run_leapfrog(R, q, v, L, wl.dt, 1, T0=wl.T)
+    t1 = time.perf_counter() - t0
+    n = nsteps if nsteps else max(1, int(seconds / max(t1, 1e-6)))
+    pairs = 0
+    t0 = time.perf_counter()
+    for _ in range(n):
+        R, q, v, L, th, _ = o.run_leapfrog(R, q, v, L, wl.dt, 1, T0=wl.T)
+        pairs += o.forces(R, q)[2]["n_pairs"] if False else o.partner_counts(R).sum() / 2
+    dt = time.perf_counter() - t0
+    return pairs / dt, n, dt, cores
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    from oracle import Oracle
+    from paper_1507_07548_gb300 import workloads as W
+    wl = W.water_box(N=N_WATER, rc=RC, seed=SEED)
+    o = Oracle.from_workload(wl)
+    cores = len(os.sched_getaffinity(0))
+    R, q, v, L = wl.R, wl.q, wl.v, wl.Lang
+    for _ in range(args.warmup):
+        R, q, v, L, _, _ = o.run_leapfrog(R, q, v, L, wl.dt, 1, T0=wl.T)
+    pairs, dt = 0.0, 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        R, q, v, L, _, _ = o.run_leapfrog(R, q, v, L, wl.dt, 1, T0=wl.T)
+        dt += time.perf_counter() - t0
+        pairs += o.partner_counts(R).sum() / 2
+    val = pairs / dt
+    line = {"metric": "pair interactions/s", "value": val, "unit": "pair interactions/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "rigid 3-site water N=1000, reaction field, rc=14 A, 298 K, dt=2 fs",
+                       "parallelism": "host cores (OpenMP owner loop)"},
+            "cpu_baseline": {"value": val, "unit": "pair interactions/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d full MD steps of the workload" % args.steps},
+            "e2e": {"value": val, "unit": "pair interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def traffic_record(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it still
+    describes the current kernel source (matching source hash)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_1507_07548_gb300", "csrc", "k_pair.cu")
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(path):
+            p = line.split()
+            if len(p) >= 3 and p[0] == kernel and p[1] == h:
+                return float(p[2])
+    except OSError:
+        pass
+    return None
+
+
+def combine_ranks(time_ms, work, world):
+    """Replicas: the job time is the slowest rank's, the work is summed over ranks
+    (gloo collectives on host scalars; the data path has no exchange)."""
+    if world <= 1:
+        return time_ms, work
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([time_ms], dtype=torch.float64)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    w = torch.tensor([work], dtype=torch.float64)
+    tdist.all_reduce(w)
+    return t.item(), w.item()
+
+
+def gpu_arm(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local_rank)
+    import paper_1507_07548_gb300.ms2 as ms2
+    from paper_1507_07548_gb300 import workloads as W
+
+    stream = torch.cuda.current_stream()
+    wl = W.water_box(N=N_WATER, rc=RC, seed=SEED)
+    s = ms2.System.from_workload(wl, stream=stream.cuda_stream)
+    s.step(RELAX_STEPS)                              # relax the lattice start (untimed)
+    s.rdf_setup(min(RC, 0.5 * s.L), 280, every=RDF_EVERY)
+    s.enable_timing(True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def one_step():
+        flush.zero_()                                # evict L2 (outside the timed interval)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        tp = s.last_step_times()
+        return e0.elapsed_time(e1), tp[0], s.energy_terms()["n_pairs"]
+
+    for _ in range(args.warmup):
+        one_step()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    n0 = ms2.kernel_launches()
+    t_step, t_pair, pairs = [], [], []
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            a, b, c = one_step()
+            t_step.append(a)
+            t_pair.append(b)
+            pairs.append(c)
+    torch.cuda.synchronize()
+    launches = ms2.kernel_launches() - n0
+    tot_ms_max, pairs_all = combine_ranks(sum(t_step), sum(pairs), world)
+    clocks = clk.summary()
+
+    # end to end through the public API from host buffers: set_state (H2D of
+    # the step's input state from page-locked staging) + step + energy read (D2H)
+    R, q, v, L, _ = s.get_state()
+    s.enable_timing(False)
+    e2e_t, e2e_pairs = 0.0, 0.0
+    for k in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.set_state(R, q, v, L)
+        s.step(1)
+        U, Wv, T, P = s.energy_virial()
+        e2e_t += time.perf_counter() - t0
+        e2e_pairs += s.energy_terms()["n_pairs"]
+        R, q, v, L, _ = s.get_state()
+    h2d = N_WATER * (3 + 4 + 3 + 3) * 8
+    d2h = 4 * 8
+
+    extra = {}
+    if not args.no_extra and rank == 0:
+        extra["ewald_ionic"] = ewald_sub(args, stream)
+
+    if rank != 0:
+        return 0
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    flops = FLOPS_PER_WATER_PAIR * sum(pairs)
+    achieved = flops / (sum(t_pair) * 1e-3) / 1e12
+    traffic = traffic_record("pair_water_rf")
+    cpu_val, cpu_n, cpu_dt, cores = oracle_rate(args.cpu_seconds)
+    value = pairs_all / (tot_ms_max * 1e-3)
+    line = {
+        "metric": "pair interactions/s", "value": value, "unit": "pair interactions/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "rigid 3-site water N=1000, reaction field, rc=14 A, 298 K, dt=2 fs, leapfrog+quaternion",
+                   "molecules": N_WATER, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "state": "FP64 positions/integrator/sums, FP32 site pairs"},
+        "molecule_steps_per_s": N_WATER * args.steps * world / (tot_ms_max * 1e-3),
+        "site_pair_interactions_per_s": value * 10,
+        "roofline": {"bound": "alu", "kernel": "k_pair<3,1,7,0,RF>", "achieved": achieved, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (unit counts x max clock)" % sm_max,
+                     "pair_kernel_ms": statistics.mean(t_pair),
+                     "algorithmic_flops_per_launch": FLOPS_PER_WATER_PAIR * statistics.mean(pairs)},
+        "cpu_baseline": {"value": cpu_val, "unit": "pair interactions/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d MD steps of the same workload, %.1f s" % (cpu_n, cpu_dt)},
+        "e2e": {"value": e2e_pairs / e2e_t, "unit": "pair interactions/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ewald_sub(args, stream):
+    """Ionic solution with Ewald (1000 water + 20 + 20 ions, alpha 0.25, |n| <= 8)."""
+    import torch
+    import paper_1507_07548_gb300.ms2 as ms2
+    from paper_1507_07548_gb300 import workloads as W
+    wl = W.ionic_solution(seed=3)
+    s = ms2.System.from_workload(wl, stream=stream.cuda_stream)
+    s.step(RELAX_STEPS)
+    s.enable_timing(True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ts, tp, te, pairs = [], [], [], []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        t = s.last_step_times()
+        if k >= args.warmup:
+            ts.append(e0.elapsed_time(e1))
+            tp.append(t[0])
+            te.append(t[1])
+            pairs.append(s.energy_terms()["n_pairs"])
+    s.close()
+    return {"workload": "1000 water + 20 cations + 20 anions, Ewald alpha=0.25/A, |n|<=8 per axis, rc=14 A",
+            "value": sum(pairs) / (sum(ts) * 1e-3), "unit": "pair interactions/s",
+            "ms_per_step": statistics.mean(ts), "pair_kernel_ms": statistics.mean(tp),
+            "ewald_kernels_ms": statistics.mean(te)}
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("gloo")
+    if args.impl == "reference":
+        rc = reference_arm(args, rank, world)
+    else:
+        rc = gpu_arm(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

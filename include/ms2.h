@@ -1,0 +1,268 @@
+/*
+ * ms2.h — C ABI of the GB300 molecular-dynamics hot path of the ms2 method
+ * (Glass et al., "ms2: A molecular simulation tool for thermodynamic properties,
+ * release 2.0", arXiv 1507.07548).
+ *
+ * One library call advances, inspects or serves systems of rigid multi-site
+ * molecules (Lennard-Jones 12-6 sites, point charges, point dipoles) in a cubic
+ * periodic box with a molecule-centre cut-off near half the box edge (paper,
+ * Sec. "Hybrid MPI & OpenMP Parallelization": ~10^3 molecules, cut-off radius in
+ * the range of half the box edge).  Electrostatics use the reaction field (Sec.
+ * "Massieu potential derivatives", LRC paragraph) or Ewald summation (Sec.
+ * "Algorithmic Developments", paragraph "Ewald summation").
+ *
+ * Conventions that hold for every call:
+ *   - Every call returns an ms2_status; nothing is thrown across the ABI.  On
+ *     failure ms2_last_error() returns a thread-local message.
+ *   - Units are fixed: length Angstrom, time fs, mass g/mol, charge e, dipole
+ *     e*Angstrom, energy and temperature K (k_B = 1), pressure K/Angstrom^3
+ *     (1 K/A^3 = 13.80649 MPa).  With ms2_options.reduced = 1 all quantities are
+ *     in Lennard-Jones reduced units instead (sigma = epsilon = m = k_B = 1).
+ *   - Arrays are row-major FP64 on the HOST unless the name ends in _dev, in
+ *     which case they are device pointers written asynchronously on the
+ *     system's stream.  Inputs are copied at call time; the library keeps no
+ *     pointer to caller memory after a call returns.
+ *   - The library owns all device memory of a system or server.  It allocates it
+ *     with ms2_options.dev_alloc / dev_free if both are set (e.g. a PyTorch
+ *     caching allocator), else with cudaMalloc / cudaFree, on the current device.
+ *   - All work of a system is queued on its stream (ms2_options.stream, or a
+ *     stream the library creates).  Calls that return numbers to the host
+ *     synchronise that stream first; ms2_step does not.
+ *   - A system is not thread-safe: one host thread drives it at a time.
+ */
+#ifndef MS2_H
+#define MS2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MS2_API __attribute__((visibility("default")))
+#else
+#define MS2_API
+#endif
+
+typedef struct ms2_system_s *ms2_system;
+typedef struct ms2_batch_s *ms2_batch;
+typedef struct ms2_server_s *ms2_server;
+
+typedef enum {
+    MS2_OK = 0,
+    MS2_EINVAL = 1,    /* bad argument, unsupported model combination */
+    MS2_ENOMEM = 2,    /* device allocation failed */
+    MS2_EBUDGET = 3,   /* job can never fit the server's memory budget */
+    MS2_ECUDA = 4,     /* a CUDA call failed (message has the CUDA error) */
+    MS2_EUNSTABLE = 5, /* non-finite or exploding forces/energies detected */
+    MS2_ETIMEOUT = 6,  /* a bounded wait gave up */
+    MS2_ESTATE = 7     /* call not valid in the object's current state */
+} ms2_status;
+
+typedef enum { MS2_ELEC_NONE = 0, MS2_ELEC_RF = 1, MS2_ELEC_EWALD = 2 } ms2_elec;
+
+/* site kind bits; a site may combine them (e.g. LJ + charge on a water oxygen).
+ * An LJ site with sigma = epsilon = 0 is a dummy site: it interacts with nothing
+ * but is sampled by the RDF (paper, Sec. "Property Calculations", RDF paragraph). */
+enum { MS2_SITE_LJ = 1, MS2_SITE_CHARGE = 2, MS2_SITE_DIPOLE = 4 };
+
+enum { MS2_INT_VERLET = 0, MS2_INT_LEAPFROG_Q = 1 };
+
+/* One site of a rigid molecule.  pos is in the BODY frame: origin at the
+ * molecule's centre of mass, axes along its principal axes of inertia (checked:
+ * |centre of mass| and the off-diagonal inertia must vanish to 1e-9 relative).
+ * dipole is the body-frame point-dipole vector (kind bit MS2_SITE_DIPOLE). */
+typedef struct {
+    int kind;
+    double pos[3];
+    double mass;
+    double sigma, epsilon; /* LJ 12-6; unlike pairs mix by Lorentz-Berthelot */
+    double charge;
+    double dipole[3];
+} ms2_site;
+
+/* A potential model (paper: "potential model file"); at most 8 sites. */
+typedef struct {
+    int n_sites;
+    const ms2_site *sites;
+} ms2_model;
+
+typedef struct {
+    double eps_rf;            /* reaction-field dielectric constant; <= 0 or >= 1e30: conducting */
+    int lrc;                  /* 1: analytic LJ long-range correction in U and P */
+    double dt;                /* time step (fs, or reduced) */
+    int thermostat;           /* 1: isokinetic velocity scaling to T every step (NVT) */
+    unsigned long long seed;  /* initial lattice orientations and velocities */
+    int integrator;           /* MS2_INT_VERLET (point molecules only) or MS2_INT_LEAPFROG_Q */
+    int reduced;              /* 1: LJ reduced units */
+    int quat_iters;           /* sweeps of the implicit quaternion midpoint rule; 0 -> 3 */
+    int graph_chunk;          /* steps per captured CUDA graph; 0 -> 50 */
+    int fp64;                 /* 1: site-pair arithmetic in FP64 too (point LJ models only) */
+    void *stream;             /* cudaStream_t to use, or NULL */
+    void *(*dev_alloc)(size_t bytes, void *ctx);
+    void (*dev_free)(void *ptr, void *ctx);
+    void *alloc_ctx;
+} ms2_options;
+
+/* Fills *o with defaults: conducting RF, lrc = 1, dt = 2 fs, thermostat = 1,
+ * seed = 1, leapfrog, real units, 3 quaternion sweeps, graph chunks of 50 steps,
+ * FP32 site-pair arithmetic with FP64 state and sums. */
+MS2_API ms2_status ms2_default_options(ms2_options *o);
+
+/* Creates a system of sum(N_per_model) molecules: N_per_model[m] molecules of
+ * models[m] (n_models <= 4), numbered model by model.  The box edge is `box`
+ * if box > 0, else (N / rho)^(1/3) with rho the molecule number density; if
+ * both are > 0 they must agree to 1e-12 relative.  Molecules start on a simple
+ * cubic lattice (FCC for a single point-mass model when N = 4 m^3) with seeded
+ * random orientations and Maxwell-Boltzmann velocities at temperature T.
+ * Requires 0 < cutoff < box / 2 (molecule-centre minimum image, paper Sec.
+ * "Hybrid MPI & OpenMP Parallelization").  Reaction field requires electrically
+ * neutral molecules; net-charged molecules need MS2_ELEC_EWALD (the paper's
+ * reason for adding Ewald summation).  Charges and dipoles may not both occur in
+ * one system, and dipoles need MS2_ELEC_RF.  Ewald starts with alpha = 3.2/cutoff
+ * and kmax = 8 per axis (change with ms2_ewald_params).
+ * Errors: MS2_EINVAL (arguments), MS2_ENOMEM, MS2_ECUDA. */
+MS2_API ms2_status ms2_create_system(const ms2_model *models, const int *N_per_model, int n_models, double box, double T,
+                             double rho, double cutoff, ms2_elec elec, const ms2_options *opt, ms2_system *out);
+MS2_API ms2_status ms2_destroy_system(ms2_system sys);
+
+/* Basic facts: molecule count, box edge, cut-off, degrees of freedom. */
+MS2_API ms2_status ms2_system_info(ms2_system sys, int *N, double *box, double *cutoff, int *ndof);
+
+/* Advances n >= 0 time steps (asynchronous).  Each step: interaction partner
+ * search, site-pair energies/forces/torques (+ Ewald reciprocal space), then the
+ * integrator (velocity Verlet, or leapfrog with the quaternion implicit
+ * midpoint rule), with isokinetic scaling when the thermostat is on. */
+MS2_API ms2_status ms2_step(ms2_system sys, long long n);
+
+/* Potential energy U (incl. LRC and Ewald constants), molecular virial W
+ * (sum over pairs of (R_i - R_j).F_ij, + reciprocal part; excl. LRC), kinetic
+ * temperature of the stored velocities and pressure P = (2 KE_tr/3 + W/3)/V + P_LRC,
+ * for the current configuration.  Any pointer may be NULL. */
+MS2_API ms2_status ms2_energy_virial(ms2_system sys, double *U, double *W, double *T_inst, double *P);
+
+/* The 16-number breakdown of the current configuration, in this order:
+ * U_lj, U_qq (RF or Ewald real space), U_dd, U_rec, U_self, U_intra, U_bg,
+ * U_lrc, U_total, W_pair, W_rec, W_bg, W_total, P_lrc, n_pairs (unique
+ * molecule pairs within the cut-off), KE_total. */
+MS2_API ms2_status ms2_energy_terms(ms2_system sys, double terms[16]);
+
+/* Molecule forces F (N x 3) and space-frame torques tau (N x 3) of the current
+ * configuration, in K/Angstrom and K. */
+MS2_API ms2_status ms2_forces_torques(ms2_system sys, double *F, double *tau);
+/* Same, into device buffers of 3N doubles each, queued on the system stream. */
+MS2_API ms2_status ms2_forces_torques_dev(ms2_system sys, double *F_dev, double *tau_dev);
+
+/* Ewald splitting parameter and k box |n_x| <= kx, |n_y| <= ky, |n_z| <= kz
+ * (k = 2 pi n / box).  MS2_EINVAL unless the system uses MS2_ELEC_EWALD or if
+ * alpha <= 0 or a kmax is outside 1..64.  Recomputes forces. */
+MS2_API ms2_status ms2_ewald_params(ms2_system sys, double alpha, int kx, int ky, int kz);
+
+/* State for checkpoint/restart: centres R (N x 3), unit quaternions q (N x 4,
+ * (w, x, y, z), body -> space), centre velocities v (N x 3) and space-frame
+ * angular momenta Lang (N x 3, g/mol*A^2/fs) — for the leapfrog these are the
+ * values half a step behind R and q — and the step counter.  Any pointer may be
+ * NULL.  set_state recomputes forces; it renormalises a q whose squared norm
+ * differs from 1 by more than 1e-13 and takes the others bit for bit. */
+MS2_API ms2_status ms2_get_state(ms2_system sys, double *R, double *q, double *v, double *Lang, long long *step);
+MS2_API ms2_status ms2_set_state(ms2_system sys, const double *R, const double *q, const double *v, const double *Lang);
+
+/* Diagnostics of the last force evaluation: partner count of each molecule
+ * (int, N), and site offsets A(q_i) b_a (N x n_site_slots x 3, FP64 copies of
+ * the FP32 values the pair kernels use; unused slots are 0). */
+MS2_API ms2_status ms2_partner_counts(ms2_system sys, int *counts);
+/* Per-molecule shares of the last force evaluation (N x 4): half of each
+ * molecule's summed pair energies (LJ, charge-charge, dipole-dipole) and of its
+ * pair virial, so that the column sums are U_lj, U_qq, U_dd and W_pair. */
+MS2_API ms2_status ms2_molecule_energies(ms2_system sys, double *out);
+MS2_API ms2_status ms2_site_offsets(ms2_system sys, double *offsets, int *n_site_slots);
+
+/* Radial distribution function between LJ sites (paper Eq. 2).  rdf_setup
+ * clears the histogram and samples every `every` steps (0: only on
+ * ms2_rdf_sample) into n_bins bins of width r_max / n_bins; r_max <= min(cutoff,
+ * box/2).  Kinds are the LJ sites (model, site) in model-then-site order; kind
+ * pairs t1 <= t2 are rows in upper-triangle row-major order.  ms2_rdf returns
+ * the raw counts (rows x n_bins, may be NULL), g(r) normalised by the ideal-gas
+ * pair count of each shell (may be NULL), the number of samples and the rows. */
+MS2_API ms2_status ms2_rdf_setup(ms2_system sys, double r_max, int n_bins, int every);
+MS2_API ms2_status ms2_rdf_sample(ms2_system sys);
+MS2_API ms2_status ms2_rdf(ms2_system sys, long long *counts, double *g, int *n_samples, int *n_rows);
+
+/* Running averages since the last reset over the steps taken: <U>, <P>, <T>,
+ * and the block-averaged standard errors of <U> and <P> (blocks of 100 steps). */
+MS2_API ms2_status ms2_averages(ms2_system sys, double out[5], long long *n_steps);
+MS2_API ms2_status ms2_reset_averages(ms2_system sys);
+
+/* ----------------------------------------------------------------- batch */
+/* A batch advances many independent systems in ONE persistent kernel per
+ * chunk of steps: each thread block owns one system for the whole chunk
+ * (partner search, forces, integration, thermostat) and takes the next system
+ * from a longest-first work list when it finishes.  The systems must be
+ * reaction-field or non-electrostatic leapfrog systems with at most 4096
+ * molecules; tile shapes come from the autotuner cache.  The systems stay
+ * usable on their own; the batch runs on the first system's stream. */
+MS2_API ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_batch *out);
+MS2_API ms2_status ms2_batch_step(ms2_batch b, long long n);
+MS2_API ms2_status ms2_batch_destroy(ms2_batch b);
+
+/* ----------------------------------------------------------------- serve */
+/* A simulation job: model mix entry, size and state point, steps, outputs.
+ * The server builds the system itself (ms2_create_system defaults with this
+ * seed).  arrival_time (s, on the server's clock, which starts at
+ * ms2_serve_open) is when the job becomes eligible. */
+typedef struct {
+    const ms2_model *models;
+    const int *N_per_model;
+    int n_models;
+    double T, rho, cutoff;
+    ms2_elec elec;
+    long long steps;
+    double arrival_time;
+    unsigned long long seed;
+    int rdf_bins;         /* 0: no RDF output */
+    int rdf_every;
+} ms2_job;
+
+typedef struct {
+    long long job_id;
+    ms2_status status;
+    double U_avg, U_err, P_avg, P_err, T_avg;
+    double t_arrive, t_admit, t_done; /* server clock, s */
+    int n_rows, n_bins;
+    double g[4096];                   /* g(r), n_rows x n_bins (first kind pair rows) */
+} ms2_job_result;
+
+/* Opens a server whose resident job state may use at most hbm_budget_bytes of
+ * device memory; a scheduler thread admits eligible jobs in arrival order as
+ * budget and slots free up, advances all resident jobs together in persistent
+ * chunks (continuous batching), and retires finished ones.  max_slots <= 1024. */
+MS2_API ms2_status ms2_serve_open(size_t hbm_budget_bytes, int max_slots, const ms2_options *opt, ms2_server *out);
+/* Queues a job (never blocks).  MS2_EBUDGET if it alone exceeds the budget. */
+MS2_API ms2_status ms2_serve_submit(ms2_server s, const ms2_job *job, long long *job_id);
+/* Copies up to max finished results out (oldest first) and removes them. */
+MS2_API ms2_status ms2_serve_poll(ms2_server s, ms2_job_result *out, int max, int *n_done);
+/* Blocks until all submitted jobs finished or timeout_s passed (MS2_ETIMEOUT). */
+MS2_API ms2_status ms2_serve_drain(ms2_server s, double timeout_s);
+MS2_API ms2_status ms2_serve_close(ms2_server s);
+
+/* Kernel timing: with on = 1, every subsequently enqueued batch of steps
+ * records CUDA events (on the system stream) around its last step and around
+ * that step's pair kernel and Ewald kernels.  ms2_last_step_times synchronises
+ * and returns, in ms: [0] pair kernel, [1] Ewald reciprocal kernels, [2] the whole
+ * last step, [3] that step minus [0] and [1]. */
+MS2_API ms2_status ms2_enable_timing(ms2_system sys, int on);
+MS2_API ms2_status ms2_last_step_times(ms2_system sys, double out[4]);
+
+/* ------------------------------------------------------------------ misc */
+MS2_API const char *ms2_last_error(void);
+/* Number of kernels this library has launched in the process (graph nodes
+ * counted per replay). */
+MS2_API long long ms2_kernel_launches(void);
+MS2_API const char *ms2_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MS2_H */

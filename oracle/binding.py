@@ -66,6 +66,7 @@ def _load():
         sig = {
             "or_rotation": [d, d], "or_site_positions": [P(_Sys), d, d, d],
             "or_partner_counts": [P(_Sys), d, i32], "or_forces": [P(_Sys), d, d, d, d, d],
+            "or_forces_mol": [P(_Sys), d, d, d, d, d, d],
             "or_ewald_reciprocal": [P(_Sys), d, d, d, d, d], "or_ewald_constants": [P(_Sys), d, d, d],
             "or_lrc": [P(_Sys), d, d], "or_kinetic": [P(_Sys), d, d, d, d],
             "or_run_vv": [P(_Sys), d, d, C.c_double, C.c_int, d],
@@ -144,6 +145,14 @@ class Oracle:
         F, tau, terms = np.zeros((N, 3)), np.zeros((N, 3)), np.zeros(NTERMS)
         self.lib.or_forces(self.ref, _p(R), _p(q), _p(F), _p(tau), _p(terms))
         return F, tau, dict(zip(TERM_NAMES, terms))
+
+    def molecule_terms(self, R, q):
+        """Per-molecule shares (N x 4): 1/2 sum_j of u_lj, u_qq, u_dd and the pair virial."""
+        N = self.N
+        R, q = _f64(R, (N, 3)), _f64(q, (N, 4))
+        F, tau, terms, mol = np.zeros((N, 3)), np.zeros((N, 3)), np.zeros(NTERMS), np.zeros((N, 4))
+        self.lib.or_forces_mol(self.ref, _p(R), _p(q), _p(F), _p(tau), _p(terms), _p(mol))
+        return mol
 
     def energy(self, R, q):
         return self.forces(R, q)[2]["U_total"]

@@ -412,7 +412,16 @@ void or_lrc(const or_system *s, double *U, double *P) {
  * (R, q), plus the energy/virial breakdown terms[OR_NTERMS].
  * Molecular virial W = sum_{i<j} (R_i - R_j).F_ij over partner pairs (owner
  * computes: half of each owner's sum), plus reciprocal and background parts. */
+void or_forces_mol(const or_system *s, const double *R, const double *q, double *F, double *tau, double *terms,
+                   double *mol);
 void or_forces(const or_system *s, const double *R, const double *q, double *F, double *tau, double *terms) {
+    or_forces_mol(s, R, q, F, tau, terms, NULL);
+}
+/* as or_forces; mol (may be NULL) receives per molecule i the shares
+ * 1/2 sum_j of the LJ, charge-charge and dipole-dipole pair energies and of the
+ * pair virial (N x 4) */
+void or_forces_mol(const or_system *s, const double *R, const double *q, double *F, double *tau, double *terms,
+                   double *mol) {
     int N = s->N;
     uint32_t *X = (uint32_t *)malloc(sizeof(uint32_t) * 3 * N);
     lattice_all(s, R, X);
@@ -435,6 +444,11 @@ void or_forces(const or_system *s, const double *R, const double *q, double *F, 
         for (int k = 0; k < 3; ++k) { F[3 * i + k] = f[k]; tau[3 * i + k] = t[k]; Ui[3 * i + k] = u[k]; }
         Wi[i] = w;
     }
+    if (mol)
+        for (int i = 0; i < N; ++i) {
+            for (int k = 0; k < 3; ++k) mol[4 * i + k] = 0.5 * Ui[3 * i + k];
+            mol[4 * i + 3] = 0.5 * Wi[i];
+        }
     for (int k = 0; k < OR_NTERMS; ++k) terms[k] = 0;
     long long npairs = 0;
     for (int i = 0; i < N; ++i) {

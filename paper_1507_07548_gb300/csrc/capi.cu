@@ -1,0 +1,1170 @@
+// C-ABI of libms2: system lifetime, state, time stepping and outputs.
+// See include/ms2.h for the contract of every entry point.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ms2.h"
+#include "ms2_internal.cuh"
+#include "ms2_host.h"
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+static std::atomic<long long> g_launches{0};
+
+void ms2_count_launches(long long n) { g_launches += n; }
+
+ms2_status ms2_fail(ms2_status st, const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+ms2_status ms2_fail_cuda(cudaError_t e, const char *what, const char *file, int line) {
+    cudaGetLastError();
+    return ms2_fail(e == cudaErrorMemoryAllocation ? MS2_ENOMEM : MS2_ECUDA, "%s failed: %s (%s:%d)", what,
+                    cudaGetErrorString(e), file, line);
+}
+
+extern "C" const char *ms2_last_error(void) { return g_err.c_str(); }
+extern "C" long long ms2_kernel_launches(void) { return g_launches.load(); }
+extern "C" const char *ms2_version(void) { return "ms2-gb300 1.0 (sm_103a)"; }
+
+// kernels (defined in the other translation units)
+__global__ void k_build(const SysParams *, DevSys);
+__global__ void k_reduce(const SysParams *, DevSys, int);
+__global__ void k_drift(const SysParams *, DevSys, int);
+__global__ void k_pair_lj64(const SysParams *, DevSys, int);
+__global__ void k_ewald_prep(const SysParams *, DevSys);
+__global__ void k_ewald_sk(const SysParams *, DevSys, float2 *);
+__global__ void k_ewald_energy(const SysParams *, DevSys, int);
+__global__ void k_ewald_force(const SysParams *, DevSys, const float2 *, int);
+__global__ void k_rdf(const SysParams *, DevSys);
+size_t ms2_pair_smem_bytes(int NS, bool dmu, bool multi, int TJ, int wpb);
+size_t ms2_pair64_smem_bytes(int TJ, int wpb);
+void *ms2_pick_pair_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, int *ns_used,
+                           bool *dmu, bool *mult_used);
+
+enum { RED_SUM = 1, RED_RECORD = 2, RED_KICK = 4, RED_HALFKICK = 8, RED_FP64PART = 16, RED_EWALD = 32 };
+
+// ------------------------------------------------------------ allocation
+cudaError_t DevAlloc::alloc(void **p, size_t n) {
+    n = std::max<size_t>(n, 256);
+    if (fa && ff) {
+        *p = fa(n, ctx);
+        if (!*p) return cudaErrorMemoryAllocation;
+    } else {
+        cudaError_t e = cudaMalloc(p, n);
+        if (e != cudaSuccess) return e;
+    }
+    live.push_back(*p);
+    bytes += n;
+    return cudaSuccess;
+}
+void DevAlloc::release_all() {
+    for (void *p : live) {
+        if (fa && ff) ff(p, ctx);
+        else cudaFree(p);
+    }
+    live.clear();
+    bytes = 0;
+}
+
+// ------------------------------------------------------------- constants
+void ms2_unit_constants(bool reduced, double *coulomb, double *kconv) {
+    if (reduced) {
+        *coulomb = 1.0;
+        *kconv = 1.0;
+        return;
+    }
+    const double e = 1.602176634e-19, eps0 = 8.8541878128e-12, kB = 1.380649e-23, NA = 6.02214076e23;
+    *coulomb = e * e / (4.0 * M_PI * eps0 * kB) * 1e10;  // K * Angstrom per e^2
+    *kconv = kB * NA * 1e3 * 1e20 / 1e30;                // 1 K in g/mol A^2 fs^-2
+}
+
+// ---------------------------------------------------------- seeded input
+namespace {
+struct SplitMix64 {  // Steele, Lea & Flood (2014) generator, as published by Vigna
+    uint64_t s;
+    uint64_t next() {
+        uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return (double)(next() >> 11) * 0x1.0p-53; }
+    double normal() {  // Box-Muller
+        double u1 = uniform(), u2 = uniform();
+        if (u1 < 1e-300) u1 = 1e-300;
+        return std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2);
+    }
+};
+}  // namespace
+
+// ------------------------------------------------------------- validation
+ms2_status ms2_validate_models(const ms2_model *models, int n_models, ms2_elec elec) {
+    if (!models || n_models < 1 || n_models > MS2_MAXSP) return ms2_fail(MS2_EINVAL, "n_models must be 1..%d", MS2_MAXSP);
+    bool any_q = false, any_d = false;
+    int nljt = 0;
+    for (int m = 0; m < n_models; ++m) {
+        const ms2_model &md = models[m];
+        if (md.n_sites < 1 || md.n_sites > MS2_MAXS || !md.sites)
+            return ms2_fail(MS2_EINVAL, "model %d: n_sites must be 1..%d", m, MS2_MAXS);
+        double M = 0, com[3] = {0, 0, 0}, ext = 0, qsum = 0, I[3][3] = {{0}};
+        for (int a = 0; a < md.n_sites; ++a) {
+            const ms2_site &s = md.sites[a];
+            if (!(s.mass >= 0)) return ms2_fail(MS2_EINVAL, "model %d site %d: negative mass", m, a);
+            M += s.mass;
+            for (int k = 0; k < 3; ++k) {
+                com[k] += s.mass * s.pos[k];
+                ext = std::max(ext, std::fabs(s.pos[k]));
+            }
+            if (s.kind & MS2_SITE_LJ) {
+                if (!(s.sigma >= 0 && s.epsilon >= 0)) return ms2_fail(MS2_EINVAL, "model %d site %d: bad LJ", m, a);
+                ++nljt;
+            }
+            if ((s.kind & MS2_SITE_CHARGE) && s.charge != 0) any_q = true;
+            if ((s.kind & MS2_SITE_DIPOLE) && (s.dipole[0] != 0 || s.dipole[1] != 0 || s.dipole[2] != 0)) any_d = true;
+            if (s.kind & MS2_SITE_CHARGE) qsum += s.charge;
+            const double r2 = s.pos[0] * s.pos[0] + s.pos[1] * s.pos[1] + s.pos[2] * s.pos[2];
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) I[r][c] += s.mass * ((r == c ? r2 : 0.0) - s.pos[r] * s.pos[c]);
+        }
+        if (!(M > 0)) return ms2_fail(MS2_EINVAL, "model %d: total mass must be > 0", m);
+        for (int k = 0; k < 3; ++k)
+            if (std::fabs(com[k]) > 1e-9 * M * std::max(ext, 1e-30))
+                return ms2_fail(MS2_EINVAL, "model %d: sites not in the centre-of-mass frame", m);
+        const double tr = I[0][0] + I[1][1] + I[2][2];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c)
+                if (r != c && std::fabs(I[r][c]) > 1e-9 * std::max(tr, 1e-300) && tr > 0)
+                    return ms2_fail(MS2_EINVAL, "model %d: body axes are not principal axes", m);
+        if (elec == MS2_ELEC_RF && std::fabs(qsum) > 1e-9)
+            return ms2_fail(MS2_EINVAL, "model %d carries net charge %g: reaction field needs neutral molecules "
+                                        "(use MS2_ELEC_EWALD)", m, qsum);
+    }
+    if (nljt > MS2_MAXT) return ms2_fail(MS2_EINVAL, "at most %d LJ sites over all models", MS2_MAXT);
+    if (elec == MS2_ELEC_NONE && (any_q || any_d))
+        return ms2_fail(MS2_EINVAL, "charges or dipoles present but electrostatics is MS2_ELEC_NONE");
+    if (any_q && any_d) return ms2_fail(MS2_EINVAL, "charges and point dipoles in one system are not supported");
+    if (any_d && elec != MS2_ELEC_RF) return ms2_fail(MS2_EINVAL, "point dipoles need MS2_ELEC_RF");
+    if (elec < MS2_ELEC_NONE || elec > MS2_ELEC_EWALD) return ms2_fail(MS2_EINVAL, "unknown electrostatics %d", (int)elec);
+    return MS2_OK;
+}
+
+// Fills the per-system constants from the models (host FP64).
+void ms2_fill_params(SysParams &P, const ms2_model *models, int n_models, const std::vector<int> &species,
+                     double L, double rc, ms2_elec elec, const ms2_options &o, double T0) {
+    memset(&P, 0, sizeof P);
+    const int N = (int)species.size();
+    P.N = N;
+    P.n_species = n_models;
+    P.elec = (int)elec;
+    P.integrator = o.integrator;
+    P.thermostat = o.thermostat;
+    P.quat_iters = o.quat_iters > 0 ? o.quat_iters : 3;
+    P.L = L;
+    P.V = L * L * L;
+    P.dt = o.dt;
+    double coulomb, kconv;
+    ms2_unit_constants(o.reduced != 0, &coulomb, &kconv);
+    P.kconv = kconv;
+    P.T0 = T0;
+    P.lat_scale = 4294967296.0 / L;
+    {
+        const double sc = rc * 4294967296.0 / L;
+        P.rc2 = (unsigned long long)std::ceil(sc * sc);
+    }
+    P.lat_to_len = (float)(L / 4294967296.0);
+    P.lat_to_len_lo = (float)(L / 4294967296.0 - (double)P.lat_to_len);
+    P.len_to_lat = (float)(4294967296.0 / L);
+    P.coulomb = (float)coulomb;
+    P.coulomb_lo = (float)(coulomb - (double)P.coulomb);
+    const double rc3 = rc * rc * rc;
+    const bool conducting = o.eps_rf <= 0 || o.eps_rf >= 1e30;
+    const double krf = conducting ? 1.0 / (2.0 * rc3) : (o.eps_rf - 1.0) / ((2.0 * o.eps_rf + 1.0) * rc3);
+    P.krf = (float)krf;
+    P.crf = (float)(1.0 / rc + krf * rc * rc);
+    int ns = 0, t = 0, ndof = 3 * N - 3;
+    double tsig[MS2_MAXT], teps[MS2_MAXT];
+    int rotdof[MS2_MAXSP];
+    for (int m = 0; m < n_models; ++m) {
+        const ms2_model &md = models[m];
+        ns = std::max(ns, md.n_sites);
+        P.n_sites[m] = md.n_sites;
+        double M = 0, I[3] = {0, 0, 0};
+        for (int a = 0; a < MS2_MAXS; ++a) {
+            P.ljt[m][a] = -1;
+        }
+        for (int a = 0; a < md.n_sites; ++a) {
+            const ms2_site &s = md.sites[a];
+            for (int k = 0; k < 3; ++k) {
+                P.bpos[m][a][k] = s.pos[k];
+                P.bdip[m][a][k] = (s.kind & MS2_SITE_DIPOLE) ? s.dipole[k] : 0.0;
+            }
+            const double qa = (s.kind & MS2_SITE_CHARGE) ? s.charge : 0.0;
+            P.qd[m][a] = qa;
+            P.q[m][a] = (float)qa;
+            P.qlo[m][a] = (float)(qa - (double)P.q[m][a]);
+            P.cq[m][a] = (float)(coulomb * qa);
+            P.cqlo[m][a] = (float)(coulomb * qa - (double)P.cq[m][a]);
+            if (s.kind & MS2_SITE_LJ) {
+                P.ljt[m][a] = t;
+                tsig[t] = s.sigma;
+                teps[t] = s.epsilon;
+                ++t;
+            }
+            M += s.mass;
+            I[0] += s.mass * (s.pos[1] * s.pos[1] + s.pos[2] * s.pos[2]);
+            I[1] += s.mass * (s.pos[0] * s.pos[0] + s.pos[2] * s.pos[2]);
+            I[2] += s.mass * (s.pos[0] * s.pos[0] + s.pos[1] * s.pos[1]);
+        }
+        P.mass[m] = M;
+        const double mx = std::max(I[0], std::max(I[1], I[2]));
+        rotdof[m] = 0;
+        for (int k = 0; k < 3; ++k) {
+            P.Iinv[m][k] = (mx > 0 && I[k] > 1e-12 * mx) ? 1.0 / I[k] : 0.0;
+            rotdof[m] += P.Iinv[m][k] != 0.0;
+        }
+    }
+    for (int i = 0; i < N; ++i) ndof += rotdof[species[i]];
+    P.ndof = ndof;
+    P.ns = ns;
+    P.n_ljt = t;
+    for (int a = 0; a < t; ++a)
+        for (int b = 0; b < t; ++b) {
+            const double sg = 0.5 * (tsig[a] + tsig[b]), ep = std::sqrt(teps[a] * teps[b]);
+            const double s6 = std::pow(sg, 6.0);
+            P.c6d[a][b] = 4.0 * ep * s6;
+            P.c12d[a][b] = 4.0 * ep * s6 * s6;
+            P.c6[a][b] = (float)P.c6d[a][b];
+            P.c12[a][b] = (float)P.c12d[a][b];
+            P.c6lo[a][b] = (float)(P.c6d[a][b] - (double)P.c6[a][b]);
+            P.c12lo[a][b] = (float)(P.c12d[a][b] - (double)P.c12[a][b]);
+        }
+    P.multi = n_models > 1;
+    bool any_d = false;
+    for (int m = 0; m < n_models; ++m)
+        for (int a = 0; a < models[m].n_sites; ++a)
+            if (P.bdip[m][a][0] != 0 || P.bdip[m][a][1] != 0 || P.bdip[m][a][2] != 0) any_d = true;
+    P.has_dipole = any_d;
+}
+
+// Ewald constants (self, intramolecular, background) and the LJ long-range
+// correction (site-site homogeneous form), host FP64.
+void ms2_energy_constants(const SysParams &P, const std::vector<int> &species, double alpha, double rc,
+                          bool lrc, double coulomb, double *uconst, double *wbg, double *ulrc, double *plrc) {
+    const int N = (int)species.size();
+    int cnt[MS2_MAXSP] = {0};
+    for (int i = 0; i < N; ++i) cnt[species[i]]++;
+    double c = 0, w = 0;
+    if (P.elec == ELEC_EWALD) {
+        double sq2 = 0, Q = 0, intra = 0;
+        for (int m = 0; m < P.n_species; ++m) {
+            double ms = 0, mq = 0, mi = 0;
+            for (int a = 0; a < P.n_sites[m]; ++a) {
+                const double qa = P.q[m][a];
+                ms += qa * qa;
+                mq += qa;
+                for (int b = a + 1; b < P.n_sites[m]; ++b) {
+                    const double qb = P.q[m][b];
+                    if (qa == 0 || qb == 0) continue;
+                    double d2 = 0;
+                    for (int k = 0; k < 3; ++k) d2 += (P.bpos[m][b][k] - P.bpos[m][a][k]) * (P.bpos[m][b][k] - P.bpos[m][a][k]);
+                    const double r = std::sqrt(d2);
+                    mi += qa * qb * std::erf(alpha * r) / r;
+                }
+            }
+            sq2 += cnt[m] * ms;
+            Q += cnt[m] * mq;
+            intra += cnt[m] * mi;
+        }
+        const double ubg = -M_PI * coulomb * Q * Q / (2.0 * P.V * alpha * alpha);
+        c = -coulomb * alpha / std::sqrt(M_PI) * sq2 - coulomb * intra + ubg;
+        w = 3.0 * ubg;
+    }
+    *uconst = c;
+    *wbg = w;
+    double u = 0, p = 0;
+    if (lrc) {
+        for (int m1 = 0; m1 < P.n_species; ++m1)
+            for (int a = 0; a < P.n_sites[m1]; ++a)
+                for (int m2 = 0; m2 < P.n_species; ++m2)
+                    for (int b = 0; b < P.n_sites[m2]; ++b) {
+                        const int ta = P.ljt[m1][a], tb = P.ljt[m2][b];
+                        if (ta < 0 || tb < 0) continue;
+                        // c6 = 4 eps sig^6, c12 = 4 eps sig^12
+                        const double c6 = P.c6d[ta][tb], c12 = P.c12d[ta][tb];
+                        const double r3 = rc * rc * rc, r9 = r3 * r3 * r3;
+                        const double Iu = c12 / (9.0 * r9) - c6 / (3.0 * r3);             // int r^2 u
+                        const double Ip = -12.0 * c12 / (9.0 * r9) + 6.0 * c6 / (3.0 * r3);  // int r^3 u'
+                        const double nn = (double)cnt[m1] * cnt[m2];
+                        u += nn * Iu;
+                        p += nn * Ip;
+                    }
+    }
+    *ulrc = 2.0 * M_PI / P.V * u;
+    *plrc = -2.0 * M_PI / (3.0 * P.V * P.V) * p;
+}
+
+// ------------------------------------------------------------------ system
+static ms2_status sys_alloc(ms2_system s) {
+    const int N = s->N, NS = s->ns;
+    DevSys &d = s->d;
+    memset(&d, 0, sizeof d);
+    d.N = N;
+    d.ns = NS;
+    d.jsplit = s->jsplit;
+    auto A = [&](void **p, size_t n) { return s->al.alloc(p, n); };
+    MS2_CUDA_OK(A((void **)&s->dP, sizeof(SysParams)));
+    MS2_CUDA_OK(A((void **)&d.R, sizeof(double) * 3 * N));
+    MS2_CUDA_OK(A((void **)&d.v, sizeof(double) * 3 * N));
+    MS2_CUDA_OK(A((void **)&d.q, sizeof(double) * 4 * N));
+    MS2_CUDA_OK(A((void **)&d.Lm, sizeof(double) * 3 * N));
+    MS2_CUDA_OK(A((void **)&d.species, sizeof(int) * N));
+    MS2_CUDA_OK(A((void **)&d.X, sizeof(uint32_t) * 3 * N));
+    MS2_CUDA_OK(A((void **)&d.s, sizeof(float) * 3 * NS * N));
+    if (s->hp.has_dipole) MS2_CUDA_OK(A((void **)&d.mu, sizeof(float) * 3 * NS * N));
+    if (s->hp.elec == ELEC_RF) MS2_CUDA_OK(A((void **)&d.mum, sizeof(float) * 3 * N));
+    if (s->fp64) MS2_CUDA_OK(A((void **)&d.part64, sizeof(double) * s->jsplit * MS2_NPV * N));
+    else MS2_CUDA_OK(A((void **)&d.part, sizeof(float) * s->jsplit * MS2_NPV * N));
+    MS2_CUDA_OK(A((void **)&d.F, sizeof(double) * 3 * N));
+    MS2_CUDA_OK(A((void **)&d.tau, sizeof(double) * 3 * N));
+    MS2_CUDA_OK(A((void **)&d.Ui, sizeof(double) * 4 * N));
+    MS2_CUDA_OK(A((void **)&d.npart, sizeof(int) * N));
+    d.nblk_red = (N + s->red_threads - 1) / s->red_threads;
+    MS2_CUDA_OK(A((void **)&d.blk, sizeof(double) * MS2_NRED * d.nblk_red));
+    MS2_CUDA_OK(A((void **)&d.counter, 256));
+    MS2_CUDA_OK(A((void **)&d.scal, sizeof(double) * SC_COUNT_));
+    MS2_CUDA_OK(A((void **)&d.acc, sizeof(double) * AC_COUNT_));
+    MS2_CUDA_OK(A((void **)&d.rdf_kind, sizeof(int) * MS2_MAXSP * MS2_MAXS));
+    MS2_CUDA_OK(cudaMemsetAsync(d.counter, 0, 256, s->stream));
+    MS2_CUDA_OK(cudaMemsetAsync(d.scal, 0, sizeof(double) * SC_COUNT_, s->stream));
+    MS2_CUDA_OK(cudaMemsetAsync(d.acc, 0, sizeof(double) * AC_COUNT_, s->stream));
+    return MS2_OK;
+}
+
+static void pick_launch_shape(ms2_system s) {
+    const int N = s->N;
+    // pair kernel: warps own molecules; split the j loop so that the grid holds
+    // ~32 warps per SM (152 SMs)
+    s->wpb = 8;
+    int js = (int)std::lround(152.0 * 32.0 / std::max(N, 1));
+    s->jsplit = std::max(1, std::min(8, js));
+    if (s->tune_jsplit > 0) s->jsplit = s->tune_jsplit;
+    if (s->tune_wpb > 0) s->wpb = s->tune_wpb;
+    // FP64-heavy kernels: spread molecules over all SMs with small blocks
+    s->red_threads = N <= 152 * 32 ? 32 : 64;
+    int dt = (N + 151) / 152;
+    int p2 = 8;
+    while (p2 < dt && p2 < 128) p2 <<= 1;
+    s->drift_threads = p2;
+}
+
+static ms2_status upload_params(ms2_system s) {
+    MS2_CUDA_OK(cudaMemcpyAsync(s->dP, &s->hp, sizeof(SysParams), cudaMemcpyHostToDevice, s->stream));
+    double sc[SC_COUNT_];
+    memset(sc, 0, sizeof sc);
+    sc[SC_UCONST] = s->uconst;
+    sc[SC_PLRC] = s->plrc;
+    sc[SC_ULRC] = s->ulrc;
+    sc[SC_WBG] = s->wbg;
+    sc[SC_LAMBDA] = 1.0;
+    // only the constant slots are written here; the others keep their values
+    MS2_CUDA_OK(cudaMemcpyAsync(s->d.scal + SC_UCONST, sc + SC_UCONST, sizeof(double) * 4, cudaMemcpyHostToDevice,
+                                s->stream));
+    return MS2_OK;
+}
+
+static ms2_status setup_pair(ms2_system s) {
+    const SysParams &P = s->hp;
+    unsigned ljm = 0, qm = 0, dm = 0;
+    for (int m = 0; m < P.n_species; ++m)
+        for (int a = 0; a < P.n_sites[m]; ++a) {
+            if (P.ljt[m][a] >= 0) ljm |= 1u << a;
+            if (P.q[m][a] != 0.f) qm |= 1u << a;
+            if (P.bdip[m][a][0] != 0 || P.bdip[m][a][1] != 0 || P.bdip[m][a][2] != 0) dm |= 1u << a;
+        }
+    s->ljm = ljm;
+    s->qm = qm;
+    s->dm = dm;
+    if (s->fp64) {
+        s->ns = 1;
+        s->pair_fn = (void *)&k_pair_lj64;
+        s->dmu = false;
+        s->multi_used = false;
+    } else {
+        s->pair_fn = ms2_pick_pair_kernel(P.ns, ljm, qm, dm, P.elec, P.multi != 0, &s->ns, &s->dmu, &s->multi_used);
+    }
+    s->hp.ns = s->ns;
+    return MS2_OK;
+}
+
+static ms2_status size_pair_tiles(ms2_system s) {
+    const int N = s->N;
+    const int range = (N + s->jsplit - 1) / s->jsplit;
+    const size_t cap = 96 * 1024;
+    int TJ = std::max(32, range);
+    auto bytes = [&](int tj) {
+        return s->fp64 ? ms2_pair64_smem_bytes(tj, s->wpb) : ms2_pair_smem_bytes(s->ns, s->dmu, s->multi_used, tj, s->wpb);
+    };
+    while (bytes(TJ) > cap && TJ > 64) TJ = (TJ + 1) / 2;
+    s->TJ = TJ;
+    s->pair_smem = bytes(TJ);
+    MS2_CUDA_OK(cudaFuncSetAttribute((const void *)s->pair_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)std::max<size_t>(s->pair_smem, 48 * 1024)));
+    return MS2_OK;
+}
+
+// ------------------------------------------------------------ launchers
+ms2_status launch_build(ms2_system s) {
+    const int th = 64;
+    k_build<<<(s->N + th - 1) / th, th, 0, s->stream>>>(s->dP, s->d);
+    s->launch_acc += 1;
+    return MS2_OK;
+}
+
+ms2_status launch_pair(ms2_system s) {
+    dim3 grid((s->N + s->wpb - 1) / s->wpb, s->jsplit);
+    void (*fn)(const SysParams *, DevSys, int) = (void (*)(const SysParams *, DevSys, int))s->pair_fn;
+    fn<<<grid, s->wpb * 32, s->pair_smem, s->stream>>>(s->dP, s->d, s->TJ);
+    s->launch_acc += 1;
+    return MS2_OK;
+}
+
+ms2_status launch_ewald(ms2_system s) {
+    if (s->hp.elec != ELEC_EWALD) return MS2_OK;
+    DevSys &d = s->d;
+    k_ewald_prep<<<(d.nsite_q + 127) / 128, 128, 0, s->stream>>>(s->dP, d);
+    const int cols = (2 * d.ky + 1) * (2 * d.kz + 1), ych = (d.kx + 1 + 7) / 8;
+    k_ewald_sk<<<dim3(cols, ych), 256, 0, s->stream>>>(s->dP, d, s->AS);
+    k_ewald_energy<<<1, 256, 0, s->stream>>>(s->dP, d, cols * ych);
+    k_ewald_force<<<dim3((d.nsite_q + 127) / 128, d.kchunks), 128, 0, s->stream>>>(s->dP, d, s->AS, s->ny_per_chunk);
+    s->launch_acc += 4;
+    return MS2_OK;
+}
+
+ms2_status launch_reduce(ms2_system s, int mode) {
+    if (s->fp64) mode |= RED_FP64PART;
+    if (s->hp.elec == ELEC_EWALD) mode |= RED_EWALD;
+    k_reduce<<<s->d.nblk_red, s->red_threads, 0, s->stream>>>(s->dP, s->d, mode);
+    s->launch_acc += 1;
+    return MS2_OK;
+}
+
+ms2_status launch_drift(ms2_system s) {
+    const int th = s->drift_threads;
+    k_drift<<<(s->N + th - 1) / th, th, 0, s->stream>>>(s->dP, s->d, s->hp.integrator == MS2_INT_VERLET ? 1 : 0);
+    s->launch_acc += 1;
+    return MS2_OK;
+}
+
+ms2_status launch_rdf(ms2_system s) {
+    const int rows = s->d.rdf_rows, nb = s->d.rdf_bins;
+    const int blocks = std::min(s->N, 2 * 152);
+    k_rdf<<<blocks, 256, sizeof(unsigned) * rows * nb, s->stream>>>(s->dP, s->d);
+    s->launch_acc += 1;
+    return MS2_OK;
+}
+
+static void flush_launches(ms2_system s) {
+    ms2_count_launches(s->launch_acc);
+    s->launch_acc = 0;
+}
+
+// forces/energies of the current configuration (no integration)
+ms2_status ms2_eval_forces(ms2_system s) {
+    launch_build(s);
+    launch_pair(s);
+    launch_ewald(s);
+    launch_reduce(s, RED_SUM);
+    flush_launches(s);
+    MS2_CUDA_OK(cudaGetLastError());
+    return MS2_OK;
+}
+
+// enqueue n steps starting at step counter s0 (no host sync)
+static void enqueue_steps(ms2_system s, long long n, long long s0) {
+    const bool verlet = s->hp.integrator == MS2_INT_VERLET;
+    const int every = s->rdf_every;
+    for (long long k = 0; k < n; ++k) {
+        const bool sample = every > 0 && ((s0 + k + 1) % every) == 0;
+        const bool tm = s->timing && k == n - 1;
+        if (tm) cudaEventRecordWithFlags(s->ev[0], s->stream, cudaEventRecordExternal);
+        if (verlet) {
+            launch_drift(s);
+            if (sample) launch_rdf(s);
+        } else {
+            launch_reduce(s, k == 0 ? RED_KICK : (RED_SUM | RED_RECORD | RED_KICK));
+            launch_drift(s);
+            if (sample) launch_rdf(s);
+        }
+        if (tm) cudaEventRecordWithFlags(s->ev[1], s->stream, cudaEventRecordExternal);
+        launch_pair(s);
+        if (tm) cudaEventRecordWithFlags(s->ev[2], s->stream, cudaEventRecordExternal);
+        launch_ewald(s);
+        if (tm) cudaEventRecordWithFlags(s->ev[3], s->stream, cudaEventRecordExternal);
+        if (verlet) launch_reduce(s, RED_SUM | RED_RECORD | RED_HALFKICK);
+        else if (k == n - 1) launch_reduce(s, RED_SUM | RED_RECORD);
+        if (tm) cudaEventRecordWithFlags(s->ev[4], s->stream, cudaEventRecordExternal);
+    }
+}
+
+static ms2_status run_graph(ms2_system s, long long n, long long s0) {
+    const int phase = s->rdf_every > 0 ? (int)(s0 % s->rdf_every) : 0;
+    const auto key = std::make_pair((int)n, phase);
+    auto it = s->graphs.find(key);
+    if (it == s->graphs.end()) {
+        if (s->graphs.size() > 16) {
+            for (auto &g : s->graphs) cudaGraphExecDestroy(g.second.exec);
+            s->graphs.clear();
+        }
+        cudaGraph_t g;
+        s->launch_acc = 0;
+        MS2_CUDA_OK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_steps(s, n, s0);
+        const long long nodes = s->launch_acc;
+        s->launch_acc = 0;
+        MS2_CUDA_OK(cudaStreamEndCapture(s->stream, &g));
+        cudaGraphExec_t ex;
+        cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        MS2_CUDA_OK(e);
+        it = s->graphs.emplace(key, GraphEntry{ex, nodes}).first;
+    }
+    MS2_CUDA_OK(cudaGraphLaunch(it->second.exec, s->stream));
+    ms2_count_launches(it->second.nodes);
+    return MS2_OK;
+}
+
+// ------------------------------------------------------------- C ABI
+extern "C" ms2_status ms2_default_options(ms2_options *o) {
+    if (!o) return ms2_fail(MS2_EINVAL, "null options");
+    memset(o, 0, sizeof *o);
+    o->eps_rf = 0.0;
+    o->lrc = 1;
+    o->dt = 2.0;
+    o->thermostat = 1;
+    o->seed = 1;
+    o->integrator = MS2_INT_LEAPFROG_Q;
+    o->quat_iters = 3;
+    o->graph_chunk = 50;
+    return MS2_OK;
+}
+
+// seeded lattice start (see ms2.h)
+static void initial_state(ms2_system s, const ms2_model *models, double T, unsigned long long seed) {
+    const int N = s->N;
+    const SysParams &P = s->hp;
+    SplitMix64 rng{seed * 0x2545F4914F6CDD1DULL + 0x1234567ULL};
+    std::vector<double> &R = s->hR, &q = s->hq, &v = s->hv, &L = s->hL;
+    R.assign(3 * N, 0);
+    q.assign(4 * N, 0);
+    v.assign(3 * N, 0);
+    L.assign(3 * N, 0);
+    const double Lb = P.L;
+    bool point = true;
+    for (int m = 0; m < P.n_species; ++m)
+        if (P.Iinv[m][0] != 0 || P.Iinv[m][1] != 0 || P.Iinv[m][2] != 0) point = false;
+    int mc = (int)std::round(std::cbrt(N / 4.0));
+    std::vector<double> pts;
+    if (point && P.n_species == 1 && 4 * mc * mc * mc == N) {
+        const double a = Lb / mc, bas[4][3] = {{0, 0, 0}, {0.5, 0.5, 0}, {0.5, 0, 0.5}, {0, 0.5, 0.5}};
+        for (int x = 0; x < mc; ++x)
+            for (int y = 0; y < mc; ++y)
+                for (int z = 0; z < mc; ++z)
+                    for (int b = 0; b < 4; ++b) {
+                        pts.push_back((x + bas[b][0]) * a);
+                        pts.push_back((y + bas[b][1]) * a);
+                        pts.push_back((z + bas[b][2]) * a);
+                    }
+    } else {
+        int m = (int)std::ceil(std::cbrt((double)N) - 1e-9);
+        while (m * m * m < N) ++m;
+        const double a = Lb / m;
+        for (int x = 0; x < m; ++x)
+            for (int y = 0; y < m; ++y)
+                for (int z = 0; z < m; ++z) {
+                    pts.push_back((x + 0.5) * a);
+                    pts.push_back((y + 0.5) * a);
+                    pts.push_back((z + 0.5) * a);
+                }
+    }
+    const int npts = (int)pts.size() / 3;
+    std::vector<int> perm(npts);
+    for (int k = 0; k < npts; ++k) perm[k] = k;
+    if (P.n_species > 1)  // mix species over the lattice (Fisher-Yates)
+        for (int k = npts - 1; k > 0; --k) std::swap(perm[k], perm[(int)(rng.uniform() * (k + 1))]);
+    double ke = 0, mom[3] = {0, 0, 0}, Mt = 0;
+    for (int i = 0; i < N; ++i) {
+        const int sp = s->species[i];
+        for (int k = 0; k < 3; ++k) R[3 * i + k] = pts[3 * perm[i] + k];
+        const bool rot = P.Iinv[sp][0] != 0 || P.Iinv[sp][1] != 0 || P.Iinv[sp][2] != 0;
+        if (rot) {  // Shoemake uniform rotation
+            const double u1 = rng.uniform(), u2 = rng.uniform(), u3 = rng.uniform();
+            const double a = std::sqrt(1 - u1), b = std::sqrt(u1);
+            q[4 * i] = a * std::sin(2 * M_PI * u2);
+            q[4 * i + 1] = a * std::cos(2 * M_PI * u2);
+            q[4 * i + 2] = b * std::sin(2 * M_PI * u3);
+            q[4 * i + 3] = b * std::cos(2 * M_PI * u3);
+        } else {
+            q[4 * i] = 1.0;
+        }
+        const double M = P.mass[sp];
+        for (int k = 0; k < 3; ++k) {
+            v[3 * i + k] = rng.normal() * std::sqrt(T * P.kconv / M);
+            mom[k] += M * v[3 * i + k];
+        }
+        Mt += M;
+        double A[9];
+        {
+            const double w = q[4 * i], x = q[4 * i + 1], y = q[4 * i + 2], z = q[4 * i + 3];
+            A[0] = 1 - 2 * (y * y + z * z); A[1] = 2 * (x * y - w * z); A[2] = 2 * (x * z + w * y);
+            A[3] = 2 * (x * y + w * z); A[4] = 1 - 2 * (x * x + z * z); A[5] = 2 * (y * z - w * x);
+            A[6] = 2 * (x * z - w * y); A[7] = 2 * (y * z + w * x); A[8] = 1 - 2 * (x * x + y * y);
+        }
+        double lb[3] = {0, 0, 0};
+        for (int k = 0; k < 3; ++k)
+            if (P.Iinv[sp][k] != 0) {
+                lb[k] = rng.normal() * std::sqrt(T * P.kconv / P.Iinv[sp][k]);
+                ke += 0.5 * lb[k] * lb[k] * P.Iinv[sp][k];
+            }
+        for (int r = 0; r < 3; ++r) L[3 * i + r] = A[3 * r] * lb[0] + A[3 * r + 1] * lb[1] + A[3 * r + 2] * lb[2];
+    }
+    for (int i = 0; i < N; ++i) {
+        const double M = P.mass[s->species[i]];
+        for (int k = 0; k < 3; ++k) {
+            v[3 * i + k] -= mom[k] / Mt;
+            ke += 0.5 * M * v[3 * i + k] * v[3 * i + k];
+        }
+    }
+    const double Tk = 2.0 * ke / P.kconv / P.ndof, lam = (Tk > 0 && T > 0) ? std::sqrt(T / Tk) : 0.0;
+    for (int k = 0; k < 3 * N; ++k) {
+        v[k] *= lam;
+        L[k] *= lam;
+    }
+}
+
+static ms2_status ensure_pinned(ms2_system s) {
+    if (!s->pinned) MS2_CUDA_OK(cudaMallocHost((void **)&s->pinned, sizeof(double) * 13 * s->N));
+    return MS2_OK;
+}
+
+static ms2_status upload_state(ms2_system s) {
+    const int N = s->N;
+    ms2_status st = ensure_pinned(s);
+    if (st != MS2_OK) return st;
+    double *buf = s->pinned;
+    size_t off = 0;
+    auto put = [&](double *dst, const std::vector<double> &src, int nc) -> cudaError_t {
+        double *b = buf + off;
+        for (int i = 0; i < N; ++i)
+            for (int k = 0; k < nc; ++k) b[k * N + i] = src[nc * i + k];
+        off += (size_t)nc * N;
+        return cudaMemcpyAsync(dst, b, sizeof(double) * nc * N, cudaMemcpyHostToDevice, s->stream);
+    };
+    MS2_CUDA_OK(put(s->d.R, s->hR, 3));
+    MS2_CUDA_OK(put(s->d.q, s->hq, 4));
+    MS2_CUDA_OK(put(s->d.v, s->hv, 3));
+    MS2_CUDA_OK(put(s->d.Lm, s->hL, 3));
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));  // the pinned buffer is reused
+    return MS2_OK;
+}
+
+static ms2_status setup_ewald(ms2_system s, double alpha, int kx, int ky, int kz) {
+    DevSys &d = s->d;
+    s->alpha = alpha;
+    s->hp.alpha = (float)alpha;
+    s->hp.two_alpha_sqrtpi = (float)(2.0 * alpha / std::sqrt(M_PI));
+    d.kx = kx;
+    d.ky = ky;
+    d.kz = kz;
+    d.nsite_q = s->N * s->ns;
+    const int M = d.nsite_q, kst = std::max(kx, std::max(ky, kz)) + 1;
+    d.kchunks = 2 * ky + 1;
+    s->ny_per_chunk = 1;
+    const int cols = (2 * ky + 1) * (2 * kz + 1), ych = (kx + 1 + 7) / 8;
+    auto A = [&](void **p, size_t n) { return s->al.alloc(p, n); };
+    // (re)allocation: old buffers stay owned by the allocator list until destroy
+    MS2_CUDA_OK(A((void **)&d.Xs, sizeof(uint32_t) * 3 * M));
+    MS2_CUDA_OK(A((void **)&d.qs, sizeof(float) * M));
+    MS2_CUDA_OK(A((void **)&d.eik, sizeof(float2) * 3 * kst * M));
+    MS2_CUDA_OK(A((void **)&d.frec, sizeof(float) * d.kchunks * 3 * M));
+    MS2_CUDA_OK(A((void **)&d.kblk, sizeof(double) * 2 * cols * ych));
+    MS2_CUDA_OK(A((void **)&s->AS, sizeof(float2) * cols * (kx + 1)));
+    double coulomb, kconv;
+    ms2_unit_constants(s->reduced, &coulomb, &kconv);
+    ms2_energy_constants(s->hp, s->species, alpha, s->rc, s->lrc, coulomb, &s->uconst, &s->wbg, &s->ulrc, &s->plrc);
+    return MS2_OK;
+}
+
+static void destroy_graphs(ms2_system s) {
+    for (auto &g : s->graphs) cudaGraphExecDestroy(g.second.exec);
+    s->graphs.clear();
+}
+
+extern "C" ms2_status ms2_create_system(const ms2_model *models, const int *N_per_model, int n_models, double box,
+                                        double T, double rho, double cutoff, ms2_elec elec, const ms2_options *opt,
+                                        ms2_system *out) {
+    if (!out) return ms2_fail(MS2_EINVAL, "null output handle");
+    *out = nullptr;
+    ms2_status st = ms2_validate_models(models, n_models, elec);
+    if (st != MS2_OK) return st;
+    if (!N_per_model) return ms2_fail(MS2_EINVAL, "null N_per_model");
+    long long Nt = 0;
+    for (int m = 0; m < n_models; ++m) {
+        if (N_per_model[m] < 0) return ms2_fail(MS2_EINVAL, "negative molecule count");
+        Nt += N_per_model[m];
+    }
+    if (Nt < 2 || Nt > (1 << 24)) return ms2_fail(MS2_EINVAL, "total molecule count %lld outside 2..2^24", Nt);
+    ms2_options o;
+    ms2_default_options(&o);
+    if (opt) o = *opt;
+    if (!(T >= 0)) return ms2_fail(MS2_EINVAL, "temperature must be >= 0");
+    double L = box;
+    if (box > 0 && rho > 0) {
+        const double L2 = std::cbrt((double)Nt / rho);
+        if (std::fabs(L2 - box) > 1e-12 * box) return ms2_fail(MS2_EINVAL, "box and rho disagree (%.15g vs %.15g)", box, L2);
+    } else if (!(box > 0)) {
+        if (!(rho > 0)) return ms2_fail(MS2_EINVAL, "give box > 0 or rho > 0");
+        L = std::cbrt((double)Nt / rho);
+    }
+    if (!(cutoff > 0) || !(cutoff < 0.5 * L))
+        return ms2_fail(MS2_EINVAL, "cutoff %.6g must satisfy 0 < rc < box/2 = %.6g", cutoff, 0.5 * L);
+    if (!(o.dt > 0)) return ms2_fail(MS2_EINVAL, "dt must be > 0");
+    if (o.integrator != MS2_INT_VERLET && o.integrator != MS2_INT_LEAPFROG_Q)
+        return ms2_fail(MS2_EINVAL, "unknown integrator");
+    ms2_system s = new ms2_system_s();
+    s->al.fa = o.dev_alloc;
+    s->al.ff = o.dev_free;
+    s->al.ctx = o.alloc_ctx;
+    cudaGetDevice(&s->device);
+    if (o.stream) {
+        s->stream = (cudaStream_t)o.stream;
+        s->own_stream = false;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete s;
+            return ms2_fail_cuda(e, "cudaStreamCreate", __FILE__, __LINE__);
+        }
+        s->own_stream = true;
+    }
+    s->N = (int)Nt;
+    for (int m = 0; m < n_models; ++m)
+        for (int k = 0; k < N_per_model[m]; ++k) s->species.push_back(m);
+    s->rc = cutoff;
+    s->lrc = o.lrc != 0;
+    s->reduced = o.reduced != 0;
+    s->graph_chunk = o.graph_chunk > 0 ? o.graph_chunk : 50;
+    ms2_fill_params(s->hp, models, n_models, s->species, L, cutoff, elec, o, T);
+    // velocity Verlet integrates point molecules only
+    bool point = true;
+    for (int m = 0; m < n_models; ++m)
+        if (s->hp.Iinv[m][0] != 0 || s->hp.Iinv[m][1] != 0 || s->hp.Iinv[m][2] != 0) point = false;
+    if (o.integrator == MS2_INT_VERLET && !point) {
+        delete s;
+        return ms2_fail(MS2_EINVAL, "velocity Verlet is for molecules without rotational freedom; use MS2_INT_LEAPFROG_Q");
+    }
+    s->fp64 = o.fp64 != 0;
+    if (s->fp64 && !(n_models == 1 && models[0].n_sites == 1 && elec == MS2_ELEC_NONE)) {
+        delete s;
+        return ms2_fail(MS2_EINVAL, "fp64 pair arithmetic is available for single-site LJ models only");
+    }
+    setup_pair(s);
+    pick_launch_shape(s);
+    st = sys_alloc(s);
+    if (st == MS2_OK) st = size_pair_tiles(s);
+    if (st == MS2_OK && elec == MS2_ELEC_EWALD) st = setup_ewald(s, 3.2 / cutoff, 8, 8, 8);
+    if (st == MS2_OK && elec != MS2_ELEC_EWALD) {
+        double coulomb, kconv;
+        ms2_unit_constants(s->reduced, &coulomb, &kconv);
+        ms2_energy_constants(s->hp, s->species, 1.0, cutoff, s->lrc, coulomb, &s->uconst, &s->wbg, &s->ulrc, &s->plrc);
+    }
+    if (st == MS2_OK) {
+        int kinds[MS2_MAXSP * MS2_MAXS];
+        for (int m = 0; m < MS2_MAXSP; ++m)
+            for (int a = 0; a < MS2_MAXS; ++a) kinds[m * MS2_MAXS + a] = m < n_models ? s->hp.ljt[m][a] : -1;
+        cudaError_t e = cudaMemcpyAsync(s->d.rdf_kind, kinds, sizeof kinds, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s->d.species, s->species.data(), sizeof(int) * s->N,
+                                                  cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) st = ms2_fail_cuda(e, "upload", __FILE__, __LINE__);
+    }
+    if (st == MS2_OK) st = upload_params(s);
+    if (st == MS2_OK) {
+        initial_state(s, models, T, o.seed);
+        st = upload_state(s);
+    }
+    if (st == MS2_OK) st = ms2_eval_forces(s);
+    if (st == MS2_OK) {
+        cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) st = ms2_fail_cuda(e, "initial force evaluation", __FILE__, __LINE__);
+    }
+    if (st != MS2_OK) {
+        std::string msg = g_err;
+        ms2_destroy_system(s);
+        g_err = msg;
+        return st;
+    }
+    *out = s;
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_enable_timing(ms2_system s, int on) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    if (on && !s->ev[0])
+        for (int k = 0; k < 5; ++k) MS2_CUDA_OK(cudaEventCreate(&s->ev[k]));
+    if ((on != 0) != s->timing) destroy_graphs(s);
+    s->timing = on != 0;
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_last_step_times(ms2_system s, double out[4]) {
+    if (!s || !out) return ms2_fail(MS2_EINVAL, "null argument");
+    if (!s->timing) return ms2_fail(MS2_ESTATE, "timing is off (ms2_enable_timing)");
+    MS2_CUDA_OK(cudaEventSynchronize(s->ev[4]));
+    float a, b, c;
+    MS2_CUDA_OK(cudaEventElapsedTime(&a, s->ev[1], s->ev[2]));
+    MS2_CUDA_OK(cudaEventElapsedTime(&b, s->ev[2], s->ev[3]));
+    MS2_CUDA_OK(cudaEventElapsedTime(&c, s->ev[0], s->ev[4]));
+    out[0] = a;
+    out[1] = b;
+    out[2] = c;
+    out[3] = c - a - b;
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_destroy_system(ms2_system s) {
+    if (!s) return MS2_OK;
+    cudaStreamSynchronize(s->stream);
+    destroy_graphs(s);
+    for (int k = 0; k < 5; ++k)
+        if (s->ev[k]) cudaEventDestroy(s->ev[k]);
+    if (s->pinned) cudaFreeHost(s->pinned);
+    s->al.release_all();
+    if (s->own_stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_system_info(ms2_system s, int *N, double *box, double *cutoff, int *ndof) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (N) *N = s->N;
+    if (box) *box = s->hp.L;
+    if (cutoff) *cutoff = s->rc;
+    if (ndof) *ndof = s->hp.ndof;
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_step(ms2_system s, long long n) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (n < 0) return ms2_fail(MS2_EINVAL, "negative step count");
+    long long done = 0;
+    const long long chunk = s->graph_chunk;
+    while (done < n) {
+        const long long m = std::min(chunk, n - done);
+        ms2_status st = run_graph(s, m, s->step + done);
+        if (st != MS2_OK) return st;
+        done += m;
+    }
+    s->step += n;
+    if (s->d.rdf && s->rdf_every > 0) {
+        // samples taken inside the steps: configurations at steps multiple of every
+        s->rdf_samples += (int)((s->step) / s->rdf_every - (s->step - n) / s->rdf_every);
+    }
+    MS2_CUDA_OK(cudaGetLastError());
+    return MS2_OK;
+}
+
+static ms2_status read_scalars(ms2_system s, double *sc) {
+    MS2_CUDA_OK(cudaMemcpyAsync(sc, s->d.scal, sizeof(double) * SC_COUNT_, cudaMemcpyDeviceToHost, s->stream));
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_energy_virial(ms2_system s, double *U, double *W, double *T_inst, double *P) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    double sc[SC_COUNT_];
+    ms2_status st = read_scalars(s, sc);
+    if (st != MS2_OK) return st;
+    if (U) *U = sc[SC_UTOT];
+    if (W) *W = sc[SC_WTOT];
+    if (T_inst) *T_inst = sc[SC_T];
+    if (P) *P = sc[SC_P];
+    if (sc[SC_UNSTABLE] != 0.0 || !std::isfinite(sc[SC_UTOT]))
+        return ms2_fail(MS2_EUNSTABLE, "non-finite or exploding forces in the current configuration");
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_energy_terms(ms2_system s, double terms[16]) {
+    if (!s || !terms) return ms2_fail(MS2_EINVAL, "null argument");
+    double sc[SC_COUNT_];
+    ms2_status st = read_scalars(s, sc);
+    if (st != MS2_OK) return st;
+    const bool ew = s->hp.elec == ELEC_EWALD;
+    double coulomb, kconv;
+    ms2_unit_constants(s->reduced, &coulomb, &kconv);
+    double uself = 0, uintra = 0, ubg = 0;
+    if (ew) {  // split of the constant part for reporting
+        SysParams P = s->hp;
+        double c_all, w, ul, pl;
+        ms2_energy_constants(P, s->species, s->alpha, s->rc, false, coulomb, &c_all, &w, &ul, &pl);
+        ubg = w / 3.0;
+        double sq2 = 0;
+        for (int i = 0; i < s->N; ++i)
+            for (int a = 0; a < P.n_sites[s->species[i]]; ++a)
+                sq2 += (double)P.q[s->species[i]][a] * P.q[s->species[i]][a];
+        uself = -coulomb * s->alpha / std::sqrt(M_PI) * sq2;
+        uintra = c_all - uself - ubg;
+    }
+    terms[0] = sc[SC_ULJ];
+    terms[1] = sc[SC_UQQ];
+    terms[2] = sc[SC_UDD];
+    terms[3] = ew ? sc[SC_UREC] : 0.0;
+    terms[4] = uself;
+    terms[5] = uintra;
+    terms[6] = ubg;
+    terms[7] = sc[SC_ULRC];
+    terms[8] = sc[SC_UTOT];
+    terms[9] = sc[SC_WPAIR];
+    terms[10] = ew ? sc[SC_WREC_AT] - sc[SC_WREC_CORR] : 0.0;
+    terms[11] = sc[SC_WBG];
+    terms[12] = sc[SC_WTOT];
+    terms[13] = sc[SC_PLRC];
+    terms[14] = sc[SC_NPAIRS];
+    terms[15] = sc[SC_KETR_NOW] + sc[SC_KEROT_NOW];
+    return MS2_OK;
+}
+
+static ms2_status ensure_pinned(ms2_system s);
+static ms2_status get_soa(ms2_system s, const double *src, int nc, double *dst) {
+    const int N = s->N;
+    ms2_status st = ensure_pinned(s);
+    if (st != MS2_OK) return st;
+    double *buf = s->pinned;
+    MS2_CUDA_OK(cudaMemcpyAsync(buf, src, sizeof(double) * nc * N, cudaMemcpyDeviceToHost, s->stream));
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    for (int i = 0; i < N; ++i)
+        for (int k = 0; k < nc; ++k) dst[nc * i + k] = buf[(size_t)k * N + i];
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_forces_torques(ms2_system s, double *F, double *tau) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    ms2_status st = MS2_OK;
+    if (F) st = get_soa(s, s->d.F, 3, F);
+    if (st == MS2_OK && tau) st = get_soa(s, s->d.tau, 3, tau);
+    return st;
+}
+
+__global__ void k_aos3(const double *src, double *dst, int N) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N)
+        for (int k = 0; k < 3; ++k) dst[3 * i + k] = src[(size_t)k * N + i];
+}
+
+extern "C" ms2_status ms2_forces_torques_dev(ms2_system s, double *F_dev, double *tau_dev) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (F_dev) k_aos3<<<(s->N + 127) / 128, 128, 0, s->stream>>>(s->d.F, F_dev, s->N);
+    if (tau_dev) k_aos3<<<(s->N + 127) / 128, 128, 0, s->stream>>>(s->d.tau, tau_dev, s->N);
+    ms2_count_launches((F_dev ? 1 : 0) + (tau_dev ? 1 : 0));
+    MS2_CUDA_OK(cudaGetLastError());
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_ewald_params(ms2_system s, double alpha, int kx, int ky, int kz) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (s->hp.elec != ELEC_EWALD) return ms2_fail(MS2_EINVAL, "system does not use Ewald summation");
+    if (!(alpha > 0) || kx < 1 || ky < 1 || kz < 1 || kx > 64 || ky > 64 || kz > 64)
+        return ms2_fail(MS2_EINVAL, "need alpha > 0 and kmax in 1..64");
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    destroy_graphs(s);
+    ms2_status st = setup_ewald(s, alpha, kx, ky, kz);
+    if (st == MS2_OK) st = upload_params(s);
+    if (st == MS2_OK) st = ms2_eval_forces(s);
+    return st;
+}
+
+extern "C" ms2_status ms2_get_state(ms2_system s, double *R, double *q, double *v, double *Lang, long long *step) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    ms2_status st = MS2_OK;
+    if (R) st = get_soa(s, s->d.R, 3, R);
+    if (st == MS2_OK && q) st = get_soa(s, s->d.q, 4, q);
+    if (st == MS2_OK && v) st = get_soa(s, s->d.v, 3, v);
+    if (st == MS2_OK && Lang) st = get_soa(s, s->d.Lm, 3, Lang);
+    if (step) *step = s->step;
+    return st;
+}
+
+extern "C" ms2_status ms2_set_state(ms2_system s, const double *R, const double *q, const double *v,
+                                    const double *Lang) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    const int N = s->N;
+    if (R || q || v || Lang) {
+        std::vector<double> cur;
+        // fetch what is not replaced
+        if (!R) { s->hR.resize(3 * N); ms2_status st = get_soa(s, s->d.R, 3, s->hR.data()); if (st) return st; }
+        else s->hR.assign(R, R + 3 * N);
+        if (!q) { s->hq.resize(4 * N); ms2_status st = get_soa(s, s->d.q, 4, s->hq.data()); if (st) return st; }
+        else s->hq.assign(q, q + 4 * N);
+        if (!v) { s->hv.resize(3 * N); ms2_status st = get_soa(s, s->d.v, 3, s->hv.data()); if (st) return st; }
+        else s->hv.assign(v, v + 3 * N);
+        if (!Lang) { s->hL.resize(3 * N); ms2_status st = get_soa(s, s->d.Lm, 3, s->hL.data()); if (st) return st; }
+        else s->hL.assign(Lang, Lang + 3 * N);
+        for (int i = 0; i < N; ++i) {
+            for (int k = 0; k < 3; ++k)
+                if (!std::isfinite(s->hR[3 * i + k]) || !std::isfinite(s->hv[3 * i + k]) || !std::isfinite(s->hL[3 * i + k]))
+                    return ms2_fail(MS2_EINVAL, "non-finite state value for molecule %d", i);
+            double n2 = 0;
+            for (int k = 0; k < 4; ++k) n2 += s->hq[4 * i + k] * s->hq[4 * i + k];
+            if (!(n2 > 0) || !std::isfinite(n2)) return ms2_fail(MS2_EINVAL, "quaternion %d has zero norm", i);
+            if (std::fabs(n2 - 1.0) > 1e-13) {  // unit quaternions are taken bit for bit
+                const double inv = 1.0 / std::sqrt(n2);
+                for (int k = 0; k < 4; ++k) s->hq[4 * i + k] *= inv;
+            }
+        }
+        ms2_status st = upload_state(s);
+        if (st != MS2_OK) return st;
+    }
+    return ms2_eval_forces(s);
+}
+
+extern "C" ms2_status ms2_partner_counts(ms2_system s, int *counts) {
+    if (!s || !counts) return ms2_fail(MS2_EINVAL, "null argument");
+    MS2_CUDA_OK(cudaMemcpyAsync(counts, s->d.npart, sizeof(int) * s->N, cudaMemcpyDeviceToHost, s->stream));
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_molecule_energies(ms2_system s, double *out) {
+    if (!s || !out) return ms2_fail(MS2_EINVAL, "null argument");
+    ms2_status st = get_soa(s, s->d.Ui, 4, out);
+    if (st != MS2_OK) return st;
+    for (int k = 0; k < 4 * s->N; ++k) out[k] *= 0.5;
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_site_offsets(ms2_system s, double *offsets, int *n_site_slots) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    const int N = s->N, NS = s->ns;
+    if (n_site_slots) *n_site_slots = NS;
+    if (!offsets) return MS2_OK;
+    std::vector<float> buf((size_t)3 * NS * N);
+    MS2_CUDA_OK(cudaMemcpyAsync(buf.data(), s->d.s, sizeof(float) * buf.size(), cudaMemcpyDeviceToHost, s->stream));
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    for (int i = 0; i < N; ++i)
+        for (int a = 0; a < NS; ++a)
+            for (int k = 0; k < 3; ++k) offsets[((size_t)i * NS + a) * 3 + k] = buf[((size_t)k * NS + a) * N + i];
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_rdf_setup(ms2_system s, double r_max, int n_bins, int every) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    const int T = s->hp.n_ljt;
+    if (T < 1) return ms2_fail(MS2_EINVAL, "no LJ sites: the RDF is sampled between LJ sites");
+    const int rows = T * (T + 1) / 2;
+    if (n_bins < 1 || rows * n_bins > 12288) return ms2_fail(MS2_EINVAL, "need 1 <= n_bins and rows*bins <= 12288");
+    if (!(r_max > 0) || r_max > std::min(s->rc, 0.5 * s->hp.L) * (1 + 1e-12))
+        return ms2_fail(MS2_EINVAL, "r_max must be in (0, min(cutoff, box/2)]");
+    if (every < 0) return ms2_fail(MS2_EINVAL, "negative sampling interval");
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    destroy_graphs(s);
+    if (!s->d.rdf || rows * n_bins > s->rdf_cap) {
+        MS2_CUDA_OK(s->al.alloc((void **)&s->d.rdf, sizeof(unsigned long long) * rows * n_bins));
+        s->rdf_cap = rows * n_bins;
+    }
+    MS2_CUDA_OK(cudaMemsetAsync(s->d.rdf, 0, sizeof(unsigned long long) * rows * n_bins, s->stream));
+    s->d.rdf_bins = n_bins;
+    s->d.rdf_rows = rows;
+    s->d.rdf_inv_dr = (float)(n_bins / r_max);
+    s->d.rdf_rmax2 = (float)(r_max * r_max);
+    s->rdf_rmax = r_max;
+    s->rdf_every = every;
+    s->rdf_samples = 0;
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_rdf_sample(ms2_system s) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (!s->d.rdf) return ms2_fail(MS2_ESTATE, "call ms2_rdf_setup first");
+    launch_rdf(s);
+    flush_launches(s);
+    MS2_CUDA_OK(cudaGetLastError());
+    s->rdf_samples += 1;
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_rdf(ms2_system s, long long *counts, double *g, int *n_samples, int *n_rows) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (!s->d.rdf) return ms2_fail(MS2_ESTATE, "call ms2_rdf_setup first");
+    const int rows = s->d.rdf_rows, nb = s->d.rdf_bins;
+    std::vector<unsigned long long> c((size_t)rows * nb);
+    MS2_CUDA_OK(cudaMemcpyAsync(c.data(), s->d.rdf, sizeof(unsigned long long) * c.size(), cudaMemcpyDeviceToHost,
+                                s->stream));
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    if (n_samples) *n_samples = s->rdf_samples;
+    if (n_rows) *n_rows = rows;
+    if (counts)
+        for (size_t k = 0; k < c.size(); ++k) counts[k] = (long long)c[k];
+    if (g) {
+        const SysParams &P = s->hp;
+        int cnt[MS2_MAXSP] = {0}, kind_sp[MS2_MAXT];
+        for (int i = 0; i < s->N; ++i) cnt[s->species[i]]++;
+        for (int m = 0; m < P.n_species; ++m)
+            for (int a = 0; a < P.n_sites[m]; ++a)
+                if (P.ljt[m][a] >= 0) kind_sp[P.ljt[m][a]] = m;
+        const int T = P.n_ljt;
+        const double dr = s->rdf_rmax / nb;
+        int row = 0;
+        for (int t1 = 0; t1 < T; ++t1)
+            for (int t2 = t1; t2 < T; ++t2, ++row) {
+                const int a = kind_sp[t1], b = kind_sp[t2];
+                double pairs = (t1 == t2) ? 0.5 * cnt[a] * (cnt[a] - 1.0)
+                                          : (a == b ? cnt[a] * (cnt[a] - 1.0) : (double)cnt[a] * cnt[b]);
+                for (int k = 0; k < nb; ++k) {
+                    const double shell = 4.0 * M_PI / 3.0 * (std::pow((k + 1) * dr, 3) - std::pow(k * dr, 3));
+                    const double ideal = pairs * shell / P.V * std::max(s->rdf_samples, 1);
+                    g[(size_t)row * nb + k] = ideal > 0 ? c[(size_t)row * nb + k] / ideal : 0.0;
+                }
+            }
+    }
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_averages(ms2_system s, double out[5], long long *n_steps) {
+    if (!s || !out) return ms2_fail(MS2_EINVAL, "null argument");
+    double ac[AC_COUNT_];
+    MS2_CUDA_OK(cudaMemcpyAsync(ac, s->d.acc, sizeof ac, cudaMemcpyDeviceToHost, s->stream));
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    const double n = std::max(ac[AC_N], 1.0), nb = ac[AC_NB];
+    out[0] = ac[AC_U] / n;
+    out[1] = ac[AC_P] / n;
+    out[2] = ac[AC_T] / n;
+    auto err = [&](double s1, double s2) {
+        if (nb < 2) return 0.0;
+        const double m = s1 / nb, var = std::max(0.0, s2 / nb - m * m);
+        return std::sqrt(var / (nb - 1));
+    };
+    out[3] = err(ac[AC_SBU], ac[AC_SBU2]);
+    out[4] = err(ac[AC_SBP], ac[AC_SBP2]);
+    if (n_steps) *n_steps = (long long)ac[AC_N];
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_reset_averages(ms2_system s) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    MS2_CUDA_OK(cudaMemsetAsync(s->d.acc, 0, sizeof(double) * AC_COUNT_, s->stream));
+    return MS2_OK;
+}

@@ -1,0 +1,70 @@
+// Host-side structures shared by the C-ABI, batch and serving translation units.
+#pragma once
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/ms2.h"
+#include "ms2_internal.cuh"
+
+// Device memory owner: user hooks (e.g. a PyTorch caching allocator) or cudaMalloc.
+struct DevAlloc {
+    void *(*fa)(size_t, void *) = nullptr;
+    void (*ff)(void *, void *) = nullptr;
+    void *ctx = nullptr;
+    std::vector<void *> live;
+    size_t bytes = 0;
+    cudaError_t alloc(void **p, size_t n);
+    void release_all();
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec;
+    long long nodes;
+};
+
+struct ms2_system_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    DevAlloc al;
+    SysParams hp;
+    SysParams *dP = nullptr;
+    DevSys d;
+    int N = 0, ns = 1;
+    std::vector<int> species;
+    double rc = 0;
+    bool lrc = true, reduced = false, fp64 = false;
+    unsigned ljm = 0, qm = 0, dm = 0;
+    bool dmu = false, multi_used = false;
+    void *pair_fn = nullptr;
+    int wpb = 8, jsplit = 1, TJ = 32;
+    size_t pair_smem = 0;
+    int tune_wpb = 0, tune_jsplit = 0;
+    int red_threads = 32, drift_threads = 8;
+    // Ewald
+    double alpha = 0;
+    float2 *AS = nullptr;
+    int ny_per_chunk = 1;
+    // energy constants
+    double uconst = 0, wbg = 0, ulrc = 0, plrc = 0;
+    long long step = 0;
+    int graph_chunk = 50;
+    std::map<std::pair<int, int>, GraphEntry> graphs;
+    long long launch_acc = 0;
+    // RDF
+    int rdf_every = 0, rdf_samples = 0, rdf_cap = 0;
+    double rdf_rmax = 0;
+    // host staging of the state
+    std::vector<double> hR, hq, hv, hL;
+    double *pinned = nullptr;  // page-locked staging for state transfers (4N doubles)
+    // timing events: [0] step start, [1] before pair, [2] after pair, [3] after Ewald, [4] step end
+    bool timing = false;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+ms2_status ms2_fail(ms2_status st, const char *fmt, ...);
+ms2_status ms2_fail_cuda(cudaError_t e, const char *what, const char *file, int line);
+void ms2_unit_constants(bool reduced, double *coulomb, double *kconv);
+ms2_status ms2_eval_forces(ms2_system s);

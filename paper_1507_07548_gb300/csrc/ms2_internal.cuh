@@ -1,0 +1,144 @@
+// Internal data layout and device helpers of libms2 (GB300, sm_103a).
+//
+// Layout in device memory (one system):
+//   FP64 state, SoA by component:  R[3][N], v[3][N], q[4][N], Lm[3][N]
+//   per step, written by the site build:
+//     X[3][N]          uint32 centre coordinates on a 2^32-point lattice per edge
+//     s[3][NS][N]      FP32 space-frame site offsets A(q_i) b_a (slot-major)
+//     mu[3][NS][N]     FP32 space-frame dipoles (only when a slot carries one)
+//     mum[3][N]        FP32 molecular charge dipoles (reaction field with charges)
+//   pair-kernel output: part[JSPLIT][NPV][N] FP32 partial sums per j-range
+//   reduced:           F[3][N], tau[3][N] FP64, per-molecule energy/virial
+//   Ewald:             site lattice coordinates, e^{i n theta} tables, S(k)
+// Everything a thread block reads for one molecule is contiguous per component,
+// so consecutive lanes (molecules) make coalesced 4- or 8-byte accesses.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MS2_MAXSP 4
+#define MS2_MAXS 8
+#define MS2_MAXT 16        // LJ site kinds (species x LJ slot)
+#define MS2_NPV 12         // values per molecule in a pair-kernel partial
+#define MS2_NRED 16        // per-block reduction scalars
+
+// partial-slot meaning
+enum { PV_FX = 0, PV_FY, PV_FZ, PV_TX, PV_TY, PV_TZ, PV_ULJ, PV_UQQ, PV_UDD, PV_W, PV_NP, PV_SPARE };
+
+enum { ELEC_NONE = 0, ELEC_RF = 1, ELEC_EWALD = 2 };
+
+// Per-system constants (models, mixing tables, electrostatics, integrator).
+struct SysParams {
+    int N, ns, n_species, n_ljt;
+    int elec, integrator, thermostat, quat_iters;
+    int has_dipole, multi, ndof, pad0;
+    double L, V, dt, kconv, T0;
+    double lat_scale;          // 2^32 / L  (FP64, exact same value as the host computes)
+    unsigned long long rc2;    // lattice cut-off threshold
+    float lat_to_len;          // L / 2^32 (FP32 rounding of it)
+    float lat_to_len_lo;       // L / 2^32 - lat_to_len (the rounding remainder)
+    float len_to_lat;          // 2^32 / L
+    float coulomb, krf, crf, alpha, two_alpha_sqrtpi;
+    // species tables
+    int n_sites[MS2_MAXSP];
+    double bpos[MS2_MAXSP][MS2_MAXS][3];   // body-frame site positions
+    double bdip[MS2_MAXSP][MS2_MAXS][3];   // body-frame dipoles
+    float q[MS2_MAXSP][MS2_MAXS];          // charges (0: none), FP32 rounding
+    float qlo[MS2_MAXSP][MS2_MAXS];        // q - (float)q
+    float cq[MS2_MAXSP][MS2_MAXS];         // C q as hi + lo floats (C q computed in FP64)
+    float cqlo[MS2_MAXSP][MS2_MAXS];
+    double qd[MS2_MAXSP][MS2_MAXS];        // FP64 charges
+    int ljt[MS2_MAXSP][MS2_MAXS];          // LJ kind or -1
+    double mass[MS2_MAXSP];                // molecule mass
+    double Iinv[MS2_MAXSP][3];             // inverse principal moments (0: free axis)
+    float c6[MS2_MAXT][MS2_MAXT];          // 4 eps sigma^6 (Lorentz-Berthelot), FP32 rounding
+    float c12[MS2_MAXT][MS2_MAXT];         // 4 eps sigma^12, FP32 rounding
+    float c6lo[MS2_MAXT][MS2_MAXT];        // remainders: c = hi + lo to ~48 bits, so that
+    float c12lo[MS2_MAXT][MS2_MAXT];       // fmaf(hi, x, lo*x) is c*x correctly rounded
+    float coulomb_lo;                      // coulomb - (float)coulomb
+    double c6d[MS2_MAXT][MS2_MAXT], c12d[MS2_MAXT][MS2_MAXT];
+};
+
+// Device pointers of one system.
+struct DevSys {
+    int N, ns, jsplit, nblk_red;
+    double *R, *v, *q, *Lm;           // FP64 state
+    int *species;
+    uint32_t *X;                       // [3][N]
+    float *s, *mu;                     // [3][ns][N]
+    float *mum;                        // [3][N] molecular dipole sum_a q_a s_ia (reaction field)
+    float *part;                       // [jsplit][NPV][N]
+    double *part64;                    // FP64 partials (FP64 pair path)
+    double *F, *tau;                   // [3][N]
+    double *Ui;                        // [4][N]: U_lj, U_qq, U_dd, W
+    int *npart;                        // [N]
+    double *blk;                       // [nblk][NRED] per-block partial sums
+    unsigned int *counter;             // last-block counter
+    double *scal;                      // system scalars (see SC_* below)
+    double *acc;                       // running averages (see AC_* below)
+    // Ewald
+    int nk, kx, ky, kz, nsite_q, kchunks;
+    uint32_t *Xs;                      // [3][nsite_q] site lattice coordinates
+    float *qs;                         // [nsite_q] site charges
+    float2 *eik;                       // [3][kmax+1][nsite_q] e^{i n theta}
+    double *Sk;                        // [nk][4]: A*Re S, A*Im S, |S|^2 A part, ... (scaled)
+    float *frec;                       // [kchunks][3][nsite_q] partial site forces
+    double *kblk;                      // per-block energy/virial partials of S(k)
+    // RDF
+    unsigned long long *rdf;           // [rows][nbins]
+    int rdf_bins, rdf_rows;
+    float rdf_inv_dr, rdf_rmax2;
+    int *rdf_kind;                     // [MAXSP*MAXS] kind or -1
+};
+
+// system scalars written by the last block of a reduction
+enum {
+    SC_ULJ = 0, SC_UQQ, SC_UDD, SC_WPAIR, SC_NPAIRS, SC_KETR, SC_KEROT, SC_LAMBDA,
+    SC_UREC, SC_WREC_AT, SC_WREC_CORR, SC_UCONST, SC_PLRC, SC_ULRC, SC_WBG, SC_UNSTABLE,
+    SC_UTOT, SC_WTOT, SC_P, SC_T, SC_KETR_NOW, SC_KEROT_NOW, SC_STEP, SC_COUNT_
+};
+// running averages
+enum { AC_N = 0, AC_U, AC_P, AC_T, AC_BN, AC_BU, AC_BP, AC_NB, AC_SBU, AC_SBU2, AC_SBP, AC_SBP2, AC_COUNT_ };
+
+// ------------------------------------------------------------ helpers
+__device__ __forceinline__ void rotmat(const double q0, const double q1, const double q2, const double q3,
+                                       double A[9]) {
+    // body -> space rotation of the unit quaternion (w, x, y, z)
+    A[0] = 1.0 - 2.0 * (q2 * q2 + q3 * q3);
+    A[1] = 2.0 * (q1 * q2 - q0 * q3);
+    A[2] = 2.0 * (q1 * q3 + q0 * q2);
+    A[3] = 2.0 * (q1 * q2 + q0 * q3);
+    A[4] = 1.0 - 2.0 * (q1 * q1 + q3 * q3);
+    A[5] = 2.0 * (q2 * q3 - q0 * q1);
+    A[6] = 2.0 * (q1 * q3 - q0 * q2);
+    A[7] = 2.0 * (q2 * q3 + q0 * q1);
+    A[8] = 1.0 - 2.0 * (q1 * q1 + q2 * q2);
+}
+
+// lattice coordinate: floor(x * 2^32/L) mod 2^32, taken with one IEEE multiply
+// (no contraction possible) so that host and device agree bit for bit.
+__device__ __forceinline__ uint32_t lattice_coord(double x, double scale) {
+    double t = __dmul_rn(x, scale);
+    return (uint32_t)(unsigned long long)(long long)floor(t);
+}
+
+__device__ __forceinline__ unsigned long long lattice_d2(int dx, int dy, int dz) {
+    return (unsigned long long)((long long)dx * dx) + (unsigned long long)((long long)dy * dy) +
+           (unsigned long long)((long long)dz * dz);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// host-side launch accounting (one increment per kernel launch or graph node replay)
+void ms2_count_launches(long long n);
+
+#define MS2_CUDA_OK(call)                                                                     \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return ms2_fail_cuda(e_, #call, __FILE__, __LINE__);           \
+    } while (0)

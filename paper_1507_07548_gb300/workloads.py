@@ -256,6 +256,8 @@ def ionic_solution(n_water=1000, n_ion_pairs=20, rc=14.0, T=298.0, seed=3, dt=2.
     ions = rng.permutation(N)[:2 * n_ion_pairs]
     sp[ions[:n_ion_pairs]] = 1
     sp[ions[n_ion_pairs:]] = 2
+    order = np.argsort(sp, kind="stable")      # molecules numbered model by model
+    sp, R = sp[order], R[order]
     q = random_quaternions(N, rng)
     q[sp != 0] = [1.0, 0, 0, 0]
     v, Ls = thermal_velocities(models, sp, q, T, KCONV, rng)
