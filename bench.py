@@ -214,7 +214,8 @@ def gpu_arm(args, rank, world, local_rank):
     import paper_1507_07548_gb300.ms2 as ms2
     from paper_1507_07548_gb300 import workloads as W
 
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()               # a real stream handle shared with the library
+    torch.cuda.set_stream(stream)
     wl = W.water_box(N=N_WATER, rc=RC, seed=SEED)
     s = ms2.System.from_workload(wl, stream=stream.cuda_stream)
     s.step(RELAX_STEPS)                              # relax the lattice start (untimed)

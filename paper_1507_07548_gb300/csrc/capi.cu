@@ -50,12 +50,13 @@ __global__ void k_ewald_sk(const SysParams *, DevSys, float2 *);
 __global__ void k_ewald_energy(const SysParams *, DevSys, int);
 __global__ void k_ewald_force(const SysParams *, DevSys, const float2 *, int);
 __global__ void k_rdf(const SysParams *, DevSys);
+__global__ void k_terms(const SysParams *, DevSys, double *);
 size_t ms2_pair_smem_bytes(int NS, bool dmu, bool multi, int TJ, int wpb);
 size_t ms2_pair64_smem_bytes(int TJ, int wpb);
 void *ms2_pick_pair_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, int *ns_used,
                            bool *dmu, bool *mult_used);
 
-enum { RED_SUM = 1, RED_RECORD = 2, RED_KICK = 4, RED_HALFKICK = 8, RED_FP64PART = 16, RED_EWALD = 32 };
+enum { RED_SUM = 1, RED_RECORD = 2, RED_LAMBDA = 4, RED_HALFKICK = 8, RED_FP64PART = 16, RED_EWALD = 32 };
 
 // ------------------------------------------------------------ allocation
 cudaError_t DevAlloc::alloc(void **p, size_t n) {
@@ -239,6 +240,11 @@ void ms2_fill_params(SysParams &P, const ms2_model *models, int n_models, const 
     }
     for (int i = 0; i < N; ++i) ndof += rotdof[species[i]];
     P.ndof = ndof;
+    P.inv_kconv = 1.0 / kconv;
+    P.inv_ndof = 1.0 / ndof;
+    P.inv_V = 1.0 / P.V;
+    P.inv_T0 = T0 > 0 ? 1.0 / T0 : 0.0;
+    for (int m = 0; m < n_models; ++m) P.inv_mass[m] = 1.0 / P.mass[m];
     P.ns = ns;
     P.n_ljt = t;
     for (int a = 0; a < t; ++a)
@@ -342,7 +348,9 @@ static ms2_status sys_alloc(ms2_system s) {
     MS2_CUDA_OK(A((void **)&d.tau, sizeof(double) * 3 * N));
     MS2_CUDA_OK(A((void **)&d.Ui, sizeof(double) * 4 * N));
     MS2_CUDA_OK(A((void **)&d.npart, sizeof(int) * N));
-    d.nblk_red = (N + s->red_threads - 1) / s->red_threads;
+    d.nblk_red = (N + 31) / 32;  // reduction: one quad of lanes per molecule, 32 molecules per block
+    MS2_CUDA_OK(A((void **)&d.terms, sizeof(double) * 8));
+    if (s->hp.elec == ELEC_EWALD) MS2_CUDA_OK(A((void **)&d.wcorr, sizeof(double) * N));
     MS2_CUDA_OK(A((void **)&d.blk, sizeof(double) * MS2_NRED * d.nblk_red));
     MS2_CUDA_OK(A((void **)&d.counter, 256));
     MS2_CUDA_OK(A((void **)&d.scal, sizeof(double) * SC_COUNT_));
@@ -358,17 +366,18 @@ static void pick_launch_shape(ms2_system s) {
     const int N = s->N;
     // pair kernel: warps own molecules; split the j loop so that the grid holds
     // ~32 warps per SM (152 SMs)
+    // ~2 resident blocks of 8 warps per SM: split the j loop only as far as
+    // the grid still fits one wave (a partial second wave costs a whole wave)
     s->wpb = 8;
-    int js = (int)std::lround(152.0 * 32.0 / std::max(N, 1));
-    s->jsplit = std::max(1, std::min(8, js));
+    const int iblocks = (N + s->wpb - 1) / s->wpb;
+    s->jsplit = std::max(1, std::min(8, (152 * 2) / std::max(iblocks, 1)));
     if (s->tune_jsplit > 0) s->jsplit = s->tune_jsplit;
     if (s->tune_wpb > 0) s->wpb = s->tune_wpb;
     // FP64-heavy kernels: spread molecules over all SMs with small blocks
     s->red_threads = N <= 152 * 32 ? 32 : 64;
-    int dt = (N + 151) / 152;
-    int p2 = 8;
-    while (p2 < dt && p2 < 128) p2 <<= 1;
-    s->drift_threads = p2;
+    // an FP64 warp instruction costs the same issue slots however many lanes are
+    // active, so the FP64 kernels use full warps
+    s->drift_threads = 32;
 }
 
 static ms2_status upload_params(ms2_system s) {
@@ -428,8 +437,8 @@ static ms2_status size_pair_tiles(ms2_system s) {
 
 // ------------------------------------------------------------ launchers
 ms2_status launch_build(ms2_system s) {
-    const int th = 64;
-    k_build<<<(s->N + th - 1) / th, th, 0, s->stream>>>(s->dP, s->d);
+    const int th = 128;  // 4 lanes per molecule
+    k_build<<<(4 * s->N + th - 1) / th, th, 0, s->stream>>>(s->dP, s->d);
     s->launch_acc += 1;
     return MS2_OK;
 }
@@ -457,14 +466,15 @@ ms2_status launch_ewald(ms2_system s) {
 ms2_status launch_reduce(ms2_system s, int mode) {
     if (s->fp64) mode |= RED_FP64PART;
     if (s->hp.elec == ELEC_EWALD) mode |= RED_EWALD;
-    k_reduce<<<s->d.nblk_red, s->red_threads, 0, s->stream>>>(s->dP, s->d, mode);
+    if (s->hp.integrator != MS2_INT_VERLET) mode |= RED_LAMBDA;
+    k_reduce<<<s->d.nblk_red, 128, 0, s->stream>>>(s->dP, s->d, mode);
     s->launch_acc += 1;
     return MS2_OK;
 }
 
 ms2_status launch_drift(ms2_system s) {
-    const int th = s->drift_threads;
-    k_drift<<<(s->N + th - 1) / th, th, 0, s->stream>>>(s->dP, s->d, s->hp.integrator == MS2_INT_VERLET ? 1 : 0);
+    const int th = 128;  // 4 lanes per molecule
+    k_drift<<<(4 * s->N + th - 1) / th, th, 0, s->stream>>>(s->dP, s->d, s->hp.integrator == MS2_INT_VERLET ? 1 : 0);
     s->launch_acc += 1;
     return MS2_OK;
 }
@@ -501,21 +511,14 @@ static void enqueue_steps(ms2_system s, long long n, long long s0) {
         const bool sample = every > 0 && ((s0 + k + 1) % every) == 0;
         const bool tm = s->timing && k == n - 1;
         if (tm) cudaEventRecordWithFlags(s->ev[0], s->stream, cudaEventRecordExternal);
-        if (verlet) {
-            launch_drift(s);
-            if (sample) launch_rdf(s);
-        } else {
-            launch_reduce(s, k == 0 ? RED_KICK : (RED_SUM | RED_RECORD | RED_KICK));
-            launch_drift(s);
-            if (sample) launch_rdf(s);
-        }
+        launch_drift(s);
+        if (sample) launch_rdf(s);
         if (tm) cudaEventRecordWithFlags(s->ev[1], s->stream, cudaEventRecordExternal);
         launch_pair(s);
         if (tm) cudaEventRecordWithFlags(s->ev[2], s->stream, cudaEventRecordExternal);
         launch_ewald(s);
         if (tm) cudaEventRecordWithFlags(s->ev[3], s->stream, cudaEventRecordExternal);
-        if (verlet) launch_reduce(s, RED_SUM | RED_RECORD | RED_HALFKICK);
-        else if (k == n - 1) launch_reduce(s, RED_SUM | RED_RECORD);
+        launch_reduce(s, verlet ? (RED_SUM | RED_RECORD | RED_HALFKICK) : (RED_SUM | RED_RECORD));
         if (tm) cudaEventRecordWithFlags(s->ev[4], s->stream, cudaEventRecordExternal);
     }
 }
@@ -928,21 +931,27 @@ extern "C" ms2_status ms2_energy_terms(ms2_system s, double terms[16]) {
         uself = -coulomb * s->alpha / std::sqrt(M_PI) * sq2;
         uintra = c_all - uself - ubg;
     }
-    terms[0] = sc[SC_ULJ];
-    terms[1] = sc[SC_UQQ];
-    terms[2] = sc[SC_UDD];
+    // breakdown of the pair part, summed on demand from the per-molecule arrays
+    double tb[8];
+    k_terms<<<1, 256, 0, s->stream>>>(s->dP, s->d, s->d.terms);
+    ms2_count_launches(1);
+    MS2_CUDA_OK(cudaMemcpyAsync(tb, s->d.terms, sizeof tb, cudaMemcpyDeviceToHost, s->stream));
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    terms[0] = 0.5 * tb[0];
+    terms[1] = 0.5 * tb[1];
+    terms[2] = 0.5 * tb[2];
     terms[3] = ew ? sc[SC_UREC] : 0.0;
     terms[4] = uself;
     terms[5] = uintra;
     terms[6] = ubg;
     terms[7] = sc[SC_ULRC];
     terms[8] = sc[SC_UTOT];
-    terms[9] = sc[SC_WPAIR];
-    terms[10] = ew ? sc[SC_WREC_AT] - sc[SC_WREC_CORR] : 0.0;
+    terms[9] = 0.5 * tb[3];
+    terms[10] = ew ? sc[SC_WREC_AT] - tb[5] : 0.0;
     terms[11] = sc[SC_WBG];
     terms[12] = sc[SC_WTOT];
     terms[13] = sc[SC_PLRC];
-    terms[14] = sc[SC_NPAIRS];
+    terms[14] = 0.5 * tb[4];
     terms[15] = sc[SC_KETR_NOW] + sc[SC_KEROT_NOW];
     return MS2_OK;
 }

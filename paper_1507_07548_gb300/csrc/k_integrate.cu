@@ -1,124 +1,128 @@
 // K1 site build, K5 integration (velocity Verlet; leapfrog + quaternion implicit
 // midpoint + isokinetic scaling) and K6 thermo reduction.
 //
-// FP64 is used for the state and the integrator.  GB300's FP64 rate is ~1/57 of
-// its FP32 rate (~1.2 vs ~67 TFLOP/s measured), so these kernels are launched with
-// small blocks that spread the per-molecule FP64 work over all SMs, and every
-// system-wide sum is a fixed-order "last block" reduction (no float atomics, so
-// results are bitwise reproducible).
+// FP64 holds the state and every accumulation (R, v, q, L, F, tau, energy and
+// virial sums).  On GB300 one warp sees ~1/4 of an SM's small FP64 unit: a
+// dependent FP64 instruction costs ~70 cycles whatever the number of active
+// lanes.  So each molecule is handled by a quad of lanes (lanes 0-2: the x, y, z
+// components; lane 3: the rotation), no FP64 divide or square root runs per
+// step (host-side reciprocals, Newton rsqrt from an FP32 seed), the rotation
+// increment of the implicit-midpoint sweeps is evaluated in FP32 and added to
+// the FP64 quaternion, and a step reduces only the five scalars it needs; the
+// energy breakdown is summed on demand.  All system-wide sums are fixed-order
+// "last block" reductions (no float atomics: bitwise reproducible).
 #include "ms2_internal.cuh"
 
-// ------------------------------------------------------------ site build
-// lattice centre coordinates; space-frame FP32 site offsets and dipoles
-__device__ __forceinline__ void build_one(const SysParams *__restrict__ P, const DevSys &S, int i) {
-    const int N = S.N, NS = S.ns;
-    const double lat = P->lat_scale;
-    const double R0 = S.R[i], R1 = S.R[N + i], R2 = S.R[2 * N + i];
-    S.X[i] = lattice_coord(R0, lat);
-    S.X[N + i] = lattice_coord(R1, lat);
-    S.X[2 * N + i] = lattice_coord(R2, lat);
-    double A[9];
-    rotmat(S.q[i], S.q[N + i], S.q[2 * N + i], S.q[3 * N + i], A);
-    const int sp = S.species[i];
-    const int nsp = P->n_sites[sp];
-    double md[3] = {0, 0, 0};
-    for (int a = 0; a < NS; ++a) {
-        double o[3] = {0, 0, 0}, m[3] = {0, 0, 0};
-        if (a < nsp) {
-            const double *b = P->bpos[sp][a];
-            const double *u = P->bdip[sp][a];
-            for (int r = 0; r < 3; ++r) {
-                o[r] = A[3 * r] * b[0] + A[3 * r + 1] * b[1] + A[3 * r + 2] * b[2];
-                m[r] = A[3 * r] * u[0] + A[3 * r + 1] * u[1] + A[3 * r + 2] * u[2];
-            }
-        }
-        for (int k = 0; k < 3; ++k) {
-            S.s[(k * NS + a) * N + i] = (float)o[k];
-            if (S.mu) S.mu[(k * NS + a) * N + i] = (float)m[k];
-            if (a < nsp) md[k] += P->qd[sp][a] * o[k];
-        }
-    }
-    if (S.mum)
-        for (int k = 0; k < 3; ++k) S.mum[k * N + i] = (float)md[k];
+__device__ __forceinline__ double rsqrt_fp64(double x) {  // FP32 seed + two Newton steps (~1 ulp)
+    double y = (double)rsqrtf((float)x);
+    y = y * fma(-0.5 * x * y, y, 1.5);
+    return y * fma(-0.5 * x * y, y, 1.5);
 }
 
+// ------------------------------------------------------------ site build
+// lattice centre coordinate of component c; row c of the space-frame site
+// offsets, dipoles and molecular charge dipole (lane c of a quad)
+__device__ __forceinline__ void build_row(const SysParams *__restrict__ P, const DevSys &S, int i, int c,
+                                          const double q[4]) {
+    const int N = S.N, NS = S.ns;
+    S.X[c * N + i] = lattice_coord(S.R[c * N + i], P->lat_scale);
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    double a0, a1, a2;  // row c of A(q)
+    if (c == 0) { a0 = 1.0 - 2.0 * (y * y + z * z); a1 = 2.0 * (x * y - w * z); a2 = 2.0 * (x * z + w * y); }
+    else if (c == 1) { a0 = 2.0 * (x * y + w * z); a1 = 1.0 - 2.0 * (x * x + z * z); a2 = 2.0 * (y * z - w * x); }
+    else { a0 = 2.0 * (x * z - w * y); a1 = 2.0 * (y * z + w * x); a2 = 1.0 - 2.0 * (x * x + y * y); }
+    const int sp = S.species[i], nsp = P->n_sites[sp];
+    double md = 0.0;
+    for (int a = 0; a < NS; ++a) {
+        double o = 0.0, m = 0.0;
+        if (a < nsp) {
+            const double *b = P->bpos[sp][a], *u = P->bdip[sp][a];
+            o = a0 * b[0] + a1 * b[1] + a2 * b[2];
+            if (S.mu) m = a0 * u[0] + a1 * u[1] + a2 * u[2];
+            md += P->qd[sp][a] * o;
+        }
+        S.s[(c * NS + a) * N + i] = (float)o;
+        if (S.mu) S.mu[(c * NS + a) * N + i] = (float)m;
+    }
+    if (S.mum) S.mum[c * N + i] = (float)md;
+}
+
+// one quad per molecule: 4 lanes, lanes 0-2 build rows 0-2
 __global__ void k_build(const SysParams *__restrict__ P, DevSys S) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < S.N) build_one(P, S, i);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, i = t >> 2, c = t & 3;
+    if (i >= S.N || c == 3) return;
+    const int N = S.N;
+    const double q[4] = {S.q[i], S.q[N + i], S.q[2 * N + i], S.q[3 * N + i]};
+    build_row(P, S, i, c, q);
 }
 
 // ------------------------------------------------------- rigid rotation
-// q1 from q0 with space-frame angular momentum Lsp held at its half-step value:
+// q1 from q0 with space-frame angular momentum L held at its half-step value:
 // implicit midpoint rule q1 = q0 + dt/2 * qm (x) (0, w_b), qm = (q0+q1)/2,
 // w_b = I^-1 A(qm/|qm|)^T L, solved by `iters` fixed-point sweeps from q1 = q0,
-// then normalised.
+// then normalised.  A(qm/|qm|) is taken in its homogeneous form
+// A_h(qm) / |qm|^2 (the same matrix).  The sweeps evaluate the increment in
+// FP32 (a ~1e-2 correction: ~1e-9 absolute error); it is added to the FP64
+// quaternion, which is renormalised in FP64.
 __device__ void rotate_q(const double Iinv[3], const double q0[4], const double Lsp[3], double dt, int iters,
                          double q1[4]) {
-    for (int k = 0; k < 4; ++k) q1[k] = q0[k];
+    const float a0 = (float)q0[0], a1 = (float)q0[1], a2 = (float)q0[2], a3 = (float)q0[3];
+    const float L0 = (float)Lsp[0], L1 = (float)Lsp[1], L2 = (float)Lsp[2];
+    const float I0 = (float)Iinv[0], I1 = (float)Iinv[1], I2 = (float)Iinv[2], h = (float)(0.5 * dt);
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;  // increment q1 - q0
     for (int it = 0; it < iters; ++it) {
-        double qm[4];
-        for (int k = 0; k < 4; ++k) qm[k] = 0.5 * (q0[k] + q1[k]);
-        const double inv = 1.0 / sqrt(qm[0] * qm[0] + qm[1] * qm[1] + qm[2] * qm[2] + qm[3] * qm[3]);
-        double A[9];
-        rotmat(qm[0] * inv, qm[1] * inv, qm[2] * inv, qm[3] * inv, A);
-        double w[3];
-        for (int c = 0; c < 3; ++c) w[c] = Iinv[c] * (A[c] * Lsp[0] + A[3 + c] * Lsp[1] + A[6 + c] * Lsp[2]);
-        // qm (x) (0, w)
-        const double d0 = -qm[1] * w[0] - qm[2] * w[1] - qm[3] * w[2];
-        const double d1 = qm[0] * w[0] + qm[2] * w[2] - qm[3] * w[1];
-        const double d2 = qm[0] * w[1] - qm[1] * w[2] + qm[3] * w[0];
-        const double d3 = qm[0] * w[2] + qm[1] * w[1] - qm[2] * w[0];
-        const double h = 0.5 * dt;
-        q1[0] = q0[0] + h * d0;
-        q1[1] = q0[1] + h * d1;
-        q1[2] = q0[2] + h * d2;
-        q1[3] = q0[3] + h * d3;
+        const float w = a0 + 0.5f * d0, x = a1 + 0.5f * d1, y = a2 + 0.5f * d2, z = a3 + 0.5f * d3;
+        const float ww = w * w, xx = x * x, yy = y * y, zz = z * z;
+        const float inv = 1.0f / (ww + xx + yy + zz);
+        const float xy = x * y, xz = x * z, yz = y * z, wx = w * x, wy = w * y, wz = w * z;
+        const float lb0 = (ww + xx - yy - zz) * L0 + 2.f * (xy + wz) * L1 + 2.f * (xz - wy) * L2;
+        const float lb1 = 2.f * (xy - wz) * L0 + (ww - xx + yy - zz) * L1 + 2.f * (yz + wx) * L2;
+        const float lb2 = 2.f * (xz + wy) * L0 + 2.f * (yz - wx) * L1 + (ww - xx - yy + zz) * L2;
+        const float o0 = I0 * lb0 * inv, o1 = I1 * lb1 * inv, o2 = I2 * lb2 * inv;
+        d0 = h * (-x * o0 - y * o1 - z * o2);
+        d1 = h * (w * o0 + y * o2 - z * o1);
+        d2 = h * (w * o1 - x * o2 + z * o0);
+        d3 = h * (w * o2 + x * o1 - y * o0);
     }
-    const double inv = 1.0 / sqrt(q1[0] * q1[0] + q1[1] * q1[1] + q1[2] * q1[2] + q1[3] * q1[3]);
+    q1[0] = q0[0] + (double)d0;
+    q1[1] = q0[1] + (double)d1;
+    q1[2] = q0[2] + (double)d2;
+    q1[3] = q0[3] + (double)d3;
+    const double inv = rsqrt_fp64(q1[0] * q1[0] + q1[1] * q1[1] + q1[2] * q1[2] + q1[3] * q1[3]);
     for (int k = 0; k < 4; ++k) q1[k] *= inv;
 }
 
-// kinetic energies (mass units; divided by kconv in the final reduction)
-__device__ __forceinline__ double ke_rot(const SysParams *__restrict__ P, int sp, const double A[9], double L0,
-                                         double L1, double L2) {
-    double e = 0;
-    for (int c = 0; c < 3; ++c) {
-        const double lb = A[c] * L0 + A[3 + c] * L1 + A[6 + c] * L2;
-        e += P->Iinv[sp][c] * lb * lb;
-    }
-    return 0.5 * e;
+// column c of A(q): the body component c of a space vector v is column_c . v
+__device__ __forceinline__ void rot_column(const double q[4], int c, double col[3]) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    if (c == 0) { col[0] = 1.0 - 2.0 * (y * y + z * z); col[1] = 2.0 * (x * y + w * z); col[2] = 2.0 * (x * z - w * y); }
+    else if (c == 1) { col[0] = 2.0 * (x * y - w * z); col[1] = 1.0 - 2.0 * (x * x + z * z); col[2] = 2.0 * (y * z + w * x); }
+    else { col[0] = 2.0 * (x * z + w * y); col[1] = 2.0 * (y * z - w * x); col[2] = 1.0 - 2.0 * (x * x + y * y); }
 }
 
 // ------------------------------------------------------------- reduction
-// reduction slots of the per-block partial sums
-enum { R_ULJ = 0, R_UQQ, R_UDD, R_W, R_NP, R_KETR, R_KEROT, R_KETR1, R_KEROT1, R_WCORR, R_BAD, R_NRED_USED };
+enum { RED_SUM = 1, RED_RECORD = 2, RED_LAMBDA = 4, RED_HALFKICK = 8, RED_FP64PART = 16, RED_EWALD = 32 };
+// per-step scalars: potential energy (pair part), virial (pair + reciprocal
+// molecular correction), kinetic energy of the stored velocities (translation,
+// rotation), kinetic energy after the kick, non-finite force flag
+enum { Q_U = 0, Q_W, Q_KTR, Q_KROT, Q_K1, Q_BAD, Q_N };
 
-enum { RED_SUM = 1, RED_RECORD = 2, RED_KICK = 4, RED_HALFKICK = 8, RED_FP64PART = 16, RED_EWALD = 32 };
-
-// final fixed-order sum of the block partials and the system scalars; run by
-// the last block to finish
-__device__ void finish_reduction(const SysParams *__restrict__ P, const DevSys &S, int mode, double *tot) {
+// final fixed-order scalars of a step; run by the last block
+__device__ void finish_step(const SysParams *__restrict__ P, const DevSys &S, int mode, const double *tot) {
     double *sc = S.scal;
-    const double kc = P->kconv;
+    const double ikc = P->inv_kconv;
     if (mode & RED_SUM) {
-        sc[SC_ULJ] = 0.5 * tot[R_ULJ];
-        sc[SC_UQQ] = 0.5 * tot[R_UQQ];
-        sc[SC_UDD] = 0.5 * tot[R_UDD];
-        sc[SC_WPAIR] = 0.5 * tot[R_W];
-        sc[SC_NPAIRS] = 0.5 * tot[R_NP];
-        sc[SC_WREC_CORR] = (mode & RED_EWALD) ? tot[R_WCORR] : 0.0;
-        sc[SC_UNSTABLE] = tot[R_BAD];
-        const double U = sc[SC_ULJ] + sc[SC_UQQ] + sc[SC_UDD] + ((mode & RED_EWALD) ? sc[SC_UREC] : 0.0) +
-                         sc[SC_UCONST] + sc[SC_ULRC];
-        const double W = sc[SC_WPAIR] + ((mode & RED_EWALD) ? sc[SC_WREC_AT] - sc[SC_WREC_CORR] : 0.0) + sc[SC_WBG];
+        const double U = 0.5 * tot[Q_U] + ((mode & RED_EWALD) ? sc[SC_UREC] : 0.0) + sc[SC_UCONST] + sc[SC_ULRC];
+        const double W = 0.5 * tot[Q_W] + ((mode & RED_EWALD) ? sc[SC_WREC_AT] : 0.0) + sc[SC_WBG];
         sc[SC_UTOT] = U;
         sc[SC_WTOT] = W;
+        sc[SC_UNSTABLE] = tot[Q_BAD] > 0 ? 1.0 : 0.0;
     }
-    const double ketr = tot[R_KETR] / kc, kerot = tot[R_KEROT] / kc;
+    const double ketr = tot[Q_KTR] * ikc, kerot = tot[Q_KROT] * ikc;
     sc[SC_KETR_NOW] = ketr;
     sc[SC_KEROT_NOW] = kerot;
-    sc[SC_T] = 2.0 * (ketr + kerot) / P->ndof;
-    sc[SC_P] = (2.0 * ketr / 3.0 + sc[SC_WTOT] / 3.0) / P->V + sc[SC_PLRC];
+    sc[SC_T] = 2.0 * (ketr + kerot) * P->inv_ndof;
+    sc[SC_P] = (2.0 * ketr + sc[SC_WTOT]) * (1.0 / 3.0) * P->inv_V + sc[SC_PLRC];
     if (mode & RED_RECORD) {
         double *ac = S.acc;
         ac[AC_N] += 1.0;
@@ -129,7 +133,7 @@ __device__ void finish_reduction(const SysParams *__restrict__ P, const DevSys &
         ac[AC_BU] += sc[SC_UTOT];
         ac[AC_BP] += sc[SC_P];
         if (ac[AC_BN] >= 100.0) {  // close a block of 100 steps
-            const double bu = ac[AC_BU] / ac[AC_BN], bp = ac[AC_BP] / ac[AC_BN];
+            const double bu = ac[AC_BU] * 0.01, bp = ac[AC_BP] * 0.01;
             ac[AC_NB] += 1.0;
             ac[AC_SBU] += bu;
             ac[AC_SBU2] += bu * bu;
@@ -138,160 +142,231 @@ __device__ void finish_reduction(const SysParams *__restrict__ P, const DevSys &
             ac[AC_BN] = ac[AC_BU] = ac[AC_BP] = 0.0;
         }
     }
-    if (mode & RED_KICK) {
-        const double k1 = tot[R_KETR1] / kc, r1 = tot[R_KEROT1] / kc;
-        const double Tp = 2.0 * (k1 + r1) / P->ndof;
-        sc[SC_LAMBDA] = (P->thermostat && Tp > 0) ? sqrt(P->T0 / Tp) : 1.0;
+    if (mode & RED_LAMBDA) {  // isokinetic factor sqrt(T0 / T') for the next drift
+        const double x = 2.0 * tot[Q_K1] * ikc * P->inv_ndof * P->inv_T0;
+        sc[SC_LAMBDA] = (P->thermostat && x > 0) ? rsqrt_fp64(x) : 1.0;
     }
 }
 
 // Sums the pair partials (and Ewald site forces) into F, tau and per-molecule
-// energies; records the kinetic energy of the stored velocities; optionally
-// kicks the velocities with the new forces (leapfrog: full step, then the
-// thermostat factor from the kicked kinetic energy; Verlet: half step).
-__global__ void k_reduce(const SysParams *__restrict__ P, DevSys S, int mode) {
-    const int N = S.N, i = blockIdx.x * blockDim.x + threadIdx.x;
-    double r[R_NRED_USED];
-    for (int k = 0; k < R_NRED_USED; ++k) r[k] = 0.0;
-    if (i < N) {
-        const int sp = S.species[i];
-        double F[3], T[3];
-        if (mode & RED_SUM) {
-            double u[4] = {0, 0, 0, 0}, np = 0;
-            for (int k = 0; k < 3; ++k) F[k] = T[k] = 0.0;
+// energies; the kinetic energy of the stored velocities.  Leapfrog
+// (RED_LAMBDA): also the kinetic energy the velocities will have after the kick
+// with these forces, hence the thermostat factor the next drift applies.
+// Verlet (RED_HALFKICK): applies the second half kick.  One quad per molecule,
+// 32 molecules per block.
+__global__ void __launch_bounds__(128) k_reduce(const SysParams *__restrict__ P, DevSys S, int mode) {
+    __shared__ double sh_f[32][3 * MS2_MAXS];   // Ewald site forces of the block's molecules
+    __shared__ double sh_t[32][3];               // torques (for the kicked rotational energy)
+    const int N = S.N, tq = threadIdx.x >> 2, c = threadIdx.x & 3;
+    const int i = blockIdx.x * (blockDim.x >> 2) + tq;
+    const bool on = i < N;
+    const int ii = on ? i : 0;
+    double r[Q_N] = {0, 0, 0, 0, 0, 0};
+    const int sp = S.species[ii];
+    double Fc = 0, Tc = 0;
+    if (mode & RED_SUM) {
+        // force / torque component c on lanes 0-2; energies and virial on lane 3
+        if (c < 3) {
             for (int p = 0; p < S.jsplit; ++p) {
                 if (mode & RED_FP64PART) {
-                    const double *o = S.part64 + (size_t)p * MS2_NPV * N + i;
-                    for (int k = 0; k < 3; ++k) { F[k] += o[(PV_FX + k) * N]; T[k] += o[(PV_TX + k) * N]; }
+                    const double *o = S.part64 + (size_t)p * MS2_NPV * N + ii;
+                    Fc += o[(PV_FX + c) * N];
+                    Tc += o[(PV_TX + c) * N];
+                } else {
+                    const float *o = S.part + (size_t)p * MS2_NPV * N + ii;
+                    Fc += (double)o[(PV_FX + c) * N];
+                    Tc += (double)o[(PV_TX + c) * N];
+                }
+            }
+        } else {
+            double u[4] = {0, 0, 0, 0}, np = 0;
+            for (int p = 0; p < S.jsplit; ++p) {
+                if (mode & RED_FP64PART) {
+                    const double *o = S.part64 + (size_t)p * MS2_NPV * N + ii;
                     u[0] += o[PV_ULJ * N]; u[1] += o[PV_UQQ * N]; u[2] += o[PV_UDD * N]; u[3] += o[PV_W * N];
                     np += o[PV_NP * N];
                 } else {
-                    const float *o = S.part + (size_t)p * MS2_NPV * N + i;
-                    for (int k = 0; k < 3; ++k) { F[k] += (double)o[(PV_FX + k) * N]; T[k] += (double)o[(PV_TX + k) * N]; }
+                    const float *o = S.part + (size_t)p * MS2_NPV * N + ii;
                     u[0] += (double)o[PV_ULJ * N]; u[1] += (double)o[PV_UQQ * N]; u[2] += (double)o[PV_UDD * N];
                     u[3] += (double)o[PV_W * N];
                     np += (double)o[PV_NP * N];
                 }
             }
-            if (mode & RED_EWALD) {  // reciprocal-space site forces, summed over k chunks
-                const int NS = S.ns, M = S.nsite_q;
-                double wc = 0;
-                for (int a = 0; a < NS; ++a) {
-                    const int s = a * N + i;
-                    double f[3] = {0, 0, 0};
-                    for (int c = 0; c < S.kchunks; ++c)
-                        for (int k = 0; k < 3; ++k) f[k] += (double)S.frec[((size_t)c * 3 + k) * M + s];
-                    const double o0 = S.s[(0 * NS + a) * N + i], o1 = S.s[(1 * NS + a) * N + i],
-                                 o2 = S.s[(2 * NS + a) * N + i];
-                    F[0] += f[0]; F[1] += f[1]; F[2] += f[2];
-                    T[0] += o1 * f[2] - o2 * f[1];
-                    T[1] += o2 * f[0] - o0 * f[2];
-                    T[2] += o0 * f[1] - o1 * f[0];
-                    wc += f[0] * o0 + f[1] * o1 + f[2] * o2;
-                }
-                r[R_WCORR] = wc;
+            r[Q_U] = u[0] + u[1] + u[2];
+            r[Q_W] = u[3];
+            if (on) {
+                for (int k = 0; k < 4; ++k) S.Ui[k * N + i] = u[k];
+                S.npart[i] = (int)np;
             }
-            for (int k = 0; k < 3; ++k) { S.F[k * N + i] = F[k]; S.tau[k * N + i] = T[k]; }
-            for (int k = 0; k < 4; ++k) S.Ui[k * N + i] = u[k];
-            S.npart[i] = (int)np;
-            r[R_ULJ] = u[0]; r[R_UQQ] = u[1]; r[R_UDD] = u[2]; r[R_W] = u[3]; r[R_NP] = np;
-            const double fm = fmax(fabs(F[0]), fmax(fabs(F[1]), fabs(F[2])));
-            r[R_BAD] = (fm < 1e30) ? 0.0 : 1.0;  // NaN fails the comparison too
-        } else {
-            for (int k = 0; k < 3; ++k) { F[k] = S.F[k * N + i]; T[k] = S.tau[k * N + i]; }
         }
-        // kinetic energy of the stored velocities
-        const double M = P->mass[sp];
-        double v[3], L[3], A[9];
-        for (int k = 0; k < 3; ++k) { v[k] = S.v[k * N + i]; L[k] = S.Lm[k * N + i]; }
-        rotmat(S.q[i], S.q[N + i], S.q[2 * N + i], S.q[3 * N + i], A);
-        r[R_KETR] = 0.5 * M * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-        r[R_KEROT] = ke_rot(P, sp, A, L[0], L[1], L[2]);
-        if (mode & (RED_KICK | RED_HALFKICK)) {
-            const double h = (mode & RED_HALFKICK) ? 0.5 * P->dt : P->dt;
-            const double cf = h * P->kconv / M, ct = h * P->kconv;
-            for (int k = 0; k < 3; ++k) {
-                v[k] += cf * F[k];
-                L[k] += ct * T[k];
-                S.v[k * N + i] = v[k];
-                S.Lm[k * N + i] = L[k];
+        if (mode & RED_EWALD) {  // reciprocal-space site forces, summed over k chunks
+            const int NS = S.ns, M = S.nsite_q;
+            if (c < 3)
+                for (int a = 0; a < NS; ++a) {
+                    double f = 0;
+                    for (int ch = 0; ch < S.kchunks; ++ch) f += (double)S.frec[((size_t)ch * 3 + c) * M + a * N + ii];
+                    sh_f[tq][3 * a + c] = f;
+                    Fc += f;
+                }
+            __syncwarp();
+            double wc = 0;
+            if (c < 3) {  // torque component c and the molecular-virial correction -F_s.s_s
+                const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+                for (int a = 0; a < NS; ++a) {
+                    const double o1 = S.s[(c1 * NS + a) * N + ii], o2 = S.s[(c2 * NS + a) * N + ii];
+                    const double oc = S.s[(c * NS + a) * N + ii];
+                    Tc += o1 * sh_f[tq][3 * a + c2] - o2 * sh_f[tq][3 * a + c1];
+                    wc += oc * sh_f[tq][3 * a + c];
+                }
+                r[Q_W] = -2.0 * wc;  // pair virial sums are halved at the end
             }
-            r[R_KETR1] = 0.5 * M * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-            r[R_KEROT1] = ke_rot(P, sp, A, L[0], L[1], L[2]);
-            if (mode & RED_HALFKICK) {  // Verlet: the recorded kinetic energy is the one at t + dt
-                r[R_KETR] = r[R_KETR1];
-                r[R_KEROT] = r[R_KEROT1];
+            // per-molecule reciprocal virial correction for the on-demand breakdown
+            const double w0 = __shfl_sync(0xffffffffu, wc, (threadIdx.x & 28) | 0);
+            const double w1 = __shfl_sync(0xffffffffu, wc, (threadIdx.x & 28) | 1);
+            const double w2 = __shfl_sync(0xffffffffu, wc, (threadIdx.x & 28) | 2);
+            if (c == 3 && on) S.wcorr[i] = w0 + w1 + w2;
+        }
+        if (c < 3 && on) {
+            S.F[c * N + i] = Fc;
+            S.tau[c * N + i] = Tc;
+        }
+        r[Q_BAD] = (c < 3 && !(fabs(Fc) < 1e30)) ? 1.0 : 0.0;  // NaN fails the comparison too
+    } else if (c < 3) {
+        Fc = S.F[c * N + ii];
+        Tc = S.tau[c * N + ii];
+    }
+    if (c < 3) sh_t[tq][c] = Tc;
+    __syncwarp();
+    // kinetic energies: lane c takes component c of v and body component c of L
+    if (c < 3) {
+        const double M = P->mass[sp], Ii = P->Iinv[sp][c];
+        const double q[4] = {S.q[ii], S.q[N + ii], S.q[2 * N + ii], S.q[3 * N + ii]};
+        double col[3], L[3];
+        rot_column(q, c, col);
+        for (int k = 0; k < 3; ++k) L[k] = S.Lm[k * N + ii];
+        double v = S.v[c * N + ii];
+        const double lb = col[0] * L[0] + col[1] * L[1] + col[2] * L[2];
+        r[Q_KTR] = 0.5 * M * v * v;
+        r[Q_KROT] = 0.5 * Ii * lb * lb;
+        if (mode & (RED_LAMBDA | RED_HALFKICK)) {
+            const double h = (mode & RED_HALFKICK) ? 0.5 * P->dt : P->dt;
+            const double ct = h * P->kconv;
+            v += ct * P->inv_mass[sp] * Fc;
+            const double lb1 = lb + ct * (col[0] * sh_t[tq][0] + col[1] * sh_t[tq][1] + col[2] * sh_t[tq][2]);
+            r[Q_K1] = 0.5 * M * v * v + 0.5 * Ii * lb1 * lb1;
+            if (mode & RED_HALFKICK) {  // Verlet: velocities at t + dt, recorded
+                if (on) S.v[c * N + i] = v;
+                r[Q_KTR] = 0.5 * M * v * v;
             }
         }
     }
-    // block reduction in fixed order: warp shuffles, then warp 0 over warps
-    __shared__ double sred[32][R_NRED_USED];
+    if (!on)
+        for (int k = 0; k < Q_N; ++k) r[k] = 0.0;
+    // block reduction (fixed shuffle tree), then the last block over blocks
+    __shared__ double sred[4][Q_N];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    for (int k = 0; k < R_NRED_USED; ++k) {
-        double x = warp_sum(r[k]);
-        if (k == R_BAD) x = x > 0 ? 1.0 : 0.0;
+    for (int k = 0; k < Q_N; ++k) {
+        const double x = warp_sum(r[k]);
         if (lane == 0) sred[warp][k] = x;
     }
     __syncthreads();
     __shared__ bool last;
+    if (threadIdx.x < Q_N) {
+        double x = 0;
+        for (int w = 0; w < nw; ++w) x += sred[w][threadIdx.x];
+        S.blk[(size_t)blockIdx.x * MS2_NRED + threadIdx.x] = x;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double *blk = S.blk + (size_t)blockIdx.x * MS2_NRED;
-        for (int k = 0; k < R_NRED_USED; ++k) {
-            double x = 0;
-            for (int w = 0; w < nw; ++w) x += sred[w][k];
-            blk[k] = x;
-        }
         __threadfence();
-        const unsigned prev = atomicAdd(S.counter, 1u);
-        last = prev == gridDim.x - 1;
+        last = atomicAdd(S.counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
     __shared__ double tot[MS2_NRED];
-    if (threadIdx.x < R_NRED_USED) {
-        double x = 0;
-        for (int b = 0; b < (int)gridDim.x; ++b) x += ((volatile double *)S.blk)[(size_t)b * MS2_NRED + threadIdx.x];
-        tot[threadIdx.x] = x;
+    if (warp == 0) {
+        for (int k = 0; k < Q_N; ++k) {
+            double x = 0;
+            for (int b = lane; b < (int)gridDim.x; b += 32) x += __ldcg(S.blk + (size_t)b * MS2_NRED + k);
+            x = warp_sum(x);
+            if (lane == 0) tot[k] = x;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        finish_reduction(P, S, mode, tot);
+        finish_step(P, S, mode, tot);
         *S.counter = 0u;
     }
 }
 
+// On-demand breakdown of the current configuration (single block, fixed order):
+// out[0..5] = sums of U_lj, U_qq, U_dd, W_pair (owner-doubled), partner counts,
+// and the reciprocal molecular-virial correction sum_s F_s.s_s.
+__global__ void k_terms(const SysParams *__restrict__ P, DevSys S, double *out) {
+    __shared__ double sh[256][6];
+    const int N = S.N;
+    double a[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        for (int k = 0; k < 3; ++k) a[k] += S.Ui[k * N + i];
+        a[4] += S.npart[i];
+        if (S.wcorr) a[5] += S.wcorr[i];
+    }
+    for (int k = 0; k < 6; ++k) sh[threadIdx.x][k] = a[k];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double x = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) x += sh[t][threadIdx.x];
+        out[threadIdx.x] = x;
+    }
+}
+
 // ------------------------------------------------------------------ drift
-// leapfrog: v, L *= lambda (thermostat); R += dt v; q <- rotate(q, L); rebuild
-// Verlet  : v += dt/2 F/M; R += dt v; rebuild
-__global__ void k_drift(const SysParams *__restrict__ P, DevSys S, int verlet) {
-    const int N = S.N, i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int sp = S.species[i];
+// One quad per molecule.  Lanes 0-2, component c:
+//   leapfrog: v_c <- lambda (v_c + dt F_c/M) (kick + isokinetic scaling with the
+//             factor from the last reduction), R_c += dt v_c;
+//   Verlet  : v_c += dt/2 F_c/M, R_c += dt v_c;
+// lane 3 (leapfrog): L <- lambda (L + dt tau), q <- rotate(q, L).  Then lanes 0-2
+// rebuild lattice coordinate c and row c of the site offsets.
+__global__ void __launch_bounds__(128) k_drift(const SysParams *__restrict__ P, DevSys S, int verlet) {
+    const int N = S.N, t = blockIdx.x * blockDim.x + threadIdx.x, i = t >> 2, c = t & 3;
+    const bool on = i < N;
+    const int ii = on ? i : 0;
+    const int sp = S.species[ii];
     const double dt = P->dt;
-    double v[3];
+    double q[4] = {S.q[ii], S.q[N + ii], S.q[2 * N + ii], S.q[3 * N + ii]};
     if (verlet) {
-        const double cf = 0.5 * dt * P->kconv / P->mass[sp];
-        for (int k = 0; k < 3; ++k) {
-            v[k] = S.v[k * N + i] + cf * S.F[k * N + i];
-            S.v[k * N + i] = v[k];
+        if (c < 3 && on) {
+            const double v = S.v[c * N + i] + 0.5 * dt * P->kconv * P->inv_mass[sp] * S.F[c * N + i];
+            S.v[c * N + i] = v;
+            S.R[c * N + i] += dt * v;
         }
     } else {
         const double lam = S.scal[SC_LAMBDA];
-        double L[3];
-        for (int k = 0; k < 3; ++k) {
-            v[k] = lam * S.v[k * N + i];
-            L[k] = lam * S.Lm[k * N + i];
-            S.v[k * N + i] = v[k];
-            S.Lm[k * N + i] = L[k];
+        if (c < 3) {
+            if (on) {
+                const double v = lam * (S.v[c * N + i] + dt * P->kconv * P->inv_mass[sp] * S.F[c * N + i]);
+                S.v[c * N + i] = v;
+                S.R[c * N + i] += dt * v;
+            }
+        } else {
+            const double ct = dt * P->kconv;
+            double L[3];
+            for (int k = 0; k < 3; ++k) {
+                L[k] = lam * (S.Lm[k * N + ii] + ct * S.tau[k * N + ii]);
+                if (on) S.Lm[k * N + i] = L[k];
+            }
+            const double *Ii = P->Iinv[sp];
+            if (Ii[0] != 0.0 || Ii[1] != 0.0 || Ii[2] != 0.0) {
+                double q1[4];
+                rotate_q(Ii, q, L, dt, P->quat_iters, q1);
+                for (int k = 0; k < 4; ++k) {
+                    q[k] = q1[k];
+                    if (on) S.q[k * N + i] = q1[k];
+                }
+            }
         }
-        const double *Ii = P->Iinv[sp];
-        if (Ii[0] != 0.0 || Ii[1] != 0.0 || Ii[2] != 0.0) {
-            double q0[4] = {S.q[i], S.q[N + i], S.q[2 * N + i], S.q[3 * N + i]}, q1[4];
-            rotate_q(Ii, q0, L, dt, P->quat_iters, q1);
-            for (int k = 0; k < 4; ++k) S.q[k * N + i] = q1[k];
-        }
+        for (int k = 0; k < 4; ++k) q[k] = __shfl_sync(0xffffffffu, q[k], (threadIdx.x & 28) | 3);
     }
-    for (int k = 0; k < 3; ++k) S.R[k * N + i] += dt * v[k];
-    build_one(P, S, i);
+    if (c < 3 && on) build_row(P, S, i, c, q);
 }

@@ -33,6 +33,8 @@ struct SysParams {
     int elec, integrator, thermostat, quat_iters;
     int has_dipole, multi, ndof, pad0;
     double L, V, dt, kconv, T0;
+    double inv_kconv, inv_ndof, inv_V, inv_T0;   // host-side reciprocals (no FP64 divide per step)
+    double inv_mass[MS2_MAXSP];
     double lat_scale;          // 2^32 / L  (FP64, exact same value as the host computes)
     unsigned long long rc2;    // lattice cut-off threshold
     float lat_to_len;          // L / 2^32 (FP32 rounding of it)
@@ -70,7 +72,9 @@ struct DevSys {
     float *part;                       // [jsplit][NPV][N]
     double *part64;                    // FP64 partials (FP64 pair path)
     double *F, *tau;                   // [3][N]
-    double *Ui;                        // [4][N]: U_lj, U_qq, U_dd, W
+    double *Ui;                        // [4][N]: U_lj, U_qq, U_dd, W (owner sums over partners)
+    double *wcorr;                     // [N] Ewald: sum_a F_rec,a . s_a (molecular-virial correction)
+    double *terms;                     // [8] on-demand breakdown sums
     int *npart;                        // [N]
     double *blk;                       // [nblk][NRED] per-block partial sums
     unsigned int *counter;             // last-block counter
