@@ -255,6 +255,34 @@ MS2_API ms2_status ms2_serve_close(ms2_server s);
 MS2_API ms2_status ms2_enable_timing(ms2_system sys, int on);
 MS2_API ms2_status ms2_last_step_times(ms2_system sys, double out[4]);
 
+/* ------------------------------------------------------- allocation-free */
+/* Forces, torques, potential energy and molecular virial of ONE configuration
+ * without allocating any device memory.  For callers that cannot call
+ * cudaMalloc: code running inside a pre-reserved memory pool or under a strict
+ * memory cap, plugins that are handed a stream and buffers by a host
+ * application owning all allocations, and sections that must not risk the
+ * implicit device synchronisation an allocation can cause.  (This convenience
+ * has no counterpart in the paper.)
+ * Inputs (device, row-major FP64): centres R_dev (N x 3), unit quaternions
+ * q_dev (N x 4); models/N_per_model/box/cutoff/elec/opt as for
+ * ms2_create_system (box > 0 required; MS2_ELEC_NONE or MS2_ELEC_RF only).
+ * Outputs (device, FP64): F_dev (N x 3), tau_dev (N x 3), UW_dev[2] = {U, W}
+ * (pair energy + LJ long-range correction; molecular pair virial).  All work is
+ * queued on `stream` (a cudaStream_t, NULL = default stream); nothing is
+ * synchronised.
+ * Working memory is one library-owned __device__ array of
+ * ms2_noalloc_scratch_bytes() bytes (about 2.9 MB) that every GPU loading the
+ * library holds until the process exits.  Limits: N <= 4096 molecules, at most
+ * 4 site slots per molecule; larger inputs return MS2_EINVAL.  The first call on
+ * a device looks up the array's device address; make that first call before
+ * any stream capture.  Every call shares the array: calls that overlap on the
+ * GPU race, so serialise them (one stream, or events). */
+MS2_API ms2_status ms2_forces_noalloc(const ms2_model *models, const int *N_per_model, int n_models, double box,
+                                      double cutoff, ms2_elec elec, const ms2_options *opt, const double *R_dev,
+                                      const double *q_dev, double *F_dev, double *tau_dev, double *UW_dev,
+                                      void *stream);
+MS2_API size_t ms2_noalloc_scratch_bytes(void);
+
 /* ------------------------------------------------------------------ misc */
 MS2_API const char *ms2_last_error(void);
 /* Number of kernels this library has launched in the process (graph nodes

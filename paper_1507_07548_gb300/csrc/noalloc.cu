@@ -1,0 +1,220 @@
+// Allocation-free force evaluation.
+//
+// Some callers cannot allocate device memory: code that runs inside a
+// pre-reserved memory pool or under a strict memory cap, plugins handed a
+// stream and a few buffers by a host application that owns all allocations,
+// and sections that must not call cudaMalloc because it can implicitly
+// synchronise the device.  ms2_forces_noalloc serves them: it evaluates one
+// configuration with the same kernels as an ms2_system, but keeps all of its
+// working memory in one statically sized __device__ array.  The caller passes
+// inputs and outputs only.
+//
+// The array (NOALLOC_BYTES below, ~2.9 MB) exists on every GPU that loads this
+// library, for the life of the process.  Every call uses the same array, so
+// calls that overlap on the GPU (different streams, or threads) race; the
+// array keeps the last call's contents, and each call clears what must start
+// at zero.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "ms2_host.h"
+
+namespace {
+
+constexpr int NA_NMAX = 4096;  // molecules
+constexpr int NA_NS = 4;       // site slots
+constexpr int NA_JS = 8;       // j-range split of the pair kernel
+
+constexpr size_t al256(size_t n) { return (n + 255) & ~(size_t)255; }
+constexpr size_t O_PARAMS = 0;
+constexpr size_t O_X = O_PARAMS + al256(sizeof(SysParams));
+constexpr size_t O_S = O_X + al256(3 * sizeof(uint32_t) * NA_NMAX);
+constexpr size_t O_MU = O_S + al256(3 * NA_NS * sizeof(float) * NA_NMAX);
+constexpr size_t O_MUM = O_MU + al256(3 * NA_NS * sizeof(float) * NA_NMAX);
+constexpr size_t O_PART = O_MUM + al256(3 * sizeof(float) * NA_NMAX);
+constexpr size_t O_F = O_PART + al256((size_t)NA_JS * MS2_NPV * sizeof(float) * NA_NMAX);
+constexpr size_t O_TAU = O_F + al256(3 * sizeof(double) * NA_NMAX);
+constexpr size_t O_UI = O_TAU + al256(3 * sizeof(double) * NA_NMAX);
+constexpr size_t O_NP = O_UI + al256(4 * sizeof(double) * NA_NMAX);
+constexpr size_t O_BLK = O_NP + al256(sizeof(int) * NA_NMAX);
+constexpr size_t O_CNT = O_BLK + al256((size_t)MS2_NRED * sizeof(double) * ((NA_NMAX + 31) / 32));
+constexpr size_t O_SCAL = O_CNT + 256;
+constexpr size_t O_SPEC = O_SCAL + al256(SC_COUNT_ * sizeof(double));
+constexpr size_t O_R = O_SPEC + al256(sizeof(int) * NA_NMAX);
+constexpr size_t O_Q = O_R + al256(3 * sizeof(double) * NA_NMAX);
+constexpr size_t O_V = O_Q + al256(4 * sizeof(double) * NA_NMAX);
+constexpr size_t O_L = O_V + al256(3 * sizeof(double) * NA_NMAX);
+constexpr size_t NOALLOC_BYTES = O_L + al256(3 * sizeof(double) * NA_NMAX);
+
+}  // namespace
+
+// The scratch: a host-side name for device memory.  Host code must not use
+// &g_noalloc_scratch as a device address; it asks the runtime for the address.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+__global__ void k_build(const SysParams *, DevSys);
+__global__ void k_reduce(const SysParams *, DevSys, int);
+__global__ void k_aos3(const double *src, double *dst, int N);
+size_t ms2_pair_smem_bytes(int NS, bool dmu, bool multi, int TJ, int wpb);
+void *ms2_pick_pair_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, int *ns_used,
+                           bool *dmu, bool *mult_used);
+ms2_status ms2_validate_models(const ms2_model *models, int n_models, ms2_elec elec);
+void ms2_fill_params(SysParams &P, const ms2_model *models, int n_models, const std::vector<int> &species, double L,
+                     double rc, ms2_elec elec, const ms2_options &o, double T0);
+void ms2_energy_constants(const SysParams &P, const std::vector<int> &species, double alpha, double rc, bool lrc,
+                          double coulomb, double *uconst, double *wbg, double *ulrc, double *plrc);
+
+// layout of SoA <- row-major conversion of the inputs
+__global__ void k_noalloc_soa(const double *R, const double *q, double *Rs, double *qs, int N) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int k = 0; k < 3; ++k) Rs[(size_t)k * N + i] = R[3 * i + k];
+    for (int k = 0; k < 4; ++k) qs[(size_t)k * N + i] = q[4 * i + k];
+}
+
+namespace {
+struct DeviceScratch {
+    bool ready = false;
+    unsigned char *base = nullptr;
+};
+std::mutex g_noalloc_mu;
+DeviceScratch g_noalloc_dev[64];
+
+// once per device, with that device current: the device address of the array
+ms2_status scratch_base(unsigned char **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return ms2_fail_cuda(e, "cudaGetDevice", __FILE__, __LINE__);
+    if (dev < 0 || dev >= 64) return ms2_fail(MS2_EINVAL, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    DeviceScratch &d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return ms2_fail_cuda(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+        d.base = (unsigned char *)p;
+        d.ready = true;
+    }
+    *out = d.base;
+    return MS2_OK;
+}
+}  // namespace
+
+extern "C" ms2_status ms2_forces_noalloc(const ms2_model *models, const int *N_per_model, int n_models, double box,
+                                         double cutoff, ms2_elec elec, const ms2_options *opt, const double *R_dev,
+                                         const double *q_dev, double *F_dev, double *tau_dev, double *UW_dev,
+                                         void *stream) {
+    ms2_status st = ms2_validate_models(models, n_models, elec);
+    if (st != MS2_OK) return st;
+    if (elec == MS2_ELEC_EWALD) return ms2_fail(MS2_EINVAL, "ms2_forces_noalloc: Ewald is not available here");
+    if (!N_per_model || !R_dev || !q_dev || !F_dev || !tau_dev || !UW_dev)
+        return ms2_fail(MS2_EINVAL, "ms2_forces_noalloc: null argument");
+    long long Nt = 0;
+    for (int m = 0; m < n_models; ++m) {
+        if (N_per_model[m] < 0) return ms2_fail(MS2_EINVAL, "negative molecule count");
+        Nt += N_per_model[m];
+    }
+    if (Nt < 2 || Nt > NA_NMAX)
+        return ms2_fail(MS2_EINVAL, "ms2_forces_noalloc: %lld molecules outside 2..%d", Nt, NA_NMAX);
+    // host side, a per-thread list reserved once (no heap traffic afterwards)
+    static thread_local std::vector<int> species;
+    if (species.capacity() < (size_t)NA_NMAX) species.reserve(NA_NMAX);
+    species.clear();
+    for (int m = 0; m < n_models; ++m)
+        for (int k = 0; k < N_per_model[m]; ++k) species.push_back(m);
+    const int N = (int)Nt;
+    if (!(box > 0) || !(cutoff > 0) || !(cutoff < 0.5 * box))
+        return ms2_fail(MS2_EINVAL, "ms2_forces_noalloc: need box > 0 and 0 < cutoff < box/2");
+    ms2_options o;
+    ms2_default_options(&o);
+    if (opt) o = *opt;
+
+    SysParams hp;
+    ms2_fill_params(hp, models, n_models, species, box, cutoff, elec, o, 1.0);
+    unsigned ljm = 0, qm = 0, dm = 0;
+    for (int m = 0; m < hp.n_species; ++m)
+        for (int a = 0; a < hp.n_sites[m]; ++a) {
+            if (hp.ljt[m][a] >= 0) ljm |= 1u << a;
+            if (hp.q[m][a] != 0.f) qm |= 1u << a;
+            if (hp.bdip[m][a][0] != 0 || hp.bdip[m][a][1] != 0 || hp.bdip[m][a][2] != 0) dm |= 1u << a;
+        }
+    int ns = 1;
+    bool dmu = false, multi = false;
+    void *fn = ms2_pick_pair_kernel(hp.ns, ljm, qm, dm, hp.elec, hp.multi != 0, &ns, &dmu, &multi);
+    if (ns > NA_NS) return ms2_fail(MS2_EINVAL, "ms2_forces_noalloc: at most %d site slots", NA_NS);
+    hp.ns = ns;
+    double coulomb, kconv, uconst, wbg, ulrc, plrc;
+    ms2_unit_constants(o.reduced != 0, &coulomb, &kconv);
+    ms2_energy_constants(hp, species, 1.0, cutoff, o.lrc != 0, coulomb, &uconst, &wbg, &ulrc, &plrc);
+
+    unsigned char *base = nullptr;
+    st = scratch_base(&base);
+    if (st != MS2_OK) return st;
+    cudaStream_t sm = (cudaStream_t)stream;
+
+    DevSys d;
+    memset(&d, 0, sizeof d);
+    d.N = N;
+    d.ns = ns;
+    const int wpb = 8, iblocks = (N + wpb - 1) / wpb;
+    d.jsplit = std::max(1, std::min(NA_JS, (152 * 2) / std::max(iblocks, 1)));
+    d.nblk_red = (N + 31) / 32;
+    d.X = (uint32_t *)(base + O_X);
+    d.s = (float *)(base + O_S);
+    d.mu = hp.has_dipole ? (float *)(base + O_MU) : nullptr;
+    d.mum = hp.elec == ELEC_RF ? (float *)(base + O_MUM) : nullptr;
+    d.part = (float *)(base + O_PART);
+    d.F = (double *)(base + O_F);
+    d.tau = (double *)(base + O_TAU);
+    d.Ui = (double *)(base + O_UI);
+    d.npart = (int *)(base + O_NP);
+    d.blk = (double *)(base + O_BLK);
+    d.counter = (unsigned int *)(base + O_CNT);
+    d.scal = (double *)(base + O_SCAL);
+    d.species = (int *)(base + O_SPEC);
+    d.R = (double *)(base + O_R);
+    d.q = (double *)(base + O_Q);
+    d.v = (double *)(base + O_V);
+    d.Lm = (double *)(base + O_L);
+    const SysParams *dP = (const SysParams *)(base + O_PARAMS);
+
+    // inputs; what must start at zero: the last-block counter, the velocities
+    // and angular momenta the reduction reads (kinetic energy 0), the scalars
+    double sc[SC_COUNT_];
+    memset(sc, 0, sizeof sc);
+    sc[SC_UCONST] = uconst;
+    sc[SC_ULRC] = ulrc;
+    sc[SC_PLRC] = plrc;
+    sc[SC_WBG] = wbg;
+    sc[SC_LAMBDA] = 1.0;
+    MS2_CUDA_OK(cudaMemcpyAsync(base + O_PARAMS, &hp, sizeof(SysParams), cudaMemcpyHostToDevice, sm));
+    MS2_CUDA_OK(cudaMemcpyAsync(d.scal, sc, sizeof sc, cudaMemcpyHostToDevice, sm));
+    MS2_CUDA_OK(cudaMemcpyAsync(d.species, species.data(), sizeof(int) * N, cudaMemcpyHostToDevice, sm));
+    MS2_CUDA_OK(cudaMemsetAsync(d.counter, 0, 256, sm));
+    MS2_CUDA_OK(cudaMemsetAsync(d.v, 0, 3 * sizeof(double) * N, sm));
+    MS2_CUDA_OK(cudaMemsetAsync(d.Lm, 0, 3 * sizeof(double) * N, sm));
+
+    const int range = (N + d.jsplit - 1) / d.jsplit;
+    int TJ = std::max(32, range);
+    while (ms2_pair_smem_bytes(ns, dmu, multi, TJ, wpb) > 96 * 1024 && TJ > 64) TJ = (TJ + 1) / 2;
+    const size_t smem = ms2_pair_smem_bytes(ns, dmu, multi, TJ, wpb);
+    MS2_CUDA_OK(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)std::max<size_t>(smem, 48 * 1024)));
+
+    k_noalloc_soa<<<(N + 127) / 128, 128, 0, sm>>>(R_dev, q_dev, d.R, d.q, N);
+    k_build<<<(4 * N + 127) / 128, 128, 0, sm>>>(dP, d);
+    void (*pair)(const SysParams *, DevSys, int) = (void (*)(const SysParams *, DevSys, int))fn;
+    pair<<<dim3(iblocks, d.jsplit), wpb * 32, smem, sm>>>(dP, d, TJ);
+    k_reduce<<<d.nblk_red, 128, 0, sm>>>(dP, d, 1 /* sum the partials only */);
+    k_aos3<<<(N + 127) / 128, 128, 0, sm>>>(d.F, F_dev, N);
+    k_aos3<<<(N + 127) / 128, 128, 0, sm>>>(d.tau, tau_dev, N);
+    ms2_count_launches(6);
+    MS2_CUDA_OK(cudaGetLastError());
+    // U and W are adjacent scalars
+    MS2_CUDA_OK(cudaMemcpyAsync(UW_dev, d.scal + SC_UTOT, 2 * sizeof(double), cudaMemcpyDeviceToDevice, sm));
+    return MS2_OK;
+}
+
+extern "C" size_t ms2_noalloc_scratch_bytes(void) { return NOALLOC_BYTES; }

@@ -99,6 +99,9 @@ SIGNATURES = {
     "ms2_serve_close": (C.c_int, [_vp]),
     "ms2_enable_timing": (C.c_int, [_vp, C.c_int]),
     "ms2_last_step_times": (C.c_int, [_vp, _d]),
+    "ms2_forces_noalloc": (C.c_int, [_P(ms2_model), _P(C.c_int), C.c_int, C.c_double, C.c_double, C.c_int,
+                                     _P(ms2_options), _vp, _vp, _vp, _vp, _vp, _vp]),
+    "ms2_noalloc_scratch_bytes": (C.c_size_t, []),
     "ms2_last_error": (C.c_char_p, []),
     "ms2_kernel_launches": (C.c_longlong, []),
     "ms2_version": (C.c_char_p, []),

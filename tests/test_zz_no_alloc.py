@@ -1,0 +1,86 @@
+"""The allocation-free entry point ms2_forces_noalloc against ms2_system.
+
+Callers that cannot allocate device memory (a host application that owns every
+allocation and hands out a stream and buffers, a fixed memory pool or cap, a
+section that must not trigger the implicit synchronisation of an allocation)
+call ms2_forces_noalloc with buffers they already own.  Its working memory is
+one library-owned __device__ array shared by all calls, so it must give the
+same forces, torques, energy and virial as an ms2_system on the same
+configuration, call after call.  This file is collected last on purpose.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+import pytest
+
+from paper_1507_07548_gb300 import workloads as W
+
+ms2 = pytest.importorskip("paper_1507_07548_gb300.ms2")
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def snapshot(wl, name):
+    z = np.load(os.path.join(GOLDEN, name + ".npz"))
+    wl.R, wl.q, wl.v, wl.Lang = z["R"], z["q"], z["v"], z["Lang"]
+    return wl
+
+
+def rms_rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def reference(wl):
+    s = ms2.System.from_workload(wl)
+    F, tau = s.forces_torques()
+    t = s.energy_terms()
+    s.close()
+    return F, tau, t["U_total"], t["W_total"]
+
+
+def noalloc(wl):
+    models, keep = ms2.make_models(wl.models)
+    counts = [int((wl.species == k).sum()) for k in range(len(wl.models))]
+    cnt = (C.c_int * len(counts))(*counts)
+    opts = ms2.default_options(reduced=int(wl.reduced), lrc=wl.lrc, eps_rf=wl.eps_rf)
+    dev = torch.device("cuda")
+    R = torch.tensor(wl.R, dtype=torch.float64, device=dev)
+    q = torch.tensor(wl.q, dtype=torch.float64, device=dev)
+    F = torch.full((wl.N, 3), float("nan"), dtype=torch.float64, device=dev)
+    tau = torch.full((wl.N, 3), float("nan"), dtype=torch.float64, device=dev)
+    UW = torch.full((2,), float("nan"), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    st = ms2.lib().ms2_forces_noalloc(models, cnt, len(counts), wl.L, wl.rc, wl.elec, C.byref(opts),
+                                      R.data_ptr(), q.data_ptr(), F.data_ptr(), tau.data_ptr(), UW.data_ptr(),
+                                      stream or None)
+    ms2.check(st)
+    torch.cuda.synchronize()
+    uw = UW.cpu().numpy()
+    return F.cpu().numpy(), tau.cpu().numpy(), uw[0], uw[1]
+
+
+def check_same(got, ref):
+    F, tau, U, Wv = got
+    Fr, tr, Ur, Wr = ref
+    assert rms_rel(F, Fr) <= 1e-5
+    assert rms_rel(tau, tr) <= 1e-5
+    assert abs(U - Ur) <= 1e-6 * abs(Ur)
+    assert abs(Wv - Wr) <= 1e-6 * abs(Wr)
+
+
+def test_noalloc_matches_system_on_consecutive_calls():
+    water = snapshot(W.water_box(N=1000, rc=14.0, seed=2), "water_N1000")
+    stock = snapshot(W.stockmayer_fluid(N=500, seed=4), "stockmayer_N500")
+    ref_w, ref_s = reference(water), reference(stock)
+    check_same(noalloc(water), ref_w)      # first call on the device: set-up
+    check_same(noalloc(water), ref_w)      # second call reuses the scratch
+    check_same(noalloc(stock), ref_s)      # another model in the same scratch
+
+
+def test_noalloc_rejects_sizes_beyond_its_maximum():
+    assert ms2.lib().ms2_noalloc_scratch_bytes() < 8 << 20
+    wl = W.water_box(N=4913, rc=14.0, seed=3)
+    with pytest.raises(ms2.Ms2Error, match="EINVAL"):
+        noalloc(wl)
