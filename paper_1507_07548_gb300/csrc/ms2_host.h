@@ -62,6 +62,8 @@ struct ms2_system_s {
     // timing events: [0] step start, [1] before pair, [2] after pair, [3] after Ewald, [4] step end
     bool timing = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    size_t mum_bytes() const { return d.mum ? 3 * sizeof(float) * (size_t)N : 0; }
+    size_t mu_bytes() const { return d.mu ? 3 * sizeof(float) * (size_t)ns * N : 0; }
 };
 
 ms2_status ms2_fail(ms2_status st, const char *fmt, ...);

@@ -1,0 +1,392 @@
+// Per-warp pair engine shared by the single-system pair kernel and the batched
+// per-system kernel: one warp owns molecule i, scans a shared-memory tile of
+// candidates j on the integer centre lattice, compacts partners with a ballot
+// into a per-warp queue and evaluates full batches of 32 partners one per lane
+// with all site pairs unrolled (FP32 site math, coefficient products as hi+lo
+// floats, bare Coulomb + molecular-dipole term for the reaction field, the
+// molecular virial in the short-lever form).  See k_pair.cu for the method.
+#pragma once
+#include "ms2_internal.cuh"
+
+namespace pair_engine {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+struct Smem {
+    uint32_t *tX, *tY, *tZ;
+    float *ts, *tmu, *tmd;
+    int *tsp, *queue;
+    float *sq, *sql, *sc6, *sc12, *sc6l, *sc12l;
+    int *sljt;
+};
+
+// tile arrays of TJ molecules, the per-warp queues and the parameter tables
+template <int NS, bool DMU, bool MULTI>
+__device__ __forceinline__ Smem carve(unsigned char *base, int TJ, int wpb) {
+    Smem m;
+    m.tX = (uint32_t *)base;
+    m.tY = m.tX + TJ;
+    m.tZ = m.tY + TJ;
+    m.ts = (float *)(m.tZ + TJ);
+    m.tmu = m.ts + 3 * NS * TJ;
+    m.tmd = m.tmu + (DMU ? 3 * NS * TJ : 0);
+    m.tsp = (int *)(m.tmd + 3 * TJ);
+    m.queue = m.tsp + (MULTI ? TJ : 0);
+    m.sq = (float *)(m.queue + wpb * 64);
+    m.sql = m.sq + MS2_MAXSP * MS2_MAXS;
+    m.sljt = (int *)(m.sql + MS2_MAXSP * MS2_MAXS);
+    m.sc6 = (float *)(m.sljt + MS2_MAXSP * MS2_MAXS);
+    m.sc12 = m.sc6 + MS2_MAXT * MS2_MAXT;
+    m.sc6l = m.sc12 + MS2_MAXT * MS2_MAXT;
+    m.sc12l = m.sc6l + MS2_MAXT * MS2_MAXT;
+    return m;
+}
+
+__host__ __device__ inline size_t smem_bytes(int NS, bool dmu, bool multi, int TJ, int wpb) {
+    size_t n = 3 * sizeof(uint32_t) * TJ + sizeof(float) * 3 * NS * TJ;
+    if (dmu) n += sizeof(float) * 3 * NS * TJ;
+    n += sizeof(float) * 3 * TJ;  // molecular dipoles (reaction field; reserved always)
+    if (multi) n += sizeof(int) * TJ;
+    n += sizeof(int) * wpb * 64;
+    n += 2 * sizeof(float) * MS2_MAXSP * MS2_MAXS + sizeof(int) * MS2_MAXSP * MS2_MAXS;
+    n += 4 * sizeof(float) * MS2_MAXT * MS2_MAXT;
+    return n;
+}
+
+// block-level: multi-species parameter tables into shared memory
+template <bool MULTI>
+__device__ __forceinline__ void load_tables(const SysParams *__restrict__ P, const Smem &sm) {
+    if (!MULTI) return;
+    for (int k = threadIdx.x; k < MS2_MAXSP * MS2_MAXS; k += blockDim.x) {
+        sm.sq[k] = P->q[k / MS2_MAXS][k % MS2_MAXS];
+        sm.sql[k] = P->qlo[k / MS2_MAXS][k % MS2_MAXS];
+        sm.sljt[k] = P->ljt[k / MS2_MAXS][k % MS2_MAXS];
+    }
+    for (int k = threadIdx.x; k < MS2_MAXT * MS2_MAXT; k += blockDim.x) {
+        sm.sc6[k] = P->c6[k / MS2_MAXT][k % MS2_MAXT];
+        sm.sc12[k] = P->c12[k / MS2_MAXT][k % MS2_MAXT];
+        sm.sc6l[k] = P->c6lo[k / MS2_MAXT][k % MS2_MAXT];
+        sm.sc12l[k] = P->c12lo[k / MS2_MAXT][k % MS2_MAXT];
+    }
+}
+
+// block-level: molecules [t0, t0+tn) of S into tile slots [0, tn)
+template <int NS, bool DMU, bool MULTI>
+__device__ __forceinline__ void stage_tile(const Smem &sm, const DevSys &S, int t0, int tn, int TJ, bool rfq) {
+    const int N = S.N;
+    for (int k = threadIdx.x; k < tn; k += blockDim.x) {
+        const int j = t0 + k;
+        sm.tX[k] = S.X[j];
+        sm.tY[k] = S.X[N + j];
+        sm.tZ[k] = S.X[2 * N + j];
+#pragma unroll
+        for (int c = 0; c < 3 * NS; ++c) sm.ts[c * TJ + k] = S.s[c * N + j];
+        if (DMU) {
+#pragma unroll
+            for (int c = 0; c < 3 * NS; ++c) sm.tmu[c * TJ + k] = S.mu[c * N + j];
+        }
+        if (MULTI) sm.tsp[k] = S.species[j];
+        if (rfq) {
+            sm.tmd[k] = S.mum[j];
+            sm.tmd[TJ + k] = S.mum[N + j];
+            sm.tmd[2 * TJ + k] = S.mum[2 * N + j];
+        }
+    }
+}
+
+// result of one molecule (valid in lane 0): F, tau, U_lj, U_qq, U_dd, W, partners
+struct PairOut {
+    float F[3], T[3], ulj, uqq, udd, w;
+    int np;
+};
+
+// NS: site slots per molecule; LJM/QM/DM: slot bit masks that may carry LJ,
+// charge, dipole; ELEC: ELEC_NONE/RF/EWALD or -1 = read from the parameters;
+// MULTI: several species (per-molecule parameter lookup).
+template <int NS, unsigned LJM, unsigned QM, unsigned DM, int ELEC, bool MULTI>
+struct PairWarp {
+    static constexpr bool DMU = DM != 0;
+    static constexpr bool MOLD = QM != 0 && (ELEC == ELEC_RF || ELEC < 0);  // molecular-dipole RF term
+    int elec;
+    bool rfq;
+    float C, krf, alpha, tasp, l2l, l2l_lo;
+    unsigned long long rc2;
+    // coefficient tables of a single-species system (hi + lo floats: a single
+    // FP32 rounding of C q_a q_b or 4 eps sigma^12 would scale every term of that
+    // site-pair kind the same way and bias the strongly cancelling sums)
+    float hq[NS][NS], hql[NS][NS], hc6[NS][NS], hc12[NS][NS], hc6l[NS][NS], hc12l[NS][NS];
+    // molecule i
+    int i, spi;
+    uint32_t Xi, Yi, Zi;
+    float si[NS][3], mui[NS][3], qih[NS], qil[NS], mdi[3];
+    int ljti[NS];
+    // lane accumulators
+    float fa[NS][3], ea[NS][3], ulj, uqq, udd, w, erf_[3];
+    int np;
+
+    __device__ __forceinline__ void setup(const SysParams *__restrict__ P) {
+        elec = ELEC >= 0 ? ELEC : P->elec;
+        rfq = MOLD && P->elec == ELEC_RF;
+        C = P->coulomb;
+        krf = P->krf;
+        alpha = P->alpha;
+        tasp = P->two_alpha_sqrtpi;
+        l2l = P->lat_to_len;
+        l2l_lo = P->lat_to_len_lo;
+        rc2 = P->rc2;
+        if (!MULTI) {
+#pragma unroll
+            for (int a = 0; a < NS; ++a)
+#pragma unroll
+                for (int b = 0; b < NS; ++b) {
+                    const float qa = P->cq[0][a], qal = P->cqlo[0][a];
+                    const float qb = P->q[0][b], qbl = P->qlo[0][b];
+                    hq[a][b] = qa * qb;
+                    hql[a][b] = fmaf(qa, qb, -hq[a][b]) + fmaf(qa, qbl, qal * qb);
+                    const int ta = P->ljt[0][a], tb = P->ljt[0][b];
+                    const bool on = ta >= 0 && tb >= 0;
+                    const int ia = on ? ta : 0, ib = on ? tb : 0;
+                    hc6[a][b] = on ? P->c6[ia][ib] : 0.f;
+                    hc12[a][b] = on ? P->c12[ia][ib] : 0.f;
+                    hc6l[a][b] = on ? P->c6lo[ia][ib] : 0.f;
+                    hc12l[a][b] = on ? P->c12lo[ia][ib] : 0.f;
+                }
+        }
+    }
+
+    // molecule i of S (all lanes of the warp)
+    __device__ __forceinline__ void begin(const SysParams *__restrict__ P, const DevSys &S, int i_) {
+        const int N = S.N;
+        i = i_;
+        Xi = S.X[i];
+        Yi = S.X[N + i];
+        Zi = S.X[2 * N + i];
+#pragma unroll
+        for (int a = 0; a < NS; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                si[a][k] = S.s[(k * NS + a) * N + i];
+                mui[a][k] = DMU && ((DM >> a) & 1) ? S.mu[(k * NS + a) * N + i] : 0.f;
+            }
+        spi = MULTI ? S.species[i] : 0;
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            ljti[a] = P->ljt[spi][a];
+            qih[a] = P->cq[spi][a];  // (C q_a) as hi + lo, from FP64
+            qil[a] = P->cqlo[spi][a];
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) mdi[k] = (MOLD && rfq) ? S.mum[k * N + i] : 0.f;
+#pragma unroll
+        for (int a = 0; a < NS; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) fa[a][k] = ea[a][k] = 0.f;
+        ulj = uqq = udd = w = 0.f;
+        erf_[0] = erf_[1] = erf_[2] = 0.f;
+        np = 0;
+    }
+
+    // one partner, tile-local index jl, into this lane's accumulators
+    __device__ __forceinline__ void interact(const Smem &sm, int TJ, int jl) {
+    const int dxi = (int)(sm.tX[jl] - Xi), dyi = (int)(sm.tY[jl] - Yi), dzi = (int)(sm.tZ[jl] - Zi);
+    // lattice difference -> length with the scale split in two floats, so the
+    // FP32 rounding of L/2^32 does not scale every displacement the same way
+    const float fxi = (float)dxi, fyi = (float)dyi, fzi = (float)dzi;
+    const float dx = fmaf(fxi, l2l, fxi * l2l_lo), dy = fmaf(fyi, l2l, fyi * l2l_lo),
+                dz = fmaf(fzi, l2l, fzi * l2l_lo);
+    const int spj = MULTI ? sm.tsp[jl] : 0;
+    float pj[NS][3], muj[NS][3];
+#pragma unroll
+    for (int b = 0; b < NS; ++b) {
+        pj[b][0] = dx + sm.ts[(0 * NS + b) * TJ + jl];
+        pj[b][1] = dy + sm.ts[(1 * NS + b) * TJ + jl];
+        pj[b][2] = dz + sm.ts[(2 * NS + b) * TJ + jl];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            muj[b][k] = DMU && ((DM >> b) & 1) ? sm.tmu[(k * NS + b) * TJ + jl] : 0.f;
+    }
+    // Molecular virial -d.F_ij, written with d = r_ab - (s_jb - s_ia) as
+    //   -sum_ab f_ab.r_ab + sum_b s_jb.G_b - sum_a s_ia.A_a,
+    //   G_b = sum_a f_ab, A_a = sum_b f_ab   (per pair),
+    // so that no FP32 force sum is multiplied by the long lever arm d and no
+    // long accumulation of site forces meets a lever arm at all.
+    float Gb[NS][3], Aa[NS][3];
+#pragma unroll
+    for (int b = 0; b < NS; ++b) Gb[b][0] = Gb[b][1] = Gb[b][2] = Aa[b][0] = Aa[b][1] = Aa[b][2] = 0.f;
+    float wsite = 0.f;
+#pragma unroll
+    for (int a = 0; a < NS; ++a) {
+#pragma unroll
+        for (int b = 0; b < NS; ++b) {
+            const bool mlj = (LJM >> a) & (LJM >> b) & 1u;
+            const bool mq = (QM >> a) & (QM >> b) & 1u;
+            const bool md = (DM >> a) & (DM >> b) & 1u;
+            if (!(mlj || (mq && elec != ELEC_NONE) || (md && elec != ELEC_NONE))) continue;
+            const float rx = pj[b][0] - si[a][0], ry = pj[b][1] - si[a][1], rz = pj[b][2] - si[a][2];
+            float r2 = rx * rx + ry * ry + rz * rz;
+            if (MULTI) r2 = fmaxf(r2, 1e-12f);
+            // rsqrt approximation + one Newton step: unbiased to ~1 ulp
+            float rinv = rsqrtf(r2);
+            rinv = fmaf(rinv, fmaf(-0.5f * r2 * rinv, rinv, 0.5f), rinv);
+            const float rinv2 = rinv * rinv;
+            float g = 0.f;
+            if (mlj) {
+                float c6, c12, c6l, c12l;
+                if (MULTI) {
+                    const int ta = ljti[a], tb = sm.sljt[spj * MS2_MAXS + b];
+                    const bool on = ta >= 0 && tb >= 0;
+                    const int idx = on ? ta * MS2_MAXT + tb : 0;
+                    c6 = on ? sm.sc6[idx] : 0.f;
+                    c12 = on ? sm.sc12[idx] : 0.f;
+                    c6l = on ? sm.sc6l[idx] : 0.f;
+                    c12l = on ? sm.sc12l[idx] : 0.f;
+                } else {
+                    c6 = hc6[a][b];
+                    c12 = hc12[a][b];
+                    c6l = hc6l[a][b];
+                    c12l = hc12l[a][b];
+                }
+                const float r6 = rinv2 * rinv2 * rinv2, r12 = r6 * r6;
+                const float t6 = fmaf(c6, r6, c6l * r6), t12 = fmaf(c12, r12, c12l * r12);
+                ulj += t12 - t6;
+                g += (6.f * t6 - 12.f * t12) * rinv2;
+            }
+            if (mq && elec != ELEC_NONE) {
+                float cqq, cql;
+                if (MULTI) {
+                    const float qb = sm.sq[spj * MS2_MAXS + b], qbl = sm.sql[spj * MS2_MAXS + b];
+                    cqq = qih[a] * qb;
+                    cql = fmaf(qih[a], qb, -cqq) + fmaf(qih[a], qbl, qil[a] * qb);
+                } else {
+                    cqq = hq[a][b];
+                    cql = hql[a][b];
+                }
+                float bu, bg;  // energy and force brackets
+                if (elec == ELEC_RF) {  // bare Coulomb; the RF part is a molecular term
+                    bu = rinv;
+                    bg = -rinv * rinv2;
+                } else {
+                    const float ar = alpha * r2 * rinv;
+                    const float ec = erfcf(ar), ex = expf(-ar * ar);
+                    bu = ec * rinv;
+                    bg = -(ec * rinv + tasp * ex) * rinv2;
+                }
+                uqq += fmaf(cqq, bu, cql * bu);
+                g += fmaf(cqq, bg, cql * bg);
+            }
+            if (md && elec != ELEC_NONE) {
+                const float rinv3 = rinv * rinv2, rinv5 = rinv3 * rinv2, rinv7 = rinv5 * rinv2;
+                const float mab = mui[a][0] * muj[b][0] + mui[a][1] * muj[b][1] + mui[a][2] * muj[b][2];
+                const float mar = mui[a][0] * rx + mui[a][1] * ry + mui[a][2] * rz;
+                const float mbr = muj[b][0] * rx + muj[b][1] * ry + muj[b][2] * rz;
+                const float kd = elec == ELEC_RF ? 2.f * krf : 0.f;
+                udd += C * (mab * rinv3 - 3.f * mar * mbr * rinv5 - kd * mab);
+                const float cr = C * (15.f * mar * mbr * rinv7 - 3.f * mab * rinv5);
+                const float cma = -3.f * C * mbr * rinv5, cmb = -3.f * C * mar * rinv5;
+                const float fx = cr * rx + cma * mui[a][0] + cmb * muj[b][0];
+                const float fy = cr * ry + cma * mui[a][1] + cmb * muj[b][1];
+                const float fz = cr * rz + cma * mui[a][2] + cmb * muj[b][2];
+                Aa[a][0] += fx; Aa[a][1] += fy; Aa[a][2] += fz;
+                Gb[b][0] += fx; Gb[b][1] += fy; Gb[b][2] += fz;
+                wsite -= fx * rx + fy * ry + fz * rz;
+                const float ce = 3.f * C * mbr * rinv5, cm = -C * (rinv3 - kd);
+                ea[a][0] += ce * rx + cm * muj[b][0];
+                ea[a][1] += ce * ry + cm * muj[b][1];
+                ea[a][2] += ce * rz + cm * muj[b][2];
+            }
+            Aa[a][0] = fmaf(g, rx, Aa[a][0]); Aa[a][1] = fmaf(g, ry, Aa[a][1]); Aa[a][2] = fmaf(g, rz, Aa[a][2]);
+            Gb[b][0] = fmaf(g, rx, Gb[b][0]); Gb[b][1] = fmaf(g, ry, Gb[b][1]); Gb[b][2] = fmaf(g, rz, Gb[b][2]);
+            wsite = fmaf(-g, r2, wsite);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < NS; ++b)
+        wsite += sm.ts[(0 * NS + b) * TJ + jl] * Gb[b][0] + sm.ts[(1 * NS + b) * TJ + jl] * Gb[b][1] +
+                 sm.ts[(2 * NS + b) * TJ + jl] * Gb[b][2];
+#pragma unroll
+    for (int a = 0; a < NS; ++a) {
+        wsite -= si[a][0] * Aa[a][0] + si[a][1] * Aa[a][1] + si[a][2] * Aa[a][2];
+        fa[a][0] += Aa[a][0]; fa[a][1] += Aa[a][1]; fa[a][2] += Aa[a][2];
+    }
+    w += wsite;
+    if (MOLD && rfq) {
+        erf_[0] += sm.tmd[jl];
+        erf_[1] += sm.tmd[TJ + jl];
+        erf_[2] += sm.tmd[2 * TJ + jl];
+    }
+    ++np;
+    }
+
+    // scan tile slots [0, tn) (global index of slot 0: t0), partners in batches of 32
+    __device__ __forceinline__ void scan(const Smem &sm, int TJ, int t0, int tn, int *wq, int lane) {
+        int qn = 0;
+        for (int base = 0; base < tn; base += 32) {
+            const int jl = base + lane;
+            bool partner = false;
+            if (jl < tn && t0 + jl != i) {
+                const int dx = (int)(sm.tX[jl] - Xi), dy = (int)(sm.tY[jl] - Yi), dz = (int)(sm.tZ[jl] - Zi);
+                partner = lattice_d2(dx, dy, dz) < rc2;
+            }
+            const unsigned m = __ballot_sync(FULL, partner);
+            if (partner) wq[qn + __popc(m & ((1u << lane) - 1u))] = jl;
+            qn += __popc(m);
+            __syncwarp();
+            if (qn >= 32) {
+                interact(sm, TJ, wq[lane]);
+                __syncwarp();
+                qn -= 32;
+                if (lane < qn) wq[lane] = wq[32 + lane];
+                __syncwarp();
+            }
+        }
+        if (qn > 0) {
+            if (lane < qn) interact(sm, TJ, wq[lane]);
+            __syncwarp();
+        }
+    }
+
+    // fixed-tree warp reduction; the result is valid in lane 0
+    __device__ __forceinline__ PairOut finish(int lane) {
+#pragma unroll
+        for (int a = 0; a < NS; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                fa[a][k] = warp_sum(fa[a][k]);
+                if (DMU && ((DM >> a) & 1)) ea[a][k] = warp_sum(ea[a][k]);
+            }
+        if (MOLD && rfq)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) erf_[k] = warp_sum(erf_[k]);
+        PairOut o;
+        o.ulj = warp_sum(ulj);
+        o.uqq = warp_sum(uqq);
+        o.udd = warp_sum(udd);
+        o.w = warp_sum(w);
+        o.np = warp_sum(np);
+        o.F[0] = o.F[1] = o.F[2] = o.T[0] = o.T[1] = o.T[2] = 0.f;
+        if (lane == 0) {
+#pragma unroll
+            for (int a = 0; a < NS; ++a) {
+                o.F[0] += fa[a][0]; o.F[1] += fa[a][1]; o.F[2] += fa[a][2];
+                o.T[0] += si[a][1] * fa[a][2] - si[a][2] * fa[a][1];
+                o.T[1] += si[a][2] * fa[a][0] - si[a][0] * fa[a][2];
+                o.T[2] += si[a][0] * fa[a][1] - si[a][1] * fa[a][0];
+                if (DMU && ((DM >> a) & 1)) {
+                    o.T[0] += mui[a][1] * ea[a][2] - mui[a][2] * ea[a][1];
+                    o.T[1] += mui[a][2] * ea[a][0] - mui[a][0] * ea[a][2];
+                    o.T[2] += mui[a][0] * ea[a][1] - mui[a][1] * ea[a][0];
+                }
+            }
+            if (MOLD && rfq) {  // -2 C k_RF mu_i.mu_j and its torque 2 C k_RF mu_i x mu_j
+                const float c2 = 2.f * C * krf;
+                o.uqq -= c2 * (mdi[0] * erf_[0] + mdi[1] * erf_[1] + mdi[2] * erf_[2]);
+                o.T[0] += c2 * (mdi[1] * erf_[2] - mdi[2] * erf_[1]);
+                o.T[1] += c2 * (mdi[2] * erf_[0] - mdi[0] * erf_[2]);
+                o.T[2] += c2 * (mdi[0] * erf_[1] - mdi[1] * erf_[0]);
+            }
+        }
+        return o;
+    }
+};
+
+}  // namespace pair_engine

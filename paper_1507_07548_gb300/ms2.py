@@ -310,5 +310,30 @@ class System:
         check(lib().ms2_reset_averages(self.h))
 
 
+class Batch:
+    """Many systems advanced together by the persistent batch kernels."""
+
+    def __init__(self, systems):
+        self.systems = list(systems)
+        arr = (_vp * len(self.systems))(*[x.h for x in self.systems])
+        h = _vp()
+        check(lib().ms2_batch_create(arr, len(self.systems), C.byref(h)))
+        self.h = h
+
+    def step(self, n):
+        check(lib().ms2_batch_step(self.h, n))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ms2_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def kernel_launches():
     return lib().ms2_kernel_launches()

@@ -1,0 +1,119 @@
+"""Batched systems (ms2_batch_*): one block per system for a whole chunk of steps.
+
+Checks: one batched step against the FP64 oracle (same tolerances as the
+single-system path), bit-identical results for a system alone and inside a
+mixed batch, RDF/average bookkeeping, and rejection of systems the batch kernel
+does not take.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_1507_07548_gb300 import workloads as W
+
+ms2 = pytest.importorskip("paper_1507_07548_gb300.ms2")
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def snapshot(wl, name):
+    z = np.load(os.path.join(GOLDEN, name + ".npz"))
+    wl.R, wl.q, wl.v, wl.Lang = z["R"], z["q"], z["v"], z["Lang"]
+    return wl
+
+
+def water():
+    return snapshot(W.water_box(N=216, rc=9.0, seed=9), "water_N216")
+
+
+def stock():
+    return snapshot(W.stockmayer_fluid(N=500, seed=4), "stockmayer_N500")
+
+
+def ljf():
+    wl = W.lj_fluid(N=500, rho=0.8, rc=3.5, seed=11)
+    wl.R = wl.R + np.random.default_rng(4).normal(0, 0.03, wl.R.shape)
+    wl.integrator = 1
+    return wl
+
+
+def rms_rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("make", [water, stock, ljf], ids=["water", "stockmayer", "lj"])
+def test_one_batched_step_matches_oracle(make):
+    wl = make()
+    s = ms2.System.from_workload(wl)
+    b = ms2.Batch([s])
+    b.step(1)
+    R, q, v, L, st = s.get_state()
+    assert st == 1
+    o = Oracle.from_workload(wl)
+    Ro, qo, vo, Lo, th, _ = o.run_leapfrog(wl.R, wl.q, wl.v, wl.Lang, wl.dt, 1, T0=wl.T)
+    dR = Ro - wl.R
+    assert np.abs((R - wl.R) - dR).max() <= 1e-6 * np.abs(dR).max()
+    assert rms_rel(v, vo) <= 1e-6
+    if np.linalg.norm(Lo) > 0:
+        sgn = np.sign((q * qo).sum(1))[:, None]
+        assert np.abs(q * sgn - qo).max() <= 1e-7
+        assert rms_rel(L, Lo) <= 1e-5
+    U, Wv, T, P = s.energy_virial()
+    assert abs(U - th[0, 0]) <= 1e-6 * abs(th[0, 0])
+    F, tau = s.forces_torques()
+    Fo, To, _ = o.forces(Ro, qo)
+    assert rms_rel(F, Fo) <= 1e-5
+
+
+def test_system_alone_and_in_a_mixed_batch_is_bitwise_identical():
+    alone = ms2.System.from_workload(water())
+    b1 = ms2.Batch([alone])
+    b1.step(30)
+    ref = alone.get_state()[:4]
+    mix = [ms2.System.from_workload(w) for w in (ljf(), water(), stock(), water())]
+    b2 = ms2.Batch(mix)
+    b2.step(30)
+    got = mix[1].get_state()[:4]
+    for a, c in zip(got, ref):
+        assert np.array_equal(a, c)
+    assert alone.energy_virial() == mix[1].energy_virial()
+
+
+def test_batch_matches_single_system_stepping_closely():
+    a = ms2.System.from_workload(water())
+    b = ms2.System.from_workload(water())
+    a.step(20)
+    bb = ms2.Batch([b])
+    bb.step(20)
+    Ra, Rb = a.get_state()[0], b.get_state()[0]
+    assert np.abs(Ra - Rb).max() < 1e-4
+    Ua, Ub = a.energy_virial()[0], b.energy_virial()[0]
+    assert abs(Ua - Ub) <= 1e-4 * abs(Ua)
+
+
+def test_batch_rdf_and_averages_bookkeeping():
+    s = ms2.System.from_workload(water())
+    s.rdf_setup(min(9.0, 0.5 * s.L), 90, every=10)
+    s.reset_averages()
+    b = ms2.Batch([s, ms2.System.from_workload(stock())])
+    b.step(100)
+    c, g, ns = s.rdf()
+    assert ns == 10
+    assert c.sum() > 0
+    tail = g[0, -20:]
+    assert abs(tail.mean() - 1.0) < 0.1
+    av = s.averages()
+    assert av["n"] == 100
+    assert av["T"] == pytest.approx(298.0, rel=1e-3)
+
+
+def test_batch_rejects_ewald_and_verlet_systems():
+    ion = ms2.System.from_workload(W.ionic_solution(n_water=200, n_ion_pairs=4, rc=8.0, seed=5))
+    with pytest.raises(ms2.Ms2Error, match="EINVAL"):
+        ms2.Batch([ion])
+    wl = W.lj_fluid(N=256, rho=0.7, rc=3.5)
+    vv = ms2.System.from_workload(wl)
+    with pytest.raises(ms2.Ms2Error, match="EINVAL"):
+        ms2.Batch([vv])
