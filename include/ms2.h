@@ -202,7 +202,9 @@ MS2_API ms2_status ms2_reset_averages(ms2_system sys);
  * from a longest-first work list when it finishes.  The systems must be
  * reaction-field or non-electrostatic leapfrog systems with at most 4096
  * molecules; tile shapes come from the autotuner cache.  The systems stay
- * usable on their own; the batch runs on the first system's stream. */
+ * usable on their own: the batch runs on a stream of its own, waits for work
+ * already queued on the systems' streams and makes their later work wait for
+ * it.  Destroy a batch before any of its systems. */
 MS2_API ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_batch *out);
 MS2_API ms2_status ms2_batch_step(ms2_batch b, long long n);
 MS2_API ms2_status ms2_batch_destroy(ms2_batch b);

@@ -474,11 +474,21 @@ static ms2_status tune(ms2_batch b) {
     return MS2_OK;
 }
 
+// whether the batch kernels take this system (used by the server)
+bool ms2_batch_accepts(ms2_system s) {
+    if (!s || s->hp.integrator != MS2_INT_LEAPFROG_Q || s->fp64 || s->hp.elec == ELEC_EWALD) return false;
+    const int kind = kind_of(s);
+    if (kind < 0) return false;
+    const int rdf = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
+    if (rdf > RDF_SMEM_MAX) return false;
+    return batch_smem(kind, s->N, 128, rdf) <= 227 * 1024;
+}
+
 extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_batch *out) {
     if (!out || !systems || n < 1) return ms2_fail(MS2_EINVAL, "need n >= 1 systems and an output handle");
     *out = nullptr;
     ms2_batch b = new ms2_batch_s();
-    b->stream = systems[0]->stream;
+    // the batch owns its stream: it must outlive none of the systems' streams
     for (int k = 0; k < n; ++k) {
         ms2_system s = systems[k];
         if (!s) { delete b; return ms2_fail(MS2_EINVAL, "system %d is null", k); }
@@ -505,6 +515,10 @@ extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_bat
     b->htab.resize(n);
     ms2_status st = MS2_OK;
     auto fail = [&](ms2_status s2) { ms2_batch_destroy(b); return s2; };
+    {
+        cudaError_t e0 = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e0 != cudaSuccess) return fail(ms2_fail_cuda(e0, "batch stream", __FILE__, __LINE__));
+    }
     for (int k = 0; k < n; ++k) {
         ms2_system s = b->sys[k];
         BatchEntry &e = b->htab[k];
@@ -573,6 +587,7 @@ extern "C" ms2_status ms2_batch_destroy(ms2_batch b) {
     }
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     b->al.release_all();
+    if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return MS2_OK;
 }

@@ -70,3 +70,4 @@ ms2_status ms2_fail(ms2_status st, const char *fmt, ...);
 ms2_status ms2_fail_cuda(cudaError_t e, const char *what, const char *file, int line);
 void ms2_unit_constants(bool reduced, double *coulomb, double *kconv);
 ms2_status ms2_eval_forces(ms2_system s);
+ms2_status ms2_validate_models(const ms2_model *models, int n_models, ms2_elec elec);

@@ -335,5 +335,54 @@ class Batch:
             pass
 
 
+class Server:
+    """Serving front end: jobs are queued, admitted by memory budget, advanced
+    together in chunks, and retired with averages and RDF (ms2_serve_*)."""
+
+    def __init__(self, budget_bytes, max_slots=256, **opts):
+        self._opts = default_options(**opts)
+        h = _vp()
+        check(lib().ms2_serve_open(budget_bytes, max_slots, C.byref(self._opts), C.byref(h)))
+        self.h = h
+        self._keep = []
+
+    def submit(self, models, counts, T, rho, cutoff, elec, steps, arrival=0.0, seed=1, rdf_bins=0, rdf_every=10):
+        m, keep = make_models(models)
+        cnt = (C.c_int * len(counts))(*[int(c) for c in counts])
+        self._keep.append((m, keep, cnt))
+        j = ms2_job(models=C.cast(m, C.POINTER(ms2_model)), N_per_model=C.cast(cnt, C.POINTER(C.c_int)),
+                    n_models=len(models), T=T, rho=rho, cutoff=cutoff, elec=elec, steps=steps,
+                    arrival_time=arrival, seed=seed, rdf_bins=rdf_bins, rdf_every=rdf_every)
+        jid = C.c_longlong()
+        check(lib().ms2_serve_submit(self.h, C.byref(j), C.byref(jid)))
+        return jid.value
+
+    def poll(self, max_results=64):
+        arr = (ms2_job_result * max_results)()
+        n = C.c_int()
+        check(lib().ms2_serve_poll(self.h, arr, max_results, C.byref(n)))
+        out = []
+        for k in range(n.value):
+            r = arr[k]
+            g = np.array(r.g[:r.n_rows * r.n_bins]).reshape(r.n_rows, r.n_bins) if r.n_bins else None
+            out.append(dict(job_id=r.job_id, status=r.status, U=r.U_avg, U_err=r.U_err, P=r.P_avg, P_err=r.P_err,
+                            T=r.T_avg, t_arrive=r.t_arrive, t_admit=r.t_admit, t_done=r.t_done, g=g))
+        return out
+
+    def drain(self, timeout=600.0):
+        check(lib().ms2_serve_drain(self.h, timeout))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ms2_serve_close(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def kernel_launches():
     return lib().ms2_kernel_launches()
