@@ -176,14 +176,21 @@ def reference_arm(args, rank, world):
 
 
 # ---------------------------------------------------------------- GPU arm
+# kernel sources a stored DRAM-traffic figure describes (it is void once they change)
+TRAFFIC_SOURCES = {"pair_water_rf": ("k_pair.cu", "pair_engine.cuh", "ms2_internal.cuh")}
+
+
 def traffic_record(kernel):
     """DRAM bytes per launch from the committed ncu summary, if it still
     describes the current kernel source (matching source hash)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.txt")
-    src = os.path.join(ROOT, "paper_1507_07548_gb300", "csrc", "k_pair.cu")
+    csrc = os.path.join(ROOT, "paper_1507_07548_gb300", "csrc")
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        hs = hashlib.sha256()
+        for f in TRAFFIC_SOURCES[kernel]:
+            hs.update(open(os.path.join(csrc, f), "rb").read())
+        h = hs.hexdigest()[:16]
         for line in open(path):
             p = line.split()
             if len(p) >= 3 and p[0] == kernel and p[1] == h:
