@@ -100,6 +100,10 @@ typedef struct {
     int quat_iters;           /* sweeps of the implicit quaternion midpoint rule; 0 -> 3 */
     int graph_chunk;          /* steps per captured CUDA graph; 0 -> 50 */
     int fp64;                 /* 1: site-pair arithmetic in FP64 too (point LJ models only) */
+    int fused_step;           /* 1 (default): a chunk of steps runs as one cooperative kernel where the
+                                 system allows it (leapfrog, no Ewald, the whole system fits one SM's
+                                 shared memory); results are bitwise those of the per-phase kernels.
+                                 0: one kernel per phase, replayed as a CUDA graph */
     void *stream;             /* cudaStream_t to use, or NULL */
     void *(*dev_alloc)(size_t bytes, void *ctx);
     void (*dev_free)(void *ptr, void *ctx);
@@ -253,8 +257,20 @@ MS2_API ms2_status ms2_serve_close(ms2_server s);
  * records CUDA events (on the system stream) around its last step and around
  * that step's pair kernel and Ewald kernels.  ms2_last_step_times synchronises
  * and returns, in ms: [0] pair kernel, [1] Ewald reciprocal kernels, [2] the whole
- * last step, [3] that step minus [0] and [1]. */
+ * last step, [3] that step minus [0] and [1].  When the last chunk ran as one
+ * fused kernel (ms2_options.fused_step), [2] is the chunk's time per step,
+ * [0] the pair phase of its last step (device timer) and [1] is 0. */
 MS2_API ms2_status ms2_enable_timing(ms2_system sys, int on);
+/* *fused = 1 if the next chunk of steps runs as the fused cooperative kernel
+ * (ms2_options.fused_step and a system it takes; an RDF histogram too large for
+ * shared memory sends the chunk to the per-phase kernels), else 0. */
+MS2_API ms2_status ms2_step_kernel(ms2_system sys, int *fused);
+/* Diagnostic of the fused step with timing on: device-timer durations (ms) of
+ * the last step of the last chunk: [0] drift and site build, [1] staging, pair
+ * and RDF, [2] reduction units, [3] totals and step record (each up to the end
+ * of its grid barrier), [4] from kernel entry to that last step.  MS2_ESTATE if
+ * timing is off or the last chunk ran as per-phase kernels. */
+MS2_API ms2_status ms2_last_step_phases(ms2_system sys, double out[5]);
 MS2_API ms2_status ms2_last_step_times(ms2_system sys, double out[4]);
 
 /* ------------------------------------------------------- allocation-free */

@@ -348,10 +348,10 @@ static ms2_status sys_alloc(ms2_system s) {
     MS2_CUDA_OK(A((void **)&d.tau, sizeof(double) * 3 * N));
     MS2_CUDA_OK(A((void **)&d.Ui, sizeof(double) * 4 * N));
     MS2_CUDA_OK(A((void **)&d.npart, sizeof(int) * N));
-    d.nblk_red = (N + 31) / 32;  // reduction: one quad of lanes per molecule, 32 molecules per block
+    d.nvb = (N + 7) / 8;  // reduction units: one warp, a quad of lanes per molecule
     MS2_CUDA_OK(A((void **)&d.terms, sizeof(double) * 8));
     if (s->hp.elec == ELEC_EWALD) MS2_CUDA_OK(A((void **)&d.wcorr, sizeof(double) * N));
-    MS2_CUDA_OK(A((void **)&d.blk, sizeof(double) * MS2_NRED * d.nblk_red));
+    MS2_CUDA_OK(A((void **)&d.blk, sizeof(double) * MS2_NRED * d.nvb));
     MS2_CUDA_OK(A((void **)&d.counter, 256));
     MS2_CUDA_OK(A((void **)&d.scal, sizeof(double) * SC_COUNT_));
     MS2_CUDA_OK(A((void **)&d.acc, sizeof(double) * AC_COUNT_));
@@ -373,11 +373,6 @@ static void pick_launch_shape(ms2_system s) {
     s->jsplit = std::max(1, std::min(8, (152 * 2) / std::max(iblocks, 1)));
     if (s->tune_jsplit > 0) s->jsplit = s->tune_jsplit;
     if (s->tune_wpb > 0) s->wpb = s->tune_wpb;
-    // FP64-heavy kernels: spread molecules over all SMs with small blocks
-    s->red_threads = N <= 152 * 32 ? 32 : 64;
-    // an FP64 warp instruction costs the same issue slots however many lanes are
-    // active, so the FP64 kernels use full warps
-    s->drift_threads = 32;
 }
 
 static ms2_status upload_params(ms2_system s) {
@@ -435,6 +430,38 @@ static ms2_status size_pair_tiles(ms2_system s) {
     return MS2_OK;
 }
 
+// fused step: picked where a variant exists and the whole system fits one SM's
+// shared memory with one 512-thread block per SM resident (cooperative launch)
+static void setup_fused(ms2_system s, const ms2_options &o) {
+    s->step_fn = nullptr;
+    if (!o.fused_step || s->fp64 || s->hp.integrator == MS2_INT_VERLET || s->hp.elec == ELEC_EWALD || s->multi_used)
+        return;
+    void *fn = ms2_pick_step_kernel(s->ns, s->ljm, s->qm, s->dm, s->hp.elec, false);
+    if (!fn) return;
+    int coop = 0, sms = 0, optin = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device) != cudaSuccess || !coop) return;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const int Np = (s->N + 3) & ~3;
+    const size_t maxdyn = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    const size_t base = ms2_step_smem_bytes(s->ns, s->dmu, false, Np, 0);
+    int nb = 0;
+    if (base > maxdyn || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxdyn) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ms2_step_threads(), base) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        return;
+    }
+    s->step_fn = fn;
+    s->step_grid = sms;
+    s->Np = Np;
+    s->step_smem_max = maxdyn;
+}
+
 // ------------------------------------------------------------ launchers
 ms2_status launch_build(ms2_system s) {
     const int th = 128;  // 4 lanes per molecule
@@ -467,7 +494,7 @@ ms2_status launch_reduce(ms2_system s, int mode) {
     if (s->fp64) mode |= RED_FP64PART;
     if (s->hp.elec == ELEC_EWALD) mode |= RED_EWALD;
     if (s->hp.integrator != MS2_INT_VERLET) mode |= RED_LAMBDA;
-    k_reduce<<<s->d.nblk_red, 128, 0, s->stream>>>(s->dP, s->d, mode);
+    k_reduce<<<(s->d.nvb + 3) / 4, 128, 0, s->stream>>>(s->dP, s->d, mode);
     s->launch_acc += 1;
     return MS2_OK;
 }
@@ -562,6 +589,7 @@ extern "C" ms2_status ms2_default_options(ms2_options *o) {
     o->integrator = MS2_INT_LEAPFROG_Q;
     o->quat_iters = 3;
     o->graph_chunk = 50;
+    o->fused_step = 1;
     return MS2_OK;
 }
 
@@ -788,6 +816,7 @@ extern "C" ms2_status ms2_create_system(const ms2_model *models, const int *N_pe
     pick_launch_shape(s);
     st = sys_alloc(s);
     if (st == MS2_OK) st = size_pair_tiles(s);
+    if (st == MS2_OK) setup_fused(s, o);
     if (st == MS2_OK && elec == MS2_ELEC_EWALD) st = setup_ewald(s, 3.2 / cutoff, 8, 8, 8);
     if (st == MS2_OK && elec != MS2_ELEC_EWALD) {
         double coulomb, kconv;
@@ -833,11 +862,44 @@ extern "C" ms2_status ms2_enable_timing(ms2_system s, int on) {
     return MS2_OK;
 }
 
+extern "C" ms2_status ms2_step_kernel(ms2_system s, int *fused) {
+    if (!s || !fused) return ms2_fail(MS2_EINVAL, "null argument");
+    const int cells = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
+    *fused = s->step_fn && ms2_step_smem_bytes(s->ns, s->dmu, false, s->Np, cells) <= s->step_smem_max ? 1 : 0;
+    return MS2_OK;
+}
+
+static ms2_status read_scalars(ms2_system s, double *sc) {
+    MS2_CUDA_OK(cudaMemcpyAsync(sc, s->d.scal, sizeof(double) * SC_COUNT_, cudaMemcpyDeviceToHost, s->stream));
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_last_step_phases(ms2_system s, double out[5]) {
+    if (!s || !out) return ms2_fail(MS2_EINVAL, "null argument");
+    if (!s->timing || !s->last_fused) return ms2_fail(MS2_ESTATE, "no timed fused chunk (timing off or per-phase kernels)");
+    double sc[SC_COUNT_];
+    ms2_status st = read_scalars(s, sc);
+    if (st != MS2_OK) return st;
+    for (int k = 0; k < 5; ++k) out[k] = sc[SC_TPH0 + k] * 1e-6;
+    return MS2_OK;
+}
+
 extern "C" ms2_status ms2_last_step_times(ms2_system s, double out[4]) {
     if (!s || !out) return ms2_fail(MS2_EINVAL, "null argument");
     if (!s->timing) return ms2_fail(MS2_ESTATE, "timing is off (ms2_enable_timing)");
     MS2_CUDA_OK(cudaEventSynchronize(s->ev[4]));
     float a, b, c;
+    if (s->last_fused) {  // one kernel per chunk: the step is the chunk's mean, the pair phase from %globaltimer
+        double tp = 0;
+        MS2_CUDA_OK(cudaMemcpy(&tp, s->d.scal + SC_TPAIR, sizeof tp, cudaMemcpyDeviceToHost));
+        MS2_CUDA_OK(cudaEventElapsedTime(&c, s->ev[0], s->ev[4]));
+        out[2] = c / std::max(1, s->last_launch_steps);
+        out[0] = tp * 1e-6;
+        out[1] = 0.0;
+        out[3] = out[2] - out[0];
+        return MS2_OK;
+    }
     MS2_CUDA_OK(cudaEventElapsedTime(&a, s->ev[1], s->ev[2]));
     MS2_CUDA_OK(cudaEventElapsedTime(&b, s->ev[2], s->ev[3]));
     MS2_CUDA_OK(cudaEventElapsedTime(&c, s->ev[0], s->ev[4]));
@@ -870,6 +932,39 @@ extern "C" ms2_status ms2_system_info(ms2_system s, int *N, double *box, double 
     return MS2_OK;
 }
 
+// one fused launch of m steps from step counter s0; false: not possible now
+// (no variant, RDF histogram too large for shared memory, launch refused)
+static bool run_fused(ms2_system s, long long m, long long s0) {
+    if (!s->step_fn) return false;
+    const int cells = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
+    const size_t smem = ms2_step_smem_bytes(s->ns, s->dmu, false, s->Np, cells);
+    if (smem > s->step_smem_max) return false;
+    unsigned *cnt = s->d.counter;
+    StepArgs A;
+    A.nsteps = (int)m;
+    A.s0 = s0;
+    A.rdf_every = s->d.rdf ? s->rdf_every : 0;
+    A.TJ = s->TJ;
+    A.Np = s->Np;
+    A.bar = cnt + 16 + 16 * s->bar_parity;
+    A.bar_next = cnt + 16 + 16 * (1 - s->bar_parity);
+    A.err = cnt + 48;
+    A.timing = s->timing ? 1 : 0;
+    if (s->timing) cudaEventRecord(s->ev[0], s->stream);
+    const cudaError_t e = ms2_launch_step(s->step_fn, s->step_grid, smem, s->stream, s->dP, s->d, A);
+    if (e != cudaSuccess) {  // e.g. co-residency refused: the per-phase kernels from now on
+        cudaGetLastError();
+        s->step_fn = nullptr;
+        return false;
+    }
+    if (s->timing) cudaEventRecord(s->ev[4], s->stream);
+    s->bar_parity ^= 1;
+    s->last_launch_steps = (int)m;
+    s->last_fused = true;
+    ms2_count_launches(1);
+    return true;
+}
+
 extern "C" ms2_status ms2_step(ms2_system s, long long n) {
     if (!s) return ms2_fail(MS2_EINVAL, "null system");
     if (n < 0) return ms2_fail(MS2_EINVAL, "negative step count");
@@ -877,8 +972,11 @@ extern "C" ms2_status ms2_step(ms2_system s, long long n) {
     const long long chunk = s->graph_chunk;
     while (done < n) {
         const long long m = std::min(chunk, n - done);
-        ms2_status st = run_graph(s, m, s->step + done);
-        if (st != MS2_OK) return st;
+        if (!run_fused(s, m, s->step + done)) {
+            ms2_status st = run_graph(s, m, s->step + done);
+            if (st != MS2_OK) return st;
+            s->last_fused = false;
+        }
         done += m;
     }
     s->step += n;
@@ -890,11 +988,6 @@ extern "C" ms2_status ms2_step(ms2_system s, long long n) {
     return MS2_OK;
 }
 
-static ms2_status read_scalars(ms2_system s, double *sc) {
-    MS2_CUDA_OK(cudaMemcpyAsync(sc, s->d.scal, sizeof(double) * SC_COUNT_, cudaMemcpyDeviceToHost, s->stream));
-    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
-    return MS2_OK;
-}
 
 extern "C" ms2_status ms2_energy_virial(ms2_system s, double *U, double *W, double *T_inst, double *P) {
     if (!s) return ms2_fail(MS2_EINVAL, "null system");
@@ -905,6 +998,13 @@ extern "C" ms2_status ms2_energy_virial(ms2_system s, double *U, double *W, doub
     if (W) *W = sc[SC_WTOT];
     if (T_inst) *T_inst = sc[SC_T];
     if (P) *P = sc[SC_P];
+    if (sc[SC_KERR] != 0.0) {  // a fused-step barrier wait ran out: the state is not to be trusted
+        const double zero = 0.0;
+        cudaMemcpyAsync(s->d.scal + SC_KERR, &zero, sizeof zero, cudaMemcpyHostToDevice, s->stream);
+        cudaMemsetAsync(s->d.counter + 48, 0, sizeof(unsigned), s->stream);
+        cudaStreamSynchronize(s->stream);
+        return ms2_fail(MS2_ETIMEOUT, "a grid-barrier wait of the fused step kernel timed out");
+    }
     if (sc[SC_UNSTABLE] != 0.0 || !std::isfinite(sc[SC_UTOT]))
         return ms2_fail(MS2_EUNSTABLE, "non-finite or exploding forces in the current configuration");
     return MS2_OK;

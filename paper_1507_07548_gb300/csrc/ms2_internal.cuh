@@ -63,7 +63,7 @@ struct SysParams {
 
 // Device pointers of one system.
 struct DevSys {
-    int N, ns, jsplit, nblk_red;
+    int N, ns, jsplit, nvb;  // nvb: reduction units of 8 molecules
     double *R, *v, *q, *Lm;           // FP64 state
     int *species;
     uint32_t *X;                       // [3][N]
@@ -99,10 +99,27 @@ struct DevSys {
 enum {
     SC_ULJ = 0, SC_UQQ, SC_UDD, SC_WPAIR, SC_NPAIRS, SC_KETR, SC_KEROT, SC_LAMBDA,
     SC_UREC, SC_WREC_AT, SC_WREC_CORR, SC_UCONST, SC_PLRC, SC_ULRC, SC_WBG, SC_UNSTABLE,
-    SC_UTOT, SC_WTOT, SC_P, SC_T, SC_KETR_NOW, SC_KEROT_NOW, SC_STEP, SC_COUNT_
+    SC_UTOT, SC_WTOT, SC_P, SC_T, SC_KETR_NOW, SC_KEROT_NOW, SC_STEP,
+    SC_TPAIR,  // fused step: pair-phase time of the last step of a chunk (ns)
+    SC_TPH0, SC_TPH1, SC_TPH2, SC_TPH3, SC_TPH4,  // fused step: device times (ns) of the last step's phases
+    SC_KERR,   // fused step: a grid-barrier wait timed out (sticky until read)
+    SC_COUNT_
 };
 // running averages
 enum { AC_N = 0, AC_U, AC_P, AC_T, AC_BN, AC_BU, AC_BP, AC_NB, AC_SBU, AC_SBU2, AC_SBP, AC_SBP2, AC_COUNT_ };
+
+// launch arguments of the fused step kernel (k_step.cu)
+struct StepArgs {
+    int nsteps;
+    long long s0;          // step counter before the chunk (RDF sampling phase)
+    int rdf_every;         // 0: no RDF sampling
+    int TJ;                // j tile segmentation of the per-phase pair kernel
+    int Np;                // stride of the staged system
+    unsigned *bar;         // this launch's barrier counter (zero at entry)
+    unsigned *bar_next;    // the next launch's counter, zeroed by this launch
+    unsigned *err;         // sticky timeout flag
+    int timing;            // record the pair-phase time of the last step (SC_TPAIR, ns)
+};
 
 // ------------------------------------------------------------ helpers
 __device__ __forceinline__ void rotmat(const double q0, const double q1, const double q2, const double q3,
@@ -119,10 +136,45 @@ __device__ __forceinline__ void rotmat(const double q0, const double q1, const d
     A[8] = 1.0 - 2.0 * (q1 * q1 + q2 * q2);
 }
 
+// IEEE binary32 <-> binary64 conversions written on the integer pipe.  On GB300
+// a conversion instruction occupies the SMSP's small FP64 unit for ~90-180
+// cycles; these take a few integer operations and return exactly what the
+// hardware conversion returns (round to nearest even), falling back to it
+// outside the normal range.
+__device__ __forceinline__ double f2d(float f) {
+    const unsigned b = __float_as_uint(f), e = (b >> 23) & 0xFFu;
+    const unsigned long long sgn = (unsigned long long)(b & 0x80000000u) << 32;
+    if (e - 1u < 254u)  // normal
+        return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 896u) << 52) |
+                                                ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+    if ((b & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sgn);  // signed zero
+    return (double)f;  // subnormal, inf, nan
+}
+
+__device__ __forceinline__ float d2f(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), sgn = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu) - 896;  // binary32 biased exponent
+    if (e >= 1 && e <= 254) {
+        const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+        const unsigned rem = (unsigned)(m & 0x1FFFFFFFull), half = 0x10000000u;
+        unsigned r = ((unsigned)e << 23) | (unsigned)(m >> 29);
+        r += (rem > half || (rem == half && (r & 1u))) ? 1u : 0u;  // a carry into the exponent is correct
+        return __uint_as_float(r | sgn);
+    }
+    if ((b & 0x7FFFFFFFFFFFFFFFull) == 0ull) return __uint_as_float(sgn);  // signed zero
+    return (float)x;  // subnormal result, overflow, inf, nan
+}
+
 // lattice coordinate: floor(x * 2^32/L) mod 2^32, taken with one IEEE multiply
-// (no contraction possible) so that host and device agree bit for bit.
+// (no contraction possible) so that host and device agree bit for bit.  For
+// |t| < 2^51 the floor comes from one round-down add of 1.5 * 2^52 (the sum's
+// unit in the last place is 1, and its low mantissa word is floor(t) mod 2^32);
+// larger |t| takes floor and an integer conversion.
 __device__ __forceinline__ uint32_t lattice_coord(double x, double scale) {
-    double t = __dmul_rn(x, scale);
+    const double t = __dmul_rn(x, scale);
+    const unsigned ex = ((unsigned)__double2hiint(t) >> 20) & 0x7FFu;
+    if (ex < 1023u + 51u) return (uint32_t)__double2loint(__dadd_rd(t, 6755399441055744.0));
     return (uint32_t)(unsigned long long)(long long)floor(t);
 }
 

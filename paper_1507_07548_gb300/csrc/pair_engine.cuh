@@ -56,17 +56,18 @@ __host__ __device__ inline size_t smem_bytes(int NS, bool dmu, bool multi, int T
 // block-level: multi-species parameter tables into shared memory
 template <bool MULTI>
 __device__ __forceinline__ void load_tables(const SysParams *__restrict__ P, const Smem &sm) {
-    if (!MULTI) return;
-    for (int k = threadIdx.x; k < MS2_MAXSP * MS2_MAXS; k += blockDim.x) {
-        sm.sq[k] = P->q[k / MS2_MAXS][k % MS2_MAXS];
-        sm.sql[k] = P->qlo[k / MS2_MAXS][k % MS2_MAXS];
-        sm.sljt[k] = P->ljt[k / MS2_MAXS][k % MS2_MAXS];
-    }
-    for (int k = threadIdx.x; k < MS2_MAXT * MS2_MAXT; k += blockDim.x) {
-        sm.sc6[k] = P->c6[k / MS2_MAXT][k % MS2_MAXT];
-        sm.sc12[k] = P->c12[k / MS2_MAXT][k % MS2_MAXT];
-        sm.sc6l[k] = P->c6lo[k / MS2_MAXT][k % MS2_MAXT];
-        sm.sc12l[k] = P->c12lo[k / MS2_MAXT][k % MS2_MAXT];
+    if constexpr (MULTI) {
+        for (int k = threadIdx.x; k < MS2_MAXSP * MS2_MAXS; k += blockDim.x) {
+            sm.sq[k] = P->q[k / MS2_MAXS][k % MS2_MAXS];
+            sm.sql[k] = P->qlo[k / MS2_MAXS][k % MS2_MAXS];
+            sm.sljt[k] = P->ljt[k / MS2_MAXS][k % MS2_MAXS];
+        }
+        for (int k = threadIdx.x; k < MS2_MAXT * MS2_MAXT; k += blockDim.x) {
+            sm.sc6[k] = P->c6[k / MS2_MAXT][k % MS2_MAXT];
+            sm.sc12[k] = P->c12[k / MS2_MAXT][k % MS2_MAXT];
+            sm.sc6l[k] = P->c6lo[k / MS2_MAXT][k % MS2_MAXT];
+            sm.sc12l[k] = P->c12lo[k / MS2_MAXT][k % MS2_MAXT];
+        }
     }
 }
 
@@ -76,22 +77,37 @@ __device__ __forceinline__ void stage_tile(const Smem &sm, const DevSys &S, int 
     const int N = S.N;
     for (int k = threadIdx.x; k < tn; k += blockDim.x) {
         const int j = t0 + k;
-        sm.tX[k] = S.X[j];
-        sm.tY[k] = S.X[N + j];
-        sm.tZ[k] = S.X[2 * N + j];
+        // L2 loads (the data may come from another block of the same persistent kernel)
+        sm.tX[k] = __ldcg(S.X + j);
+        sm.tY[k] = __ldcg(S.X + N + j);
+        sm.tZ[k] = __ldcg(S.X + 2 * N + j);
 #pragma unroll
-        for (int c = 0; c < 3 * NS; ++c) sm.ts[c * TJ + k] = S.s[c * N + j];
+        for (int c = 0; c < 3 * NS; ++c) sm.ts[c * TJ + k] = __ldcg(S.s + c * N + j);
         if (DMU) {
 #pragma unroll
-            for (int c = 0; c < 3 * NS; ++c) sm.tmu[c * TJ + k] = S.mu[c * N + j];
+            for (int c = 0; c < 3 * NS; ++c) sm.tmu[c * TJ + k] = __ldcg(S.mu + c * N + j);
         }
         if (MULTI) sm.tsp[k] = S.species[j];
         if (rfq) {
-            sm.tmd[k] = S.mum[j];
-            sm.tmd[TJ + k] = S.mum[N + j];
-            sm.tmd[2 * TJ + k] = S.mum[2 * N + j];
+            sm.tmd[k] = __ldcg(S.mum + j);
+            sm.tmd[TJ + k] = __ldcg(S.mum + N + j);
+            sm.tmd[2 * TJ + k] = __ldcg(S.mum + 2 * N + j);
         }
     }
+}
+
+// the tile arrays seen from slot t0 on (same stride): a j-range inside a tile
+// that holds the whole system
+__device__ __forceinline__ Smem shifted(const Smem &m, int t0) {
+    Smem v = m;
+    v.tX += t0;
+    v.tY += t0;
+    v.tZ += t0;
+    v.ts += t0;
+    v.tmu += t0;
+    v.tmd += t0;
+    v.tsp += t0;
+    return v;
 }
 
 // result of one molecule (valid in lane 0): F, tau, U_lj, U_qq, U_dd, W, partners
@@ -170,13 +186,36 @@ struct PairWarp {
             }
         spi = MULTI ? S.species[i] : 0;
 #pragma unroll
+        for (int k = 0; k < 3; ++k) mdi[k] = (MOLD && rfq) ? S.mum[k * N + i] : 0.f;
+        begin_common(P);
+    }
+
+    // molecule i from a tile that holds the whole system with stride TJ
+    __device__ __forceinline__ void begin_tile(const SysParams *__restrict__ P, const Smem &sm, int TJ, int i_) {
+        i = i_;
+        Xi = sm.tX[i];
+        Yi = sm.tY[i];
+        Zi = sm.tZ[i];
+#pragma unroll
+        for (int a = 0; a < NS; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                si[a][k] = sm.ts[(k * NS + a) * TJ + i];
+                mui[a][k] = DMU && ((DM >> a) & 1) ? sm.tmu[(k * NS + a) * TJ + i] : 0.f;
+            }
+        spi = MULTI ? sm.tsp[i] : 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) mdi[k] = (MOLD && rfq) ? sm.tmd[k * TJ + i] : 0.f;
+        begin_common(P);
+    }
+
+    __device__ __forceinline__ void begin_common(const SysParams *__restrict__ P) {
+#pragma unroll
         for (int a = 0; a < NS; ++a) {
             ljti[a] = P->ljt[spi][a];
             qih[a] = P->cq[spi][a];  // (C q_a) as hi + lo, from FP64
             qil[a] = P->cqlo[spi][a];
         }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) mdi[k] = (MOLD && rfq) ? S.mum[k * N + i] : 0.f;
 #pragma unroll
         for (int a = 0; a < NS; ++a)
 #pragma unroll

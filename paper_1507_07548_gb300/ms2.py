@@ -46,7 +46,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 class ms2_options(C.Structure):
     _fields_ = [("eps_rf", C.c_double), ("lrc", C.c_int), ("dt", C.c_double), ("thermostat", C.c_int),
                 ("seed", C.c_ulonglong), ("integrator", C.c_int), ("reduced", C.c_int), ("quat_iters", C.c_int),
-                ("graph_chunk", C.c_int), ("fp64", C.c_int), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN),
+                ("graph_chunk", C.c_int), ("fp64", C.c_int), ("fused_step", C.c_int), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN),
                 ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
@@ -98,6 +98,8 @@ SIGNATURES = {
     "ms2_serve_drain": (C.c_int, [_vp, C.c_double]),
     "ms2_serve_close": (C.c_int, [_vp]),
     "ms2_enable_timing": (C.c_int, [_vp, C.c_int]),
+    "ms2_step_kernel": (C.c_int, [_vp, _P(C.c_int)]),
+    "ms2_last_step_phases": (C.c_int, [_vp, _d]),
     "ms2_last_step_times": (C.c_int, [_vp, _d]),
     "ms2_forces_noalloc": (C.c_int, [_P(ms2_model), _P(C.c_int), C.c_int, C.c_double, C.c_double, C.c_int,
                                      _P(ms2_options), _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -293,6 +295,18 @@ class System:
 
     def enable_timing(self, on=True):
         check(lib().ms2_enable_timing(self.h, int(on)))
+
+    def fused_step(self):
+        """1 if the next chunk of steps runs as the fused cooperative kernel."""
+        f = C.c_int()
+        check(lib().ms2_step_kernel(self.h, C.byref(f)))
+        return f.value
+
+    def last_step_phases(self):
+        """Fused step, timing on: (drift, pair, reduction, totals, entry-to-last-step) device ms."""
+        out = np.zeros(5)
+        check(lib().ms2_last_step_phases(self.h, _dp(out)))
+        return out
 
     def last_step_times(self):
         """(pair kernel ms, Ewald kernels ms, whole last step ms, rest ms) of the last enqueued step."""
