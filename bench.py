@@ -47,7 +47,7 @@ SMS, FP32_LANES = 152, 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ms2", choices=["ms2", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle CPU-baseline sample length")
@@ -177,7 +177,8 @@ def reference_arm(args, rank, world):
 
 # ---------------------------------------------------------------- GPU arm
 # kernel sources a stored DRAM-traffic figure describes (it is void once they change)
-TRAFFIC_SOURCES = {"pair_water_rf": ("k_pair.cu", "pair_engine.cuh", "ms2_internal.cuh")}
+TRAFFIC_SOURCES = {"pair_water_rf": ("k_pair.cu", "pair_engine.cuh", "ms2_internal.cuh"),
+                   "step_water_rf": ("k_step.cu", "pair_engine.cuh", "integrate_dev.cuh", "ms2_internal.cuh")}
 
 
 def traffic_record(kernel):
@@ -237,8 +238,8 @@ def gpu_arm(args, rank, world, local_rank):
         s.step(1)
         e1.record(stream)
         e1.synchronize()
-        tp = s.last_step_times()
-        return e0.elapsed_time(e1), tp[0], s.energy_terms()["n_pairs"]
+        tp = s.last_step_times()    # [0] pair kernel (or fused pair phase), [2] the step's kernels
+        return e0.elapsed_time(e1), tp[0], tp[2], s.energy_terms()["n_pairs"]
 
     for _ in range(args.warmup):
         one_step()
@@ -246,13 +247,15 @@ def gpu_arm(args, rank, world, local_rank):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     n0 = ms2.kernel_launches()
-    t_step, t_pair, pairs = [], [], []
+    fused = s.fused_step() == 1
+    t_step, t_pair, t_kern, pairs = [], [], [], []
     with ClockSampler(local_rank) as clk:
         for _ in range(args.steps):
-            a, b, c = one_step()
+            a, b, c, d = one_step()
             t_step.append(a)
             t_pair.append(b)
-            pairs.append(c)
+            t_kern.append(c)
+            pairs.append(d)
     torch.cuda.synchronize()
     launches = ms2.kernel_launches() - n0
     tot_ms_max, pairs_all = combine_ranks(sum(t_step), sum(pairs), world)
@@ -285,8 +288,10 @@ def gpu_arm(args, rank, world, local_rank):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
     flops = FLOPS_PER_WATER_PAIR * sum(pairs)
-    achieved = flops / (sum(t_pair) * 1e-3) / 1e12
-    traffic = traffic_record("pair_water_rf")
+    # dominant kernel: the fused step kernel (one launch per step) or, per phase, the pair kernel
+    kern_ms = t_kern if fused else t_pair
+    achieved = flops / (sum(kern_ms) * 1e-3) / 1e12
+    traffic = traffic_record("step_water_rf" if fused else "pair_water_rf")
     cpu_val, cpu_n, cpu_dt, cores = oracle_rate(args.cpu_seconds)
     value = pairs_all / (tot_ms_max * 1e-3)
     line = {
@@ -299,10 +304,13 @@ def gpu_arm(args, rank, world, local_rank):
                    "state": "FP64 positions/integrator/sums, FP32 site pairs"},
         "molecule_steps_per_s": N_WATER * args.steps * world / (tot_ms_max * 1e-3),
         "site_pair_interactions_per_s": value * 10,
-        "roofline": {"bound": "alu", "kernel": "k_pair<3,1,7,0,RF>", "achieved": achieved, "peak": peak_tflops,
+        "roofline": {"bound": "alu",
+                     "kernel": "k_step<3,1,7,0,RF> (fused MD step)" if fused else "k_pair<3,1,7,0,RF>",
+                     "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (unit counts x max clock)" % sm_max,
-                     "pair_kernel_ms": statistics.mean(t_pair),
+                     "kernel_ms": statistics.mean(kern_ms),
+                     "pair_phase_ms": statistics.mean(t_pair),
                      "algorithmic_flops_per_launch": FLOPS_PER_WATER_PAIR * statistics.mean(pairs)},
         "cpu_baseline": {"value": cpu_val, "unit": "pair interactions/s", "cores": cores, "kind": "oracle",
                          "sample": "%d MD steps of the same workload, %.1f s" % (cpu_n, cpu_dt)},

@@ -266,11 +266,12 @@ MS2_API ms2_status ms2_enable_timing(ms2_system sys, int on);
  * shared memory sends the chunk to the per-phase kernels), else 0. */
 MS2_API ms2_status ms2_step_kernel(ms2_system sys, int *fused);
 /* Diagnostic of the fused step with timing on: device-timer durations (ms) of
- * the last step of the last chunk: [0] drift and site build, [1] staging, pair
- * and RDF, [2] reduction units, [3] totals and step record (each up to the end
- * of its grid barrier), [4] from kernel entry to that last step.  MS2_ESTATE if
+ * the last step of the last chunk: [0] drift and site build, [2] staging, pair
+ * and RDF, [3] unit reduction (each until the slowest block is done), [1] and
+ * [4] the grid barriers after [0] and [3], [5] totals and thermostat factor,
+ * [6] kernel entry to that last step, [7] the whole last step.  MS2_ESTATE if
  * timing is off or the last chunk ran as per-phase kernels. */
-MS2_API ms2_status ms2_last_step_phases(ms2_system sys, double out[5]);
+MS2_API ms2_status ms2_last_step_phases(ms2_system sys, double out[8]);
 MS2_API ms2_status ms2_last_step_times(ms2_system sys, double out[4]);
 
 /* ------------------------------------------------------- allocation-free */

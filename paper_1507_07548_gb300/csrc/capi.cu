@@ -348,10 +348,10 @@ static ms2_status sys_alloc(ms2_system s) {
     MS2_CUDA_OK(A((void **)&d.tau, sizeof(double) * 3 * N));
     MS2_CUDA_OK(A((void **)&d.Ui, sizeof(double) * 4 * N));
     MS2_CUDA_OK(A((void **)&d.npart, sizeof(int) * N));
-    d.nvb = (N + 7) / 8;  // reduction units: one warp, a quad of lanes per molecule
+    d.nunits = s->nunits;  // reduction units: one warp each, a quad of lanes per molecule
     MS2_CUDA_OK(A((void **)&d.terms, sizeof(double) * 8));
     if (s->hp.elec == ELEC_EWALD) MS2_CUDA_OK(A((void **)&d.wcorr, sizeof(double) * N));
-    MS2_CUDA_OK(A((void **)&d.blk, sizeof(double) * MS2_NRED * d.nvb));
+    MS2_CUDA_OK(A((void **)&d.blk, sizeof(double) * MS2_NRED * d.nunits));
     MS2_CUDA_OK(A((void **)&d.counter, 256));
     MS2_CUDA_OK(A((void **)&d.scal, sizeof(double) * SC_COUNT_));
     MS2_CUDA_OK(A((void **)&d.acc, sizeof(double) * AC_COUNT_));
@@ -371,6 +371,11 @@ static void pick_launch_shape(ms2_system s) {
     s->wpb = 8;
     const int iblocks = (N + s->wpb - 1) / s->wpb;
     s->jsplit = std::max(1, std::min(8, (152 * 2) / std::max(iblocks, 1)));
+    s->nunits = (N + 7) / 8;  // reduction units of 8 molecules
+    if (s->fuse_fn) {         // the fused decomposition (see setup_fused)
+        s->jsplit = std::max(1, std::min(8, 16 / s->mcap));
+        s->nunits = s->step_grid;
+    }
     if (s->tune_jsplit > 0) s->jsplit = s->tune_jsplit;
     if (s->tune_wpb > 0) s->wpb = s->tune_wpb;
 }
@@ -430,35 +435,44 @@ static ms2_status size_pair_tiles(ms2_system s) {
     return MS2_OK;
 }
 
-// fused step: picked where a variant exists and the whole system fits one SM's
-// shared memory with one 512-thread block per SM resident (cooperative launch)
+// fused step: a system is fusable where a variant exists, the device launches
+// cooperative kernels, every block owns at most 16 molecules (one pair item per
+// warp for j-split >= 1) and the whole system plus the own region fits one
+// SM's shared memory.  A fusable system gets the fused decomposition (reduction
+// units = the grid's block ranges, j-split 16 / molecules per block) on both
+// paths, so fused and per-phase chunks agree bit for bit; ms2_options.fused_step
+// only chooses which path runs.
 static void setup_fused(ms2_system s, const ms2_options &o) {
-    s->step_fn = nullptr;
-    if (!o.fused_step || s->fp64 || s->hp.integrator == MS2_INT_VERLET || s->hp.elec == ELEC_EWALD || s->multi_used)
-        return;
+    s->fuse_fn = s->step_fn = nullptr;
+    if (s->fp64 || s->hp.integrator == MS2_INT_VERLET || s->hp.elec == ELEC_EWALD || s->multi_used) return;
     void *fn = ms2_pick_step_kernel(s->ns, s->ljm, s->qm, s->dm, s->hp.elec, false);
     if (!fn) return;
     int coop = 0, sms = 0, optin = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device) != cudaSuccess || !coop) return;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+    const int mcap = (s->N + sms - 1) / std::max(sms, 1);
+    if (sms < 1 || mcap > 16) return;
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
         cudaGetLastError();
         return;
     }
+    const int js = std::max(1, std::min(8, 16 / mcap));
     const int Np = (s->N + 3) & ~3;
     const size_t maxdyn = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
-    const size_t base = ms2_step_smem_bytes(s->ns, s->dmu, false, Np, 0);
+    const size_t base = ms2_step_smem_bytes(s->ns, s->dmu, false, Np, mcap, js, 0);
     int nb = 0;
     if (base > maxdyn || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxdyn) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ms2_step_threads(), base) != cudaSuccess || nb < 1) {
         cudaGetLastError();
         return;
     }
-    s->step_fn = fn;
+    s->fuse_fn = fn;
+    s->step_fn = o.fused_step ? fn : nullptr;
     s->step_grid = sms;
     s->Np = Np;
+    s->mcap = mcap;
     s->step_smem_max = maxdyn;
 }
 
@@ -494,7 +508,7 @@ ms2_status launch_reduce(ms2_system s, int mode) {
     if (s->fp64) mode |= RED_FP64PART;
     if (s->hp.elec == ELEC_EWALD) mode |= RED_EWALD;
     if (s->hp.integrator != MS2_INT_VERLET) mode |= RED_LAMBDA;
-    k_reduce<<<(s->d.nvb + 3) / 4, 128, 0, s->stream>>>(s->dP, s->d, mode);
+    k_reduce<<<(s->d.nunits + 3) / 4, 128, 0, s->stream>>>(s->dP, s->d, mode);
     s->launch_acc += 1;
     return MS2_OK;
 }
@@ -813,10 +827,10 @@ extern "C" ms2_status ms2_create_system(const ms2_model *models, const int *N_pe
         return ms2_fail(MS2_EINVAL, "fp64 pair arithmetic is available for single-site LJ models only");
     }
     setup_pair(s);
+    setup_fused(s, o);
     pick_launch_shape(s);
     st = sys_alloc(s);
     if (st == MS2_OK) st = size_pair_tiles(s);
-    if (st == MS2_OK) setup_fused(s, o);
     if (st == MS2_OK && elec == MS2_ELEC_EWALD) st = setup_ewald(s, 3.2 / cutoff, 8, 8, 8);
     if (st == MS2_OK && elec != MS2_ELEC_EWALD) {
         double coulomb, kconv;
@@ -865,7 +879,8 @@ extern "C" ms2_status ms2_enable_timing(ms2_system s, int on) {
 extern "C" ms2_status ms2_step_kernel(ms2_system s, int *fused) {
     if (!s || !fused) return ms2_fail(MS2_EINVAL, "null argument");
     const int cells = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
-    *fused = s->step_fn && ms2_step_smem_bytes(s->ns, s->dmu, false, s->Np, cells) <= s->step_smem_max ? 1 : 0;
+    *fused = s->step_fn && ms2_step_smem_bytes(s->ns, s->dmu, false, s->Np, s->mcap, s->jsplit, cells) <= s->step_smem_max
+                 ? 1 : 0;
     return MS2_OK;
 }
 
@@ -875,13 +890,13 @@ static ms2_status read_scalars(ms2_system s, double *sc) {
     return MS2_OK;
 }
 
-extern "C" ms2_status ms2_last_step_phases(ms2_system s, double out[5]) {
+extern "C" ms2_status ms2_last_step_phases(ms2_system s, double out[8]) {
     if (!s || !out) return ms2_fail(MS2_EINVAL, "null argument");
     if (!s->timing || !s->last_fused) return ms2_fail(MS2_ESTATE, "no timed fused chunk (timing off or per-phase kernels)");
     double sc[SC_COUNT_];
     ms2_status st = read_scalars(s, sc);
     if (st != MS2_OK) return st;
-    for (int k = 0; k < 5; ++k) out[k] = sc[SC_TPH0 + k] * 1e-6;
+    for (int k = 0; k < 8; ++k) out[k] = sc[SC_TPH0 + k] * 1e-6;
     return MS2_OK;
 }
 
@@ -937,7 +952,7 @@ extern "C" ms2_status ms2_system_info(ms2_system s, int *N, double *box, double 
 static bool run_fused(ms2_system s, long long m, long long s0) {
     if (!s->step_fn) return false;
     const int cells = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
-    const size_t smem = ms2_step_smem_bytes(s->ns, s->dmu, false, s->Np, cells);
+    const size_t smem = ms2_step_smem_bytes(s->ns, s->dmu, false, s->Np, s->mcap, s->jsplit, cells);
     if (smem > s->step_smem_max) return false;
     unsigned *cnt = s->d.counter;
     StepArgs A;
@@ -946,10 +961,12 @@ static bool run_fused(ms2_system s, long long m, long long s0) {
     A.rdf_every = s->d.rdf ? s->rdf_every : 0;
     A.TJ = s->TJ;
     A.Np = s->Np;
+    A.mcap = s->mcap;
     A.bar = cnt + 16 + 16 * s->bar_parity;
     A.bar_next = cnt + 16 + 16 * (1 - s->bar_parity);
     A.err = cnt + 48;
     A.timing = s->timing ? 1 : 0;
+    A.tmax = (unsigned long long *)(cnt + 56);  // 3 x 8 bytes at byte 224 of the counter block (zero at entry)
     if (s->timing) cudaEventRecord(s->ev[0], s->stream);
     const cudaError_t e = ms2_launch_step(s->step_fn, s->step_grid, smem, s->stream, s->dP, s->d, A);
     if (e != cudaSuccess) {  // e.g. co-residency refused: the per-phase kernels from now on

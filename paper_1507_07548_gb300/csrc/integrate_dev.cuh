@@ -15,22 +15,27 @@ __device__ __forceinline__ double rsqrt_fp64(double x) {  // FP32 seed + two New
 // lattice centre coordinate of component c; row c of the space-frame site
 // offsets, dipoles and molecular charge dipole (lane c of a quad)
 __device__ __forceinline__ void build_row(const SysParams *__restrict__ P, const DevSys &S, int i, int c,
-                                          const double q[4]) {
+                                          const double q[4], double Rc) {
     const int N = S.N, NS = S.ns;
-    S.X[c * N + i] = lattice_coord(S.R[c * N + i], P->lat_scale);
-    const double w = q[0], x = q[1], y = q[2], z = q[3];
-    double a0, a1, a2;  // row c of A(q)
-    if (c == 0) { a0 = 1.0 - 2.0 * (y * y + z * z); a1 = 2.0 * (x * y - w * z); a2 = 2.0 * (x * z + w * y); }
-    else if (c == 1) { a0 = 2.0 * (x * y + w * z); a1 = 1.0 - 2.0 * (x * x + z * z); a2 = 2.0 * (y * z - w * x); }
-    else { a0 = 2.0 * (x * z - w * y); a1 = 2.0 * (y * z + w * x); a2 = 1.0 - 2.0 * (x * x + y * y); }
+    S.X[c * N + i] = lattice_coord(Rc, P->lat_scale);
+    // row c of A(q) for the cyclic order (c, c1, c2), with v = (x, y, z):
+    //   A[c][c] = 1 - 2 (v_c1^2 + v_c2^2), A[c][c1] = 2 (v_c v_c1 - w v_c2),
+    //   A[c][c2] = 2 (v_c v_c2 + w v_c1)
+    // (one instruction stream for the three lanes: no branch on c)
+    const double w = q[0];
+    const double vc = c == 0 ? q[1] : (c == 1 ? q[2] : q[3]);
+    const double v1 = c == 0 ? q[2] : (c == 1 ? q[3] : q[1]);
+    const double v2 = c == 0 ? q[3] : (c == 1 ? q[1] : q[2]);
+    const int c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
+    const double acc = 1.0 - 2.0 * (v1 * v1 + v2 * v2), ac1 = 2.0 * (vc * v1 - w * v2), ac2 = 2.0 * (vc * v2 + w * v1);
     const int sp = S.species[i], nsp = P->n_sites[sp];
     double md = 0.0;
     for (int a = 0; a < NS; ++a) {
         double o = 0.0, m = 0.0;
         if (a < nsp) {
             const double *b = P->bpos[sp][a], *u = P->bdip[sp][a];
-            o = a0 * b[0] + a1 * b[1] + a2 * b[2];
-            if (S.mu) m = a0 * u[0] + a1 * u[1] + a2 * u[2];
+            o = acc * b[c] + ac1 * b[c1] + ac2 * b[c2];
+            if (S.mu) m = acc * u[c] + ac1 * u[c1] + ac2 * u[c2];
             md += P->qd[sp][a] * o;
         }
         S.s[(c * NS + a) * N + i] = d2f(o);
@@ -75,12 +80,19 @@ __device__ __forceinline__ void rotate_q(const double Iinv[3], const double q0[4
     for (int k = 0; k < 4; ++k) q1[k] *= inv;
 }
 
-// column c of A(q): the body component c of a space vector v is column_c . v
+// column c of A(q): the body component c of a space vector u is column_c . u.
+// For the cyclic order (c, c1, c2): A[c][c] = 1 - 2 (v_c1^2 + v_c2^2),
+// A[c1][c] = 2 (v_c1 v_c + w v_c2), A[c2][c] = 2 (v_c2 v_c - w v_c1); the
+// entries come back in space order (no branch on c).
 __device__ __forceinline__ void rot_column(const double q[4], int c, double col[3]) {
-    const double w = q[0], x = q[1], y = q[2], z = q[3];
-    if (c == 0) { col[0] = 1.0 - 2.0 * (y * y + z * z); col[1] = 2.0 * (x * y + w * z); col[2] = 2.0 * (x * z - w * y); }
-    else if (c == 1) { col[0] = 2.0 * (x * y - w * z); col[1] = 1.0 - 2.0 * (x * x + z * z); col[2] = 2.0 * (y * z + w * x); }
-    else { col[0] = 2.0 * (x * z + w * y); col[1] = 2.0 * (y * z - w * x); col[2] = 1.0 - 2.0 * (x * x + y * y); }
+    const double w = q[0];
+    const double vc = c == 0 ? q[1] : (c == 1 ? q[2] : q[3]);
+    const double v1 = c == 0 ? q[2] : (c == 1 ? q[3] : q[1]);
+    const double v2 = c == 0 ? q[3] : (c == 1 ? q[1] : q[2]);
+    const double acc = 1.0 - 2.0 * (v1 * v1 + v2 * v2), a1c = 2.0 * (v1 * vc + w * v2), a2c = 2.0 * (v2 * vc - w * v1);
+    col[0] = c == 0 ? acc : (c == 1 ? a2c : a1c);
+    col[1] = c == 0 ? a1c : (c == 1 ? acc : a2c);
+    col[2] = c == 0 ? a2c : (c == 1 ? a1c : acc);
 }
 
 // ------------------------------------------------------------- reduction
@@ -132,38 +144,62 @@ __device__ __forceinline__ void finish_step(const SysParams *__restrict__ P, con
 }
 
 // ------------------------------------------------------ one step, per quad
-// Drift of molecule i by the 4 lanes of a quad (c = lane & 3), all lanes on one
-// instruction stream (an FP64 instruction costs the warp the same whatever its
-// active lanes, so divergent lane roles would add up):
+// Per-molecule state as seen by a kernel: component c of molecule m at
+// [c * ld + m] (global arrays: ld = N, m = i; the fused step keeps a block's
+// molecules in shared memory: ld = its capacity, m = i - first molecule).
+struct StateView {
+    double *R, *v, *q, *L, *F, *tau;
+    int ld;
+};
+
+// load from a view: SH = shared memory (plain load), else global memory through
+// L2 (data another block may have written in a persistent kernel)
+template <bool SH, typename T>
+__device__ __forceinline__ T ldv(const T *p) {
+    if constexpr (SH) return *p;
+    else return __ldcg(p);
+}
+
+__device__ __forceinline__ StateView global_view(const DevSys &S) {
+    return StateView{S.R, S.v, S.q, S.Lm, S.F, S.tau, S.N};
+}
+
+// Drift of molecule i (state slot m) by the 4 lanes of a quad (c = lane & 3),
+// all lanes on one instruction stream (an FP64 instruction costs the warp the
+// same whatever its active lanes, so divergent lane roles would add up):
 //   leapfrog: lanes 0-2 kick, scale and drift component c of v and R and update
 //             L_c <- lambda (L_c + dt tau_c); every lane then rotates the whole
 //             quaternion (identical results in the 4 lanes) and lane c stores
 //             component c;
 //   Verlet  : v_c += dt/2 F_c/M, R_c += dt v_c (point molecules, no rotation).
 // Lanes 0-2 then rebuild lattice coordinate c and row c of the site offsets.
-// `on` is false for padding quads: they compute on molecule 0 and store nothing.
-// Cross-block data (F, tau) is read with __ldcg so that the persistent step
-// kernel never sees a stale L1 line.
-__device__ __forceinline__ void drift_quad(const SysParams *__restrict__ P, const DevSys &S, int i, bool on, int c,
-                                           bool verlet, double lam) {
-    const int N = S.N, ii = on ? i : 0, cc = c < 3 ? c : 2;
+// `on` is false for padding quads: they compute on slot/molecule 0 and store
+// nothing.  F and tau come through L2 loads (another block may have written
+// them in a persistent kernel).
+template <bool SH>
+__device__ __forceinline__ void drift_quad(const SysParams *__restrict__ P, const DevSys &S, const StateView &sv, int m,
+                                           int i, bool on, int c, bool verlet, double lam) {
+    const int ld = sv.ld, mm = on ? m : 0, ii = on ? i : 0, cc = c < 3 ? c : 2;
     const int sp = S.species[ii];
     const double dt = P->dt;
     const unsigned qb = threadIdx.x & 28u;  // first lane of the quad within the warp
-    double q[4] = {S.q[ii], S.q[N + ii], S.q[2 * N + ii], S.q[3 * N + ii]};
+    double q[4] = {sv.q[mm], sv.q[ld + mm], sv.q[2 * ld + mm], sv.q[3 * ld + mm]};
+    double Rc = sv.R[cc * ld + mm];
     if (verlet) {
         if (c < 3 && on) {
-            const double v = S.v[c * N + i] + 0.5 * dt * P->kconv * P->inv_mass[sp] * __ldcg(S.F + c * N + i);
-            S.v[c * N + i] = v;
-            S.R[c * N + i] += dt * v;
+            const double v = sv.v[c * ld + m] + 0.5 * dt * P->kconv * P->inv_mass[sp] * ldv<SH>(sv.F + c * ld + m);
+            sv.v[c * ld + m] = v;
+            Rc += dt * v;
+            sv.R[c * ld + m] = Rc;
         }
     } else {
-        const double v = lam * (S.v[cc * N + ii] + dt * P->kconv * P->inv_mass[sp] * __ldcg(S.F + cc * N + ii));
-        const double Lc = lam * (S.Lm[cc * N + ii] + dt * P->kconv * __ldcg(S.tau + cc * N + ii));
+        const double v = lam * (sv.v[cc * ld + mm] + dt * P->kconv * P->inv_mass[sp] * ldv<SH>(sv.F + cc * ld + mm));
+        const double Lc = lam * (sv.L[cc * ld + mm] + dt * P->kconv * ldv<SH>(sv.tau + cc * ld + mm));
+        Rc += dt * v;
         if (c < 3 && on) {
-            S.v[c * N + i] = v;
-            S.R[c * N + i] += dt * v;
-            S.Lm[c * N + i] = Lc;
+            sv.v[c * ld + m] = v;
+            sv.R[c * ld + m] = Rc;
+            sv.L[c * ld + m] = Lc;
         }
         double L[3];
 #pragma unroll
@@ -174,10 +210,10 @@ __device__ __forceinline__ void drift_quad(const SysParams *__restrict__ P, cons
             rotate_q(Ii, q, L, dt, P->quat_iters, q1);
 #pragma unroll
             for (int k = 0; k < 4; ++k) q[k] = q1[k];
-            if (on) S.q[c * N + i] = q1[c];
+            if (on) sv.q[c * ld + m] = q1[c];
         }
     }
-    if (c < 3 && on) build_row(P, S, i, c, q);
+    if (c < 3 && on) build_row(P, S, i, c, q, Rc);
 }
 
 // Fixed-tree sum of 8 values over a warp: 9 FP64 adds instead of 8 x 5.  On
@@ -204,111 +240,138 @@ __device__ __forceinline__ double warp_sum8(double x[8], int lane) {
     return x[0];
 }
 
-// Reduction unit `vb`: molecules 8 vb .. 8 vb + 7, one quad each, one warp.
-// With RED_SUM the quad sums the pair partials over the j-ranges (lane c takes
-// the partial values c, c+4, c+8 in j-range order) into F, tau, the
-// per-molecule energies and the partner count; then lanes 0-2 form the kinetic
-// energies of component c (and, for RED_LAMBDA / RED_HALFKICK, after the kick).
-// RED_EWALD folds the reciprocal-space site forces into F, tau and the
-// molecular virial.  The warp's totals of the Q_N step scalars go to blk[vb][*].
-__device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, const DevSys &S, int mode, int vb,
-                                            int lane) {
+// Where a reduction unit reads the pair partials and writes the per-molecule
+// results: partial value v of j-range p for slot m at [(p * NPV + v) * pld + m];
+// energies k at Ui[k * uld + m], partner counts at np[m]; state through sv.
+// Slot m holds molecule i0 + m.
+struct RedIO {
+    const float *part;
+    const double *part64;
+    int pld;
+    StateView sv;
+    double *Ui;
+    int *np;
+    int uld;
+    int i0;
+};
+
+__device__ __forceinline__ RedIO global_io(const DevSys &S) {
+    return RedIO{S.part, S.part64, S.N, global_view(S), S.Ui, S.npart, S.N, 0};
+}
+
+// Reduction unit u of U: molecules [N u / U, N (u+1) / U), one warp, a quad per
+// molecule, passes of 8 molecules.  With RED_SUM the quad sums the pair partials
+// over the j-ranges (lane c takes the partial values c, c+4, c+8 in j-range
+// order) into F, tau, the per-molecule energies and the partner count; then
+// lanes 0-2 form the kinetic energies of component c (and, for RED_LAMBDA /
+// RED_HALFKICK, after the kick).  RED_EWALD folds the reciprocal-space site
+// forces into F, tau and the molecular virial.  Each lane accumulates its passes
+// in order; the warp's totals of the Q_N step scalars go to blk[u][*].
+template <bool SH>
+__device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, const DevSys &S, const RedIO &io, int mode,
+                                            int u, int U, int lane) {
     const unsigned F = 0xffffffffu, qb = lane & 28;
-    const int N = S.N, c = lane & 3, i = vb * 8 + (lane >> 2);
-    const bool on = i < N;
-    const int ii = on ? i : 0, cc = c < 3 ? c : 2;
-    const int sp = S.species[ii];
+    const int N = S.N, c = lane & 3, cc = c < 3 ? c : 2;
+    const int i_lo = (int)((long long)N * u / U), i_hi = (int)((long long)N * (u + 1) / U);
+    const StateView &sv = io.sv;
+    const int ld = sv.ld;
     double r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    double Fc, Tc;
-    if (mode & RED_SUM) {
-        double a[3] = {0, 0, 0};  // partial values c, c + 4, c + 8
-        for (int p = 0; p < S.jsplit; ++p)
+    for (int base = i_lo; base < i_hi; base += 8) {
+        const int i = base + (lane >> 2);
+        const bool on = i < i_hi;
+        const int ii = on ? i : i_lo, m = ii - io.i0;
+        const int sp = S.species[ii];
+        double x[Q_N] = {0, 0, 0, 0, 0, 0};
+        double Fc, Tc;
+        if (mode & RED_SUM) {
+            double a[3] = {0, 0, 0};  // partial values c, c + 4, c + 8
+            for (int p = 0; p < S.jsplit; ++p)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const size_t o = ((size_t)p * MS2_NPV + c + 4 * k) * io.pld + m;
+                    a[k] += (mode & RED_FP64PART) ? ldv<SH>(io.part64 + o) : f2d(ldv<SH>(io.part + o));
+                }
+            // value v sits in lane v % 4, slot v / 4
+            auto val = [&](int v) { return __shfl_sync(F, a[v >> 2], qb | (v & 3)); };
+            const double fx = val(PV_FX), fy = val(PV_FY), fz = val(PV_FZ);
+            const double tx = val(PV_TX), ty = val(PV_TY), tz = val(PV_TZ);
+            const double ulj = val(PV_ULJ), uqq = val(PV_UQQ), udd = val(PV_UDD), w = val(PV_W), np = val(PV_NP);
+            Fc = c == 0 ? fx : (c == 1 ? fy : fz);
+            Tc = c == 0 ? tx : (c == 1 ? ty : tz);
+            x[Q_U] = c == 0 ? ulj + uqq + udd : 0.0;
+            x[Q_W] = c == 0 ? w : 0.0;
+            if (!SH && (mode & RED_EWALD)) {  // reciprocal-space site forces, summed over k chunks (global layout)
+                const int NS = S.ns, M = S.nsite_q, c1 = (cc + 1) % 3, c2 = (cc + 2) % 3;
+                double wc = 0;  // -F_s.s_s molecular-virial correction, component c
+                for (int a2 = 0; a2 < NS; ++a2) {
+                    double f = 0;
+                    for (int ch = 0; ch < S.kchunks; ++ch)
+                        f += f2d(__ldcg(S.frec + ((size_t)ch * 3 + cc) * M + a2 * N + ii));
+                    const double f1 = __shfl_sync(F, f, qb | c1), f2 = __shfl_sync(F, f, qb | c2);
+                    const double o1 = f2d(S.s[(c1 * NS + a2) * N + ii]), o2 = f2d(S.s[(c2 * NS + a2) * N + ii]);
+                    const double oc = f2d(S.s[(cc * NS + a2) * N + ii]);
+                    Fc += f;
+                    Tc += o1 * f2 - o2 * f1;
+                    wc += oc * f;
+                }
+                if (c == 3) wc = 0.0;
+                x[Q_W] += -2.0 * wc;  // pair virial sums are halved at the end
+                const double w0 = __shfl_sync(F, wc, qb), w1 = __shfl_sync(F, wc, qb | 1), w2 = __shfl_sync(F, wc, qb | 2);
+                if (c == 0 && on) S.wcorr[i] = w0 + w1 + w2;  // per molecule, for the on-demand breakdown
+            }
+            if (on) {
+                if (c < 3) {
+                    sv.F[c * ld + m] = Fc;
+                    sv.tau[c * ld + m] = Tc;
+                }
+                const double uk = c == 0 ? ulj : (c == 1 ? uqq : (c == 2 ? udd : w));
+                io.Ui[c * io.uld + m] = uk;
+                if (c == 0) io.np[m] = (int)np;
+            }
+            const unsigned hiF = (unsigned)__double2hiint(Fc) & 0x7FF00000u;  // |F| >= 2^99, inf or nan
+            x[Q_BAD] = (c < 3 && hiF >= ((1023u + 99u) << 20)) ? 1.0 : 0.0;
+        } else {
+            Fc = ldv<SH>(sv.F + cc * ld + m);
+            Tc = ldv<SH>(sv.tau + cc * ld + m);
+        }
+        // kinetic energies: lane c takes component c of v and body component c of L.
+        // The state may have been written by another block of a persistent kernel: L2 loads.
+        {
+            const double M = P->mass[sp], Ii = P->Iinv[sp][cc];
+            const double q[4] = {ldv<SH>(sv.q + m), ldv<SH>(sv.q + ld + m), ldv<SH>(sv.q + 2 * ld + m),
+                                 ldv<SH>(sv.q + 3 * ld + m)};
+            double col[3], L[3], tq[3];
+            rot_column(q, cc, col);
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const size_t o = ((size_t)p * MS2_NPV + c + 4 * k) * N + ii;
-                a[k] += (mode & RED_FP64PART) ? __ldcg(S.part64 + o) : f2d(__ldcg(S.part + o));
+                L[k] = ldv<SH>(sv.L + k * ld + m);
+                tq[k] = __shfl_sync(F, Tc, qb | k);
             }
-        // value v sits in lane v % 4, slot v / 4
-        auto val = [&](int v) { return __shfl_sync(F, a[v >> 2], qb | (v & 3)); };
-        const double fx = val(PV_FX), fy = val(PV_FY), fz = val(PV_FZ);
-        const double tx = val(PV_TX), ty = val(PV_TY), tz = val(PV_TZ);
-        const double ulj = val(PV_ULJ), uqq = val(PV_UQQ), udd = val(PV_UDD), w = val(PV_W), np = val(PV_NP);
-        Fc = c == 0 ? fx : (c == 1 ? fy : fz);
-        Tc = c == 0 ? tx : (c == 1 ? ty : tz);
-        r[Q_U] = c == 0 ? ulj + uqq + udd : 0.0;
-        r[Q_W] = c == 0 ? w : 0.0;
-        if (mode & RED_EWALD) {  // reciprocal-space site forces, summed over k chunks
-            const int NS = S.ns, M = S.nsite_q, c1 = (cc + 1) % 3, c2 = (cc + 2) % 3;
-            double wc = 0;  // -F_s.s_s molecular-virial correction, component c
-            for (int a = 0; a < NS; ++a) {
-                double f = 0;
-                for (int ch = 0; ch < S.kchunks; ++ch) f += f2d(__ldcg(S.frec + ((size_t)ch * 3 + cc) * M + a * N + ii));
-                const double f1 = __shfl_sync(F, f, qb | c1), f2 = __shfl_sync(F, f, qb | c2);
-                const double o1 = f2d(S.s[(c1 * NS + a) * N + ii]), o2 = f2d(S.s[(c2 * NS + a) * N + ii]);
-                const double oc = f2d(S.s[(cc * NS + a) * N + ii]);
-                Fc += f;
-                Tc += o1 * f2 - o2 * f1;
-                wc += oc * f;
-            }
-            if (c == 3) wc = 0.0;
-            r[Q_W] += -2.0 * wc;  // pair virial sums are halved at the end
-            const double w0 = __shfl_sync(F, wc, qb), w1 = __shfl_sync(F, wc, qb | 1), w2 = __shfl_sync(F, wc, qb | 2);
-            if (c == 0 && on) S.wcorr[i] = w0 + w1 + w2;  // per molecule, for the on-demand breakdown
-        }
-        if (on) {
+            double v = ldv<SH>(sv.v + cc * ld + m);
+            const double lb = col[0] * L[0] + col[1] * L[1] + col[2] * L[2];
             if (c < 3) {
-                S.F[c * N + i] = Fc;
-                S.tau[c * N + i] = Tc;
+                x[Q_KTR] = 0.5 * M * v * v;
+                x[Q_KROT] = 0.5 * Ii * lb * lb;
             }
-            const double uk = c == 0 ? ulj : (c == 1 ? uqq : (c == 2 ? udd : w));
-            S.Ui[c * N + i] = uk;
-            if (c == 0) S.npart[i] = (int)np;
-        }
-        const unsigned hiF = (unsigned)__double2hiint(Fc) & 0x7FF00000u;  // |F| >= 2^99, inf or nan
-        r[Q_BAD] = (c < 3 && hiF >= ((1023u + 99u) << 20)) ? 1.0 : 0.0;
-    } else {
-        Fc = __ldcg(S.F + cc * N + ii);
-        Tc = __ldcg(S.tau + cc * N + ii);
-    }
-    // kinetic energies: lane c takes component c of v and body component c of L
-    {
-        // state written by another block's drift in the persistent step kernel: L2 loads
-        const double M = P->mass[sp], Ii = P->Iinv[sp][cc];
-        const double q[4] = {__ldcg(S.q + ii), __ldcg(S.q + N + ii), __ldcg(S.q + 2 * N + ii), __ldcg(S.q + 3 * N + ii)};
-        double col[3], L[3], tq[3];
-        rot_column(q, cc, col);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            L[k] = __ldcg(S.Lm + k * N + ii);
-            tq[k] = __shfl_sync(F, Tc, qb | k);
-        }
-        double v = __ldcg(S.v + cc * N + ii);
-        const double lb = col[0] * L[0] + col[1] * L[1] + col[2] * L[2];
-        if (c < 3) {
-            r[Q_KTR] = 0.5 * M * v * v;
-            r[Q_KROT] = 0.5 * Ii * lb * lb;
-        }
-        if (mode & (RED_LAMBDA | RED_HALFKICK)) {
-            const double h = (mode & RED_HALFKICK) ? 0.5 * P->dt : P->dt;
-            const double ct = h * P->kconv;
-            v += ct * P->inv_mass[sp] * Fc;
-            const double lb1 = lb + ct * (col[0] * tq[0] + col[1] * tq[1] + col[2] * tq[2]);
-            if (c < 3) r[Q_K1] = 0.5 * M * v * v + 0.5 * Ii * lb1 * lb1;
-            if (mode & RED_HALFKICK) {  // Verlet: velocities at t + dt, recorded
-                if (on && c < 3) S.v[c * N + i] = v;
-                if (c < 3) r[Q_KTR] = 0.5 * M * v * v;
+            if (mode & (RED_LAMBDA | RED_HALFKICK)) {
+                const double h = (mode & RED_HALFKICK) ? 0.5 * P->dt : P->dt;
+                const double ct = h * P->kconv;
+                v += ct * P->inv_mass[sp] * Fc;
+                const double lb1 = lb + ct * (col[0] * tq[0] + col[1] * tq[1] + col[2] * tq[2]);
+                if (c < 3) x[Q_K1] = 0.5 * M * v * v + 0.5 * Ii * lb1 * lb1;
+                if (mode & RED_HALFKICK) {  // Verlet: velocities at t + dt, recorded
+                    if (on && c < 3) sv.v[c * ld + m] = v;
+                    if (c < 3) x[Q_KTR] = 0.5 * M * v * v;
+                }
             }
         }
-    }
-    if (!on)
+        if (on)
 #pragma unroll
-        for (int k = 0; k < 8; ++k) r[k] = 0.0;
+            for (int k = 0; k < Q_N; ++k) r[k] += x[k];
+    }
     const double t = warp_sum8(r, lane);
     const int k = (lane >> 2) & 7;
-    if ((lane & 3) == 0 && k < Q_N) {
-        S.blk[(size_t)vb * MS2_NRED + k] = t;
-        __threadfence();
-    }
+    if ((lane & 3) == 0 && k < Q_N) S.blk[(size_t)u * MS2_NRED + k] = t;
 }
 
 // Totals of the step scalars over the reduction units, fixed order: warp w

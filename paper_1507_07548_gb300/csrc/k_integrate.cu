@@ -23,7 +23,7 @@ __global__ void k_build(const SysParams *__restrict__ P, DevSys S) {
     if (i >= S.N || c == 3) return;
     const int N = S.N;
     const double q[4] = {S.q[i], S.q[N + i], S.q[2 * N + i], S.q[3 * N + i]};
-    build_row(P, S, i, c, q);
+    build_row(P, S, i, c, q, S.R[c * N + i]);
 }
 
 // Sums the pair partials (and Ewald site forces) into F, tau and per-molecule
@@ -31,11 +31,11 @@ __global__ void k_build(const SysParams *__restrict__ P, DevSys S) {
 // (RED_LAMBDA): also the kinetic energy the velocities will have after the kick
 // with these forces, hence the thermostat factor the next drift applies.
 // Verlet (RED_HALFKICK): applies the second half kick.  One warp per reduction
-// unit of 8 molecules (a quad each), 4 units per block; the last block sums the
-// units in fixed order and finishes the step.
+// unit (a contiguous molecule range, a quad per molecule), 4 units per block;
+// the last block sums the units in fixed order and finishes the step.
 __global__ void __launch_bounds__(128) k_reduce(const SysParams *__restrict__ P, DevSys S, int mode) {
-    const int lane = threadIdx.x & 31, vb = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (vb < S.nvb) reduce_unit(P, S, mode, vb, lane);
+    const int lane = threadIdx.x & 31, u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (u < S.nunits) reduce_unit<false>(P, S, global_io(S), mode, u, S.nunits, lane);
     __shared__ bool last;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(128) k_reduce(const SysParams *__restrict__ P,
     if (!last) return;
     __threadfence();
     __shared__ double tot[MS2_NRED];
-    reduce_totals(S, S.nvb, tot);
+    reduce_totals(S, S.nunits, tot);
     __syncthreads();
     if (threadIdx.x == 0) {
         finish_step(P, S, mode, tot);
@@ -82,5 +82,5 @@ __global__ void k_terms(const SysParams *__restrict__ P, DevSys S, double *out) 
 __global__ void __launch_bounds__(128) k_drift(const SysParams *__restrict__ P, DevSys S, int verlet) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x, i = t >> 2;
     const double lam = verlet ? 1.0 : S.scal[SC_LAMBDA];
-    drift_quad(P, S, i, i < S.N, t & 3, verlet != 0, lam);
+    drift_quad<false>(P, S, global_view(S), i, i, i < S.N, t & 3, verlet != 0, lam);
 }

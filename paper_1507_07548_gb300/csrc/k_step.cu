@@ -2,25 +2,32 @@
 // 512 threads per SM, runs a whole chunk of leapfrog steps (paper, Sec. "Hybrid
 // MPI & OpenMP Parallelization": the partner search, energy and force loops over
 // molecules; the rigid-body leapfrog with isokinetic scaling and the thermo
-// reduction as in k_integrate.cu).  Per step:
+// reduction as in k_integrate.cu).
 //
-//   drift + site build   (molecules spread over all blocks, a quad each)
+// Block b owns the molecules [N b / G, N (b+1) / G) for the whole launch; their
+// FP64 state (R, v, q, L, F, tau) stays in its shared memory and goes back to
+// global memory at the end.  Per step:
+//
+//   stage the whole system's lattice coordinates and site offsets in shared
+//   memory; pair items (own molecule i, j-range p), one per warp; every
+//   'rdf_every' steps the RDF; the partials stay in shared memory
+//   reduction unit b (the own molecules, one warp): F, tau, energies, kinetic
+//   energies; its totals to global memory
 //   -- grid barrier --
-//   stage the whole system in shared memory; pair items (molecule i, j-range p)
-//   spread over all warps of the grid; every 'rdf_every' steps the RDF
+//   every block sums the G units in fixed order and derives the thermostat
+//   factor itself; drift and site build of the own molecules; their lattice
+//   coordinates and offsets to global memory (block 0 records the step during
+//   the next pair phase, on a warp without a pair item)
 //   -- grid barrier --
-//   reduction units (8 molecules per warp): F, tau, energies, kinetic energies
-//   -- grid barrier --
-//   every block sums the units in fixed order and derives the thermostat
-//   factor itself; block 0 records the step scalars.
 //
 // The phases are the device functions of the per-phase kernels (drift_quad,
-// PairWarp, reduce_unit, reduce_totals, finish_step) on the same work
-// decomposition (j-ranges, tile segmentation, reduction units), so a chunk run
-// here is bitwise identical to the same chunk run as separate kernels.  What the
-// fusion saves is the kernel boundaries (a launch costs ~2 us, a bounded grid
-// barrier ~1.2 us on GB300), the last-block tail of the reduction and the
-// re-staging of tiles per block.
+// PairWarp, reduce_unit, reduce_totals, finish_step) and the per-phase path of a
+// fusable system uses the same decomposition (j-ranges, tile segmentation,
+// reduction units = the G block ranges), so a chunk run here is bitwise
+// identical to the same chunk run as separate kernels.  What the fusion saves
+// is the kernel boundaries (a launch costs ~5 us event to event, a bounded grid
+// barrier ~1.2 us on GB300), the state round trips through L2 and the last-block
+// tail of the reduction.
 //
 // Every grid-barrier wait is bounded (2 s of %globaltimer).  A block that gives
 // up sets a sticky flag that ends every other wait at once and marks the system
@@ -57,12 +64,14 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // monotone-counter grid barrier: the k-th barrier of a launch waits for
-// count >= k * gridDim.x
+// count >= k * gridDim.x.  Ordering: the block's writes happen before thread 0's
+// arrival (bar.sync), which is a gpu-scope release; thread 0's polling load is a
+// gpu-scope acquire, and the closing bar.sync orders the block's later reads
+// after it (release/acquire are cumulative in the PTX memory model).
 __device__ __forceinline__ void grid_sync(unsigned *count, unsigned *err, unsigned &target, double *scal) {
     __syncthreads();
     target += gridDim.x;
     if (threadIdx.x == 0) {
-        __threadfence();
         red_release_u32(count, 1u);
         const unsigned long long t0 = global_ns();
         while (ld_acquire_u32(count) < target) {
@@ -73,7 +82,6 @@ __device__ __forceinline__ void grid_sync(unsigned *count, unsigned *err, unsign
                 break;
             }
         }
-        __threadfence();
     }
     __syncthreads();
 }
@@ -123,97 +131,184 @@ __device__ void rdf_tile(const SysParams *__restrict__ P, const DevSys &S, const
 
 }  // namespace
 
+// per-block region after the staged system: own state and partials
+struct OwnLayout {
+    size_t state, ui, np, part, hist, end;  // byte offsets from the region start
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline OwnLayout own_layout(int mcap, int js, int rdf_cells) {
+    OwnLayout o;
+    o.state = 0;                                                      // 19 doubles per slot
+    o.ui = al16(o.state + sizeof(double) * 19 * (size_t)mcap);        // 4 doubles per slot
+    o.np = al16(o.ui + sizeof(double) * 4 * (size_t)mcap);            // 1 int per slot
+    o.part = al16(o.np + sizeof(int) * (size_t)mcap);                 // [js][NPV][mcap] floats
+    o.hist = al16(o.part + sizeof(float) * MS2_NPV * (size_t)js * mcap);
+    o.end = al16(o.hist + sizeof(unsigned) * (size_t)rdf_cells);
+    return o;
+}
+
 template <int NS, unsigned LJM, unsigned QM, unsigned DM, int ELEC, bool MULTI>
 __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__restrict__ P, DevSys S, StepArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using Eng = PairWarp<NS, LJM, QM, DM, ELEC, MULTI>;
     __shared__ double tot[MS2_NRED];
-    __shared__ double lam_s;
-    const int N = S.N, G = gridDim.x, b = blockIdx.x, JS = S.jsplit;
+    __shared__ double lam_s;                    // thermostat factor for the next drift
+    __shared__ unsigned long long tph[6];       // timing: entry, then the phase marks of the last step
+    const int N = S.N, G = gridDim.x, b = blockIdx.x, JS = S.jsplit, MC = A.mcap;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lo = (int)((long long)N * b / G), hi = (int)((long long)N * (b + 1) / G), nm = hi - lo;
     Smem sm = carve<NS, Eng::DMU, MULTI>(smem_raw, A.Np, STEP_WARPS);
-    unsigned *hist = (unsigned *)(smem_raw + ((smem_bytes(NS, Eng::DMU, MULTI, A.Np, STEP_WARPS) + 15) & ~(size_t)15));
+    unsigned char *own = smem_raw + al16(smem_bytes(NS, Eng::DMU, MULTI, A.Np, STEP_WARPS));
+    // the own region's arrays, rebuilt where needed (short live ranges: the
+    // pair loop keeps its registers)
+    auto view = [&]() {
+        double *st = (double *)(own + own_layout(MC, JS, 0).state);
+        return StateView{st, st + 3 * MC, st + 6 * MC, st + 10 * MC, st + 13 * MC, st + 16 * MC, MC};
+    };
+    auto part_at = [&]() { return (float *)(own + own_layout(MC, JS, 0).part); };
     int *wq = sm.queue + warp * 64;
+    // own state into shared memory
+    for (int t = threadIdx.x; t < nm; t += blockDim.x) {
+        const StateView sv = view();
+        const int i = lo + t;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            sv.R[c * MC + t] = __ldcg(S.R + c * N + i);
+            sv.v[c * MC + t] = __ldcg(S.v + c * N + i);
+            sv.L[c * MC + t] = __ldcg(S.Lm + c * N + i);
+            sv.F[c * MC + t] = __ldcg(S.F + c * N + i);
+            sv.tau[c * MC + t] = __ldcg(S.tau + c * N + i);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sv.q[c * MC + t] = __ldcg(S.q + c * N + i);
+    }
     load_tables<MULTI>(P, sm);
     Eng e;
     e.setup(P);
     if (b == 0 && threadIdx.x == 0) *A.bar_next = 0u;
     unsigned target = 0;
-    double lam = __ldcg(S.scal + SC_LAMBDA);
-    // drift share of this block: molecules [lo, hi), by warps 1.. (warp 0 of
-    // block 0 records the previous step meanwhile)
-    const int lo = (int)((long long)N * b / G), hi = (int)((long long)N * (b + 1) / G);
     const bool rfq = Eng::MOLD && e.rfq;
-    const int nitems = N * JS;
-    const unsigned long long t_entry = (A.timing && b == 0 && threadIdx.x == 0) ? global_ns() : 0ull;
-    unsigned long long t_ph[5] = {0, 0, 0, 0, 0};
+    const bool rec = A.timing && b == 0 && threadIdx.x == 0;
+    // timing of the last step: every block marks the end of its compute phases
+    auto mark = [&](int k, int slot) {
+        if (A.timing && k == A.nsteps - 1) {  // uniform over the grid
+            __syncthreads();
+            if (threadIdx.x == 0) atomicMax(A.tmax + slot, global_ns());
+        }
+    };
+    if (threadIdx.x == 0) {
+        lam_s = __ldcg(S.scal + SC_LAMBDA);
+        if (rec) tph[5] = global_ns();
+    }
+    __syncthreads();
     for (int k = 0; k < A.nsteps; ++k) {
-        if (A.timing && b == 0 && threadIdx.x == 0 && k == A.nsteps - 1) t_ph[0] = global_ns();
-        // ---- drift + site build
+        const bool tm = rec && k == A.nsteps - 1;
+        if (tm) tph[0] = global_ns();
+        // ---- drift + site build of the own molecules
         if (warp >= 1)
-            for (int m0 = lo + 8 * (warp - 1); m0 < hi; m0 += 8 * (STEP_WARPS - 1)) {
-                const int i = m0 + (lane >> 2);
-                drift_quad(P, S, i, i < hi, lane & 3, false, lam);
+            for (int m0 = 8 * (warp - 1); m0 < nm; m0 += 8 * (STEP_WARPS - 1)) {
+                const int m = m0 + (lane >> 2);
+                drift_quad<true>(P, S, view(), m, lo + m, m < nm, lane & 3, false, lam_s);
             }
+        mark(k, 0);
         grid_sync(A.bar, A.err, target, S.scal);
-        const bool tm = A.timing && b == 0 && threadIdx.x == 0 && k == A.nsteps - 1;
-        const unsigned long long tp0 = tm ? global_ns() : 0ull;
-        if (tm) t_ph[1] = tp0;
-        // ---- stage the whole system, pair items, RDF
+        if (tm) tph[1] = global_ns();
+        // ---- stage the whole system; pair items of the own molecules; RDF
         stage_tile<NS, Eng::DMU, MULTI>(sm, S, 0, N, A.Np, rfq);
         __syncthreads();
-        for (int it = b + G * warp; it < nitems; it += G * STEP_WARPS) {
-            const int i = it % N, p = it / N;
+        // the previous step's record (U, W, T, P, averages), off the critical
+        // path: block 0's last warp, which has no pair item unless 16 are due
+        if (k > 0 && b == 0 && threadIdx.x == STEP_THREADS - 32)
+            finish_step(P, S, RED_SUM | RED_RECORD | RED_LAMBDA, tot);
+        for (int t = warp; t < nm * JS; t += STEP_WARPS) {
+            const int m = t % nm, p = t / nm, i = lo + m;
             const int j0 = (int)(((long long)N * p) / JS), j1 = (int)(((long long)N * (p + 1)) / JS);
             e.begin_tile(P, sm, A.Np, i);
             for (int t0 = j0; t0 < j1; t0 += A.TJ) e.scan(shifted(sm, t0), A.Np, t0, min(A.TJ, j1 - t0), wq, lane);
             const PairOut o = e.finish(lane);
             if (lane == 0) {
-                float *q = S.part + (size_t)p * MS2_NPV * N + i;
-                q[PV_FX * N] = o.F[0]; q[PV_FY * N] = o.F[1]; q[PV_FZ * N] = o.F[2];
-                q[PV_TX * N] = o.T[0]; q[PV_TY * N] = o.T[1]; q[PV_TZ * N] = o.T[2];
-                q[PV_ULJ * N] = o.ulj; q[PV_UQQ * N] = o.uqq; q[PV_UDD * N] = o.udd; q[PV_W * N] = o.w;
-                q[PV_NP * N] = (float)o.np;
+                float *q = part_at() + (size_t)p * MS2_NPV * MC + m;
+                q[PV_FX * MC] = o.F[0]; q[PV_FY * MC] = o.F[1]; q[PV_FZ * MC] = o.F[2];
+                q[PV_TX * MC] = o.T[0]; q[PV_TY * MC] = o.T[1]; q[PV_TZ * MC] = o.T[2];
+                q[PV_ULJ * MC] = o.ulj; q[PV_UQQ * MC] = o.uqq; q[PV_UDD * MC] = o.udd; q[PV_W * MC] = o.w;
+                q[PV_NP * MC] = (float)o.np;
             }
         }
         if (A.rdf_every > 0 && ((A.s0 + k + 1) % A.rdf_every) == 0) {
             __syncthreads();
-            rdf_tile<NS, MULTI>(P, S, sm, A.Np, hist);
+            rdf_tile<NS, MULTI>(P, S, sm, A.Np, (unsigned *)(own + own_layout(MC, JS, 0).hist));
         }
-        grid_sync(A.bar, A.err, target, S.scal);
+        __syncthreads();
+        mark(k, 1);
         if (tm) {
-            t_ph[2] = global_ns();
-            S.scal[SC_TPAIR] = (double)(t_ph[2] - tp0);
+            tph[2] = global_ns();
+            S.scal[SC_TPAIR] = (double)(tph[2] - tph[1]);
         }
-        // ---- reduction units
-        for (int vb = b + G * warp; vb < S.nvb; vb += G * STEP_WARPS)
-            reduce_unit(P, S, RED_SUM | RED_LAMBDA, vb, lane);
+        // ---- reduction unit b: the own molecules
+        if (warp == 0) {
+            const OwnLayout ol = own_layout(MC, JS, 0);
+            const RedIO io{part_at(), nullptr, MC, view(), (double *)(own + ol.ui), (int *)(own + ol.np), MC, lo};
+            reduce_unit<true>(P, S, io, RED_SUM | RED_LAMBDA, b, G, lane);
+        }
+        mark(k, 2);
         grid_sync(A.bar, A.err, target, S.scal);
-        if (tm) t_ph[3] = global_ns();
+        if (tm) tph[3] = global_ns();
         // ---- totals in every block; thermostat factor for the next drift
-        reduce_totals(S, S.nvb, tot);
+        reduce_totals(S, G, tot);
         __syncthreads();
         if (threadIdx.x == 0) lam_s = lambda_of(P, tot);
         __syncthreads();
-        lam = lam_s;
-        if (b == 0 && threadIdx.x == 0) finish_step(P, S, RED_SUM | RED_RECORD | RED_LAMBDA, tot);
         if (tm) {
-            t_ph[4] = global_ns();
-            S.scal[SC_TPH0] = (double)(t_ph[1] - t_ph[0]);  // drift + site build + barrier
-            S.scal[SC_TPH1] = (double)(t_ph[2] - t_ph[1]);  // staging + pair + RDF + barrier
-            S.scal[SC_TPH2] = (double)(t_ph[3] - t_ph[2]);  // reduction units + barrier
-            S.scal[SC_TPH3] = (double)(t_ph[4] - t_ph[3]);  // totals, thermostat factor, step record
-            S.scal[SC_TPH4] = (double)(t_ph[0] - t_entry);  // kernel entry to the last step
+            const unsigned long long t4 = global_ns();
+            const unsigned long long m0 = __ldcg(A.tmax), m1 = __ldcg(A.tmax + 1), m2 = __ldcg(A.tmax + 2);
+            S.scal[SC_TPH0] = (double)(m0 - tph[0]);     // drift + site build (slowest block)
+            S.scal[SC_TPH1] = (double)(tph[1] - m0);     // grid barrier after it
+            S.scal[SC_TPH2] = (double)(m1 - tph[1]);     // staging + pair + RDF (slowest block)
+            S.scal[SC_TPH3] = (double)(m2 - m1);         // unit reduction (slowest block)
+            S.scal[SC_TPH4] = (double)(tph[3] - m2);     // grid barrier after it
+            S.scal[SC_TPH5] = (double)(t4 - tph[3]);     // totals and thermostat factor (block 0)
+            S.scal[SC_TPH6] = (double)(tph[0] - tph[5]); // kernel entry to the last step
+            S.scal[SC_TPH7] = (double)(t4 - tph[0]);     // the last step
+            // every mark of this step came before the last barrier: zero for the next launch
+            A.tmax[0] = A.tmax[1] = A.tmax[2] = 0ull;
         }
+    }
+    // ---- the last step's record; own state, forces and per-molecule results
+    // back to global memory
+    if (A.nsteps > 0 && b == 0 && threadIdx.x == 0) finish_step(P, S, RED_SUM | RED_RECORD | RED_LAMBDA, tot);
+    __syncthreads();
+    const OwnLayout ol = own_layout(MC, JS, 0);
+    const double *ui_s = (const double *)(own + ol.ui);
+    const int *np_s = (const int *)(own + ol.np);
+    for (int t = threadIdx.x; t < nm; t += blockDim.x) {
+        const StateView sv = view();
+        const int i = lo + t;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            S.R[c * N + i] = sv.R[c * MC + t];
+            S.v[c * N + i] = sv.v[c * MC + t];
+            S.Lm[c * N + i] = sv.L[c * MC + t];
+            S.F[c * N + i] = sv.F[c * MC + t];
+            S.tau[c * N + i] = sv.tau[c * MC + t];
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            S.q[c * N + i] = sv.q[c * MC + t];
+            S.Ui[c * N + i] = ui_s[c * MC + t];
+        }
+        S.npart[i] = np_s[t];
     }
 }
 
 // ------------------------------------------------------------ host side
 // shared memory of the fused step: the staged system, the partner queues of 16
-// warps, the parameter tables and an RDF histogram of rdf_cells counters
-size_t ms2_step_smem_bytes(int NS, bool dmu, bool multi, int Np, int rdf_cells) {
-    return ((pair_engine::smem_bytes(NS, dmu, multi, Np, STEP_WARPS) + 15) & ~(size_t)15) +
-           sizeof(unsigned) * (size_t)rdf_cells;
+// warps, the parameter tables, then the own region (state and partials of at
+// most mcap molecules, j-split js) and an RDF histogram of rdf_cells counters
+size_t ms2_step_smem_bytes(int NS, bool dmu, bool multi, int Np, int mcap, int js, int rdf_cells) {
+    const size_t own = own_layout(mcap, js, 0).hist;
+    return al16(pair_engine::smem_bytes(NS, dmu, multi, Np, STEP_WARPS)) + own + sizeof(unsigned) * (size_t)rdf_cells;
 }
 
 int ms2_step_threads() { return STEP_THREADS; }

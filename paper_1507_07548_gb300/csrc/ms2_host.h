@@ -44,7 +44,8 @@ struct ms2_system_s {
     int tune_wpb = 0, tune_jsplit = 0;
     // fused step (k_step.cu): null when the per-phase kernels run every step
     void *step_fn = nullptr;
-    int step_grid = 0, Np = 0, bar_parity = 0;
+    void *fuse_fn = nullptr;  // the variant when the system is fusable (decides the decomposition)
+    int step_grid = 0, Np = 0, bar_parity = 0, mcap = 0, nunits = 1;
     size_t step_smem_max = 0;
     int last_launch_steps = 0;
     bool last_fused = false;
@@ -77,7 +78,7 @@ void ms2_unit_constants(bool reduced, double *coulomb, double *kconv);
 ms2_status ms2_eval_forces(ms2_system s);
 ms2_status ms2_validate_models(const ms2_model *models, int n_models, ms2_elec elec);
 // fused step kernel (k_step.cu)
-size_t ms2_step_smem_bytes(int NS, bool dmu, bool multi, int Np, int rdf_cells);
+size_t ms2_step_smem_bytes(int NS, bool dmu, bool multi, int Np, int mcap, int js, int rdf_cells);
 int ms2_step_threads();
 void *ms2_pick_step_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi);
 cudaError_t ms2_launch_step(void *fn, int grid, size_t smem, cudaStream_t st, const SysParams *P, const DevSys &S,

@@ -63,7 +63,7 @@ struct SysParams {
 
 // Device pointers of one system.
 struct DevSys {
-    int N, ns, jsplit, nvb;  // nvb: reduction units of 8 molecules
+    int N, ns, jsplit, nunits;  // nunits: reduction units (contiguous molecule ranges)
     double *R, *v, *q, *Lm;           // FP64 state
     int *species;
     uint32_t *X;                       // [3][N]
@@ -101,7 +101,7 @@ enum {
     SC_UREC, SC_WREC_AT, SC_WREC_CORR, SC_UCONST, SC_PLRC, SC_ULRC, SC_WBG, SC_UNSTABLE,
     SC_UTOT, SC_WTOT, SC_P, SC_T, SC_KETR_NOW, SC_KEROT_NOW, SC_STEP,
     SC_TPAIR,  // fused step: pair-phase time of the last step of a chunk (ns)
-    SC_TPH0, SC_TPH1, SC_TPH2, SC_TPH3, SC_TPH4,  // fused step: device times (ns) of the last step's phases
+    SC_TPH0, SC_TPH1, SC_TPH2, SC_TPH3, SC_TPH4, SC_TPH5, SC_TPH6, SC_TPH7,  // fused step: phase times (ns)
     SC_KERR,   // fused step: a grid-barrier wait timed out (sticky until read)
     SC_COUNT_
 };
@@ -115,10 +115,12 @@ struct StepArgs {
     int rdf_every;         // 0: no RDF sampling
     int TJ;                // j tile segmentation of the per-phase pair kernel
     int Np;                // stride of the staged system
+    int mcap;              // molecules a block owns at most: ceil(N / gridDim.x)
     unsigned *bar;         // this launch's barrier counter (zero at entry)
     unsigned *bar_next;    // the next launch's counter, zeroed by this launch
     unsigned *err;         // sticky timeout flag
-    int timing;            // record the pair-phase time of the last step (SC_TPAIR, ns)
+    int timing;            // record the phase times of the last step (SC_TPAIR, SC_TPH*, ns)
+    unsigned long long *tmax;  // timing: [3] latest compute-end times over blocks (zero at entry, re-zeroed after use)
 };
 
 // ------------------------------------------------------------ helpers

@@ -160,7 +160,7 @@ extern "C" ms2_status ms2_forces_noalloc(const ms2_model *models, const int *N_p
     d.ns = ns;
     const int wpb = 8, iblocks = (N + wpb - 1) / wpb;
     d.jsplit = std::max(1, std::min(NA_JS, (152 * 2) / std::max(iblocks, 1)));
-    d.nvb = (N + 7) / 8;
+    d.nunits = (N + 7) / 8;
     d.X = (uint32_t *)(base + O_X);
     d.s = (float *)(base + O_S);
     d.mu = hp.has_dipole ? (float *)(base + O_MU) : nullptr;
@@ -207,7 +207,7 @@ extern "C" ms2_status ms2_forces_noalloc(const ms2_model *models, const int *N_p
     k_build<<<(4 * N + 127) / 128, 128, 0, sm>>>(dP, d);
     void (*pair)(const SysParams *, DevSys, int) = (void (*)(const SysParams *, DevSys, int))fn;
     pair<<<dim3(iblocks, d.jsplit), wpb * 32, smem, sm>>>(dP, d, TJ);
-    k_reduce<<<(d.nvb + 3) / 4, 128, 0, sm>>>(dP, d, 1 /* sum the partials only */);
+    k_reduce<<<(d.nunits + 3) / 4, 128, 0, sm>>>(dP, d, 1 /* sum the partials only */);
     k_aos3<<<(N + 127) / 128, 128, 0, sm>>>(d.F, F_dev, N);
     k_aos3<<<(N + 127) / 128, 128, 0, sm>>>(d.tau, tau_dev, N);
     ms2_count_launches(6);

@@ -303,8 +303,9 @@ class System:
         return f.value
 
     def last_step_phases(self):
-        """Fused step, timing on: (drift, pair, reduction, totals, entry-to-last-step) device ms."""
-        out = np.zeros(5)
+        """Fused step, timing on, device ms of the last step: drift, barrier, pair, reduction,
+        barrier, totals, kernel entry to the last step, the whole last step."""
+        out = np.zeros(8)
         check(lib().ms2_last_step_phases(self.h, _dp(out)))
         return out
 
