@@ -269,9 +269,10 @@ MS2_API ms2_status ms2_step_kernel(ms2_system sys, int *fused);
  * the last step of the last chunk: [0] drift and site build, [2] staging, pair
  * and RDF, [3] unit reduction (each until the slowest block is done), [1] and
  * [4] the grid barriers after [0] and [3], [5] totals and thermostat factor,
- * [6] kernel entry to that last step, [7] the whole last step.  MS2_ESTATE if
- * timing is off or the last chunk ran as per-phase kernels. */
-MS2_API ms2_status ms2_last_step_phases(ms2_system sys, double out[8]);
+ * [6] kernel entry to that last step, [7] the whole last step, [8] its end to
+ * the kernel's exit (write-back of the block-held state).  MS2_ESTATE if timing
+ * is off or the last chunk ran as per-phase kernels. */
+MS2_API ms2_status ms2_last_step_phases(ms2_system sys, double out[9]);
 MS2_API ms2_status ms2_last_step_times(ms2_system sys, double out[4]);
 
 /* ------------------------------------------------------- allocation-free */

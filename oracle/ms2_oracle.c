@@ -225,8 +225,14 @@ static int has_dipole(const or_system *s, int sp, int a) {
 /* Interaction of owner molecule i with partner j.  d = centre minimum image
  * R_j - R_i.  Adds to the owner's force F, torque tau, energies u[3]
  * (LJ, charge-charge, dipole-dipole) and returns F_ij (force on i due to j). */
+/* Site-pair sums of molecule pair (i, j), d = minimum-image R_j - R_i: force F and
+ * torque tau on i, energies u[3] (LJ, charge-charge, dipole-dipole), the force
+ * Fij on i from j, and wown += sum_ab (-r_ab.f_ab - 2 s_ia.f_ab): the owner share
+ * of the molecular virial (summed over the partners j of i, and halved, the shares
+ * add up to W = sum_{i<j} (R_i - R_j).F_ij, because the s_jb terms of the pair
+ * virial move to molecule j's sum). */
 static void pair_ij(const or_system *s, int i, int j, const double *Ai, const double *Aj, const double *d,
-                    double *F, double *tau, double *u, double *Fij) {
+                    double *F, double *tau, double *u, double *Fij, double *wown) {
     int si = s->species[i], sj = s->species[j];
     double krf = (s->elec == 1) ? k_rf(s) : 0.0, crf = (s->elec == 1) ? c_rf(s) : 0.0;
     Fij[0] = Fij[1] = Fij[2] = 0;
@@ -284,6 +290,7 @@ static void pair_ij(const or_system *s, int i, int j, const double *Ai, const do
                 Fij[k] += f[k];
                 tau[k] += t[k];
             }
+            *wown += -dot3(r, f) - 2.0 * dot3(oa, f);
         }
     }
 }
@@ -418,8 +425,11 @@ void or_forces(const or_system *s, const double *R, const double *q, double *F, 
     or_forces_mol(s, R, q, F, tau, terms, NULL);
 }
 /* as or_forces; mol (may be NULL) receives per molecule i the shares
- * 1/2 sum_j of the LJ, charge-charge and dipole-dipole pair energies and of the
- * pair virial (N x 4) */
+ * 1/2 sum_j of the LJ, charge-charge and dipole-dipole pair energies and the
+ * owner share of the molecular virial, 1/2 (sum_j sum_ab -r_ab.f_ab
+ * - 2 sum_a s_ia.F_ia) with F_ia the total force on site a (N x 4).  The paper
+ * defines W only as a system total; the shares add up to it (the pair form
+ * sum_j (R_i - R_j).F_ij gives other shares with the same total). */
 void or_forces_mol(const or_system *s, const double *R, const double *q, double *F, double *tau, double *terms,
                    double *mol) {
     int N = s->N;
@@ -429,26 +439,29 @@ void or_forces_mol(const or_system *s, const double *R, const double *q, double 
     double *A = (double *)malloc(sizeof(double) * 9 * N);
     for (int i = 0; i < N; ++i) or_rotation(q + 4 * i, A + 9 * i);
     double *Ui = (double *)calloc(3 * N, sizeof(double)), *Wi = (double *)calloc(N, sizeof(double));
+    double *Wo = (double *)calloc(N, sizeof(double));
     int *np = (int *)calloc(N, sizeof(int));
 #pragma omp parallel for schedule(dynamic, 4)
     for (int i = 0; i < N; ++i) {
-        double f[3] = {0, 0, 0}, t[3] = {0, 0, 0}, u[3] = {0, 0, 0}, w = 0;
+        double f[3] = {0, 0, 0}, t[3] = {0, 0, 0}, u[3] = {0, 0, 0}, w = 0, wo = 0;
         for (int j = 0; j < N; ++j) {
             if (j == i || !(lattice_d2(X + 3 * i, X + 3 * j) < rc2)) continue;
             double d[3], Fij[3];
             min_image(s, R + 3 * i, R + 3 * j, d);
-            pair_ij(s, i, j, A + 9 * i, A + 9 * j, d, f, t, u, Fij);
+            pair_ij(s, i, j, A + 9 * i, A + 9 * j, d, f, t, u, Fij, &wo);
             w += -dot3(d, Fij);
             np[i]++;
         }
         for (int k = 0; k < 3; ++k) { F[3 * i + k] = f[k]; tau[3 * i + k] = t[k]; Ui[3 * i + k] = u[k]; }
         Wi[i] = w;
+        Wo[i] = wo;
     }
     if (mol)
         for (int i = 0; i < N; ++i) {
             for (int k = 0; k < 3; ++k) mol[4 * i + k] = 0.5 * Ui[3 * i + k];
-            mol[4 * i + 3] = 0.5 * Wi[i];
+            mol[4 * i + 3] = 0.5 * Wo[i];
         }
+    free(Wo);
     for (int k = 0; k < OR_NTERMS; ++k) terms[k] = 0;
     long long npairs = 0;
     for (int i = 0; i < N; ++i) {

@@ -84,7 +84,7 @@ __device__ __forceinline__ void batch_drift(const SysParams *__restrict__ P, con
             }
         }
         for (int k = 0; k < 4; ++k) q[k] = __shfl_sync(0xffffffffu, q[k], (threadIdx.x & 28) | 3);
-        if (c < 3 && on) build_row(P, S, i, c, q, S.R[c * N + i]);
+        if (c < 3 && on) build_row(P, S, i, c, q, S.R[c * N + i], S.species[i]);
     }
 }
 

@@ -245,6 +245,13 @@ void ms2_fill_params(SysParams &P, const ms2_model *models, int n_models, const 
     P.inv_V = 1.0 / P.V;
     P.inv_T0 = T0 > 0 ? 1.0 / T0 : 0.0;
     for (int m = 0; m < n_models; ++m) P.inv_mass[m] = 1.0 / P.mass[m];
+    P.dtk = P.dt * P.kconv;
+    for (int m = 0; m < n_models; ++m) {
+        P.kick[m] = P.dtk * P.inv_mass[m];
+        P.half_mass[m] = 0.5 * P.mass[m];
+        for (int k = 0; k < 3; ++k) P.half_Iinv[m][k] = 0.5 * P.Iinv[m][k];
+    }
+    P.lam_c = 2.0 * P.inv_kconv * P.inv_ndof * P.inv_T0;
     P.ns = ns;
     P.n_ljt = t;
     for (int a = 0; a < t; ++a)
@@ -890,13 +897,13 @@ static ms2_status read_scalars(ms2_system s, double *sc) {
     return MS2_OK;
 }
 
-extern "C" ms2_status ms2_last_step_phases(ms2_system s, double out[8]) {
+extern "C" ms2_status ms2_last_step_phases(ms2_system s, double out[9]) {
     if (!s || !out) return ms2_fail(MS2_EINVAL, "null argument");
     if (!s->timing || !s->last_fused) return ms2_fail(MS2_ESTATE, "no timed fused chunk (timing off or per-phase kernels)");
     double sc[SC_COUNT_];
     ms2_status st = read_scalars(s, sc);
     if (st != MS2_OK) return st;
-    for (int k = 0; k < 8; ++k) out[k] = sc[SC_TPH0 + k] * 1e-6;
+    for (int k = 0; k < 9; ++k) out[k] = sc[SC_TPH0 + k] * 1e-6;
     return MS2_OK;
 }
 

@@ -15,7 +15,7 @@ __device__ __forceinline__ double rsqrt_fp64(double x) {  // FP32 seed + two New
 // lattice centre coordinate of component c; row c of the space-frame site
 // offsets, dipoles and molecular charge dipole (lane c of a quad)
 __device__ __forceinline__ void build_row(const SysParams *__restrict__ P, const DevSys &S, int i, int c,
-                                          const double q[4], double Rc) {
+                                          const double q[4], double Rc, int sp) {
     const int N = S.N, NS = S.ns;
     S.X[c * N + i] = lattice_coord(Rc, P->lat_scale);
     // row c of A(q) for the cyclic order (c, c1, c2), with v = (x, y, z):
@@ -28,7 +28,7 @@ __device__ __forceinline__ void build_row(const SysParams *__restrict__ P, const
     const double v2 = c == 0 ? q[3] : (c == 1 ? q[1] : q[2]);
     const int c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
     const double acc = 1.0 - 2.0 * (v1 * v1 + v2 * v2), ac1 = 2.0 * (vc * v1 - w * v2), ac2 = 2.0 * (vc * v2 + w * v1);
-    const int sp = S.species[i], nsp = P->n_sites[sp];
+    const int nsp = P->n_sites[sp];
     double md = 0.0;
     for (int a = 0; a < NS; ++a) {
         double o = 0.0, m = 0.0;
@@ -78,6 +78,46 @@ __device__ __forceinline__ void rotate_q(const double Iinv[3], const double q0[4
     q1[3] = q0[3] + f2d(d3);
     const double inv = rsqrt_fp64(q1[0] * q1[0] + q1[1] * q1[1] + q1[2] * q1[2] + q1[3] * q1[3]);
     for (int k = 0; k < 4; ++k) q1[k] *= inv;
+}
+
+// rotate_q for the 4 lanes of a quad (lane c = component c): the FP32 sweeps run
+// in every lane (identical), the FP64 update and normalisation one component
+// per lane (the norm by a quad shuffle tree whose result is the same in all 4
+// lanes); returns q1[c].  The normalisation 1/|q1| = (1 + e)^-1/2,
+// e = |q1|^2 - 1, takes the series 1 - e/2 + 3e^2/8 - 5e^3/16 + 35e^4/128
+// (error below 63/256 e^5, under 1e-20 for |e| < 1e-4) and rsqrt_fp64 beyond.
+__device__ __forceinline__ double rotate_q_quad(const double Iinv[3], const double q0[4], const double Lsp[3],
+                                                double dt, int iters, int c) {
+    const float a0 = d2f(q0[0]), a1 = d2f(q0[1]), a2 = d2f(q0[2]), a3 = d2f(q0[3]);
+    const float L0 = d2f(Lsp[0]), L1 = d2f(Lsp[1]), L2 = d2f(Lsp[2]);
+    const float I0 = d2f(Iinv[0]), I1 = d2f(Iinv[1]), I2 = d2f(Iinv[2]), h = d2f(0.5 * dt);
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;  // increment q1 - q0
+    for (int it = 0; it < iters; ++it) {
+        const float w = a0 + 0.5f * d0, x = a1 + 0.5f * d1, y = a2 + 0.5f * d2, z = a3 + 0.5f * d3;
+        const float ww = w * w, xx = x * x, yy = y * y, zz = z * z;
+        const float inv = 1.0f / (ww + xx + yy + zz);
+        const float xy = x * y, xz = x * z, yz = y * z, wx = w * x, wy = w * y, wz = w * z;
+        const float lb0 = (ww + xx - yy - zz) * L0 + 2.f * (xy + wz) * L1 + 2.f * (xz - wy) * L2;
+        const float lb1 = 2.f * (xy - wz) * L0 + (ww - xx + yy - zz) * L1 + 2.f * (yz + wx) * L2;
+        const float lb2 = 2.f * (xz + wy) * L0 + 2.f * (yz - wx) * L1 + (ww - xx - yy + zz) * L2;
+        const float o0 = I0 * lb0 * inv, o1 = I1 * lb1 * inv, o2 = I2 * lb2 * inv;
+        d0 = h * (-x * o0 - y * o1 - z * o2);
+        d1 = h * (w * o0 + y * o2 - z * o1);
+        d2 = h * (w * o1 - x * o2 + z * o0);
+        d3 = h * (w * o2 + x * o1 - y * o0);
+    }
+    const float dc = c == 0 ? d0 : (c == 1 ? d1 : (c == 2 ? d2 : d3));
+    const double qc = (c == 0 ? q0[0] : (c == 1 ? q0[1] : (c == 2 ? q0[2] : q0[3]))) + f2d(dc);
+    double n2 = qc * qc;
+    n2 += __shfl_xor_sync(0xffffffffu, n2, 1);
+    n2 += __shfl_xor_sync(0xffffffffu, n2, 2);
+    const double e = n2 - 1.0;
+    double inv;
+    if (fabs(e) < 1e-4)
+        inv = fma(e, fma(e, fma(e, fma(e, 35.0 / 128.0, -5.0 / 16.0), 3.0 / 8.0), -0.5), 1.0);
+    else
+        inv = rsqrt_fp64(n2);
+    return qc * inv;
 }
 
 // column c of A(q): the body component c of a space vector u is column_c . u.
@@ -137,9 +177,9 @@ __device__ __forceinline__ void finish_step(const SysParams *__restrict__ P, con
             ac[AC_BN] = ac[AC_BU] = ac[AC_BP] = 0.0;
         }
     }
-    if (mode & RED_LAMBDA) {  // isokinetic factor sqrt(T0 / T') for the next drift
-        const double x = 2.0 * tot[Q_K1] * ikc * P->inv_ndof * P->inv_T0;
-        sc[SC_LAMBDA] = (P->thermostat && x > 0) ? rsqrt_fp64(x) : 1.0;  // == lambda_of(P, tot)
+    if (mode & RED_LAMBDA) {  // isokinetic factor sqrt(T0 / T') for the next drift (as lambda_of)
+        const double x = P->lam_c * tot[Q_K1];
+        sc[SC_LAMBDA] = (P->thermostat && x > 0) ? rsqrt_fp64(x) : 1.0;
     }
 }
 
@@ -149,6 +189,7 @@ __device__ __forceinline__ void finish_step(const SysParams *__restrict__ P, con
 // molecules in shared memory: ld = its capacity, m = i - first molecule).
 struct StateView {
     double *R, *v, *q, *L, *F, *tau;
+    const int *spc;  // species of each slot
     int ld;
 };
 
@@ -161,7 +202,7 @@ __device__ __forceinline__ T ldv(const T *p) {
 }
 
 __device__ __forceinline__ StateView global_view(const DevSys &S) {
-    return StateView{S.R, S.v, S.q, S.Lm, S.F, S.tau, S.N};
+    return StateView{S.R, S.v, S.q, S.Lm, S.F, S.tau, S.species, S.N};
 }
 
 // Drift of molecule i (state slot m) by the 4 lanes of a quad (c = lane & 3),
@@ -179,8 +220,8 @@ __device__ __forceinline__ StateView global_view(const DevSys &S) {
 template <bool SH>
 __device__ __forceinline__ void drift_quad(const SysParams *__restrict__ P, const DevSys &S, const StateView &sv, int m,
                                            int i, bool on, int c, bool verlet, double lam) {
-    const int ld = sv.ld, mm = on ? m : 0, ii = on ? i : 0, cc = c < 3 ? c : 2;
-    const int sp = S.species[ii];
+    const int ld = sv.ld, mm = on ? m : 0, cc = c < 3 ? c : 2;
+    const int sp = sv.spc[mm];
     const double dt = P->dt;
     const unsigned qb = threadIdx.x & 28u;  // first lane of the quad within the warp
     double q[4] = {sv.q[mm], sv.q[ld + mm], sv.q[2 * ld + mm], sv.q[3 * ld + mm]};
@@ -193,8 +234,8 @@ __device__ __forceinline__ void drift_quad(const SysParams *__restrict__ P, cons
             sv.R[c * ld + m] = Rc;
         }
     } else {
-        const double v = lam * (sv.v[cc * ld + mm] + dt * P->kconv * P->inv_mass[sp] * ldv<SH>(sv.F + cc * ld + mm));
-        const double Lc = lam * (sv.L[cc * ld + mm] + dt * P->kconv * ldv<SH>(sv.tau + cc * ld + mm));
+        const double v = lam * (sv.v[cc * ld + mm] + P->kick[sp] * ldv<SH>(sv.F + cc * ld + mm));
+        const double Lc = lam * (sv.L[cc * ld + mm] + P->dtk * ldv<SH>(sv.tau + cc * ld + mm));
         Rc += dt * v;
         if (c < 3 && on) {
             sv.v[c * ld + m] = v;
@@ -205,15 +246,20 @@ __device__ __forceinline__ void drift_quad(const SysParams *__restrict__ P, cons
 #pragma unroll
         for (int k = 0; k < 3; ++k) L[k] = __shfl_sync(0xffffffffu, Lc, qb | k);
         const double *Ii = P->Iinv[sp];
-        if (Ii[0] != 0.0 || Ii[1] != 0.0 || Ii[2] != 0.0) {
-            double q1[4];
-            rotate_q(Ii, q, L, dt, P->quat_iters, q1);
+        const bool rot = Ii[0] != 0.0 || Ii[1] != 0.0 || Ii[2] != 0.0;
+        // quads of one warp may differ in species: every lane takes the same
+        // shuffles, a non-rotating quad just keeps its quaternion
+        const double q1c = rotate_q_quad(Ii, q, L, dt, rot ? P->quat_iters : 0, c);
+        double qn[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) q[k] = q1[k];
-            if (on) sv.q[c * ld + m] = q1[c];
+        for (int k = 0; k < 4; ++k) qn[k] = __shfl_sync(0xffffffffu, q1c, qb | k);
+        if (rot) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[k] = qn[k];
+            if (on) sv.q[c * ld + m] = q1c;
         }
     }
-    if (c < 3 && on) build_row(P, S, i, c, q, Rc);
+    if (c < 3 && on) build_row(P, S, i, c, q, Rc, sp);
 }
 
 // Fixed-tree sum of 8 values over a warp: 9 FP64 adds instead of 8 x 5.  On
@@ -280,12 +326,17 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
         const int i = base + (lane >> 2);
         const bool on = i < i_hi;
         const int ii = on ? i : i_lo, m = ii - io.i0;
-        const int sp = S.species[ii];
+        const int sp = sv.spc[m];
         double x[Q_N] = {0, 0, 0, 0, 0, 0};
         double Fc, Tc;
         if (mode & RED_SUM) {
-            double a[3] = {0, 0, 0};  // partial values c, c + 4, c + 8
-            for (int p = 0; p < S.jsplit; ++p)
+            double a[3];  // partial values c, c + 4, c + 8, summed in j-range order
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const size_t o = (size_t)(c + 4 * k) * io.pld + m;
+                a[k] = (mode & RED_FP64PART) ? ldv<SH>(io.part64 + o) : f2d(ldv<SH>(io.part + o));
+            }
+            for (int p = 1; p < S.jsplit; ++p)
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const size_t o = ((size_t)p * MS2_NPV + c + 4 * k) * io.pld + m;
@@ -337,7 +388,7 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
         // kinetic energies: lane c takes component c of v and body component c of L.
         // The state may have been written by another block of a persistent kernel: L2 loads.
         {
-            const double M = P->mass[sp], Ii = P->Iinv[sp][cc];
+            const double hM = P->half_mass[sp], hI = P->half_Iinv[sp][cc];
             const double q[4] = {ldv<SH>(sv.q + m), ldv<SH>(sv.q + ld + m), ldv<SH>(sv.q + 2 * ld + m),
                                  ldv<SH>(sv.q + 3 * ld + m)};
             double col[3], L[3], tq[3];
@@ -350,24 +401,26 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
             double v = ldv<SH>(sv.v + cc * ld + m);
             const double lb = col[0] * L[0] + col[1] * L[1] + col[2] * L[2];
             if (c < 3) {
-                x[Q_KTR] = 0.5 * M * v * v;
-                x[Q_KROT] = 0.5 * Ii * lb * lb;
+                x[Q_KTR] = hM * v * v;
+                x[Q_KROT] = hI * lb * lb;
             }
-            if (mode & (RED_LAMBDA | RED_HALFKICK)) {
-                const double h = (mode & RED_HALFKICK) ? 0.5 * P->dt : P->dt;
-                const double ct = h * P->kconv;
-                v += ct * P->inv_mass[sp] * Fc;
-                const double lb1 = lb + ct * (col[0] * tq[0] + col[1] * tq[1] + col[2] * tq[2]);
-                if (c < 3) x[Q_K1] = 0.5 * M * v * v + 0.5 * Ii * lb1 * lb1;
-                if (mode & RED_HALFKICK) {  // Verlet: velocities at t + dt, recorded
-                    if (on && c < 3) sv.v[c * ld + m] = v;
-                    if (c < 3) x[Q_KTR] = 0.5 * M * v * v;
-                }
+            if (mode & RED_HALFKICK) {  // Verlet: velocities at t + dt, recorded
+                v += 0.5 * P->kick[sp] * Fc;
+                if (on && c < 3) sv.v[c * ld + m] = v;
+                if (c < 3) x[Q_KTR] = x[Q_K1] = hM * v * v;
+            } else if (mode & RED_LAMBDA) {  // the kinetic energy after the kick
+                v += P->kick[sp] * Fc;
+                const double lb1 = lb + P->dtk * (col[0] * tq[0] + col[1] * tq[1] + col[2] * tq[2]);
+                if (c < 3) x[Q_K1] = hM * v * v + hI * lb1 * lb1;
             }
         }
-        if (on)
+        if (base == i_lo) {  // first pass: no add
+#pragma unroll
+            for (int k = 0; k < Q_N; ++k) r[k] = on ? x[k] : 0.0;
+        } else if (on) {
 #pragma unroll
             for (int k = 0; k < Q_N; ++k) r[k] += x[k];
+        }
     }
     const double t = warp_sum8(r, lane);
     const int k = (lane >> 2) & 7;
@@ -389,7 +442,7 @@ __device__ __forceinline__ void reduce_totals(const DevSys &S, int nvb, double *
 
 // isokinetic factor sqrt(T0 / T') from the kicked kinetic energy (as finish_step)
 __device__ __forceinline__ double lambda_of(const SysParams *__restrict__ P, const double *tot) {
-    const double x = 2.0 * tot[Q_K1] * P->inv_kconv * P->inv_ndof * P->inv_T0;
+    const double x = P->lam_c * tot[Q_K1];  // T' / T0
     return (P->thermostat && x > 0) ? rsqrt_fp64(x) : 1.0;
 }
 

@@ -23,7 +23,7 @@ __global__ void k_build(const SysParams *__restrict__ P, DevSys S) {
     if (i >= S.N || c == 3) return;
     const int N = S.N;
     const double q[4] = {S.q[i], S.q[N + i], S.q[2 * N + i], S.q[3 * N + i]};
-    build_row(P, S, i, c, q, S.R[c * N + i]);
+    build_row(P, S, i, c, q, S.R[c * N + i], S.species[i]);
 }
 
 // Sums the pair partials (and Ewald site forces) into F, tau and per-molecule

@@ -131,19 +131,23 @@ __device__ void rdf_tile(const SysParams *__restrict__ P, const DevSys &S, const
 
 }  // namespace
 
-// per-block region after the staged system: own state and partials
+static_assert(sizeof(SysParams) % 16 == 0, "the parameter copy moves 16-byte words");
+
+// per-block region after the staged system: parameters, own state and partials
 struct OwnLayout {
-    size_t state, ui, np, part, hist, end;  // byte offsets from the region start
+    size_t params, state, ui, np, sp, part, hist, end;  // byte offsets from the region start
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 __host__ __device__ inline OwnLayout own_layout(int mcap, int js, int rdf_cells) {
     OwnLayout o;
-    o.state = 0;                                                      // 19 doubles per slot
+    o.params = 0;                                                     // a copy of the system parameters
+    o.state = al16(o.params + sizeof(SysParams));                     // 19 doubles per slot
     o.ui = al16(o.state + sizeof(double) * 19 * (size_t)mcap);        // 4 doubles per slot
     o.np = al16(o.ui + sizeof(double) * 4 * (size_t)mcap);            // 1 int per slot
-    o.part = al16(o.np + sizeof(int) * (size_t)mcap);                 // [js][NPV][mcap] floats
+    o.sp = al16(o.np + sizeof(int) * (size_t)mcap);                   // species, 1 int per slot
+    o.part = al16(o.sp + sizeof(int) * (size_t)mcap);                 // [js][NPV][mcap] floats
     o.hist = al16(o.part + sizeof(float) * MS2_NPV * (size_t)js * mcap);
     o.end = al16(o.hist + sizeof(unsigned) * (size_t)rdf_cells);
     return o;
@@ -159,14 +163,20 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     const int N = S.N, G = gridDim.x, b = blockIdx.x, JS = S.jsplit, MC = A.mcap;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lo = (int)((long long)N * b / G), hi = (int)((long long)N * (b + 1) / G), nm = hi - lo;
+    if (A.timing && b == 0 && threadIdx.x == 0) tph[5] = global_ns();  // kernel entry
     Smem sm = carve<NS, Eng::DMU, MULTI>(smem_raw, A.Np, STEP_WARPS);
     unsigned char *own = smem_raw + al16(smem_bytes(NS, Eng::DMU, MULTI, A.Np, STEP_WARPS));
     // the own region's arrays, rebuilt where needed (short live ranges: the
     // pair loop keeps its registers)
     auto view = [&]() {
-        double *st = (double *)(own + own_layout(MC, JS, 0).state);
-        return StateView{st, st + 3 * MC, st + 6 * MC, st + 10 * MC, st + 13 * MC, st + 16 * MC, MC};
+        const OwnLayout l = own_layout(MC, JS, 0);
+        double *st = (double *)(own + l.state);
+        return StateView{st, st + 3 * MC, st + 6 * MC, st + 10 * MC, st + 13 * MC, st + 16 * MC,
+                         (const int *)(own + l.sp), MC};
     };
+    // the system parameters, copied into shared memory once: the per-step phases
+    // then read no parameter through L2 after a grid barrier
+    const SysParams *Ps = (const SysParams *)(own + own_layout(MC, JS, 0).params);
     auto part_at = [&]() { return (float *)(own + own_layout(MC, JS, 0).part); };
     int *wq = sm.queue + warp * 64;
     // own state into shared memory
@@ -183,6 +193,12 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) sv.q[c * MC + t] = __ldcg(S.q + c * N + i);
+        ((int *)sv.spc)[t] = S.species[i];
+    }
+    {
+        const int4 *src = (const int4 *)P;
+        int4 *dst = (int4 *)(own + own_layout(MC, JS, 0).params);
+        for (int k = threadIdx.x; k < (int)(sizeof(SysParams) / sizeof(int4)); k += blockDim.x) dst[k] = src[k];
     }
     load_tables<MULTI>(P, sm);
     Eng e;
@@ -198,10 +214,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
             if (threadIdx.x == 0) atomicMax(A.tmax + slot, global_ns());
         }
     };
-    if (threadIdx.x == 0) {
-        lam_s = __ldcg(S.scal + SC_LAMBDA);
-        if (rec) tph[5] = global_ns();
-    }
+    if (threadIdx.x == 0) lam_s = __ldcg(S.scal + SC_LAMBDA);
     __syncthreads();
     for (int k = 0; k < A.nsteps; ++k) {
         const bool tm = rec && k == A.nsteps - 1;
@@ -210,7 +223,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         if (warp >= 1)
             for (int m0 = 8 * (warp - 1); m0 < nm; m0 += 8 * (STEP_WARPS - 1)) {
                 const int m = m0 + (lane >> 2);
-                drift_quad<true>(P, S, view(), m, lo + m, m < nm, lane & 3, false, lam_s);
+                drift_quad<true>(Ps, S, view(), m, lo + m, m < nm, lane & 3, false, lam_s);
             }
         mark(k, 0);
         grid_sync(A.bar, A.err, target, S.scal);
@@ -221,11 +234,11 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         // the previous step's record (U, W, T, P, averages), off the critical
         // path: block 0's last warp, which has no pair item unless 16 are due
         if (k > 0 && b == 0 && threadIdx.x == STEP_THREADS - 32)
-            finish_step(P, S, RED_SUM | RED_RECORD | RED_LAMBDA, tot);
+            finish_step(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA, tot);
         for (int t = warp; t < nm * JS; t += STEP_WARPS) {
             const int m = t % nm, p = t / nm, i = lo + m;
             const int j0 = (int)(((long long)N * p) / JS), j1 = (int)(((long long)N * (p + 1)) / JS);
-            e.begin_tile(P, sm, A.Np, i);
+            e.begin_tile(Ps, sm, A.Np, i);
             for (int t0 = j0; t0 < j1; t0 += A.TJ) e.scan(shifted(sm, t0), A.Np, t0, min(A.TJ, j1 - t0), wq, lane);
             const PairOut o = e.finish(lane);
             if (lane == 0) {
@@ -238,7 +251,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         }
         if (A.rdf_every > 0 && ((A.s0 + k + 1) % A.rdf_every) == 0) {
             __syncthreads();
-            rdf_tile<NS, MULTI>(P, S, sm, A.Np, (unsigned *)(own + own_layout(MC, JS, 0).hist));
+            rdf_tile<NS, MULTI>(Ps, S, sm, A.Np, (unsigned *)(own + own_layout(MC, JS, 0).hist));
         }
         __syncthreads();
         mark(k, 1);
@@ -250,7 +263,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         if (warp == 0) {
             const OwnLayout ol = own_layout(MC, JS, 0);
             const RedIO io{part_at(), nullptr, MC, view(), (double *)(own + ol.ui), (int *)(own + ol.np), MC, lo};
-            reduce_unit<true>(P, S, io, RED_SUM | RED_LAMBDA, b, G, lane);
+            reduce_unit<true>(Ps, S, io, RED_SUM | RED_LAMBDA, b, G, lane);
         }
         mark(k, 2);
         grid_sync(A.bar, A.err, target, S.scal);
@@ -258,7 +271,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         // ---- totals in every block; thermostat factor for the next drift
         reduce_totals(S, G, tot);
         __syncthreads();
-        if (threadIdx.x == 0) lam_s = lambda_of(P, tot);
+        if (threadIdx.x == 0) lam_s = lambda_of(Ps, tot);
         __syncthreads();
         if (tm) {
             const unsigned long long t4 = global_ns();
@@ -271,13 +284,14 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
             S.scal[SC_TPH5] = (double)(t4 - tph[3]);     // totals and thermostat factor (block 0)
             S.scal[SC_TPH6] = (double)(tph[0] - tph[5]); // kernel entry to the last step
             S.scal[SC_TPH7] = (double)(t4 - tph[0]);     // the last step
+            tph[4] = t4;
             // every mark of this step came before the last barrier: zero for the next launch
             A.tmax[0] = A.tmax[1] = A.tmax[2] = 0ull;
         }
     }
     // ---- the last step's record; own state, forces and per-molecule results
     // back to global memory
-    if (A.nsteps > 0 && b == 0 && threadIdx.x == 0) finish_step(P, S, RED_SUM | RED_RECORD | RED_LAMBDA, tot);
+    if (A.nsteps > 0 && b == 0 && threadIdx.x == 0) finish_step(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA, tot);
     __syncthreads();
     const OwnLayout ol = own_layout(MC, JS, 0);
     const double *ui_s = (const double *)(own + ol.ui);
@@ -299,6 +313,10 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
             S.Ui[c * N + i] = ui_s[c * MC + t];
         }
         S.npart[i] = np_s[t];
+    }
+    if (A.timing && b == 0) {  // uniform within block 0
+        __syncthreads();
+        if (threadIdx.x == 0) S.scal[SC_TPH8] = (double)(global_ns() - tph[4]);  // last step end to exit
     }
 }
 

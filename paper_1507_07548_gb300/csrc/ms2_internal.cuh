@@ -35,6 +35,10 @@ struct SysParams {
     double L, V, dt, kconv, T0;
     double inv_kconv, inv_ndof, inv_V, inv_T0;   // host-side reciprocals (no FP64 divide per step)
     double inv_mass[MS2_MAXSP];
+    // per-step products, formed once on the host (an FP64 multiply costs a warp
+    // ~68 cycles on GB300): dt kconv, the kick dt kconv / M, M/2, I^-1 / 2 and
+    // the thermostat constant 2 / (kconv ndof T0)
+    double dtk, kick[MS2_MAXSP], half_mass[MS2_MAXSP], half_Iinv[MS2_MAXSP][3], lam_c;
     double lat_scale;          // 2^32 / L  (FP64, exact same value as the host computes)
     unsigned long long rc2;    // lattice cut-off threshold
     float lat_to_len;          // L / 2^32 (FP32 rounding of it)
@@ -101,7 +105,7 @@ enum {
     SC_UREC, SC_WREC_AT, SC_WREC_CORR, SC_UCONST, SC_PLRC, SC_ULRC, SC_WBG, SC_UNSTABLE,
     SC_UTOT, SC_WTOT, SC_P, SC_T, SC_KETR_NOW, SC_KEROT_NOW, SC_STEP,
     SC_TPAIR,  // fused step: pair-phase time of the last step of a chunk (ns)
-    SC_TPH0, SC_TPH1, SC_TPH2, SC_TPH3, SC_TPH4, SC_TPH5, SC_TPH6, SC_TPH7,  // fused step: phase times (ns)
+    SC_TPH0, SC_TPH1, SC_TPH2, SC_TPH3, SC_TPH4, SC_TPH5, SC_TPH6, SC_TPH7, SC_TPH8,  // fused step: phase times (ns)
     SC_KERR,   // fused step: a grid-barrier wait timed out (sticky until read)
     SC_COUNT_
 };

@@ -4,7 +4,7 @@
 // into a per-warp queue and evaluates full batches of 32 partners one per lane
 // with all site pairs unrolled (FP32 site math, coefficient products as hi+lo
 // floats, bare Coulomb + molecular-dipole term for the reaction field, the
-// molecular virial in the short-lever form).  See k_pair.cu for the method.
+// molecular virial as the owner share).  See k_pair.cu for the method.
 #pragma once
 #include "ms2_internal.cuh"
 
@@ -244,14 +244,9 @@ struct PairWarp {
         for (int k = 0; k < 3; ++k)
             muj[b][k] = DMU && ((DM >> b) & 1) ? sm.tmu[(k * NS + b) * TJ + jl] : 0.f;
     }
-    // Molecular virial -d.F_ij, written with d = r_ab - (s_jb - s_ia) as
-    //   -sum_ab f_ab.r_ab + sum_b s_jb.G_b - sum_a s_ia.A_a,
-    //   G_b = sum_a f_ab, A_a = sum_b f_ab   (per pair),
-    // so that no FP32 force sum is multiplied by the long lever arm d and no
-    // long accumulation of site forces meets a lever arm at all.
-    float Gb[NS][3], Aa[NS][3];
-#pragma unroll
-    for (int b = 0; b < NS; ++b) Gb[b][0] = Gb[b][1] = Gb[b][2] = Aa[b][0] = Aa[b][1] = Aa[b][2] = 0.f;
+    // Molecular virial, owner share: the site-pair part -sum_ab f_ab.r_ab here
+    // (short levers, no FP32 force sum meets the long lever d), the
+    // intramolecular part -2 sum_a s_ia.F_ia once per molecule in finish().
     float wsite = 0.f;
 #pragma unroll
     for (int a = 0; a < NS; ++a) {
@@ -325,27 +320,16 @@ struct PairWarp {
                 const float fx = cr * rx + cma * mui[a][0] + cmb * muj[b][0];
                 const float fy = cr * ry + cma * mui[a][1] + cmb * muj[b][1];
                 const float fz = cr * rz + cma * mui[a][2] + cmb * muj[b][2];
-                Aa[a][0] += fx; Aa[a][1] += fy; Aa[a][2] += fz;
-                Gb[b][0] += fx; Gb[b][1] += fy; Gb[b][2] += fz;
+                fa[a][0] += fx; fa[a][1] += fy; fa[a][2] += fz;
                 wsite -= fx * rx + fy * ry + fz * rz;
                 const float ce = 3.f * C * mbr * rinv5, cm = -C * (rinv3 - kd);
                 ea[a][0] += ce * rx + cm * muj[b][0];
                 ea[a][1] += ce * ry + cm * muj[b][1];
                 ea[a][2] += ce * rz + cm * muj[b][2];
             }
-            Aa[a][0] = fmaf(g, rx, Aa[a][0]); Aa[a][1] = fmaf(g, ry, Aa[a][1]); Aa[a][2] = fmaf(g, rz, Aa[a][2]);
-            Gb[b][0] = fmaf(g, rx, Gb[b][0]); Gb[b][1] = fmaf(g, ry, Gb[b][1]); Gb[b][2] = fmaf(g, rz, Gb[b][2]);
+            fa[a][0] = fmaf(g, rx, fa[a][0]); fa[a][1] = fmaf(g, ry, fa[a][1]); fa[a][2] = fmaf(g, rz, fa[a][2]);
             wsite = fmaf(-g, r2, wsite);
         }
-    }
-#pragma unroll
-    for (int b = 0; b < NS; ++b)
-        wsite += sm.ts[(0 * NS + b) * TJ + jl] * Gb[b][0] + sm.ts[(1 * NS + b) * TJ + jl] * Gb[b][1] +
-                 sm.ts[(2 * NS + b) * TJ + jl] * Gb[b][2];
-#pragma unroll
-    for (int a = 0; a < NS; ++a) {
-        wsite -= si[a][0] * Aa[a][0] + si[a][1] * Aa[a][1] + si[a][2] * Aa[a][2];
-        fa[a][0] += Aa[a][0]; fa[a][1] += Aa[a][1]; fa[a][2] += Aa[a][2];
     }
     w += wsite;
     if (MOLD && rfq) {
@@ -404,6 +388,12 @@ struct PairWarp {
         o.np = warp_sum(np);
         o.F[0] = o.F[1] = o.F[2] = o.T[0] = o.T[1] = o.T[2] = 0.f;
         if (lane == 0) {
+            // intramolecular part of the owner virial share: -2 sum_a s_ia.F_ia
+            // (linear in the site forces, so j-range partials add up)
+            float sf = 0.f;
+#pragma unroll
+            for (int a = 0; a < NS; ++a) sf += si[a][0] * fa[a][0] + si[a][1] * fa[a][1] + si[a][2] * fa[a][2];
+            o.w -= 2.f * sf;
 #pragma unroll
             for (int a = 0; a < NS; ++a) {
                 o.F[0] += fa[a][0]; o.F[1] += fa[a][1]; o.F[2] += fa[a][2];

@@ -218,6 +218,37 @@ def test_virial_is_minus_volume_derivative(name, o, R, q):
     assert fd == pytest.approx(T["W_total"], rel=1e-6, abs=1e-7 * abs(T["U_total"]))
 
 
+@pytest.mark.parametrize("name,o,R,q", list(small_systems()), ids=lambda x: x if isinstance(x, str) else "")
+def test_virial_owner_shares_add_up_to_the_molecular_virial(name, o, R, q):
+    """The per-molecule owner shares 1/2 (sum_j sum_ab -r_ab.f_ab - 2 sum_a s_ia.F_ia)
+    add up to the pair-form W_pair, itself pinned by the volume derivative above."""
+    _, _, T = o.forces(R, q)
+    mol = o.molecule_terms(R, q)
+    assert mol[:, 3].sum() == pytest.approx(T["W_pair"], rel=1e-11, abs=1e-11 * abs(T["U_total"]))
+    for k, key in enumerate(("U_lj", "U_qq", "U_dd")):
+        assert mol[:, k].sum() == pytest.approx(T[key], rel=1e-11, abs=1e-11 * abs(T["U_total"]))
+
+
+def test_virial_owner_share_of_point_molecules_is_the_pair_share():
+    """Without site offsets the owner share is 1/2 sum_j (R_i - R_j).F_ij: checked
+    against a brute-force LJ sum over minimum images."""
+    wl = W.lj_fluid(N=108, rho=0.5, T=1.0, rc=2.5, seed=3)
+    wl.R = wl.R + np.random.default_rng(5).normal(0, 0.05, wl.R.shape)
+    o = Oracle.from_workload(wl)
+    mol = o.molecule_terms(wl.R, wl.q)
+    L = wl.L
+    want = np.zeros(wl.N)
+    for i in range(wl.N):
+        d = wl.R - wl.R[i]
+        d -= L * np.rint(d / L)
+        r2 = (d * d).sum(1)
+        m = (r2 < wl.rc ** 2) & (np.arange(wl.N) != i)
+        sr6 = (1.0 / r2[m]) ** 3
+        # force on i from j: 24 (2 sr^12 - sr^6) / r^2 * (R_i - R_j); virial (R_i - R_j).F
+        want[i] = 0.5 * (24.0 * (2.0 * sr6 * sr6 - sr6)).sum()
+    assert np.abs(mol[:, 3] - want).max() <= 1e-12 * np.abs(want).max()
+
+
 # ------------------------------------------------------------ reaction field
 def test_rf_shift_invariance_for_neutral_molecules():
     wl = W.water_box(N=64, rc=6.0, seed=41)
