@@ -281,6 +281,8 @@ def gpu_arm(args, rank, world, local_rank):
     extra = {}
     if not args.no_extra and rank == 0:
         extra["ewald_ionic"] = ewald_sub(args, stream)
+        extra["batch"] = batch_sub(args, flush)
+        extra["serve"] = serve_sub(args, extra["batch"]["batched"]["value"])
 
     if rank != 0:
         return 0
@@ -322,6 +324,91 @@ def gpu_arm(args, rank, world, local_rank):
     line.update(extra)
     print(json.dumps(line), flush=True)
     return 0
+
+
+BATCH_SYSTEMS, BATCH_STEPS = 512, 200      # many-system mix (production runs: 1e4 steps in chunks of 100)
+SERVE_JOBS, SERVE_STEPS = 48, (100, 1000)  # job stream (production: 256 jobs of 1e4 - 1e5 steps)
+
+
+def batch_sub(args, flush):
+    """The same work -- BATCH_SYSTEMS independent systems of the LJ / Stockmayer /
+    water mix, BATCH_STEPS steps each -- run one system at a time on one stream
+    (each on its best single-system path: the fused step kernel) and as one
+    persistent batch (one block per system per chunk).  Host wall time between
+    device synchronisations (each run is far longer than a launch), L2 flushed
+    before each run."""
+    import torch
+    import paper_1507_07548_gb300.ms2 as ms2
+    from paper_1507_07548_gb300 import workloads as W
+    specs = W.system_mix(BATCH_SYSTEMS, seed=4)
+    one = torch.cuda.Stream()
+
+    def make(**kw):
+        return [ms2.System(sp["models"], sp["counts"], sp["T"], sp["cutoff"], sp["elec"], rho=sp["rho"],
+                           seed=sp["seed"], dt=2.0, **kw) for sp in specs]
+
+    plain, batched = make(stream=one.cuda_stream), make()
+    work = sum(sp["counts"][0] for sp in specs) * BATCH_STEPS
+    b = ms2.Batch(batched)
+    for s in plain:       # warm-up: one chunk-sized step each, both sets
+        s.step(1)
+    b.step(1)
+    torch.cuda.synchronize()
+    flush.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in plain:
+        s.step(BATCH_STEPS)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    flush.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(BATCH_STEPS)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    fused = sum(s.fused_step() for s in plain)
+    b.close()
+    for s in plain + batched:
+        s.close()
+    kinds = {k: sum(1 for sp in specs if sp["name"] == k) for k in W.MIX_STATES}
+    return {"workload": "%d independent systems (%s), N ~ U[256, 2048], T ~ U[0.7, 1.3] T0, rho ~ U[0.5, 1.0] rho0; "
+                        "%d steps each (production: 1e4)" % (BATCH_SYSTEMS, ", ".join("%d %s" % (v, k) for k, v in
+                                                                                      kinds.items()), BATCH_STEPS),
+            "unit": "molecule-steps/s",
+            "plain": {"value": work / t_plain, "seconds": t_plain, "path": "one system at a time, %d of %d fused"
+                      % (fused, len(plain))},
+            "batched": {"value": work / t_batch, "seconds": t_batch, "path": "persistent batch kernels"},
+            "speedup": t_plain / t_batch}
+
+
+def serve_sub(args, capacity):
+    """Job stream through the server (ms2_serve_*): SERVE_JOBS jobs, Poisson
+    arrivals at ~0.7 of the batch capacity measured above, 20 % ionic (Ewald),
+    a 2 GiB admission budget.  Latency = result on the host minus arrival."""
+    import numpy as np
+    import paper_1507_07548_gb300.ms2 as ms2
+    from paper_1507_07548_gb300 import workloads as W
+    probe = W.job_stream(SERVE_JOBS, 1.0, seed=5, steps=SERVE_STEPS)
+    mean_work = np.mean([sum(j["counts"]) * j["steps"] for j in probe])
+    rate = 0.7 * capacity / mean_work
+    jobs = W.job_stream(SERVE_JOBS, rate, seed=5, steps=SERVE_STEPS)
+    srv = ms2.Server(2 << 30, 256)
+    for j in jobs:
+        srv.submit(j["models"], j["counts"], j["T"], j["rho"], j["cutoff"], j["elec"], j["steps"],
+                   arrival=j["arrival"], seed=j["seed"], rdf_bins=100)
+    srv.drain(600.0)
+    res = srv.poll(SERVE_JOBS)
+    srv.close()
+    lat = np.array([r["t_done"] - r["t_arrive"] for r in res])
+    span = max(r["t_done"] for r in res) - min(r["t_arrive"] for r in res)
+    work = sum(sum(j["counts"]) * j["steps"] for j in jobs)
+    return {"workload": "%d jobs, N ~ U[500, 4000], %d-%d steps, 20%% ionic (Ewald), Poisson arrivals at %.1f/s "
+                        "(~0.7 of the measured batch capacity), 2 GiB budget" % (SERVE_JOBS, SERVE_STEPS[0],
+                                                                               SERVE_STEPS[1], rate),
+            "completed": int(sum(1 for r in res if r["status"] == 0)), "jobs": len(jobs),
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "value": work / span, "unit": "molecule-steps/s"}
 
 
 def ewald_sub(args, stream):

@@ -280,3 +280,67 @@ def stockmayer_fluid(N=500, rho=0.012, T=300.0, rc=17.5, seed=4, dt=2.0) -> Work
 # unit conversion of the fixed unit system, needed to make thermal velocities:
 # 1 K (energy) in g/mol * A^2 / fs^2
 KCONV = 1.380649e-23 * 6.02214076e23 * 1e3 * 1e20 / 1e30
+
+
+# ------------------------------------------------- many systems and jobs
+def argon() -> Model:
+    """LJ atom in the fixed unit system (argon-like: sigma 3.405 A, eps 119.8 K)."""
+    return Model("argon", [Site((0.0, 0.0, 0.0), 39.948, 3.405, 119.8, lj=True)])
+
+
+# nominal states of the three members of the many-system mix:
+# (model factory, T0 in K, number density rho0 in 1/A^3, model cutoff in A, electrostatics)
+MIX_STATES = {
+    "lj": (argon, 119.8, 0.7 / 3.405 ** 3, 3.5 * 3.405, 0),           # T* = 1, rho* = 0.7, rc = 3.5 sigma
+    "stockmayer": (stockmayer, 300.0, 0.012, 17.5, 1),
+    "water": (water, 298.0, WATER_NUMBER_DENSITY, 14.0, 1),
+}
+
+
+def system_mix(n_systems=512, seed=4, n_range=(256, 2048)):
+    """Independent systems: model uniform over {LJ, Stockmayer, water}, N uniform
+    over n_range, T uniform in [0.7, 1.3] T0, rho uniform in [0.5, 1.0] rho0, and
+    the model cutoff capped at 0.49 L.  Returns a list of dicts with keys name,
+    models, counts, T, rho, cutoff, elec, seed."""
+    rng = np.random.default_rng(seed)
+    names = list(MIX_STATES)
+    out = []
+    for k in range(n_systems):
+        name = names[int(rng.integers(len(names)))]
+        make, T0, rho0, rc, elec = MIX_STATES[name]
+        N = int(rng.integers(n_range[0], n_range[1] + 1))
+        T = T0 * rng.uniform(0.7, 1.3)
+        rho = rho0 * rng.uniform(0.5, 1.0)
+        L = (N / rho) ** (1 / 3)
+        out.append(dict(name=name, models=[make()], counts=[N], T=T, rho=rho, cutoff=min(rc, 0.49 * L),
+                        elec=elec, seed=seed * 100003 + k))
+    return out
+
+
+def job_stream(n_jobs=256, rate=50.0, seed=5, n_range=(500, 4000), steps=(10000, 100000), ionic_fraction=0.2):
+    """Simulation jobs with Poisson arrivals (rate per second): N uniform over
+    n_range, steps uniform over the multiples of 100 in the steps range; a
+    fraction are ionic solutions (water + 2% ion pairs, Ewald), the rest drawn
+    like system_mix.  Returns dicts as system_mix plus steps and arrival (s)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    names = list(MIX_STATES)
+    out = []
+    for k in range(n_jobs):
+        t += rng.exponential(1.0 / rate)
+        N = int(rng.integers(n_range[0], n_range[1] + 1))
+        nsteps = 100 * int(rng.integers(steps[0] // 100, steps[1] // 100 + 1))
+        if rng.uniform() < ionic_fraction:
+            pairs = max(1, int(round(0.02 * N)))
+            job = dict(name="ionic", models=[water(), cation(), anion()], counts=[N - 2 * pairs, pairs, pairs],
+                       T=298.0 * rng.uniform(0.9, 1.1), rho=WATER_NUMBER_DENSITY, elec=2)
+            job["cutoff"] = min(14.0, 0.49 * (N / job["rho"]) ** (1 / 3))
+        else:
+            name = names[int(rng.integers(len(names)))]
+            make, T0, rho0, rc, elec = MIX_STATES[name]
+            T, rho = T0 * rng.uniform(0.7, 1.3), rho0 * rng.uniform(0.5, 1.0)
+            job = dict(name=name, models=[make()], counts=[N], T=T, rho=rho,
+                       cutoff=min(rc, 0.49 * (N / rho) ** (1 / 3)), elec=elec)
+        job.update(steps=nsteps, arrival=t, seed=seed * 100003 + k)
+        out.append(job)
+    return out
