@@ -242,8 +242,13 @@ typedef struct {
 
 /* Opens a server whose resident job state may use at most hbm_budget_bytes of
  * device memory; a scheduler thread admits eligible jobs in arrival order as
- * budget and slots free up, advances all resident jobs together in persistent
- * chunks (continuous batching), and retires finished ones.  max_slots <= 1024. */
+ * budget and slots free up, advances all resident jobs together chunk by chunk
+ * (continuous batching), and retires finished ones.  max_slots <= 1024.  A job's
+ * path is fixed at admission: with 64 or more jobs resident, jobs the batch
+ * kernels take join the batch; otherwise a job steps with its own
+ * single-system kernels.  All the server's systems share one stream.  Results
+ * are reproducible for a given arrival sequence; the two paths agree within the
+ * parity tolerances, not bit for bit. */
 MS2_API ms2_status ms2_serve_open(size_t hbm_budget_bytes, int max_slots, const ms2_options *opt, ms2_server *out);
 /* Queues a job (never blocks).  MS2_EBUDGET if it alone exceeds the budget. */
 MS2_API ms2_status ms2_serve_submit(ms2_server s, const ms2_job *job, long long *job_id);

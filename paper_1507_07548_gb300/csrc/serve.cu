@@ -5,13 +5,16 @@
 //   2. admits eligible jobs (arrival time reached) in arrival order while the
 //      memory budget and the slot table allow (head-of-line: a job that does
 //      not fit yet blocks the ones behind it, so admission is FIFO-fair),
-//   3. advances every resident job by one chunk: jobs the batch kernels take
-//      (leapfrog, reaction field or no electrostatics, fits one block) go
-//      through one batch object rebuilt whenever the resident set changes;
-//      the others (Ewald, very large) step on their own streams, concurrently.
+//   3. advances every resident job by one chunk.
 // Jobs that arrive while others run are admitted at the next chunk boundary
-// (continuous batching).  Each job's arithmetic depends only on the job, so a
-// result is the same alone and in the mix.
+// (continuous batching).  A job's path is fixed at admission: while at least
+// BATCH_MIN_RESIDENT jobs are resident, a job the batch kernels take goes into
+// the batch (one block per system, efficient once the systems outnumber the
+// SMs); otherwise it steps with its own single-system kernels (the fused step
+// where the system allows, each chunk on the whole GPU).  All systems of a
+// server share one stream, so cooperative fused launches never overlap each
+// other or the batch.  Results are reproducible for a given arrival sequence;
+// the two paths agree within the parity tolerances, not bit for bit.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -26,6 +29,8 @@
 bool ms2_batch_accepts(ms2_system s);  // batch.cu
 
 namespace {
+
+constexpr int BATCH_MIN_RESIDENT = 64;  // resident jobs from which new jobs join the batch
 
 struct JobSpec {
     long long id = 0;
@@ -84,6 +89,7 @@ struct ms2_server_s {
     std::thread th;
     ms2_batch batch = nullptr;
     bool batch_dirty = true;
+    cudaStream_t stream = nullptr;  // shared by all the server's systems
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -153,7 +159,7 @@ static void admit(ms2_server S) {
         }
         ms2_options o = S->opt;
         o.seed = j.seed;
-        o.stream = nullptr;
+        o.stream = (void *)S->stream;
         ms2_status st = ms2_create_system(models.data(), j.counts.data(), (int)models.size(), 0.0, j.T, j.rho,
                                           j.cutoff, j.elec, &o, &sl.sys);
         if (st == MS2_OK && j.rdf_bins > 0) {
@@ -170,7 +176,7 @@ static void admit(ms2_server S) {
         }
         S->resident += j.bytes;
         sl.remaining = j.steps;
-        sl.batched = ms2_batch_accepts(sl.sys);
+        sl.batched = (int)S->slots.size() + 1 >= BATCH_MIN_RESIDENT && ms2_batch_accepts(sl.sys);
         S->slots.push_back(sl);
         S->batch_dirty = true;
     }
@@ -268,6 +274,13 @@ extern "C" ms2_status ms2_serve_open(size_t hbm_budget_bytes, int max_slots, con
     ms2_default_options(&S->opt);
     if (opt) S->opt = *opt;
     cudaGetDevice(&S->device);
+    {
+        const cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete S;
+            return ms2_fail_cuda(e, "server stream", __FILE__, __LINE__);
+        }
+    }
     S->t0 = std::chrono::steady_clock::now();
     S->th = std::thread(scheduler, S);
     *out = S;
@@ -339,6 +352,7 @@ extern "C" ms2_status ms2_serve_close(ms2_server S) {
         S->cv.notify_all();
     }
     if (S->th.joinable()) S->th.join();
+    if (S->stream) cudaStreamDestroy(S->stream);  // after every system of the server is gone
     delete S;
     return MS2_OK;
 }
