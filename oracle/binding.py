@@ -75,6 +75,8 @@ def _load():
             "or_rdf_edge_pairs": [P(_Sys), d, d, C.c_double, C.c_int, C.c_double, P(C.c_longlong)],
             "or_rdf_kinds": [P(_Sys), i32], "or_ndof": [P(_Sys)],
             "or_rc2_lattice": [C.c_double, C.c_double], "or_lattice": [C.c_double, C.c_double],
+            "or_volume_derivatives": [P(_Sys), d, d, d],
+            "or_massieu": [d, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, d],
         }
         for name, args in sig.items():
             getattr(_lib, name).argtypes = args
@@ -179,6 +181,22 @@ class Oracle:
         a, b, c = C.c_double(), C.c_double(), C.c_double()
         self.lib.or_ewald_constants(self.ref, C.byref(a), C.byref(b), C.byref(c))
         return a.value, b.value, c.value
+
+    def volume_derivatives(self, R, q):
+        """(dU/dV, d2U/dV2) at fixed scaled centres and orientations (Sec. 2, Eq. 1)."""
+        out = np.zeros(2)
+        self.lib.or_volume_derivatives(self.ref, _p(np.ascontiguousarray(R, np.float64)),
+                                       _p(np.ascontiguousarray(q, np.float64)), _p(out))
+        return out[0], out[1]
+
+    @staticmethod
+    def massieu(acc, U0, V0, beta, V, N):
+        """A^r_mn for mn = 10, 01, 20, 11, 02, 30, 21, 12 from the moment sums acc (11 values)."""
+        lib = _load()
+        a = np.ascontiguousarray(acc, np.float64)
+        out = np.zeros(8)
+        lib.or_massieu(_p(a), C.c_double(U0), C.c_double(V0), C.c_double(beta), C.c_double(V), C.c_int(N), _p(out))
+        return out
 
     def lrc(self):
         U, P = C.c_double(), C.c_double()

@@ -525,6 +525,113 @@ double or_pressure(const or_system *s, double ke_tr, const double *terms) {
     return (2.0 * ke_tr / 3.0 + terms[T_WTOT] / 3.0) / V + terms[T_PLRC];
 }
 
+/* -------------------------------- Massieu potential derivatives (Sec. 2, Eq. 1) */
+/* Volume derivatives of the potential energy at fixed scaled centres and fixed
+ * orientations (the scaling that defines the molecular virial).  With
+ * r_ab(lambda) = lambda d_ij + s_jb - s_ia and V' = lambda^3 V:
+ *   dU/dV   = g'(1) / (3 V),   d2U/dV2 = (g''(1) - 2 g'(1)) / (9 V^2),
+ *   g'  = sum_ab u'(r) (r.d) / r,
+ *   g'' = sum_ab [u''(r) (r.d)^2 / r^2 + u'(r) / r (d^2 - (r.d)^2 / r^2)],
+ * summed over partner pairs, plus the long-range parts -P_LRC and 2 P_LRC / V:
+ * the mean-field tail pressure and its volume derivative (reading: the paper
+ * leaves the LRC of these derivatives to its supplement; -P_LRC is what makes
+ * -dU/dV the residual pressure).  LJ and point charges with the reaction field
+ * (whose k_RF r^2 and c_RF terms drop out of neutral molecule pairs) or without
+ * electrostatics; the paper does not combine these derivatives with Ewald, and
+ * dipoles are not covered.  out[0] = dU/dV, out[1] = d2U/dV2. */
+void or_volume_derivatives(const or_system *s, const double *R, const double *q, double *out) {
+    int N = s->N;
+    uint32_t *X = (uint32_t *)malloc(sizeof(uint32_t) * 3 * N);
+    lattice_all(s, R, X);
+    uint64_t rc2 = or_rc2_lattice(s->rc, s->L);
+    double *A = (double *)malloc(sizeof(double) * 9 * N);
+    for (int i = 0; i < N; ++i) or_rotation(q + 4 * i, A + 9 * i);
+    double krf = (s->elec == 1) ? k_rf(s) : 0.0, g1 = 0, g2 = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : g1, g2)
+    for (int i = 0; i < N; ++i) {
+        int si = s->species[i];
+        for (int j = 0; j < N; ++j) {
+            if (j == i || !(lattice_d2(X + 3 * i, X + 3 * j) < rc2)) continue;
+            int sj = s->species[j];
+            double d[3];
+            min_image(s, R + 3 * i, R + 3 * j, d);
+            double d2 = dot3(d, d);
+            for (int a = 0; a < s->n_sites[si]; ++a) {
+                double oa[3];
+                matvec(A + 9 * i, s->pos[si][a], oa);
+                for (int b = 0; b < s->n_sites[sj]; ++b) {
+                    double ob[3], r[3];
+                    matvec(A + 9 * j, s->pos[sj][b], ob);
+                    for (int k = 0; k < 3; ++k) r[k] = d[k] + ob[k] - oa[k];
+                    double r2 = dot3(r, r), rr = sqrt(r2), rd = dot3(r, d), u1 = 0, u2 = 0;  /* u', u'' */
+                    if (s->lj[si][a] && s->lj[sj][b]) {
+                        double sig = 0.5 * (s->sigma[si][a] + s->sigma[sj][b]);
+                        double eps = sqrt(s->epsilon[si][a] * s->epsilon[sj][b]);
+                        double sr6 = pow(sig * sig / r2, 3), sr12 = sr6 * sr6;
+                        u1 += 4.0 * eps * (-12.0 * sr12 + 6.0 * sr6) / rr;
+                        u2 += 4.0 * eps * (156.0 * sr12 - 42.0 * sr6) / r2;
+                    }
+                    double qa = s->charge[si][a], qb = s->charge[sj][b];
+                    if (s->elec == 1 && qa != 0 && qb != 0) {
+                        double cqq = s->coulomb * qa * qb;   /* u = cqq (1/r + k_RF r^2 - c_RF) */
+                        u1 += cqq * (-1.0 / r2 + 2.0 * krf * rr);
+                        u2 += cqq * (2.0 / (r2 * rr) + 2.0 * krf);
+                    }
+                    g1 += u1 * rd / rr;
+                    g2 += u2 * rd * rd / r2 + u1 / rr * (d2 - rd * rd / r2);
+                }
+            }
+        }
+    }
+    free(X);
+    free(A);
+    double V = s->L * s->L * s->L, Ul = 0, Pl = 0;
+    if (s->lrc) or_lrc(s, &Ul, &Pl);
+    g1 *= 0.5;  /* each pair was visited from both molecules */
+    g2 *= 0.5;
+    out[0] = g1 / (3.0 * V) - Pl;
+    out[1] = (g2 - 2.0 * g1) / (9.0 * V * V) + 2.0 * Pl / V;
+}
+
+/* Residual Massieu derivatives A^r_mn = beta^m rho^n d^(m+n)(A^r/(N k T)) /
+ * d beta^m d rho^n (Eq. 1; k = 1) of the NVT ensemble, from canonical averages.
+ * Written out from f = -(1/N) ln(Z_c / V^N), Z_c the configurational integral
+ * taken over scaled centres, so that
+ *   df/dbeta = <U>/N,  df/dV = beta <U_V>/N,  rho d/drho = -V d/dV,
+ *   rho^2 d^2/drho^2 = 2 V d/dV + V^2 d^2/dV^2,
+ *   d<X>/dbeta = -cov(X, U),  d<X>/dV = <X_V> - beta cov(X, U_V),
+ * with U_V = dU/dV and U_VV = d2U/dV2 at fixed scaled centres.  This gives
+ *   A10 = beta <U> / N                A01 = -beta V <U_V> / N
+ *   A20 = -beta^2 var(U) / N          A11 = -(beta V / N) (<U_V> - beta cov(U, U_V))
+ *   A02 = (beta / N) (2 V <U_V> + V^2 (<U_VV> - beta var(U_V)))
+ *   A30 = beta^3 <dU^3> / N
+ *   A21 = (beta^2 V / N) (2 cov(U, U_V) - beta <dU^2 dU_V>)
+ *   A12 = (beta / N) (2 V (<U_V> - beta cov(U, U_V))
+ *         + V^2 (<U_VV> - 2 beta var(U_V) - beta cov(U, U_VV) + beta^2 <dU dU_V^2>))
+ * (dX = X - <X>).  acc holds the sample weight and weighted sums over samples of
+ * x = U - U0, y = U_V - V0 and w = U_VV (the shifts keep the central moments
+ * free of cancellation):
+ *   acc = {n, x, x^2, x^3, y, y^2, x y, x^2 y, x y^2, w, x w}.
+ * out = {A10, A01, A20, A11, A02, A30, A21, A12}. */
+void or_massieu(const double *acc, double U0, double V0, double beta, double V, int N, double *out) {
+    double n = acc[0];
+    double mx = acc[1] / n, my = acc[4] / n, mw = acc[9] / n;
+    double vx = acc[2] / n - mx * mx, vy = acc[5] / n - my * my, cxy = acc[6] / n - mx * my;
+    double k3 = acc[3] / n - 3.0 * mx * acc[2] / n + 2.0 * mx * mx * mx;
+    double m21 = acc[7] / n - 2.0 * mx * acc[6] / n - my * acc[2] / n + 2.0 * mx * mx * my;
+    double m12 = acc[8] / n - 2.0 * my * acc[6] / n - mx * acc[5] / n + 2.0 * mx * my * my;
+    double cxw = acc[10] / n - mx * mw;
+    double U = U0 + mx, UV = V0 + my, b = beta;
+    out[0] = b * U / N;
+    out[1] = -b * V * UV / N;
+    out[2] = -b * b * vx / N;
+    out[3] = -(b * V / N) * (UV - b * cxy);
+    out[4] = (b / N) * (2.0 * V * UV + V * V * (mw - b * vy));
+    out[5] = b * b * b * k3 / N;
+    out[6] = (b * b * V / N) * (2.0 * cxy - b * m21);
+    out[7] = (b / N) * (2.0 * V * (UV - b * cxy) + V * V * (mw - 2.0 * b * vy - b * cxw + b * b * m12));
+}
+
 /* ------------------------------------------------------ integrators (a5) */
 /* thermo record per step: U, W, KE_tr, KE_rot, P (after the step) */
 static void record(const or_system *s, const double *q, const double *v, const double *Lang, const double *terms,

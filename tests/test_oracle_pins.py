@@ -571,3 +571,89 @@ def test_rdf_kind_pairs_for_mixture():
     d -= wl.L * np.rint(d / wl.L)
     r = np.sqrt((d ** 2).sum(1))
     assert c.sum() == int((r < 5.0).sum())
+
+
+# ------------------------------------------------- Massieu derivatives (Eq. 1)
+def _volume_cases():
+    wl = W.water_box(N=64, rc=6.0, seed=21)
+    yield "water_rf", Oracle.from_workload(wl), wl.R, wl.q
+    lj = W.lj_fluid(N=108, rho=0.7, rc=2.5)
+    R = lj.R + np.random.default_rng(9).normal(0, 0.05, lj.R.shape)
+    yield "lj", Oracle.from_workload(lj), R, lj.q
+
+
+@pytest.mark.parametrize("name,o,R,q", list(_volume_cases()), ids=lambda x: x if isinstance(x, str) else "")
+def test_volume_derivatives_are_finite_differences_of_U(name, o, R, q):
+    """dU/dV and d2U/dV2 at fixed scaled centres and orientations against central
+    differences of U(s) with centres and box edge scaled by s (V = s^3 V0); the
+    long-range parts are -P_LRC and 2 P_LRC / V."""
+    s = o.s
+    L0, h = s.L, 5e-6
+    V = L0 ** 3
+    # no centre pair so close to the cutoff that the scaling moves it across
+    d = R[:, None, :] - R[None, :, :]
+    d -= L0 * np.rint(d / L0)
+    r = np.sqrt((d * d).sum(-1))
+    assert np.min(np.abs(r - s.rc)) > 10 * h * s.rc
+
+    def U(scale):
+        s.L = L0 * scale
+        try:
+            t = o.forces(R * scale, q)[2]
+        finally:
+            s.L = L0
+        return t["U_total"] - t["U_lrc"]
+
+    up, u0, um = U(1 + h), U(1.0), U(1 - h)
+    d1, d2 = (up - um) / (2 * h), (up - 2 * u0 + um) / h ** 2
+    UV, UVV = o.volume_derivatives(R, q)
+    Pl = o.forces(R, q)[2]["P_lrc"]
+    assert UV + Pl == pytest.approx(d1 / (3 * V), rel=1e-7)
+    assert UVV - 2 * Pl / V == pytest.approx((d2 - 2 * d1) / (9 * V * V), rel=1e-5)
+
+
+def test_massieu_estimators_are_derivatives_of_the_exact_partition_function():
+    """Two particles in a periodic box with the smooth pair potential
+    u = eps exp(-(r/a)^2) (negligible at rc < L/2): Z_c / V^2 = 1 + B(beta) / V with
+    B = int_0^rc 4 pi r^2 (exp(-beta u) - 1) dr, so A^r = -(1/2) ln(1 + rho B / 2)
+    differentiates exactly; the canonical moments that feed the estimators are
+    quadratures over the same weights."""
+    sympy = pytest.importorskip("sympy")
+    eps, a, rc, L, beta = 1.3, 0.5, 3.5, 8.0, 0.7
+    V, N = L ** 3, 2
+    x, w = np.polynomial.legendre.leggauss(400)
+    r = 0.5 * rc * (x + 1)
+    w = 0.5 * rc * w * 4 * np.pi * r ** 2
+    u = eps * np.exp(-(r / a) ** 2)
+    u1 = -2 * r / a ** 2 * u                      # u'
+    u2 = (4 * r ** 2 / a ** 4 - 2 / a ** 2) * u   # u''
+    e = np.exp(-beta * u)
+    # centres scale with V: U_V = u' r / (3V), U_VV = (u'' r^2 - 2 u' r) / (9 V^2)
+    UV = u1 * r / (3 * V)
+    UVV = (u2 * r * r - 2 * u1 * r) / (9 * V * V)
+    wout = V - 4 / 3 * np.pi * rc ** 3           # the rest of the cell: u = 0
+    U0, V0 = 0.1, -0.002                          # arbitrary shifts
+    X, Y = u - U0, UV - V0
+    ww = w * e
+    acc = [ww.sum() + wout]
+    for f in (X, X ** 2, X ** 3, Y, Y ** 2, X * Y, X * X * Y, X * Y * Y, UVV, X * UVV):
+        acc.append((ww * f).sum())
+    xo, yo = -U0, -V0                             # the outer region's shifted values
+    for k, f in enumerate((xo, xo ** 2, xo ** 3, yo, yo ** 2, xo * yo, xo * xo * yo, xo * yo * yo, 0.0, 0.0)):
+        acc[k + 1] += wout * f
+    got = Oracle.massieu(np.array(acc), U0, V0, beta, V, N)
+    # exact: f(beta, rho) = -(1/2) ln(1 + rho B(beta) / 2)
+    b, rho = sympy.symbols("b rho")
+    Bf = sympy.Function("B")
+    f = -sympy.Rational(1, 2) * sympy.log(1 + rho * Bf(b) / 2)
+    vals = {rho: N / V}
+    Bk = [(w * (e - 1)).sum()] + [(w * (-u) ** k * e).sum() for k in (1, 2, 3)]   # B and its beta-derivatives
+    want = []
+    for m, nn in ((1, 0), (0, 1), (2, 0), (1, 1), (0, 2), (3, 0), (2, 1), (1, 2)):
+        expr = sympy.diff(f, b, m, rho, nn) if nn else sympy.diff(f, b, m)
+        expr = expr * b ** m * rho ** nn
+        for k in (3, 2, 1):
+            expr = expr.subs(sympy.Derivative(Bf(b), (b, k)), Bk[k])
+        expr = expr.subs(Bf(b), Bk[0]).subs(vals).subs(b, beta)
+        want.append(float(expr))
+    np.testing.assert_allclose(got, want, rtol=1e-8, atol=1e-14)
