@@ -100,6 +100,8 @@ typedef struct {
     int quat_iters;           /* sweeps of the implicit quaternion midpoint rule; 0 -> 3 */
     int graph_chunk;          /* steps per captured CUDA graph; 0 -> 50 */
     int fp64;                 /* 1: site-pair arithmetic in FP64 too (point LJ models only) */
+    int massieu;              /* 1: also sample the Massieu-derivative moments (ms2_massieu); LJ and
+                                 point-charge models, reaction field or no electrostatics; not in batches */
     int fused_step;           /* 1 (default): a chunk of steps runs as one cooperative kernel where the
                                  system allows it (leapfrog, no Ewald, the whole system fits one SM's
                                  shared memory); results are bitwise those of the per-phase kernels.
@@ -257,6 +259,29 @@ MS2_API ms2_status ms2_serve_poll(ms2_server s, ms2_job_result *out, int max, in
 /* Blocks until all submitted jobs finished or timeout_s passed (MS2_ETIMEOUT). */
 MS2_API ms2_status ms2_serve_drain(ms2_server s, double timeout_s);
 MS2_API ms2_status ms2_serve_close(ms2_server s);
+
+/* ------------------------------------------------- Massieu derivatives */
+/* Paper Sec. 2, Eq. 1: A_mn = beta^m rho^n d^(m+n)(F/(N k T)) / d beta^m d rho^n
+ * (beta = 1/T, rho = N/V) splits into an ideal and a residual part; the
+ * residual parts of the NVT ensemble are canonical moments of the potential
+ * energy U and of its volume derivatives U_V = dU/dV, U_VV = d2U/dV2 taken at
+ * fixed scaled centres and orientations (the scaling of the molecular virial):
+ *   A10 = beta <U>/N                  A01 = -beta V <U_V>/N
+ *   A20 = -beta^2 var(U)/N            A11 = -(beta V/N) (<U_V> - beta cov(U,U_V))
+ *   A02 = (beta/N) (2 V <U_V> + V^2 (<U_VV> - beta var(U_V)))
+ *   A30 = beta^3 <dU^3>/N             A21 = (beta^2 V/N) (2 cov(U,U_V) - beta <dU^2 dU_V>)
+ *   A12 = (beta/N) (2 V (<U_V> - beta cov(U,U_V))
+ *         + V^2 (<U_VV> - 2 beta var(U_V) - beta cov(U,U_VV) + beta^2 <dU dU_V^2>))
+ * (dX = X - <X>; N molecules; energies in K, k = 1; beta = 1/T0 of the
+ * thermostat).  U_V = -W/(3V) - P_LRC and U_VV include the long-range parts
+ * -P_LRC and 2 P_LRC/V.  The paper does not offer these with Ewald summation;
+ * point dipoles are not covered either.  Needs ms2_options.massieu = 1 at
+ * creation, otherwise MS2_ESTATE. */
+/* U_V and U_VV of the current configuration. */
+MS2_API ms2_status ms2_volume_derivatives(ms2_system sys, double *dUdV, double *d2UdV2);
+/* A^r_mn, mn = 10, 01, 20, 11, 02, 30, 21, 12, from the samples of every step
+ * since ms2_reset_averages (MS2_ESTATE without samples); *n_samples may be NULL. */
+MS2_API ms2_status ms2_massieu(ms2_system sys, double A[8], long long *n_samples);
 
 /* Kernel timing: with on = 1, every subsequently enqueued batch of steps
  * records CUDA events (on the system stream) around its last step and around

@@ -54,7 +54,7 @@ __global__ void k_terms(const SysParams *, DevSys, double *);
 size_t ms2_pair_smem_bytes(int NS, bool dmu, bool multi, int TJ, int wpb);
 size_t ms2_pair64_smem_bytes(int TJ, int wpb);
 void *ms2_pick_pair_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, int *ns_used,
-                           bool *dmu, bool *mult_used);
+                           bool *dmu, bool *mult_used, bool mass);
 
 enum { RED_SUM = 1, RED_RECORD = 2, RED_LAMBDA = 4, RED_HALFKICK = 8, RED_FP64PART = 16, RED_EWALD = 32 };
 
@@ -271,6 +271,7 @@ void ms2_fill_params(SysParams &P, const ms2_model *models, int n_models, const 
         for (int a = 0; a < models[m].n_sites; ++a)
             if (P.bdip[m][a][0] != 0 || P.bdip[m][a][1] != 0 || P.bdip[m][a][2] != 0) any_d = true;
     P.has_dipole = any_d;
+    P.massieu = o.massieu != 0;
 }
 
 // Ewald constants (self, intramolecular, background) and the LJ long-range
@@ -420,7 +421,8 @@ static ms2_status setup_pair(ms2_system s) {
         s->dmu = false;
         s->multi_used = false;
     } else {
-        s->pair_fn = ms2_pick_pair_kernel(P.ns, ljm, qm, dm, P.elec, P.multi != 0, &s->ns, &s->dmu, &s->multi_used);
+        s->pair_fn = ms2_pick_pair_kernel(P.ns, ljm, qm, dm, P.elec, P.multi != 0, &s->ns, &s->dmu, &s->multi_used,
+                                          P.massieu != 0);
     }
     s->hp.ns = s->ns;
     return MS2_OK;
@@ -452,7 +454,7 @@ static ms2_status size_pair_tiles(ms2_system s) {
 static void setup_fused(ms2_system s, const ms2_options &o) {
     s->fuse_fn = s->step_fn = nullptr;
     if (s->fp64 || s->hp.integrator == MS2_INT_VERLET || s->hp.elec == ELEC_EWALD || s->multi_used) return;
-    void *fn = ms2_pick_step_kernel(s->ns, s->ljm, s->qm, s->dm, s->hp.elec, false);
+    void *fn = ms2_pick_step_kernel(s->ns, s->ljm, s->qm, s->dm, s->hp.elec, false, s->hp.massieu != 0);
     if (!fn) return;
     int coop = 0, sms = 0, optin = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device) != cudaSuccess || !coop) return;
@@ -834,6 +836,11 @@ extern "C" ms2_status ms2_create_system(const ms2_model *models, const int *N_pe
         return ms2_fail(MS2_EINVAL, "fp64 pair arithmetic is available for single-site LJ models only");
     }
     setup_pair(s);
+    if (s->hp.massieu && (elec == MS2_ELEC_EWALD || s->hp.has_dipole || !s->pair_fn)) {
+        delete s;
+        return ms2_fail(MS2_EINVAL, "Massieu derivatives: LJ and point-charge models with the reaction field or no "
+                                    "electrostatics (no Ewald, no point dipoles)");
+    }
     setup_fused(s, o);
     pick_launch_shape(s);
     st = sys_alloc(s);
@@ -1293,6 +1300,49 @@ extern "C" ms2_status ms2_averages(ms2_system s, double out[5], long long *n_ste
     out[3] = err(ac[AC_SBU], ac[AC_SBU2]);
     out[4] = err(ac[AC_SBP], ac[AC_SBP2]);
     if (n_steps) *n_steps = (long long)ac[AC_N];
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_volume_derivatives(ms2_system s, double *dUdV, double *d2UdV2) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (!s->hp.massieu) return ms2_fail(MS2_ESTATE, "created without ms2_options.massieu");
+    double sc[SC_COUNT_];
+    ms2_status st = read_scalars(s, sc);
+    if (st != MS2_OK) return st;
+    if (dUdV) *dUdV = sc[SC_UV];
+    if (d2UdV2) *d2UdV2 = sc[SC_UVV];
+    return MS2_OK;
+}
+
+// Residual Massieu derivatives from the running moments (formulas in ms2.h):
+// canonical moments of U, U_V = dU/dV and U_VV = d2U/dV2, with beta = 1/T0.
+extern "C" ms2_status ms2_massieu(ms2_system s, double A[8], long long *n_samples) {
+    if (!s || !A) return ms2_fail(MS2_EINVAL, "null argument");
+    if (!s->hp.massieu) return ms2_fail(MS2_ESTATE, "created without ms2_options.massieu");
+    double ac[AC_COUNT_];
+    MS2_CUDA_OK(cudaMemcpyAsync(ac, s->d.acc, sizeof ac, cudaMemcpyDeviceToHost, s->stream));
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    if (n_samples) *n_samples = (long long)ac[AC_MN];
+    if (ac[AC_MN] < 1.0) return ms2_fail(MS2_ESTATE, "no samples since the last ms2_reset_averages");
+    const double n = ac[AC_MN], b = s->hp.inv_T0, V = s->hp.V, Nm = (double)s->N;
+    // first moments of the shifted samples, then central second and third moments
+    const double ex = ac[AC_MX] / n, ey = ac[AC_MY] / n, ew = ac[AC_MW] / n;
+    const double exx = ac[AC_MX2] / n, eyy = ac[AC_MY2] / n, exy = ac[AC_MXY] / n;
+    const double varU = exx - ex * ex, varV = eyy - ey * ey, covUV = exy - ex * ey;
+    const double covUW = ac[AC_MXW] / n - ex * ew;
+    const double cU3 = ac[AC_MX3] / n - 3.0 * ex * exx + 2.0 * ex * ex * ex;
+    const double cU2V = ac[AC_MX2Y] / n - 2.0 * ex * exy - ey * exx + 2.0 * ex * ex * ey;
+    const double cUV2 = ac[AC_MXY2] / n - 2.0 * ey * exy - ex * eyy + 2.0 * ex * ey * ey;
+    const double mU = ac[AC_MU0] + ex, mUV = ac[AC_MV0] + ey;
+    A[0] = b * mU / Nm;                                                    // A10
+    A[1] = -b * V * mUV / Nm;                                              // A01
+    A[2] = -b * b * varU / Nm;                                             // A20
+    A[3] = -b * V / Nm * (mUV - b * covUV);                                // A11
+    A[4] = b / Nm * (2.0 * V * mUV + V * V * (ew - b * varV));             // A02
+    A[5] = b * b * b * cU3 / Nm;                                           // A30
+    A[6] = b * b * V / Nm * (2.0 * covUV - b * cU2V);                      // A21
+    A[7] = b / Nm * (2.0 * V * (mUV - b * covUV) +
+                     V * V * (ew - 2.0 * b * varV - b * covUW + b * b * cUV2));  // A12
     return MS2_OK;
 }
 

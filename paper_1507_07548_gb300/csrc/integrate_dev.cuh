@@ -140,7 +140,7 @@ enum { RED_SUM = 1, RED_RECORD = 2, RED_LAMBDA = 4, RED_HALFKICK = 8, RED_FP64PA
 // per-step scalars: potential energy (pair part), virial (pair + reciprocal
 // molecular correction), kinetic energy of the stored velocities (translation,
 // rotation), kinetic energy after the kick, non-finite force flag
-enum { Q_U = 0, Q_W, Q_KTR, Q_KROT, Q_K1, Q_BAD, Q_N };
+enum { Q_U = 0, Q_W, Q_KTR, Q_KROT, Q_K1, Q_BAD, Q_VV, Q_N };  // Q_VV: d2U/dV2 owner sums
 
 // final fixed-order scalars of a step; run by the last block
 __device__ __forceinline__ void finish_step(const SysParams *__restrict__ P, const DevSys &S, int mode, const double *tot) {
@@ -152,6 +152,10 @@ __device__ __forceinline__ void finish_step(const SysParams *__restrict__ P, con
         sc[SC_UTOT] = U;
         sc[SC_WTOT] = W;
         sc[SC_UNSTABLE] = tot[Q_BAD] > 0 ? 1.0 : 0.0;
+    }
+    if ((mode & RED_SUM) && P->massieu) {  // volume derivatives of this configuration (Sec. 2, Eq. 1)
+        sc[SC_UV] = -sc[SC_WTOT] * (1.0 / 3.0) * P->inv_V - sc[SC_PLRC];
+        sc[SC_UVV] = 0.5 * tot[Q_VV] * (1.0 / 9.0) * P->inv_V * P->inv_V + 2.0 * sc[SC_PLRC] * P->inv_V;
     }
     const double ketr = tot[Q_KTR] * ikc, kerot = tot[Q_KROT] * ikc;
     sc[SC_KETR_NOW] = ketr;
@@ -167,6 +171,24 @@ __device__ __forceinline__ void finish_step(const SysParams *__restrict__ P, con
         ac[AC_BN] += 1.0;
         ac[AC_BU] += sc[SC_UTOT];
         ac[AC_BP] += sc[SC_P];
+        if (P->massieu) {  // Massieu-derivative moments, shifted by the first sample
+            if (ac[AC_MN] == 0.0) {
+                ac[AC_MU0] = sc[SC_UTOT];
+                ac[AC_MV0] = sc[SC_UV];
+            }
+            const double x = sc[SC_UTOT] - ac[AC_MU0], y = sc[SC_UV] - ac[AC_MV0], w = sc[SC_UVV];
+            ac[AC_MN] += 1.0;
+            ac[AC_MX] += x;
+            ac[AC_MX2] += x * x;
+            ac[AC_MX3] += x * x * x;
+            ac[AC_MY] += y;
+            ac[AC_MY2] += y * y;
+            ac[AC_MXY] += x * y;
+            ac[AC_MX2Y] += x * x * y;
+            ac[AC_MXY2] += x * y * y;
+            ac[AC_MW] += w;
+            ac[AC_MXW] += x * w;
+        }
         if (ac[AC_BN] >= 100.0) {  // close a block of 100 steps
             const double bu = ac[AC_BU] * 0.01, bp = ac[AC_BP] * 0.01;
             ac[AC_NB] += 1.0;
@@ -327,7 +349,7 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
         const bool on = i < i_hi;
         const int ii = on ? i : i_lo, m = ii - io.i0;
         const int sp = sv.spc[m];
-        double x[Q_N] = {0, 0, 0, 0, 0, 0};
+        double x[Q_N] = {0, 0, 0, 0, 0, 0, 0};
         double Fc, Tc;
         if (mode & RED_SUM) {
             double a[3];  // partial values c, c + 4, c + 8, summed in j-range order
@@ -347,10 +369,12 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
             const double fx = val(PV_FX), fy = val(PV_FY), fz = val(PV_FZ);
             const double tx = val(PV_TX), ty = val(PV_TY), tz = val(PV_TZ);
             const double ulj = val(PV_ULJ), uqq = val(PV_UQQ), udd = val(PV_UDD), w = val(PV_W), np = val(PV_NP);
+            const double vvm = val(PV_VV);
             Fc = c == 0 ? fx : (c == 1 ? fy : fz);
             Tc = c == 0 ? tx : (c == 1 ? ty : tz);
             x[Q_U] = c == 0 ? ulj + uqq + udd : 0.0;
             x[Q_W] = c == 0 ? w : 0.0;
+            x[Q_VV] = c == 0 ? vvm : 0.0;
             if (!SH && (mode & RED_EWALD)) {  // reciprocal-space site forces, summed over k chunks (global layout)
                 const int NS = S.ns, M = S.nsite_q, c1 = (cc + 1) % 3, c2 = (cc + 2) % 3;
                 double wc = 0;  // -F_s.s_s molecular-virial correction, component c

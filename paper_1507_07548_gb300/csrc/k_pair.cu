@@ -34,10 +34,10 @@ size_t ms2_pair_smem_bytes(int NS, bool dmu, bool multi, int TJ, int wpb) {
 
 // grid: x = blocks of wpb molecules (one warp each), y = j-range; one FP32
 // partial per (j-range, molecule)
-template <int NS, unsigned LJM, unsigned QM, unsigned DM, int ELEC, bool MULTI>
+template <int NS, unsigned LJM, unsigned QM, unsigned DM, int ELEC, bool MULTI, bool MASS = false>
 __global__ void __launch_bounds__(256) k_pair(const SysParams *__restrict__ P, DevSys S, int TJ) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    using Eng = PairWarp<NS, LJM, QM, DM, ELEC, MULTI>;
+    using Eng = PairWarp<NS, LJM, QM, DM, ELEC, MULTI, MASS>;
     const int N = S.N;
     const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * wpb + warp;
@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(256) k_pair(const SysParams *__restrict__ P, D
         q[PV_TX * N] = o.T[0]; q[PV_TY * N] = o.T[1]; q[PV_TZ * N] = o.T[2];
         q[PV_ULJ * N] = o.ulj; q[PV_UQQ * N] = o.uqq; q[PV_UDD * N] = o.udd; q[PV_W * N] = o.w;
         q[PV_NP * N] = (float)o.np;
+        q[PV_VV * N] = o.vv;
     }
 }
 
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(256) k_pair_lj64(const SysParams *__restrict__
     const int ii = active ? i : 0;
     const uint32_t Xi = S.X[ii], Yi = S.X[N + ii], Zi = S.X[2 * N + ii];
     const double Rxi = S.R[ii], Ryi = S.R[N + ii], Rzi = S.R[2 * N + ii];
-    double fx = 0, fy = 0, fz = 0, u = 0, w = 0;
+    double fx = 0, fy = 0, fz = 0, u = 0, w = 0, vv = 0;
     int np = 0;
     for (int t0 = j0; t0 < j1; t0 += TJ) {
         const int tn = min(TJ, j1 - t0);
@@ -109,6 +110,7 @@ __global__ void __launch_bounds__(256) k_pair_lj64(const SysParams *__restrict__
             u += t12 - t6;
             fx += g * d[0]; fy += g * d[1]; fz += g * d[2];
             w -= g * r2;
+            vv += 180.0 * t12 - 54.0 * t6;  // u'' r^2 - 2 u' r of a point pair (Massieu derivatives)
             ++np;
         };
         for (int base = 0; base < tn; base += 32) {
@@ -137,13 +139,14 @@ __global__ void __launch_bounds__(256) k_pair_lj64(const SysParams *__restrict__
     }
     if (!active) return;
     fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
-    u = warp_sum(u); w = warp_sum(w); np = warp_sum(np);
+    u = warp_sum(u); w = warp_sum(w); vv = warp_sum(vv); np = warp_sum(np);
     if (lane == 0) {
         double *o = S.part64 + (size_t)p * MS2_NPV * N + i;
         o[PV_FX * N] = fx; o[PV_FY * N] = fy; o[PV_FZ * N] = fz;
         o[PV_TX * N] = 0; o[PV_TY * N] = 0; o[PV_TZ * N] = 0;
         o[PV_ULJ * N] = u; o[PV_UQQ * N] = 0; o[PV_UDD * N] = 0; o[PV_W * N] = w;
         o[PV_NP * N] = (double)np;
+        o[PV_VV * N] = vv;
     }
 }
 
@@ -158,35 +161,44 @@ struct PairVariant {
     int elec;
     bool multi;
     void (*fn)(const SysParams *, DevSys, int);
+    void (*mass)(const SysParams *, DevSys, int);  // variant that also sums d2U/dV2, or null
 };
 
-#define V(NS, LJM, QM, DM, E, M) {NS, LJM, QM, DM, E, M, &k_pair<NS, LJM, QM, DM, E, M>}
+#define V(NS, LJM, QM, DM, E, M) {NS, LJM, QM, DM, E, M, &k_pair<NS, LJM, QM, DM, E, M>, nullptr}
+#define VM(NS, LJM, QM, DM, E, M) \
+    {NS, LJM, QM, DM, E, M, &k_pair<NS, LJM, QM, DM, E, M>, &k_pair<NS, LJM, QM, DM, E, M, true>}
 static const PairVariant kVariants[] = {
-    V(1, 1u, 0u, 0u, ELEC_NONE, false),      // point LJ
-    V(3, 1u, 7u, 0u, ELEC_RF, false),        // 3-site water, reaction field
+    VM(1, 1u, 0u, 0u, ELEC_NONE, false),     // point LJ
+    VM(3, 1u, 7u, 0u, ELEC_RF, false),       // 3-site water, reaction field
     V(3, 1u, 7u, 0u, ELEC_EWALD, false),     // 3-site water, Ewald
     V(3, 1u, 7u, 0u, ELEC_EWALD, true),      // water + single-site ions, Ewald
     V(3, 3u, 0u, 4u, ELEC_RF, false),        // 2 LJ + dipole (Stockmayer-like)
 };
 #undef V
+#undef VM
 
 // generic fallbacks: runtime electrostatics, all slots may carry everything
 static void (*const kGeneric[2][2])(const SysParams *, DevSys, int) = {
     {&k_pair<4, 0xFu, 0xFu, 0u, -1, true>, &k_pair<4, 0xFu, 0xFu, 0xFu, -1, true>},
     {&k_pair<8, 0xFFu, 0xFFu, 0u, -1, true>, &k_pair<8, 0xFFu, 0xFFu, 0xFFu, -1, true>},
 };
+static void (*const kGenericMass)(const SysParams *, DevSys, int) = &k_pair<4, 0xFu, 0xFu, 0u, -1, true, true>;
 
 // Picks the kernel for a system's slot pattern.  Returns the padded slot count
 // the kernel expects in *ns_used (the site arrays must be laid out with it).
+// With mass, the variant that also sums the second volume derivative (null where
+// none is built: dipoles, Ewald, 8 site slots).
 void *ms2_pick_pair_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, int *ns_used,
-                           bool *dmu, bool *mult_used) {
+                           bool *dmu, bool *mult_used, bool mass) {
     for (const PairVariant &v : kVariants) {
-        if (v.ns == ns && v.ljm == ljm && v.qm == qm && v.dm == dm && v.elec == elec && v.multi == multi) {
+        if (v.ns == ns && v.ljm == ljm && v.qm == qm && v.dm == dm && v.elec == elec && v.multi == multi &&
+            (!mass || v.mass)) {
             *ns_used = ns;
             *dmu = dm != 0;
             *mult_used = multi;
-            return (void *)v.fn;
+            return (void *)(mass ? v.mass : v.fn);
         }
+        if (mass) continue;
         // a single-species system can use the multi-species variant of its pattern
         if (v.ns == ns && v.ljm == ljm && v.qm == qm && v.dm == dm && v.elec == elec && v.multi && !multi) {
             bool exact_single = false;
@@ -205,5 +217,6 @@ void *ms2_pick_pair_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int e
     *ns_used = g ? 8 : 4;
     *dmu = dm != 0;
     *mult_used = true;
+    if (mass) return (g == 0 && dm == 0 && elec != ELEC_EWALD) ? (void *)kGenericMass : nullptr;
     return (void *)kGeneric[g][dm != 0];
 }

@@ -153,10 +153,10 @@ __host__ __device__ inline OwnLayout own_layout(int mcap, int js, int rdf_cells)
     return o;
 }
 
-template <int NS, unsigned LJM, unsigned QM, unsigned DM, int ELEC, bool MULTI>
+template <int NS, unsigned LJM, unsigned QM, unsigned DM, int ELEC, bool MULTI, bool MASS = false>
 __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__restrict__ P, DevSys S, StepArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    using Eng = PairWarp<NS, LJM, QM, DM, ELEC, MULTI>;
+    using Eng = PairWarp<NS, LJM, QM, DM, ELEC, MULTI, MASS>;
     __shared__ double tot[MS2_NRED];
     __shared__ double lam_s;                    // thermostat factor for the next drift
     __shared__ unsigned long long tph[6];       // timing: entry, then the phase marks of the last step
@@ -247,6 +247,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
                 q[PV_TX * MC] = o.T[0]; q[PV_TY * MC] = o.T[1]; q[PV_TZ * MC] = o.T[2];
                 q[PV_ULJ * MC] = o.ulj; q[PV_UQQ * MC] = o.uqq; q[PV_UDD * MC] = o.udd; q[PV_W * MC] = o.w;
                 q[PV_NP * MC] = (float)o.np;
+                q[PV_VV * MC] = o.vv;
             }
         }
         if (A.rdf_every > 0 && ((A.s0 + k + 1) % A.rdf_every) == 0) {
@@ -333,14 +334,16 @@ int ms2_step_threads() { return STEP_THREADS; }
 
 // fused-step kernel of a pair-kernel variant, or null where the per-phase
 // kernels are used (Ewald, FP64, 8 site slots)
-void *ms2_pick_step_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi) {
+void *ms2_pick_step_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, bool mass) {
     if (elec == ELEC_EWALD) return nullptr;
     if (!multi) {
         if (ns == 1 && ljm == 1 && qm == 0 && dm == 0 && elec == ELEC_NONE)
-            return (void *)&k_step<1, 1u, 0u, 0u, ELEC_NONE, false>;
+            return mass ? (void *)&k_step<1, 1u, 0u, 0u, ELEC_NONE, false, true>
+                        : (void *)&k_step<1, 1u, 0u, 0u, ELEC_NONE, false>;
         if (ns == 3 && ljm == 1 && qm == 7 && dm == 0 && elec == ELEC_RF)
-            return (void *)&k_step<3, 1u, 7u, 0u, ELEC_RF, false>;
-        if (ns == 3 && ljm == 3 && qm == 0 && dm == 4 && elec == ELEC_RF)
+            return mass ? (void *)&k_step<3, 1u, 7u, 0u, ELEC_RF, false, true>
+                        : (void *)&k_step<3, 1u, 7u, 0u, ELEC_RF, false>;
+        if (ns == 3 && ljm == 3 && qm == 0 && dm == 4 && elec == ELEC_RF && !mass)
             return (void *)&k_step<3, 3u, 0u, 4u, ELEC_RF, false>;
     }
     return nullptr;

@@ -80,6 +80,6 @@ ms2_status ms2_validate_models(const ms2_model *models, int n_models, ms2_elec e
 // fused step kernel (k_step.cu)
 size_t ms2_step_smem_bytes(int NS, bool dmu, bool multi, int Np, int mcap, int js, int rdf_cells);
 int ms2_step_threads();
-void *ms2_pick_step_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi);
+void *ms2_pick_step_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, bool mass);
 cudaError_t ms2_launch_step(void *fn, int grid, size_t smem, cudaStream_t st, const SysParams *P, const DevSys &S,
                             const StepArgs &A);

@@ -23,7 +23,7 @@
 #define MS2_NRED 16        // per-block reduction scalars
 
 // partial-slot meaning
-enum { PV_FX = 0, PV_FY, PV_FZ, PV_TX, PV_TY, PV_TZ, PV_ULJ, PV_UQQ, PV_UDD, PV_W, PV_NP, PV_SPARE };
+enum { PV_FX = 0, PV_FY, PV_FZ, PV_TX, PV_TY, PV_TZ, PV_ULJ, PV_UQQ, PV_UDD, PV_W, PV_NP, PV_VV };  // PV_VV: d2U/dV2 sum
 
 enum { ELEC_NONE = 0, ELEC_RF = 1, ELEC_EWALD = 2 };
 
@@ -31,7 +31,7 @@ enum { ELEC_NONE = 0, ELEC_RF = 1, ELEC_EWALD = 2 };
 struct SysParams {
     int N, ns, n_species, n_ljt;
     int elec, integrator, thermostat, quat_iters;
-    int has_dipole, multi, ndof, pad0;
+    int has_dipole, multi, ndof, massieu;  // massieu: sample the Massieu-derivative moments
     double L, V, dt, kconv, T0;
     double inv_kconv, inv_ndof, inv_V, inv_T0;   // host-side reciprocals (no FP64 divide per step)
     double inv_mass[MS2_MAXSP];
@@ -104,13 +104,16 @@ enum {
     SC_ULJ = 0, SC_UQQ, SC_UDD, SC_WPAIR, SC_NPAIRS, SC_KETR, SC_KEROT, SC_LAMBDA,
     SC_UREC, SC_WREC_AT, SC_WREC_CORR, SC_UCONST, SC_PLRC, SC_ULRC, SC_WBG, SC_UNSTABLE,
     SC_UTOT, SC_WTOT, SC_P, SC_T, SC_KETR_NOW, SC_KEROT_NOW, SC_STEP,
+    SC_UV, SC_UVV,  // dU/dV and d2U/dV2 of the current configuration (with the Massieu option)
     SC_TPAIR,  // fused step: pair-phase time of the last step of a chunk (ns)
     SC_TPH0, SC_TPH1, SC_TPH2, SC_TPH3, SC_TPH4, SC_TPH5, SC_TPH6, SC_TPH7, SC_TPH8,  // fused step: phase times (ns)
     SC_KERR,   // fused step: a grid-barrier wait timed out (sticky until read)
     SC_COUNT_
 };
-// running averages
-enum { AC_N = 0, AC_U, AC_P, AC_T, AC_BN, AC_BU, AC_BP, AC_NB, AC_SBU, AC_SBU2, AC_SBP, AC_SBP2, AC_COUNT_ };
+// running averages; AC_M*: Massieu-derivative moment sums of x = U - U0, y = U_V - V0, w = U_VV
+enum { AC_N = 0, AC_U, AC_P, AC_T, AC_BN, AC_BU, AC_BP, AC_NB, AC_SBU, AC_SBU2, AC_SBP, AC_SBP2,
+       AC_MN, AC_MX, AC_MX2, AC_MX3, AC_MY, AC_MY2, AC_MXY, AC_MX2Y, AC_MXY2, AC_MW, AC_MXW, AC_MU0, AC_MV0,
+       AC_COUNT_ };
 
 // launch arguments of the fused step kernel (k_step.cu)
 struct StepArgs {

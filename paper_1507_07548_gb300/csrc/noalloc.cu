@@ -59,7 +59,7 @@ __global__ void k_reduce(const SysParams *, DevSys, int);
 __global__ void k_aos3(const double *src, double *dst, int N);
 size_t ms2_pair_smem_bytes(int NS, bool dmu, bool multi, int TJ, int wpb);
 void *ms2_pick_pair_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, int *ns_used,
-                           bool *dmu, bool *mult_used);
+                           bool *dmu, bool *mult_used, bool mass);
 ms2_status ms2_validate_models(const ms2_model *models, int n_models, ms2_elec elec);
 void ms2_fill_params(SysParams &P, const ms2_model *models, int n_models, const std::vector<int> &species, double L,
                      double rc, ms2_elec elec, const ms2_options &o, double T0);
@@ -142,7 +142,7 @@ extern "C" ms2_status ms2_forces_noalloc(const ms2_model *models, const int *N_p
         }
     int ns = 1;
     bool dmu = false, multi = false;
-    void *fn = ms2_pick_pair_kernel(hp.ns, ljm, qm, dm, hp.elec, hp.multi != 0, &ns, &dmu, &multi);
+    void *fn = ms2_pick_pair_kernel(hp.ns, ljm, qm, dm, hp.elec, hp.multi != 0, &ns, &dmu, &multi, false);
     if (ns > NA_NS) return ms2_fail(MS2_EINVAL, "ms2_forces_noalloc: at most %d site slots", NA_NS);
     hp.ns = ns;
     double coulomb, kconv, uconst, wbg, ulrc, plrc;

@@ -110,17 +110,24 @@ __device__ __forceinline__ Smem shifted(const Smem &m, int t0) {
     return v;
 }
 
-// result of one molecule (valid in lane 0): F, tau, U_lj, U_qq, U_dd, W, partners
+// result of one molecule (valid in lane 0): F, tau, U_lj, U_qq, U_dd, W,
+// the second-volume-derivative sum vv (MASS) and the partner count
 struct PairOut {
-    float F[3], T[3], ulj, uqq, udd, w;
+    float F[3], T[3], ulj, uqq, udd, w, vv;
     int np;
 };
 
 // NS: site slots per molecule; LJM/QM/DM: slot bit masks that may carry LJ,
 // charge, dipole; ELEC: ELEC_NONE/RF/EWALD or -1 = read from the parameters;
-// MULTI: several species (per-molecule parameter lookup).
-template <int NS, unsigned LJM, unsigned QM, unsigned DM, int ELEC, bool MULTI>
+// MULTI: several species (per-molecule parameter lookup); MASS: also the
+// second volume derivative of U for the Massieu derivatives (Sec. 2, Eq. 1):
+// per site pair h (r.d)^2 + g (d^2 - 2 r.d), with g = u'(r)/r and
+// h = (u''(r) - g)/r^2, whose owner sums over partners, halved and divided by
+// 9 V^2, give d2U/dV2 at fixed scaled centres (LJ and bare Coulomb; the
+// reaction-field k_RF and c_RF terms drop out of neutral molecule pairs).
+template <int NS, unsigned LJM, unsigned QM, unsigned DM, int ELEC, bool MULTI, bool MASS = false>
 struct PairWarp {
+    static_assert(!MASS || (DM == 0 && ELEC != ELEC_EWALD), "volume derivatives: LJ and point charges, no Ewald");
     static constexpr bool DMU = DM != 0;
     static constexpr bool MOLD = QM != 0 && (ELEC == ELEC_RF || ELEC < 0);  // molecular-dipole RF term
     int elec;
@@ -137,7 +144,7 @@ struct PairWarp {
     float si[NS][3], mui[NS][3], qih[NS], qil[NS], mdi[3];
     int ljti[NS];
     // lane accumulators
-    float fa[NS][3], ea[NS][3], ulj, uqq, udd, w, erf_[3];
+    float fa[NS][3], ea[NS][3], ulj, uqq, udd, w, vv, erf_[3];
     int np;
 
     __device__ __forceinline__ void setup(const SysParams *__restrict__ P) {
@@ -220,7 +227,7 @@ struct PairWarp {
         for (int a = 0; a < NS; ++a)
 #pragma unroll
             for (int k = 0; k < 3; ++k) fa[a][k] = ea[a][k] = 0.f;
-        ulj = uqq = udd = w = 0.f;
+        ulj = uqq = udd = w = vv = 0.f;
         erf_[0] = erf_[1] = erf_[2] = 0.f;
         np = 0;
     }
@@ -247,7 +254,8 @@ struct PairWarp {
     // Molecular virial, owner share: the site-pair part -sum_ab f_ab.r_ab here
     // (short levers, no FP32 force sum meets the long lever d), the
     // intramolecular part -2 sum_a s_ia.F_ia once per molecule in finish().
-    float wsite = 0.f;
+    float wsite = 0.f, wvv = 0.f;
+    const float dd2 = MASS ? dx * dx + dy * dy + dz * dz : 0.f;
 #pragma unroll
     for (int a = 0; a < NS; ++a) {
 #pragma unroll
@@ -263,7 +271,7 @@ struct PairWarp {
             float rinv = rsqrtf(r2);
             rinv = fmaf(rinv, fmaf(-0.5f * r2 * rinv, rinv, 0.5f), rinv);
             const float rinv2 = rinv * rinv;
-            float g = 0.f;
+            float g = 0.f, hh = 0.f;  // u'/r and (u'' - u'/r)/r^2 (MASS)
             if (mlj) {
                 float c6, c12, c6l, c12l;
                 if (MULTI) {
@@ -284,6 +292,7 @@ struct PairWarp {
                 const float t6 = fmaf(c6, r6, c6l * r6), t12 = fmaf(c12, r12, c12l * r12);
                 ulj += t12 - t6;
                 g += (6.f * t6 - 12.f * t12) * rinv2;
+                if (MASS) hh += (168.f * t12 - 48.f * t6) * (rinv2 * rinv2);
             }
             if (mq && elec != ELEC_NONE) {
                 float cqq, cql;
@@ -306,7 +315,9 @@ struct PairWarp {
                     bg = -(ec * rinv + tasp * ex) * rinv2;
                 }
                 uqq += fmaf(cqq, bu, cql * bu);
-                g += fmaf(cqq, bg, cql * bg);
+                const float gq = fmaf(cqq, bg, cql * bg);
+                g += gq;
+                if (MASS) hh -= 3.f * gq * rinv2;  // bare Coulomb: h = 3 C q q / r^5
             }
             if (md && elec != ELEC_NONE) {
                 const float rinv3 = rinv * rinv2, rinv5 = rinv3 * rinv2, rinv7 = rinv5 * rinv2;
@@ -329,9 +340,14 @@ struct PairWarp {
             }
             fa[a][0] = fmaf(g, rx, fa[a][0]); fa[a][1] = fmaf(g, ry, fa[a][1]); fa[a][2] = fmaf(g, rz, fa[a][2]);
             wsite = fmaf(-g, r2, wsite);
+            if (MASS) {
+                const float rd = rx * dx + ry * dy + rz * dz;
+                wvv += fmaf(hh * rd, rd, g * (dd2 - 2.f * rd));
+            }
         }
     }
     w += wsite;
+    if (MASS) vv += wvv;
     if (MOLD && rfq) {
         erf_[0] += sm.tmd[jl];
         erf_[1] += sm.tmd[TJ + jl];
@@ -385,6 +401,7 @@ struct PairWarp {
         o.uqq = warp_sum(uqq);
         o.udd = warp_sum(udd);
         o.w = warp_sum(w);
+        o.vv = MASS ? warp_sum(vv) : 0.f;
         o.np = warp_sum(np);
         o.F[0] = o.F[1] = o.F[2] = o.T[0] = o.T[1] = o.T[2] = 0.f;
         if (lane == 0) {

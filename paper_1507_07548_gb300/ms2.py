@@ -46,7 +46,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 class ms2_options(C.Structure):
     _fields_ = [("eps_rf", C.c_double), ("lrc", C.c_int), ("dt", C.c_double), ("thermostat", C.c_int),
                 ("seed", C.c_ulonglong), ("integrator", C.c_int), ("reduced", C.c_int), ("quat_iters", C.c_int),
-                ("graph_chunk", C.c_int), ("fp64", C.c_int), ("fused_step", C.c_int), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN),
+                ("graph_chunk", C.c_int), ("fp64", C.c_int), ("massieu", C.c_int), ("fused_step", C.c_int), ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN),
                 ("dev_free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
@@ -98,6 +98,8 @@ SIGNATURES = {
     "ms2_serve_drain": (C.c_int, [_vp, C.c_double]),
     "ms2_serve_close": (C.c_int, [_vp]),
     "ms2_enable_timing": (C.c_int, [_vp, C.c_int]),
+    "ms2_volume_derivatives": (C.c_int, [_vp, _d, _d]),
+    "ms2_massieu": (C.c_int, [_vp, _d, _P(C.c_longlong)]),
     "ms2_step_kernel": (C.c_int, [_vp, _P(C.c_int)]),
     "ms2_last_step_phases": (C.c_int, [_vp, _d]),
     "ms2_last_step_times": (C.c_int, [_vp, _d]),
@@ -295,6 +297,21 @@ class System:
 
     def enable_timing(self, on=True):
         check(lib().ms2_enable_timing(self.h, int(on)))
+
+    def volume_derivatives(self):
+        """(dU/dV, d2U/dV2) of the current configuration (needs massieu=1 at creation)."""
+        a, b = C.c_double(), C.c_double()
+        check(lib().ms2_volume_derivatives(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    MASSIEU_NAMES = ("A10", "A01", "A20", "A11", "A02", "A30", "A21", "A12")
+
+    def massieu(self):
+        """Residual Massieu derivatives A^r_mn from the samples since reset_averages, and their count."""
+        out = np.zeros(8)
+        n = C.c_longlong()
+        check(lib().ms2_massieu(self.h, _dp(out), C.byref(n)))
+        return dict(zip(self.MASSIEU_NAMES, out)), n.value
 
     def fused_step(self):
         """1 if the next chunk of steps runs as the fused cooperative kernel."""
