@@ -77,9 +77,12 @@ def _load():
             "or_rc2_lattice": [C.c_double, C.c_double], "or_lattice": [C.c_double, C.c_double],
             "or_volume_derivatives": [P(_Sys), d, d, d],
             "or_massieu": [d, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, d],
+            "or_current": [P(_Sys), d, d], "or_flux_acf": [d, C.c_int, C.c_int, d],
+            "or_conductivity": [d, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int],
         }
         for name, args in sig.items():
             getattr(_lib, name).argtypes = args
+        _lib.or_conductivity.restype = C.c_double
         _lib.or_pressure.argtypes = [P(_Sys), C.c_double, d]
         _lib.or_pressure.restype = C.c_double
         _lib.or_ndof.restype = C.c_int
@@ -188,6 +191,27 @@ class Oracle:
         self.lib.or_volume_derivatives(self.ref, _p(np.ascontiguousarray(R, np.float64)),
                                        _p(np.ascontiguousarray(q, np.float64)), _p(out))
         return out[0], out[1]
+
+    def current(self, v):
+        """Electric current flux sum_k q_k v_k over net-charged molecules (Eq. 4)."""
+        j = np.zeros(3)
+        self.lib.or_current(self.ref, _p(np.ascontiguousarray(v, np.float64)), _p(j))
+        return j
+
+    @staticmethod
+    def flux_acf(j, n_lags):
+        """Autocorrelation <j(t).j(0)> of a flux series j (n x 3) over all time origins."""
+        a = np.ascontiguousarray(j, np.float64)
+        out = np.zeros(n_lags)
+        _load().or_flux_acf(_p(a), C.c_int(len(a)), C.c_int(n_lags), _p(out))
+        return out
+
+    @staticmethod
+    def conductivity(acf, dt_ext, V, T, reduced=False):
+        """Green-Kubo electric conductivity (Eq. 3) from the current ACF: S/m, or reduced."""
+        a = np.ascontiguousarray(acf, np.float64)
+        return _load().or_conductivity(_p(a), C.c_int(len(a)), C.c_double(dt_ext), C.c_double(V), C.c_double(T),
+                                       C.c_int(int(reduced)))
 
     @staticmethod
     def massieu(acc, U0, V0, beta, V, N):

@@ -632,6 +632,44 @@ void or_massieu(const double *acc, double U0, double V0, double beta, double V, 
     out[7] = (b / N) * (2.0 * V * (UV - b * cxy) + V * V * (mw - 2.0 * b * vy - b * cxw + b * b * m12));
 }
 
+/* ------------------------------ Green-Kubo electric conductivity (Sec. 4, Eqs. 3-4) */
+/* Electric current flux j_e = sum_k q_k v_k over the molecules with a net charge
+ * q_k = sum_a q_a (the neutral ones drop out), v_k the centre velocities. */
+void or_current(const or_system *s, const double *v, double *j) {
+    j[0] = j[1] = j[2] = 0.0;
+    for (int k = 0; k < s->N; ++k) {
+        int sp = s->species[k];
+        double qk = 0.0;
+        for (int a = 0; a < s->n_sites[sp]; ++a) qk += s->charge[sp][a];
+        for (int c = 0; c < 3; ++c) j[c] += qk * v[3 * k + c];
+    }
+}
+
+/* Autocorrelation of a flux series j[t][3], t = 0 .. n-1, sampled every extended
+ * time step, over all time origins: acf[m] = (1/(n - m)) sum_{t=m}^{n-1}
+ * j(t).j(t-m) for m < min(n, n_lags) (0 beyond).  The dot product sums the three
+ * spatial elements, as the 1/3 in the conductivity expects. */
+void or_flux_acf(const double *j, int n, int n_lags, double *acf) {
+    for (int m = 0; m < n_lags; ++m) {
+        double c = 0.0;
+        for (int t = m; t < n; ++t) c += dot3(j + 3 * t, j + 3 * (t - m));
+        acf[m] = m < n ? c / (double)(n - m) : 0.0;
+    }
+}
+
+/* sigma = 1/(3 V kB T) int_0^tmax <j_e(t).j_e(0)> dt with the trapezoidal rule over
+ * the n_lags lags of spacing dt_ext.  Units: q in e, v in A/fs, V in A^3, T in K,
+ * dt in fs -> sigma in S/m; reduced = 1: all quantities reduced, sigma reduced. */
+double or_conductivity(const double *acf, int n_lags, double dt_ext, double V, double T, int reduced) {
+    double integral = 0.0;
+    for (int m = 0; m < n_lags; ++m) integral += ((m == 0 || m == n_lags - 1) ? 0.5 : 1.0) * acf[m];
+    integral *= dt_ext;
+    if (reduced) return integral / (3.0 * V * T);
+    const double e = 1.602176634e-19, kB = 1.380649e-23;
+    /* (e A/fs)^2 fs = e^2 1e10 m^2/s^2 1e-15 s; V in 1e-30 m^3 */
+    return integral * e * e * 1e-5 / (3.0 * V * 1e-30 * kB * T);
+}
+
 /* ------------------------------------------------------ integrators (a5) */
 /* thermo record per step: U, W, KE_tr, KE_rot, P (after the step) */
 static void record(const or_system *s, const double *q, const double *v, const double *Lang, const double *terms,

@@ -657,3 +657,39 @@ def test_massieu_estimators_are_derivatives_of_the_exact_partition_function():
         expr = expr.subs(Bf(b), Bk[0]).subs(vals).subs(b, beta)
         want.append(float(expr))
     np.testing.assert_allclose(got, want, rtol=1e-8, atol=1e-14)
+
+
+# ------------------------------------------ Green-Kubo conductivity (Eqs. 3-4)
+def test_current_counts_net_charges_only():
+    wl = W.ionic_solution(n_water=30, n_ion_pairs=3, rc=5.0, seed=6)
+    o = Oracle.from_workload(wl)
+    v = np.zeros_like(wl.v)
+    assert np.allclose(o.current(v + np.array([0.3, -0.1, 0.2])), 0.0, atol=1e-15)  # neutral overall: no current
+    k = int(np.nonzero(wl.species == 1)[0][0])                                      # one cation alone
+    v[k] = [1.0, 2.0, -3.0]
+    np.testing.assert_allclose(o.current(v), [1.0, 2.0, -3.0], rtol=1e-15)
+    v[:] = 0.0
+    v[wl.species == 0] = 5.0                                                         # water carries no current
+    assert np.allclose(o.current(v), 0.0, atol=1e-12)
+
+
+def test_flux_acf_of_a_rotating_current_is_a_cosine():
+    """j(t) = A (cos w t, sin w t, 0): j(t).j(t - m) = A^2 cos(w m dt) for every origin."""
+    A, w, dt, n, M = 1.7, 0.31, 0.5, 300, 40
+    t = np.arange(n) * dt
+    j = A * np.stack([np.cos(w * t), np.sin(w * t), np.zeros(n)], 1)
+    acf = Oracle.flux_acf(j, M)
+    np.testing.assert_allclose(acf, A * A * np.cos(w * np.arange(M) * dt), rtol=1e-12, atol=1e-13)
+    assert Oracle.flux_acf(j[:10], 20)[10:].max() == 0.0     # lags beyond the series stay empty
+
+
+def test_conductivity_units_and_rule():
+    """A constant ACF c over M lags integrates to c (M-1) dt; 1 (e A/fs)^2 fs over
+    3 V kB T with V = 1000 A^3, T = 300 K is e^2 1e-5 / (3e-27 kB 300) S/m."""
+    acf = np.full(11, 2.0)
+    got = Oracle.conductivity(acf, 0.5, 1000.0, 300.0)
+    e, kB = 1.602176634e-19, 1.380649e-23
+    assert got == pytest.approx(2.0 * 10 * 0.5 * e * e * 1e-5 / (3 * 1000e-30 * kB * 300.0), rel=1e-14)
+    cos_acf = np.cos(0.2 * np.arange(50))
+    assert Oracle.conductivity(cos_acf, 1.0, 1.0, 1.0, reduced=True) == pytest.approx(
+        np.trapezoid(cos_acf) / 3.0, rel=1e-14)
