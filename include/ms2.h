@@ -283,6 +283,24 @@ MS2_API ms2_status ms2_volume_derivatives(ms2_system sys, double *dUdV, double *
  * since ms2_reset_averages (MS2_ESTATE without samples); *n_samples may be NULL. */
 MS2_API ms2_status ms2_massieu(ms2_system sys, double A[8], long long *n_samples);
 
+/* ------------------------------------------- Green-Kubo conductivity */
+/* Paper Sec. 4, Eqs. 3-4: sigma = 1/(3 V kB T) int_0^inf <j_e(t).j_e(0)> dt with
+ * the electric current flux j_e = sum_k q_k v_k over the net-charged molecules
+ * (q_k = sum of the molecule's site charges; neutral molecules drop out), sampled
+ * every `every` MD steps (the extended time step).  Reading: v_k is the stored
+ * centre velocity after the step (the half-step velocity of the leapfrog, the one
+ * the reported temperature uses).  The autocorrelation runs over all time origins
+ * on the device: a ring of the last n_lags samples and one sum per lag in sample
+ * order.  Setup (re)allocates and zeroes the sampling state; MS2_EINVAL for
+ * every < 1 or n_lags outside 2..2^20.  Systems that sample are not batched. */
+MS2_API ms2_status ms2_conductivity_setup(ms2_system sys, int every, int n_lags);
+/* The flux j_e (e A/fs, or reduced) of the last sample. */
+MS2_API ms2_status ms2_current(ms2_system sys, double j[3]);
+/* sigma (S/m; reduced units for reduced systems) from the trapezoidal integral of
+ * the autocorrelation over the n_lags lags, T = T0; acf (n_lags values of
+ * <j(t).j(0)>, may be NULL) and *n_samples (may be NULL).  MS2_ESTATE without setup. */
+MS2_API ms2_status ms2_conductivity(ms2_system sys, double *sigma, double *acf, long long *n_samples);
+
 /* Kernel timing: with on = 1, every subsequently enqueued batch of steps
  * records CUDA events (on the system stream) around its last step and around
  * that step's pair kernel and Ewald kernels.  ms2_last_step_times synchronises

@@ -56,7 +56,6 @@ size_t ms2_pair64_smem_bytes(int TJ, int wpb);
 void *ms2_pick_pair_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, int *ns_used,
                            bool *dmu, bool *mult_used, bool mass);
 
-enum { RED_SUM = 1, RED_RECORD = 2, RED_LAMBDA = 4, RED_HALFKICK = 8, RED_FP64PART = 16, RED_EWALD = 32 };
 
 // ------------------------------------------------------------ allocation
 cudaError_t DevAlloc::alloc(void **p, size_t n) {
@@ -252,6 +251,11 @@ void ms2_fill_params(SysParams &P, const ms2_model *models, int n_models, const 
         for (int k = 0; k < 3; ++k) P.half_Iinv[m][k] = 0.5 * P.Iinv[m][k];
     }
     P.lam_c = 2.0 * P.inv_kconv * P.inv_ndof * P.inv_T0;
+    for (int m = 0; m < MS2_MAXSP; ++m) {
+        P.qmol[m] = 0.0;
+        if (m < n_models)
+            for (int a = 0; a < models[m].n_sites; ++a) P.qmol[m] += models[m].sites[a].charge;
+    }
     P.ns = ns;
     P.n_ljt = t;
     for (int a = 0; a < t; ++a)
@@ -559,6 +563,7 @@ static void enqueue_steps(ms2_system s, long long n, long long s0) {
     const int every = s->rdf_every;
     for (long long k = 0; k < n; ++k) {
         const bool sample = every > 0 && ((s0 + k + 1) % every) == 0;
+        const bool gk = s->d.gk && s->gk_every > 0 && ((s0 + k + 1) % s->gk_every) == 0;
         const bool tm = s->timing && k == n - 1;
         if (tm) cudaEventRecordWithFlags(s->ev[0], s->stream, cudaEventRecordExternal);
         launch_drift(s);
@@ -568,14 +573,15 @@ static void enqueue_steps(ms2_system s, long long n, long long s0) {
         if (tm) cudaEventRecordWithFlags(s->ev[2], s->stream, cudaEventRecordExternal);
         launch_ewald(s);
         if (tm) cudaEventRecordWithFlags(s->ev[3], s->stream, cudaEventRecordExternal);
-        launch_reduce(s, verlet ? (RED_SUM | RED_RECORD | RED_HALFKICK) : (RED_SUM | RED_RECORD));
+        launch_reduce(s, (verlet ? (RED_SUM | RED_RECORD | RED_HALFKICK) : (RED_SUM | RED_RECORD)) | (gk ? RED_GK : 0));
         if (tm) cudaEventRecordWithFlags(s->ev[4], s->stream, cudaEventRecordExternal);
     }
 }
 
 static ms2_status run_graph(ms2_system s, long long n, long long s0) {
     const int phase = s->rdf_every > 0 ? (int)(s0 % s->rdf_every) : 0;
-    const auto key = std::make_pair((int)n, phase);
+    const int gphase = (s->d.gk && s->gk_every > 0) ? (int)(s0 % s->gk_every) : -1;
+    const auto key = std::make_tuple((int)n, phase, gphase);
     auto it = s->graphs.find(key);
     if (it == s->graphs.end()) {
         if (s->graphs.size() > 16) {
@@ -973,6 +979,7 @@ static bool run_fused(ms2_system s, long long m, long long s0) {
     A.nsteps = (int)m;
     A.s0 = s0;
     A.rdf_every = s->d.rdf ? s->rdf_every : 0;
+    A.gk_every = s->d.gk ? s->gk_every : 0;
     A.TJ = s->TJ;
     A.Np = s->Np;
     A.mcap = s->mcap;
@@ -1343,6 +1350,63 @@ extern "C" ms2_status ms2_massieu(ms2_system s, double A[8], long long *n_sample
     A[6] = b * b * V / Nm * (2.0 * covUV - b * cU2V);                      // A21
     A[7] = b / Nm * (2.0 * V * (mUV - b * covUV) +
                      V * V * (ew - 2.0 * b * varV - b * covUW + b * b * cUV2));  // A12
+    return MS2_OK;
+}
+
+// ------------------------------------------------ Green-Kubo conductivity
+extern "C" ms2_status ms2_conductivity_setup(ms2_system s, int every, int n_lags) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (every < 1 || n_lags < 2 || n_lags > (1 << 20))
+        return ms2_fail(MS2_EINVAL, "need every >= 1 and 2 <= n_lags <= 2^20");
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    if (!s->d.gk || s->d.gk_lags != n_lags) {
+        double *g = nullptr;
+        MS2_CUDA_OK(s->al.alloc((void **)&g, sizeof(double) * (4 + 4 * (size_t)n_lags)));
+        s->d.gk = g;  // a previous, smaller buffer stays with the system until it is destroyed
+        s->d.gk_lags = n_lags;
+    }
+    MS2_CUDA_OK(cudaMemsetAsync(s->d.gk, 0, sizeof(double) * (4 + 4 * (size_t)n_lags), s->stream));
+    s->gk_every = every;
+    destroy_graphs(s);
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_current(ms2_system s, double j[3]) {
+    if (!s || !j) return ms2_fail(MS2_EINVAL, "null argument");
+    if (!s->d.gk) return ms2_fail(MS2_ESTATE, "conductivity sampling is off (ms2_conductivity_setup)");
+    double sc[SC_COUNT_];
+    ms2_status st = read_scalars(s, sc);
+    if (st != MS2_OK) return st;
+    for (int k = 0; k < 3; ++k) j[k] = sc[SC_JX + k];
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_conductivity(ms2_system s, double *sigma, double *acf, long long *n_samples) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (!s->d.gk) return ms2_fail(MS2_ESTATE, "conductivity sampling is off (ms2_conductivity_setup)");
+    const int M = s->d.gk_lags;
+    std::vector<double> g(4 + 4 * (size_t)M);
+    MS2_CUDA_OK(cudaMemcpyAsync(g.data(), s->d.gk, sizeof(double) * g.size(), cudaMemcpyDeviceToHost, s->stream));
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    const long long n = (long long)g[0];
+    if (n_samples) *n_samples = n;
+    const double *sums = g.data() + 4 + 3 * (size_t)M;
+    // autocorrelation over all time origins, then the trapezoidal integral
+    double integral = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const double c = m < n ? sums[m] / (double)(n - m) : 0.0;
+        if (acf) acf[m] = c;
+        integral += ((m == 0 || m == M - 1) ? 0.5 : 1.0) * c;
+    }
+    integral *= s->gk_every * s->hp.dt;
+    if (sigma) {
+        if (s->reduced) {
+            *sigma = integral / (3.0 * s->hp.V * s->hp.T0);
+        } else {  // e^2 (A/fs)^2 fs / (A^3 kB K) -> S/m
+            const double e = 1.602176634e-19, kB = 1.380649e-23;
+            *sigma = integral * e * e * 1e-5 / (3.0 * s->hp.V * 1e-30 * kB * s->hp.T0);
+        }
+    }
     return MS2_OK;
 }
 

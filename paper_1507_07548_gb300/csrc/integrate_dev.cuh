@@ -136,7 +136,7 @@ __device__ __forceinline__ void rot_column(const double q[4], int c, double col[
 }
 
 // ------------------------------------------------------------- reduction
-enum { RED_SUM = 1, RED_RECORD = 2, RED_LAMBDA = 4, RED_HALFKICK = 8, RED_FP64PART = 16, RED_EWALD = 32 };
+// reduction modes (RED_*) are in ms2_internal.cuh
 // per-step scalars: potential energy (pair part), virial (pair + reciprocal
 // molecular correction), kinetic energy of the stored velocities (translation,
 // rotation), kinetic energy after the kick, non-finite force flag
@@ -156,6 +156,11 @@ __device__ __forceinline__ void finish_step(const SysParams *__restrict__ P, con
     if ((mode & RED_SUM) && P->massieu) {  // volume derivatives of this configuration (Sec. 2, Eq. 1)
         sc[SC_UV] = -sc[SC_WTOT] * (1.0 / 3.0) * P->inv_V - sc[SC_PLRC];
         sc[SC_UVV] = 0.5 * tot[Q_VV] * (1.0 / 9.0) * P->inv_V * P->inv_V + 2.0 * sc[SC_PLRC] * P->inv_V;
+    }
+    if (mode & RED_GK) {
+        sc[SC_JX] = tot[Q_N];
+        sc[SC_JY] = tot[Q_N + 1];
+        sc[SC_JZ] = tot[Q_N + 2];
     }
     const double ketr = tot[Q_KTR] * ikc, kerot = tot[Q_KROT] * ikc;
     sc[SC_KETR_NOW] = ketr;
@@ -308,6 +313,26 @@ __device__ __forceinline__ double warp_sum8(double x[8], int lane) {
     return x[0];
 }
 
+// Fixed-tree sum of 4 values over a warp (5 FP64 adds); on return lane l holds
+// the total of value (l >> 3) & 3.
+__device__ __forceinline__ double warp_sum4(double x[4], int lane) {
+    const unsigned F = 0xffffffffu;
+    const bool u16 = lane & 16, u8 = lane & 8;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const double send = u16 ? x[k] : x[k + 2], keep = u16 ? x[k + 2] : x[k];
+        x[k] = keep + __shfl_xor_sync(F, send, 16);
+    }
+    {
+        const double send = u8 ? x[0] : x[1], keep = u8 ? x[1] : x[0];
+        x[0] = keep + __shfl_xor_sync(F, send, 8);
+    }
+    x[0] += __shfl_xor_sync(F, x[0], 4);
+    x[0] += __shfl_xor_sync(F, x[0], 2);
+    x[0] += __shfl_xor_sync(F, x[0], 1);
+    return x[0];
+}
+
 // Where a reduction unit reads the pair partials and writes the per-molecule
 // results: partial value v of j-range p for slot m at [(p * NPV + v) * pld + m];
 // energies k at Ui[k * uld + m], partner counts at np[m]; state through sv.
@@ -344,6 +369,7 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
     const StateView &sv = io.sv;
     const int ld = sv.ld;
     double r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double jr = 0.0;  // lane accumulator of the current flux, component c (RED_GK)
     for (int base = i_lo; base < i_hi; base += 8) {
         const int i = base + (lane >> 2);
         const bool on = i < i_hi;
@@ -445,23 +471,57 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
 #pragma unroll
             for (int k = 0; k < Q_N; ++k) r[k] += x[k];
         }
+        if (mode & RED_GK) {  // electric current flux: q_k v_k, component c in lane c
+            const double jc = (c < 3 && on) ? P->qmol[sp] * ldv<SH>(sv.v + cc * ld + m) : 0.0;
+            jr = (base == i_lo) ? jc : jr + jc;
+        }
     }
     const double t = warp_sum8(r, lane);
     const int k = (lane >> 2) & 7;
     if ((lane & 3) == 0 && k < Q_N) S.blk[(size_t)u * MS2_NRED + k] = t;
+    if (mode & RED_GK) {  // the three flux components: a 4-value fixed tree
+        double y[4] = {(lane & 3) == 0 ? jr : 0.0, (lane & 3) == 1 ? jr : 0.0, (lane & 3) == 2 ? jr : 0.0, 0.0};
+        const double tj = warp_sum4(y, lane);
+        const int kj = (lane >> 3) & 3;
+        if ((lane & 7) == 0 && kj < 3) S.blk[(size_t)u * MS2_NRED + Q_N + kj] = tj;
+    }
 }
 
 // Totals of the step scalars over the reduction units, fixed order: warp w
 // takes scalars w, w + nwarps, ...; lane l sums units l, l + 32, ... in order,
 // then a fixed shuffle tree.  Result in tot[0 .. Q_N) (shared memory).
-__device__ __forceinline__ void reduce_totals(const DevSys &S, int nvb, double *tot) {
+__device__ __forceinline__ void reduce_totals(const DevSys &S, int nvb, double *tot, int nq = Q_N) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = warp; k < Q_N; k += nw) {
+    for (int k = warp; k < nq; k += nw) {
         double x = 0;
         for (int b = lane; b < nvb; b += 32) x += __ldcg(S.blk + (size_t)b * MS2_NRED + k);
         x = warp_sum(x);
         if (lane == 0) tot[k] = x;
     }
+}
+
+// One conductivity sample j = tot[Q_N .. Q_N+2] into the flux ring and the lag
+// sums, by a whole warp: sums[m] += j(t).j(t - m) for m < min(samples, lags),
+// each sum in sample order (Sec. 4, Eqs. 3-4; the extended time step is the
+// sampling interval).
+__device__ __forceinline__ void gk_update(const DevSys &S, const double *tot, int lane) {
+    double *g = S.gk, *ring = g + 4, *sums = ring + 3 * (size_t)S.gk_lags;
+    const long long n = (long long)g[0];
+    const int M = S.gk_lags, slot = (int)(n % M);
+    const double j0 = tot[Q_N], j1 = tot[Q_N + 1], j2 = tot[Q_N + 2];
+    if (lane == 0) {
+        ring[3 * slot] = j0;
+        ring[3 * slot + 1] = j1;
+        ring[3 * slot + 2] = j2;
+    }
+    __syncwarp();
+    const int upto = (int)(n + 1 < M ? n + 1 : M);
+    for (int m = lane; m < upto; m += 32) {
+        const int sm = (slot - m + M) % M;
+        sums[m] += j0 * ring[3 * sm] + j1 * ring[3 * sm + 1] + j2 * ring[3 * sm + 2];
+    }
+    __syncwarp();
+    if (lane == 0) g[0] = (double)(n + 1);
 }
 
 // isokinetic factor sqrt(T0 / T') from the kicked kinetic energy (as finish_step)

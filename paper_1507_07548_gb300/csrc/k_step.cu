@@ -129,6 +129,11 @@ __device__ void rdf_tile(const SysParams *__restrict__ P, const DevSys &S, const
         if (hist[k]) atomicAdd(&S.rdf[k], (unsigned long long)hist[k]);
 }
 
+// step k of the launch samples the electric current flux
+__device__ __forceinline__ bool gk_step(const StepArgs &A, int k) {
+    return A.gk_every > 0 && ((A.s0 + k + 1) % A.gk_every) == 0;
+}
+
 }  // namespace
 
 static_assert(sizeof(SysParams) % 16 == 0, "the parameter copy moves 16-byte words");
@@ -231,10 +236,14 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         // ---- stage the whole system; pair items of the own molecules; RDF
         stage_tile<NS, Eng::DMU, MULTI>(sm, S, 0, N, A.Np, rfq);
         __syncthreads();
-        // the previous step's record (U, W, T, P, averages), off the critical
-        // path: block 0's last warp, which has no pair item unless 16 are due
-        if (k > 0 && b == 0 && threadIdx.x == STEP_THREADS - 32)
-            finish_step(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA, tot);
+        // the previous step's record (U, W, T, P, averages, a conductivity
+        // sample), off the critical path: block 0's last warp, which has no pair
+        // item unless 16 are due
+        if (k > 0 && b == 0 && warp == STEP_WARPS - 1) {
+            const int gk = gk_step(A, k - 1) ? RED_GK : 0;
+            if (lane == 0) finish_step(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA | gk, tot);
+            if (gk) gk_update(S, tot, lane);
+        }
         for (int t = warp; t < nm * JS; t += STEP_WARPS) {
             const int m = t % nm, p = t / nm, i = lo + m;
             const int j0 = (int)(((long long)N * p) / JS), j1 = (int)(((long long)N * (p + 1)) / JS);
@@ -264,13 +273,13 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         if (warp == 0) {
             const OwnLayout ol = own_layout(MC, JS, 0);
             const RedIO io{part_at(), nullptr, MC, view(), (double *)(own + ol.ui), (int *)(own + ol.np), MC, lo};
-            reduce_unit<true>(Ps, S, io, RED_SUM | RED_LAMBDA, b, G, lane);
+            reduce_unit<true>(Ps, S, io, RED_SUM | RED_LAMBDA | (gk_step(A, k) ? RED_GK : 0), b, G, lane);
         }
         mark(k, 2);
         grid_sync(A.bar, A.err, target, S.scal);
         if (tm) tph[3] = global_ns();
         // ---- totals in every block; thermostat factor for the next drift
-        reduce_totals(S, G, tot);
+        reduce_totals(S, G, tot, gk_step(A, k) ? Q_N + 3 : Q_N);
         __syncthreads();
         if (threadIdx.x == 0) lam_s = lambda_of(Ps, tot);
         __syncthreads();
@@ -292,7 +301,11 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     }
     // ---- the last step's record; own state, forces and per-molecule results
     // back to global memory
-    if (A.nsteps > 0 && b == 0 && threadIdx.x == 0) finish_step(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA, tot);
+    if (A.nsteps > 0 && b == 0 && warp == 0) {
+        const int gk = gk_step(A, A.nsteps - 1) ? RED_GK : 0;
+        if (lane == 0) finish_step(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA | gk, tot);
+        if (gk) gk_update(S, tot, lane);
+    }
     __syncthreads();
     const OwnLayout ol = own_layout(MC, JS, 0);
     const double *ui_s = (const double *)(own + ol.ui);

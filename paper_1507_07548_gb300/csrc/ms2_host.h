@@ -1,6 +1,7 @@
 // Host-side structures shared by the C-ABI, batch and serving translation units.
 #pragma once
 #include <map>
+#include <tuple>
 #include <string>
 #include <utility>
 #include <vector>
@@ -57,10 +58,11 @@ struct ms2_system_s {
     double uconst = 0, wbg = 0, ulrc = 0, plrc = 0;
     long long step = 0;
     int graph_chunk = 50;
-    std::map<std::pair<int, int>, GraphEntry> graphs;
+    std::map<std::tuple<int, int, int>, GraphEntry> graphs;  // (steps, RDF phase, conductivity phase)
     long long launch_acc = 0;
     // RDF
     int rdf_every = 0, rdf_samples = 0, rdf_cap = 0;
+    int gk_every = 0;  // conductivity: extended time step (0: off)
     double rdf_rmax = 0;
     // host staging of the state
     std::vector<double> hR, hq, hv, hL;

@@ -39,6 +39,7 @@ struct SysParams {
     // ~68 cycles on GB300): dt kconv, the kick dt kconv / M, M/2, I^-1 / 2 and
     // the thermostat constant 2 / (kconv ndof T0)
     double dtk, kick[MS2_MAXSP], half_mass[MS2_MAXSP], half_Iinv[MS2_MAXSP][3], lam_c;
+    double qmol[MS2_MAXSP];  // net molecular charge of each species (electric current flux)
     double lat_scale;          // 2^32 / L  (FP64, exact same value as the host computes)
     unsigned long long rc2;    // lattice cut-off threshold
     float lat_to_len;          // L / 2^32 (FP32 rounding of it)
@@ -73,6 +74,8 @@ struct DevSys {
     uint32_t *X;                       // [3][N]
     float *s, *mu;                     // [3][ns][N]
     float *mum;                        // [3][N] molecular dipole sum_a q_a s_ia (reaction field)
+    double *gk;                        // conductivity: [0] samples, [1..3] -, ring [gk_lags][3], lag sums [gk_lags]
+    int gk_lags;
     float *part;                       // [jsplit][NPV][N]
     double *part64;                    // FP64 partials (FP64 pair path)
     double *F, *tau;                   // [3][N]
@@ -105,6 +108,7 @@ enum {
     SC_UREC, SC_WREC_AT, SC_WREC_CORR, SC_UCONST, SC_PLRC, SC_ULRC, SC_WBG, SC_UNSTABLE,
     SC_UTOT, SC_WTOT, SC_P, SC_T, SC_KETR_NOW, SC_KEROT_NOW, SC_STEP,
     SC_UV, SC_UVV,  // dU/dV and d2U/dV2 of the current configuration (with the Massieu option)
+    SC_JX, SC_JY, SC_JZ,  // electric current flux of the last conductivity sample
     SC_TPAIR,  // fused step: pair-phase time of the last step of a chunk (ns)
     SC_TPH0, SC_TPH1, SC_TPH2, SC_TPH3, SC_TPH4, SC_TPH5, SC_TPH6, SC_TPH7, SC_TPH8,  // fused step: phase times (ns)
     SC_KERR,   // fused step: a grid-barrier wait timed out (sticky until read)
@@ -115,11 +119,18 @@ enum { AC_N = 0, AC_U, AC_P, AC_T, AC_BN, AC_BU, AC_BP, AC_NB, AC_SBU, AC_SBU2, 
        AC_MN, AC_MX, AC_MX2, AC_MX3, AC_MY, AC_MY2, AC_MXY, AC_MX2Y, AC_MXY2, AC_MW, AC_MXW, AC_MU0, AC_MV0,
        AC_COUNT_ };
 
+// modes of the reduction (k_reduce, the fused step): sum the pair partials,
+// record the step, form the thermostat factor, Verlet second half kick, FP64
+// partials, Ewald site forces, sample the electric current flux
+enum { RED_SUM = 1, RED_RECORD = 2, RED_LAMBDA = 4, RED_HALFKICK = 8, RED_FP64PART = 16, RED_EWALD = 32,
+       RED_GK = 64 };
+
 // launch arguments of the fused step kernel (k_step.cu)
 struct StepArgs {
     int nsteps;
     long long s0;          // step counter before the chunk (RDF sampling phase)
     int rdf_every;         // 0: no RDF sampling
+    int gk_every;          // 0: no conductivity sampling, else the extended time step in steps
     int TJ;                // j tile segmentation of the per-phase pair kernel
     int Np;                // stride of the staged system
     int mcap;              // molecules a block owns at most: ceil(N / gridDim.x)

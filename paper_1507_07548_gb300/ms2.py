@@ -100,6 +100,9 @@ SIGNATURES = {
     "ms2_enable_timing": (C.c_int, [_vp, C.c_int]),
     "ms2_volume_derivatives": (C.c_int, [_vp, _d, _d]),
     "ms2_massieu": (C.c_int, [_vp, _d, _P(C.c_longlong)]),
+    "ms2_conductivity_setup": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "ms2_current": (C.c_int, [_vp, _d]),
+    "ms2_conductivity": (C.c_int, [_vp, _d, _d, _P(C.c_longlong)]),
     "ms2_step_kernel": (C.c_int, [_vp, _P(C.c_int)]),
     "ms2_last_step_phases": (C.c_int, [_vp, _d]),
     "ms2_last_step_times": (C.c_int, [_vp, _d]),
@@ -303,6 +306,25 @@ class System:
         a, b = C.c_double(), C.c_double()
         check(lib().ms2_volume_derivatives(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def conductivity_setup(self, every, n_lags):
+        """Sample the electric current flux every `every` steps into an ACF of n_lags lags."""
+        check(lib().ms2_conductivity_setup(self.h, every, n_lags))
+        self._gk_lags = n_lags
+
+    def current(self):
+        """Electric current flux of the last sample (e A/fs)."""
+        j = np.zeros(3)
+        check(lib().ms2_current(self.h, _dp(j)))
+        return j
+
+    def conductivity(self):
+        """(sigma in S/m, the flux ACF, number of samples)."""
+        sig = C.c_double()
+        acf = np.zeros(self._gk_lags)
+        n = C.c_longlong()
+        check(lib().ms2_conductivity(self.h, C.byref(sig), _dp(acf), C.byref(n)))
+        return sig.value, acf, n.value
 
     MASSIEU_NAMES = ("A10", "A01", "A20", "A11", "A02", "A30", "A21", "A12")
 
