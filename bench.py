@@ -413,7 +413,7 @@ def serve_sub(args, capacity):
 
 
 MASSIEU_STEPS = 1000
-GK_STEPS = 2000
+GK_STEPS = 20000
 
 
 def massieu_sub(args, stream, flush):
@@ -470,11 +470,11 @@ def ewald_sub(args, stream):
             tp.append(t[0])
             te.append(t[1])
             pairs.append(s.energy_terms()["n_pairs"])
-    # the same system sampling the Green-Kubo current every 5 steps (200 lags),
+    # the same system sampling the Green-Kubo current every 5 steps (100 lags = 1 ps),
     # run in chunks as a production run would; the conductivity of so short a
     # run only illustrates the output
     s.enable_timing(False)
-    s.conductivity_setup(every=5, n_lags=200)
+    s.conductivity_setup(every=5, n_lags=100)
     nrun = GK_STEPS
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -489,7 +489,7 @@ def ewald_sub(args, stream):
             "ms_per_step": statistics.mean(ts), "pair_kernel_ms": statistics.mean(tp),
             "ewald_kernels_ms": statistics.mean(te),
             "conductivity": {"ms_per_step_in_chunks": e0.elapsed_time(e1) / nrun, "steps": nrun,
-                             "samples": nsamp, "extended_step": 5, "lags": 200, "sigma_S_per_m": sigma,
+                             "samples": nsamp, "extended_step": 5, "lags": 100, "sigma_S_per_m": sigma,
                              "note": "short run: sigma illustrates the output, it is not converged"}}
 
 
