@@ -78,6 +78,7 @@ def _load():
             "or_volume_derivatives": [P(_Sys), d, d, d],
             "or_massieu": [d, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, d],
             "or_current": [P(_Sys), d, d], "or_flux_acf": [d, C.c_int, C.c_int, d],
+            "or_residence": [P(_Sys), d, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, d, d],
             "or_conductivity": [d, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int],
         }
         for name, args in sig.items():
@@ -197,6 +198,16 @@ class Oracle:
         j = np.zeros(3)
         self.lib.or_current(self.ref, _p(np.ascontiguousarray(v, np.float64)), _p(j))
         return j
+
+    def residence(self, R_series, si, sj, r_shell, t_star, n_lags):
+        """Residence correlation (Eq. 7, Impey tolerance t_star in samples) of species sj
+        around si over configurations R_series (T x N x 3); returns (corr, solvation number)."""
+        Rs = np.ascontiguousarray(R_series, np.float64)
+        corr = np.zeros(n_lags)
+        nsol = C.c_double()
+        self.lib.or_residence(self.ref, _p(Rs), C.c_int(len(Rs)), C.c_int(si), C.c_int(sj), C.c_double(r_shell),
+                              C.c_int(t_star), C.c_int(n_lags), _p(corr), C.byref(nsol))
+        return corr, nsol.value
 
     @staticmethod
     def flux_acf(j, n_lags):

@@ -670,6 +670,60 @@ double or_conductivity(const double *acf, int n_lags, double dt_ext, double V, d
     return integral * e * e * 1e-5 / (3.0 * V * 1e-30 * kB * T);
 }
 
+/* ---------------------------------- residence time, solvation number (Sec. 4, Eq. 7) */
+/* Residence correlation of molecules of species sj around molecules of species si
+ * over a series of T configurations R[t][N][3] sampled every extended time step.
+ * "Within r_shell" is the minimum-image centre distance, decided on the integer
+ * centre lattice as the partner search decides the cut-off (R4).  Following Impey
+ * et al., molecule k (of species sj, k != i) counts at lag tau for origin t0 and
+ * centre i if it is in the shell at t0 and at t0 + tau and was never outside for
+ * more than t_star consecutive samples in between.  For every origin t0 and centre
+ * i with n_i(t0) > 0 shell members, the fraction (count at tau) / n_i(t0) enters
+ * the average at lag tau, for tau < min(n_lags, T - t0):
+ *   corr[tau] = sum over (t0, i) of fraction / number of (t0, i) terms.
+ * The solvation number is the mean of n_i(t0) over all origins and centres. */
+void or_residence(const or_system *s, const double *R, int T, int si, int sj, double r_shell, int t_star,
+                  int n_lags, double *corr, double *solvation) {
+    int N = s->N;
+    uint64_t r2 = or_rc2_lattice(r_shell, s->L);
+    uint32_t *X = (uint32_t *)malloc(sizeof(uint32_t) * 3 * N * (size_t)T);
+    for (int t = 0; t < T; ++t) lattice_all(s, R + (size_t)t * 3 * N, X + (size_t)t * 3 * N);
+    double *num = (double *)calloc(n_lags, sizeof(double));
+    double *cnt = (double *)calloc(n_lags, sizeof(double));
+    double nsum = 0.0, ncount = 0.0;
+#define INSIDE(t, i, k) (lattice_d2(X + ((size_t)(t) * N + (i)) * 3, X + ((size_t)(t) * N + (k)) * 3) < r2)
+    for (int t0 = 0; t0 < T; ++t0)
+        for (int i = 0; i < N; ++i) {
+            if (s->species[i] != si) continue;
+            int n0 = 0;
+            for (int k = 0; k < N; ++k)
+                if (k != i && s->species[k] == sj && INSIDE(t0, i, k)) ++n0;
+            nsum += n0;
+            ncount += 1.0;
+            if (n0 == 0) continue;
+            for (int tau = 0; tau < n_lags && t0 + tau < T; ++tau) {
+                int alive = 0;
+                for (int k = 0; k < N; ++k) {
+                    if (k == i || s->species[k] != sj || !INSIDE(t0, i, k)) continue;
+                    int out = 0, gone = 0;
+                    for (int u = 1; u <= tau && !gone; ++u) {  /* excursions up to tau */
+                        if (INSIDE(t0 + u, i, k)) out = 0;
+                        else if (++out > t_star) gone = 1;
+                    }
+                    if (!gone && INSIDE(t0 + tau, i, k)) ++alive;
+                }
+                num[tau] += (double)alive / n0;
+                cnt[tau] += 1.0;
+            }
+        }
+#undef INSIDE
+    for (int tau = 0; tau < n_lags; ++tau) corr[tau] = cnt[tau] > 0 ? num[tau] / cnt[tau] : 0.0;
+    *solvation = ncount > 0 ? nsum / ncount : 0.0;
+    free(X);
+    free(num);
+    free(cnt);
+}
+
 /* ------------------------------------------------------ integrators (a5) */
 /* thermo record per step: U, W, KE_tr, KE_rot, P (after the step) */
 static void record(const or_system *s, const double *q, const double *v, const double *Lang, const double *terms,

@@ -693,3 +693,46 @@ def test_conductivity_units_and_rule():
     cos_acf = np.cos(0.2 * np.arange(50))
     assert Oracle.conductivity(cos_acf, 1.0, 1.0, 1.0, reduced=True) == pytest.approx(
         np.trapezoid(cos_acf) / 3.0, rel=1e-14)
+
+
+# -------------------------------------------- residence time (Eq. 7, Impey)
+def _two_species_line():
+    """One centre (species 0) at the origin and four shell molecules (species 1)
+    on a line, far from the box edges; a scripted trajectory moves them."""
+    models = [W.ion(1.0, 2.35, 65.0, 22.99, "c"), W.ion(-1.0, 4.40, 50.0, 35.45, "a")]
+    sp = np.array([0, 1, 1, 1, 1], np.int32)
+    o = Oracle(models, sp, 40.0, 10.0, elec=0, lrc=0)
+    return o
+
+
+def test_residence_of_a_static_shell_is_one():
+    o = _two_species_line()
+    R = np.array([[20.0, 20, 20], [22.0, 20, 20], [20, 22.5, 20], [20, 20, 17.0], [29.0, 20, 20]])
+    corr, nsol = o.residence(np.repeat(R[None], 12, 0), 0, 1, 4.0, 0, 6)
+    np.testing.assert_allclose(corr, 1.0)
+    assert nsol == 3.0
+
+
+def test_residence_departures_and_impey_tolerance():
+    """Molecule 1 leaves at sample 3 for good; molecule 2 steps out for exactly two
+    samples (4, 5) and returns; molecule 3 stays; molecule 4 is never in the shell."""
+    o = _two_species_line()
+    T = 8
+    R = np.zeros((T, 5, 3)) + 20.0
+    for t in range(T):
+        R[t, 1] = [22.0 if t < 3 else 30.0, 20, 20]
+        R[t, 2] = [20, 30.0 if t in (4, 5) else 22.0, 20]
+        R[t, 3] = [20, 20, 17.0]
+        R[t, 4] = [35.0, 20, 20]
+    corr2, nsol = o.residence(R, 0, 1, 4.0, 2, T)
+    corr1, _ = o.residence(R, 0, 1, 4.0, 1, T)
+    # lag 7 has only origin 0 (members 1, 2, 3): molecule 1 is gone; molecule 2's
+    # two-sample excursion is tolerated with t* = 2 but not with t* = 1
+    assert corr2[7] == pytest.approx(2.0 / 3.0)
+    assert corr1[7] == pytest.approx(1.0 / 3.0)
+    assert corr2[0] == 1.0
+    # lag 1, by hand: members(t0) that are inside again at t0 + 1, over origins 0..6
+    inside = {t: [k for k in (1, 2, 3) if (k != 1 or t < 3) and (k != 2 or t not in (4, 5))] for t in range(T)}
+    frac = [len([k for k in inside[t] if k in inside[t + 1]]) / len(inside[t]) for t in range(T - 1)]
+    assert corr2[1] == pytest.approx(np.mean(frac))
+    assert nsol == pytest.approx(np.mean([len(inside[t]) for t in range(T)]))
