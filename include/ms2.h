@@ -283,6 +283,24 @@ MS2_API ms2_status ms2_volume_derivatives(ms2_system sys, double *dUdV, double *
  * since ms2_reset_averages (MS2_ESTATE without samples); *n_samples may be NULL. */
 MS2_API ms2_status ms2_massieu(ms2_system sys, double A[8], long long *n_samples);
 
+/* ----------------------------------------------------- residence time */
+/* Paper Sec. 4, Eq. 7: tau_j = int <(1/n_ij(0)) sum_k Theta_k(t) Theta_k(0)> dt for
+ * molecules of species j around molecules of species i, with the tolerance of
+ * Impey et al.  Readings: "within r_ij" is the minimum-image centre distance
+ * below r_shell, decided exactly on the integer centre lattice like the cut-off;
+ * a member counts at lag t if it is in the shell at the origin and at t and was
+ * never outside for more than t_star consecutive samples in between; the average
+ * runs over all origins (one every `every` steps) and centres with a non-empty
+ * shell.  The solvation number n_ij is the mean shell count.  Setup (re)allocates
+ * and zeroes the state; MS2_EINVAL for bad species, r_shell outside (0, L/2),
+ * every < 1, n_lags outside 2..4096 or t_star outside 0..254.  Sampling systems
+ * step with the per-phase kernels and are not batched. */
+MS2_API ms2_status ms2_residence_setup(ms2_system sys, int species_i, int species_j, double r_shell, int every,
+                                       int n_lags, int t_star);
+/* corr (n_lags values, may be NULL), tau = trapezoidal integral of corr (fs, or
+ * reduced time), the solvation number and the sample count (each may be NULL). */
+MS2_API ms2_status ms2_residence(ms2_system sys, double *corr, double *tau, double *solvation, long long *n_samples);
+
 /* ------------------------------------------- Green-Kubo conductivity */
 /* Paper Sec. 4, Eqs. 3-4: sigma = 1/(3 V kB T) int_0^inf <j_e(t).j_e(0)> dt with
  * the electric current flux j_e = sum_k q_k v_k over the net-charged molecules

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libms2.so")
-SOURCES = ["capi.cu", "k_pair.cu", "k_integrate.cu", "k_ewald.cu", "k_rdf.cu", "batch.cu", "serve.cu", "noalloc.cu", "k_step.cu"]
+SOURCES = ["capi.cu", "k_pair.cu", "k_integrate.cu", "k_ewald.cu", "k_rdf.cu", "batch.cu", "serve.cu", "noalloc.cu", "k_step.cu", "k_residence.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo", "--extended-lambda",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "-Wno-deprecated-gpu-targets"]

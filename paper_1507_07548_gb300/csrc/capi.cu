@@ -564,10 +564,15 @@ static void enqueue_steps(ms2_system s, long long n, long long s0) {
     for (long long k = 0; k < n; ++k) {
         const bool sample = every > 0 && ((s0 + k + 1) % every) == 0;
         const bool gk = s->d.gk && s->gk_every > 0 && ((s0 + k + 1) % s->gk_every) == 0;
+        const bool res = s->res_every > 0 && ((s0 + k + 1) % s->res_every) == 0;
         const bool tm = s->timing && k == n - 1;
         if (tm) cudaEventRecordWithFlags(s->ev[0], s->stream, cudaEventRecordExternal);
         launch_drift(s);
         if (sample) launch_rdf(s);
+        if (res) {
+            ms2_launch_residence(s->stream, s->dP, s->d, s->res);
+            s->launch_acc += 2;
+        }
         if (tm) cudaEventRecordWithFlags(s->ev[1], s->stream, cudaEventRecordExternal);
         launch_pair(s);
         if (tm) cudaEventRecordWithFlags(s->ev[2], s->stream, cudaEventRecordExternal);
@@ -581,7 +586,8 @@ static void enqueue_steps(ms2_system s, long long n, long long s0) {
 static ms2_status run_graph(ms2_system s, long long n, long long s0) {
     const int phase = s->rdf_every > 0 ? (int)(s0 % s->rdf_every) : 0;
     const int gphase = (s->d.gk && s->gk_every > 0) ? (int)(s0 % s->gk_every) : -1;
-    const auto key = std::make_tuple((int)n, phase, gphase);
+    const int rphase = s->res_every > 0 ? (int)(s0 % s->res_every) : -1;
+    const auto key = std::make_tuple((int)n, phase, gphase, rphase);
     auto it = s->graphs.find(key);
     if (it == s->graphs.end()) {
         if (s->graphs.size() > 16) {
@@ -899,7 +905,8 @@ extern "C" ms2_status ms2_enable_timing(ms2_system s, int on) {
 extern "C" ms2_status ms2_step_kernel(ms2_system s, int *fused) {
     if (!s || !fused) return ms2_fail(MS2_EINVAL, "null argument");
     const int cells = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
-    *fused = s->step_fn && ms2_step_smem_bytes(s->ns, s->dmu, false, s->Np, s->mcap, s->jsplit, cells) <= s->step_smem_max
+    *fused = s->step_fn && s->res_every == 0 &&
+                     ms2_step_smem_bytes(s->ns, s->dmu, false, s->Np, s->mcap, s->jsplit, cells) <= s->step_smem_max
                  ? 1 : 0;
     return MS2_OK;
 }
@@ -970,7 +977,7 @@ extern "C" ms2_status ms2_system_info(ms2_system s, int *N, double *box, double 
 // one fused launch of m steps from step counter s0; false: not possible now
 // (no variant, RDF histogram too large for shared memory, launch refused)
 static bool run_fused(ms2_system s, long long m, long long s0) {
-    if (!s->step_fn) return false;
+    if (!s->step_fn || s->res_every > 0) return false;  // residence sampling runs on the per-phase path
     const int cells = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
     const size_t smem = ms2_step_smem_bytes(s->ns, s->dmu, false, s->Np, s->mcap, s->jsplit, cells);
     if (smem > s->step_smem_max) return false;
@@ -1350,6 +1357,70 @@ extern "C" ms2_status ms2_massieu(ms2_system s, double A[8], long long *n_sample
     A[6] = b * b * V / Nm * (2.0 * covUV - b * cU2V);                      // A21
     A[7] = b / Nm * (2.0 * V * (mUV - b * covUV) +
                      V * V * (ew - 2.0 * b * varV - b * covUW + b * b * cUV2));  // A12
+    return MS2_OK;
+}
+
+// ------------------------------------------------ residence time (Eq. 7)
+extern "C" ms2_status ms2_residence_setup(ms2_system s, int species_i, int species_j, double r_shell, int every,
+                                          int n_lags, int t_star) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    const int ns = s->hp.n_species;
+    if (species_i < 0 || species_i >= ns || species_j < 0 || species_j >= ns)
+        return ms2_fail(MS2_EINVAL, "species indices must be in 0..%d", ns - 1);
+    if (!(r_shell > 0) || !(r_shell < 0.5 * s->hp.L)) return ms2_fail(MS2_EINVAL, "need 0 < r_shell < L/2");
+    if (every < 1 || n_lags < 2 || n_lags > 4096 || t_star < 0 || t_star > 254)
+        return ms2_fail(MS2_EINVAL, "need every >= 1, 2 <= n_lags <= 4096, 0 <= t_star <= 254");
+    int first[MS2_MAXSP + 1] = {0}, count[MS2_MAXSP] = {0};
+    for (int sp : s->species) count[sp]++;
+    for (int m = 0; m < ns; ++m) first[m + 1] = first[m] + count[m];
+    ResArgs a{};
+    a.A0 = first[species_i];
+    a.NA = count[species_i];
+    a.B0 = first[species_j];
+    a.NB = count[species_j];
+    a.WB = (a.NB + 31) / 32;
+    a.M = n_lags;
+    a.t_star = t_star;
+    if (a.NA < 1 || a.NB < 1) return ms2_fail(MS2_EINVAL, "both species need molecules");
+    const double sc = r_shell * 4294967296.0 / s->hp.L;
+    a.r2 = (unsigned long long)std::ceil(sc * sc);
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    const size_t M = (size_t)a.M, NA = (size_t)a.NA;
+    MS2_CUDA_OK(s->al.alloc((void **)&a.alive, sizeof(unsigned) * M * NA * a.WB));
+    MS2_CUDA_OK(s->al.alloc((void **)&a.out, M * NA * (size_t)a.NB));
+    MS2_CUDA_OK(s->al.alloc((void **)&a.n0, sizeof(int) * M * NA));
+    MS2_CUDA_OK(s->al.alloc((void **)&a.counts, sizeof(int) * M * NA));
+    MS2_CUDA_OK(s->al.alloc((void **)&a.state, sizeof(double) * ms2_residence_state_doubles(a.M)));
+    MS2_CUDA_OK(cudaMemsetAsync(a.alive, 0, sizeof(unsigned) * M * NA * a.WB, s->stream));
+    MS2_CUDA_OK(cudaMemsetAsync(a.out, 0, M * NA * (size_t)a.NB, s->stream));
+    MS2_CUDA_OK(cudaMemsetAsync(a.n0, 0, sizeof(int) * M * NA, s->stream));
+    MS2_CUDA_OK(cudaMemsetAsync(a.counts, 0, sizeof(int) * M * NA, s->stream));
+    MS2_CUDA_OK(cudaMemsetAsync(a.state, 0, sizeof(double) * ms2_residence_state_doubles(a.M), s->stream));
+    s->res = a;  // buffers of an earlier setup stay with the system until it is destroyed
+    s->res_every = every;
+    destroy_graphs(s);
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_residence(ms2_system s, double *corr, double *tau, double *solvation,
+                                    long long *n_samples) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (s->res_every <= 0) return ms2_fail(MS2_ESTATE, "residence sampling is off (ms2_residence_setup)");
+    const int M = s->res.M;
+    std::vector<double> st(ms2_residence_state_doubles(M));
+    MS2_CUDA_OK(cudaMemcpyAsync(st.data(), s->res.state, sizeof(double) * st.size(), cudaMemcpyDeviceToHost,
+                                s->stream));
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    if (n_samples) *n_samples = (long long)st[0];
+    if (solvation) *solvation = st[2] > 0 ? st[1] / st[2] : 0.0;
+    const double *num = st.data() + 3, *cnt = num + M;
+    double integral = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const double c = cnt[m] > 0 ? num[m] / cnt[m] : 0.0;
+        if (corr) corr[m] = c;
+        integral += ((m == 0 || m == M - 1) ? 0.5 : 1.0) * c;
+    }
+    if (tau) *tau = integral * s->res_every * s->hp.dt;
     return MS2_OK;
 }
 

@@ -58,11 +58,13 @@ struct ms2_system_s {
     double uconst = 0, wbg = 0, ulrc = 0, plrc = 0;
     long long step = 0;
     int graph_chunk = 50;
-    std::map<std::tuple<int, int, int>, GraphEntry> graphs;  // (steps, RDF phase, conductivity phase)
+    std::map<std::tuple<int, int, int, int>, GraphEntry> graphs;  // (steps, RDF, conductivity, residence phase)
     long long launch_acc = 0;
     // RDF
     int rdf_every = 0, rdf_samples = 0, rdf_cap = 0;
     int gk_every = 0;  // conductivity: extended time step (0: off)
+    int res_every = 0;  // residence time: extended time step (0: off)
+    ResArgs res{};
     double rdf_rmax = 0;
     // host staging of the state
     std::vector<double> hR, hq, hv, hL;
@@ -79,6 +81,9 @@ ms2_status ms2_fail_cuda(cudaError_t e, const char *what, const char *file, int 
 void ms2_unit_constants(bool reduced, double *coulomb, double *kconv);
 ms2_status ms2_eval_forces(ms2_system s);
 ms2_status ms2_validate_models(const ms2_model *models, int n_models, ms2_elec elec);
+// residence-time sampling (k_residence.cu)
+void ms2_launch_residence(cudaStream_t st, const SysParams *P, const DevSys &S, const ResArgs &a);
+size_t ms2_residence_state_doubles(int M);
 // fused step kernel (k_step.cu)
 size_t ms2_step_smem_bytes(int NS, bool dmu, bool multi, int Np, int mcap, int js, int rdf_cells);
 int ms2_step_threads();

@@ -125,6 +125,19 @@ enum { AC_N = 0, AC_U, AC_P, AC_T, AC_BN, AC_BU, AC_BP, AC_NB, AC_SBU, AC_SBU2, 
 enum { RED_SUM = 1, RED_RECORD = 2, RED_LAMBDA = 4, RED_HALFKICK = 8, RED_FP64PART = 16, RED_EWALD = 32,
        RED_GK = 64 };
 
+// residence-time sampling state (k_residence.cu): centres [A0, A0 + NA), solvent
+// molecules [B0, B0 + NB) (species are contiguous), WB = ceil(NB / 32) words,
+// a ring of M origins
+struct ResArgs {
+    int A0, NA, B0, NB, WB, M, t_star;
+    unsigned long long r2;   // shell threshold on the integer lattice
+    unsigned *alive;         // [M][NA][WB] members still resident, per origin
+    unsigned char *out;      // [M][NA][NB] current excursion length of each member
+    int *n0;                 // [M][NA] shell count at each origin
+    int *counts;             // [NA][M] members alive and inside at this sample
+    double *state;           // samples, solvation sums, then [M] fraction sums and [M] term counts
+};
+
 // launch arguments of the fused step kernel (k_step.cu)
 struct StepArgs {
     int nsteps;

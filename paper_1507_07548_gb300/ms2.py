@@ -103,6 +103,8 @@ SIGNATURES = {
     "ms2_conductivity_setup": (C.c_int, [_vp, C.c_int, C.c_int]),
     "ms2_current": (C.c_int, [_vp, _d]),
     "ms2_conductivity": (C.c_int, [_vp, _d, _d, _P(C.c_longlong)]),
+    "ms2_residence_setup": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int]),
+    "ms2_residence": (C.c_int, [_vp, _d, _d, _d, _P(C.c_longlong)]),
     "ms2_step_kernel": (C.c_int, [_vp, _P(C.c_int)]),
     "ms2_last_step_phases": (C.c_int, [_vp, _d]),
     "ms2_last_step_times": (C.c_int, [_vp, _d]),
@@ -307,6 +309,18 @@ class System:
         check(lib().ms2_volume_derivatives(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
 
+    def residence_setup(self, species_i, species_j, r_shell, every, n_lags, t_star=0):
+        """Residence correlation of species_j molecules within r_shell of species_i ones."""
+        check(lib().ms2_residence_setup(self.h, species_i, species_j, r_shell, every, n_lags, t_star))
+        self._res_lags = n_lags
+
+    def residence(self):
+        """(correlation per lag, residence time tau, solvation number, samples)."""
+        corr = np.zeros(getattr(self, "_res_lags", 1))
+        tau, nsol, n = C.c_double(), C.c_double(), C.c_longlong()
+        check(lib().ms2_residence(self.h, _dp(corr), C.byref(tau), C.byref(nsol), C.byref(n)))
+        return corr, tau.value, nsol.value, n.value
+
     def conductivity_setup(self, every, n_lags):
         """Sample the electric current flux every `every` steps into an ACF of n_lags lags."""
         check(lib().ms2_conductivity_setup(self.h, every, n_lags))
@@ -321,7 +335,7 @@ class System:
     def conductivity(self):
         """(sigma in S/m, the flux ACF, number of samples)."""
         sig = C.c_double()
-        acf = np.zeros(self._gk_lags)
+        acf = np.zeros(getattr(self, "_gk_lags", 1))
         n = C.c_longlong()
         check(lib().ms2_conductivity(self.h, C.byref(sig), _dp(acf), C.byref(n)))
         return sig.value, acf, n.value
