@@ -79,11 +79,14 @@ def _load():
             "or_massieu": [d, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, d],
             "or_current": [P(_Sys), d, d], "or_flux_acf": [d, C.c_int, C.c_int, d],
             "or_residence": [P(_Sys), d, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, d, d],
+            "or_heat_flux": [P(_Sys), d, d, d, d, d, d],
+            "or_thermal_conductivity": [d, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int],
             "or_conductivity": [d, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int],
         }
         for name, args in sig.items():
             getattr(_lib, name).argtypes = args
         _lib.or_conductivity.restype = C.c_double
+        _lib.or_thermal_conductivity.restype = C.c_double
         _lib.or_pressure.argtypes = [P(_Sys), C.c_double, d]
         _lib.or_pressure.restype = C.c_double
         _lib.or_ndof.restype = C.c_int
@@ -198,6 +201,22 @@ class Oracle:
         j = np.zeros(3)
         self.lib.or_current(self.ref, _p(np.ascontiguousarray(v, np.float64)), _p(j))
         return j
+
+    def heat_flux(self, R, q, v, Lang, h):
+        """Microscopic heat flow J_q (Eqs. 5-6; K A/fs) with per-species partial enthalpies h (K)."""
+        J = np.zeros(3)
+        hh = np.zeros(8)
+        hh[:len(h)] = h
+        f = lambda a: _p(np.ascontiguousarray(a, np.float64))
+        self.lib.or_heat_flux(self.ref, f(R), f(q), f(v), f(Lang), _p(hh), _p(J))
+        return J
+
+    @staticmethod
+    def thermal_conductivity(acf, dt_ext, V, T, reduced=False):
+        """lambda (W/(m K), or reduced) from the ACF <J_q(t).J_q(0)> (Eq. 5)."""
+        a = np.ascontiguousarray(acf, np.float64)
+        return _load().or_thermal_conductivity(_p(a), C.c_int(len(a)), C.c_double(dt_ext), C.c_double(V),
+                                               C.c_double(T), C.c_int(int(reduced)))
 
     def residence(self, R_series, si, sj, r_shell, t_star, n_lags):
         """Residence correlation (Eq. 7, Impey tolerance t_star in samples) of species sj

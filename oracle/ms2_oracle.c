@@ -670,6 +670,79 @@ double or_conductivity(const double *acf, int n_lags, double dt_ext, double V, d
     return integral * e * e * 1e-5 / (3.0 * V * 1e-30 * kB * T);
 }
 
+/* ---------------------------- thermal conductivity of mixtures (Sec. 4, Eqs. 5-6) */
+/* Microscopic heat flow of a configuration with centre velocities v and
+ * space-frame angular momenta Lang:
+ *   J_q = sum_k (E_k - h_{s(k)}) v_k + 1/2 sum_k sum_{l != k} r_kl (F_kl.v_k + tau_kl.w_k)
+ * E_k = 1/2 M v_k^2 + 1/2 w_k.I.w_k + 1/2 sum_l u_kl (K), r_kl = R_k - R_l (minimum
+ * image), F_kl and tau_kl the force and torque on k from l, w_k = A I^-1 A^T L_k
+ * the angular velocity, h the per-molecule partial enthalpy of each species (K).
+ * Reading of Eq. 6: its Gamma_kl is the orientational gradient of u, i.e. minus
+ * the torque, so that the bracket is minus the power F_kl.v_k + tau_kl.w_k of the
+ * pair on molecule k; without the h term J_q is then d/dt sum_k R_k E_k.  LJ and
+ * point charges, reaction field or none (the pair sums of pair_ij).  J in K A/fs. */
+void or_heat_flux(const or_system *s, const double *R, const double *q, const double *v, const double *Lang,
+                  const double *h, double *J) {
+    int N = s->N;
+    uint32_t *X = (uint32_t *)malloc(sizeof(uint32_t) * 3 * N);
+    lattice_all(s, R, X);
+    uint64_t rc2 = or_rc2_lattice(s->rc, s->L);
+    double *A = (double *)malloc(sizeof(double) * 9 * N), *w = (double *)malloc(sizeof(double) * 3 * N);
+    for (int k = 0; k < N; ++k) {
+        int sp = s->species[k];
+        double Iinv[3], Lb[3], wb[3];
+        or_rotation(q + 4 * k, A + 9 * k);
+        mol_inv_inertia(s, sp, Iinv);
+        matTvec(A + 9 * k, Lang + 3 * k, Lb);
+        for (int c = 0; c < 3; ++c) wb[c] = Iinv[c] * Lb[c];
+        matvec(A + 9 * k, wb, w + 3 * k);
+    }
+    double J0 = 0, J1 = 0, J2 = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : J0, J1, J2)
+    for (int k = 0; k < N; ++k) {
+        int sp = s->species[k];
+        double uk = 0, jc[3] = {0, 0, 0};
+        for (int l = 0; l < N; ++l) {
+            if (l == k || !(lattice_d2(X + 3 * k, X + 3 * l) < rc2)) continue;
+            double d[3], f[3] = {0, 0, 0}, t[3] = {0, 0, 0}, u[3] = {0, 0, 0}, Fkl[3], wo = 0;
+            min_image(s, R + 3 * k, R + 3 * l, d);  /* R_l - R_k */
+            pair_ij(s, k, l, A + 9 * k, A + 9 * l, d, f, t, u, Fkl, &wo);
+            uk += u[0] + u[1] + u[2];
+            double P = dot3(Fkl, v + 3 * k) + dot3(t, w + 3 * k);
+            for (int c = 0; c < 3; ++c) jc[c] += 0.5 * (-d[c]) * P;
+        }
+        double Iinv[3], Lb[3];
+        mol_inv_inertia(s, sp, Iinv);
+        matTvec(A + 9 * k, Lang + 3 * k, Lb);
+        double ke = 0.5 * mol_mass(s, sp) * dot3(v + 3 * k, v + 3 * k);
+        for (int c = 0; c < 3; ++c) ke += 0.5 * Iinv[c] * Lb[c] * Lb[c];
+        double Ek = ke / s->kconv + 0.5 * uk - h[sp];
+        J0 += Ek * v[3 * k] + jc[0];
+        J1 += Ek * v[3 * k + 1] + jc[1];
+        J2 += Ek * v[3 * k + 2] + jc[2];
+    }
+    J[0] = J0;
+    J[1] = J1;
+    J[2] = J2;
+    free(X);
+    free(A);
+    free(w);
+}
+
+/* lambda = 1/(V kB T^2) int <J^x(t) J^x(0)> dt, averaged over the three elements:
+ * acf holds <J(t).J(0)> (the sum of the three), so lambda = trapz(acf) dt / (3 V T^2)
+ * in K^2 A^2/fs^2 fs / (A^3 K^2) scaled to W/(m K) (kB in J/K, 1 A/fs = 1e5 m/s);
+ * reduced = 1: reduced units. */
+double or_thermal_conductivity(const double *acf, int n_lags, double dt_ext, double V, double T, int reduced) {
+    double integral = 0.0;
+    for (int m = 0; m < n_lags; ++m) integral += ((m == 0 || m == n_lags - 1) ? 0.5 : 1.0) * acf[m];
+    integral *= dt_ext;
+    if (reduced) return integral / (3.0 * V * T * T);
+    const double kB = 1.380649e-23;
+    /* (K A/fs)^2 fs -> kB^2 1e10 m^2/s^2 1e-15 s; / (V 1e-30 m^3 kB K^2) */
+    return integral * kB * 1e-5 / (3.0 * V * 1e-30 * T * T);
+}
+
 /* ---------------------------------- residence time, solvation number (Sec. 4, Eq. 7) */
 /* Residence correlation of molecules of species sj around molecules of species si
  * over a series of T configurations R[t][N][3] sampled every extended time step.

@@ -736,3 +736,56 @@ def test_residence_departures_and_impey_tolerance():
     frac = [len([k for k in inside[t] if k in inside[t + 1]]) / len(inside[t]) for t in range(T - 1)]
     assert corr2[1] == pytest.approx(np.mean(frac))
     assert nsol == pytest.approx(np.mean([len(inside[t]) for t in range(T)]))
+
+
+# --------------------------------------- thermal conductivity (Eqs. 5-6)
+def test_heat_flux_is_the_time_derivative_of_the_energy_moment():
+    """Without the enthalpy term, J_q = d/dt sum_k R_k E_k for Newtonian dynamics of
+    an isolated cluster (E_k = kinetic energies + half the pair energies of k).
+    Leapfrog NVE from the oracle; integer-time velocities as half-step means;
+    central differences of the moment against J_q at the middle step."""
+    rng = np.random.default_rng(41)
+    n, L = 8, 60.0
+    models = [W.water()]
+    sp = np.zeros(n, np.int32)
+    R = 30.0 + 3.1 * np.array([[x, y, z] for x in (0, 1) for y in (0, 1) for z in (0, 1)], float)
+    R += rng.normal(0, 0.1, R.shape)
+    q = W.random_quaternions(n, rng)
+    o = Oracle(models, sp, L, 25.0, elec=1, lrc=0)
+    v, Lg = W.thermal_velocities(models, sp, q, 30.0, o.s.kconv, rng)
+    dt = 0.25
+    states = [(R, q, v, Lg)]
+    for _ in range(3):
+        R, q, v, Lg, _, _ = o.run_leapfrog(R, q, v, Lg, dt, 1, T0=0.0)
+        states.append((R, q, v, Lg))
+    # state k holds R_k, q_k and the velocities v_{k-1/2}, L_{k-1/2}
+    M = sum(s.mass for s in models[0].sites)
+    Iinv = 1.0 / W.principal_moments(models[0])
+
+    def moment(k):
+        Rk, qk = states[k][0], states[k][1]
+        vk = 0.5 * (states[k][2] + states[k + 1][2])
+        Lk = 0.5 * (states[k][3] + states[k + 1][3])
+        A = W.quat_to_matrix(qk)
+        Lb = np.einsum("nij,ni->nj", A, Lk)
+        ke = (0.5 * M * (vk * vk).sum(1) + 0.5 * (Iinv * Lb * Lb).sum(1)) / o.s.kconv
+        u = o.molecule_terms(Rk, qk)[:, :3].sum(1)          # half of each pair energy per molecule
+        return ((ke + u)[:, None] * Rk).sum(0), (Rk, qk, vk, Lk)
+
+    D0, _ = moment(0)
+    D2, _ = moment(2)
+    _, mid = moment(1)
+    J = o.heat_flux(*mid, h=[0.0])
+    np.testing.assert_allclose((D2 - D0) / (2 * dt), J, rtol=2e-3, atol=2e-3 * np.abs(J).max())
+
+
+def test_heat_flux_enthalpy_term_and_units():
+    """The partial-enthalpy term subtracts h sum_k v_k; lambda units on a constant ACF."""
+    wl = W.water_box(N=64, rc=6.0, seed=21)
+    o = Oracle.from_workload(wl)
+    J0 = o.heat_flux(wl.R, wl.q, wl.v, wl.Lang, h=[0.0])
+    J1 = o.heat_flux(wl.R, wl.q, wl.v, wl.Lang, h=[1234.5])
+    np.testing.assert_allclose(J0 - J1, 1234.5 * wl.v.sum(0), rtol=1e-9, atol=1e-9 * np.abs(J0).max())
+    kB = 1.380649e-23
+    lam = Oracle.thermal_conductivity(np.full(5, 3.0), 2.0, 500.0, 300.0)
+    assert lam == pytest.approx(3.0 * 4 * 2.0 * kB * 1e-5 / (3 * 500e-30 * 300.0 ** 2), rel=1e-14)
