@@ -319,6 +319,33 @@ MS2_API ms2_status ms2_current(ms2_system sys, double j[3]);
  * <j(t).j(0)>, may be NULL) and *n_samples (may be NULL).  MS2_ESTATE without setup. */
 MS2_API ms2_status ms2_conductivity(ms2_system sys, double *sigma, double *acf, long long *n_samples);
 
+/* ------------------------------------ Green-Kubo thermal conductivity */
+/* Paper Sec. 4, Eqs. 5-6: lambda = 1/(3 V kB T^2) int_0^inf <J_q(t).J_q(0)> dt with
+ * the microscopic heat flux of a mixture of rigid molecules
+ *   J_q = sum_k (E_k - h_k) v_k + 1/2 sum_k sum_{l != k} (R_k - R_l) (F_kl.v_k + tau_kl.w_k),
+ *   E_k = M_k v_k^2 / 2 + w_k.I_k w_k / 2 + 1/2 sum_{l != k} u_kl,
+ * F_kl and tau_kl the force and torque (about R_k) of l on k, h_k the partial
+ * molar enthalpy of k's component (h[species], energy units per molecule: K, or
+ * reduced; h may be NULL for zeros).  Reading: Gamma_kl of the paper is the
+ * torque of l on k, entering as tau_kl.w_k (the sign that makes J_q the time
+ * derivative of sum_k R_k E_k); v_k, w_k are taken at the integer time of the
+ * forces, v = v(n - 1/2) + dt/2 F/M and L = L(n - 1/2) + dt/2 tau (the leapfrog
+ * half-step mean without the thermostat factor; the velocity-Verlet state as is).
+ * Sampled every `every` steps: on such a step a second pair pass forms
+ * sum_l d_kl P_kl with the integer-time site velocities (no change to the
+ * trajectory).  Pairwise interactions only: MS2_EINVAL for Ewald systems, the
+ * FP64 pair path, 8-slot models, every < 1, n_lags outside 2..2^20 or a
+ * non-finite h.  Setup (re)allocates and zeroes the sampling state.  Systems
+ * that sample are not batched. */
+MS2_API ms2_status ms2_heat_setup(ms2_system sys, int every, int n_lags, const double *h);
+/* The heat flux J_q (K A/fs with energies in K, or reduced) of the last sample. */
+MS2_API ms2_status ms2_heat_flux(ms2_system sys, double J[3]);
+/* lambda (W/(m K); reduced units for reduced systems) from the trapezoidal
+ * integral of the autocorrelation over the n_lags lags, T = T0; acf (n_lags
+ * values of <J_q(t).J_q(0)>, may be NULL) and *n_samples (may be NULL).
+ * MS2_ESTATE without setup. */
+MS2_API ms2_status ms2_thermal_conductivity(ms2_system sys, double *lambda, double *acf, long long *n_samples);
+
 /* Kernel timing: with on = 1, every subsequently enqueued batch of steps
  * records CUDA events (on the system stream) around its last step and around
  * that step's pair kernel and Ewald kernels.  ms2_last_step_times synchronises

@@ -477,7 +477,7 @@ static ms2_status tune(ms2_batch b) {
 // whether the batch kernels take this system (used by the server)
 bool ms2_batch_accepts(ms2_system s) {
     if (!s || s->hp.integrator != MS2_INT_LEAPFROG_Q || s->fp64 || s->hp.elec == ELEC_EWALD || s->hp.massieu ||
-        s->d.gk || s->res_every > 0)
+        s->d.gk || s->res_every > 0 || s->hf_every > 0)
         return false;
     const int kind = kind_of(s);
     if (kind < 0) return false;
@@ -495,11 +495,11 @@ extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_bat
         ms2_system s = systems[k];
         if (!s) { delete b; return ms2_fail(MS2_EINVAL, "system %d is null", k); }
         if (s->hp.integrator != MS2_INT_LEAPFROG_Q || s->fp64 || s->hp.elec == ELEC_EWALD || s->hp.massieu || s->d.gk ||
-            s->res_every > 0) {
+            s->res_every > 0 || s->hf_every > 0) {
             delete b;
             return ms2_fail(MS2_EINVAL, "system %d: batches take leapfrog systems with FP32 pair arithmetic and "
-                                        "reaction field or no electrostatics, without Massieu, conductivity or "
-                                        "residence sampling", k);
+                                        "reaction field or no electrostatics, without Massieu, conductivity, "
+                                        "residence or heat-flux sampling", k);
         }
         const int kind = kind_of(s);
         if (kind < 0) { delete b; return ms2_fail(MS2_EINVAL, "system %d: more than 4 site slots", k); }

@@ -43,6 +43,7 @@ extern "C" const char *ms2_version(void) { return "ms2-gb300 1.0 (sm_103a)"; }
 // kernels (defined in the other translation units)
 __global__ void k_build(const SysParams *, DevSys);
 __global__ void k_reduce(const SysParams *, DevSys, int);
+__global__ void k_heat_reduce(const SysParams *, DevSys);
 __global__ void k_drift(const SysParams *, DevSys, int);
 __global__ void k_pair_lj64(const SysParams *, DevSys, int);
 __global__ void k_ewald_prep(const SysParams *, DevSys);
@@ -55,6 +56,7 @@ size_t ms2_pair_smem_bytes(int NS, bool dmu, bool multi, int TJ, int wpb);
 size_t ms2_pair64_smem_bytes(int TJ, int wpb);
 void *ms2_pick_pair_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, int *ns_used,
                            bool *dmu, bool *mult_used, bool mass);
+void *ms2_pick_heat_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, const void *pair_fn);
 
 
 // ------------------------------------------------------------ allocation
@@ -458,7 +460,7 @@ static ms2_status size_pair_tiles(ms2_system s) {
 static void setup_fused(ms2_system s, const ms2_options &o) {
     s->fuse_fn = s->step_fn = nullptr;
     if (s->fp64 || s->hp.integrator == MS2_INT_VERLET || s->hp.elec == ELEC_EWALD || s->multi_used) return;
-    void *fn = ms2_pick_step_kernel(s->ns, s->ljm, s->qm, s->dm, s->hp.elec, false, s->hp.massieu != 0);
+    void *fn = ms2_pick_step_kernel(s->ns, s->ljm, s->qm, s->dm, s->hp.elec, false, s->hp.massieu != 0, false);
     if (!fn) return;
     int coop = 0, sms = 0, optin = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device) != cudaSuccess || !coop) return;
@@ -526,6 +528,16 @@ ms2_status launch_reduce(ms2_system s, int mode) {
     return MS2_OK;
 }
 
+// heat-flux pass of a sampled step (after launch_reduce): the pair decomposition
+ms2_status launch_heat(ms2_system s) {
+    dim3 grid((s->N + s->wpb - 1) / s->wpb, s->jsplit);
+    void (*fn)(const SysParams *, DevSys, int) = (void (*)(const SysParams *, DevSys, int))s->heat_fn;
+    fn<<<grid, s->wpb * 32, s->pair_smem, s->stream>>>(s->dP, s->d, s->TJ);
+    k_heat_reduce<<<(s->d.nunits + 3) / 4, 128, 0, s->stream>>>(s->dP, s->d);
+    s->launch_acc += 2;
+    return MS2_OK;
+}
+
 ms2_status launch_drift(ms2_system s) {
     const int th = 128;  // 4 lanes per molecule
     k_drift<<<(4 * s->N + th - 1) / th, th, 0, s->stream>>>(s->dP, s->d, s->hp.integrator == MS2_INT_VERLET ? 1 : 0);
@@ -565,6 +577,7 @@ static void enqueue_steps(ms2_system s, long long n, long long s0) {
         const bool sample = every > 0 && ((s0 + k + 1) % every) == 0;
         const bool gk = s->d.gk && s->gk_every > 0 && ((s0 + k + 1) % s->gk_every) == 0;
         const bool res = s->res_every > 0 && ((s0 + k + 1) % s->res_every) == 0;
+        const bool hf = s->hf_every > 0 && ((s0 + k + 1) % s->hf_every) == 0;
         const bool tm = s->timing && k == n - 1;
         if (tm) cudaEventRecordWithFlags(s->ev[0], s->stream, cudaEventRecordExternal);
         launch_drift(s);
@@ -579,6 +592,7 @@ static void enqueue_steps(ms2_system s, long long n, long long s0) {
         launch_ewald(s);
         if (tm) cudaEventRecordWithFlags(s->ev[3], s->stream, cudaEventRecordExternal);
         launch_reduce(s, (verlet ? (RED_SUM | RED_RECORD | RED_HALFKICK) : (RED_SUM | RED_RECORD)) | (gk ? RED_GK : 0));
+        if (hf) launch_heat(s);
         if (tm) cudaEventRecordWithFlags(s->ev[4], s->stream, cudaEventRecordExternal);
     }
 }
@@ -587,7 +601,8 @@ static ms2_status run_graph(ms2_system s, long long n, long long s0) {
     const int phase = s->rdf_every > 0 ? (int)(s0 % s->rdf_every) : 0;
     const int gphase = (s->d.gk && s->gk_every > 0) ? (int)(s0 % s->gk_every) : -1;
     const int rphase = s->res_every > 0 ? (int)(s0 % s->res_every) : -1;
-    const auto key = std::make_tuple((int)n, phase, gphase, rphase);
+    const int hphase = s->hf_every > 0 ? (int)(s0 % s->hf_every) : -1;
+    const auto key = std::make_tuple((int)n, phase, gphase, rphase, hphase);
     auto it = s->graphs.find(key);
     if (it == s->graphs.end()) {
         if (s->graphs.size() > 16) {
@@ -905,7 +920,7 @@ extern "C" ms2_status ms2_enable_timing(ms2_system s, int on) {
 extern "C" ms2_status ms2_step_kernel(ms2_system s, int *fused) {
     if (!s || !fused) return ms2_fail(MS2_EINVAL, "null argument");
     const int cells = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
-    *fused = s->step_fn && s->res_every == 0 &&
+    *fused = s->step_fn && s->res_every == 0 && (s->hf_every == 0 || s->step_heat_fn) &&
                      ms2_step_smem_bytes(s->ns, s->dmu, false, s->Np, s->mcap, s->jsplit, cells) <= s->step_smem_max
                  ? 1 : 0;
     return MS2_OK;
@@ -978,6 +993,8 @@ extern "C" ms2_status ms2_system_info(ms2_system s, int *N, double *box, double 
 // (no variant, RDF histogram too large for shared memory, launch refused)
 static bool run_fused(ms2_system s, long long m, long long s0) {
     if (!s->step_fn || s->res_every > 0) return false;  // residence sampling runs on the per-phase path
+    void *fn = s->hf_every > 0 ? s->step_heat_fn : s->step_fn;
+    if (!fn) return false;
     const int cells = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
     const size_t smem = ms2_step_smem_bytes(s->ns, s->dmu, false, s->Np, s->mcap, s->jsplit, cells);
     if (smem > s->step_smem_max) return false;
@@ -987,6 +1004,7 @@ static bool run_fused(ms2_system s, long long m, long long s0) {
     A.s0 = s0;
     A.rdf_every = s->d.rdf ? s->rdf_every : 0;
     A.gk_every = s->d.gk ? s->gk_every : 0;
+    A.hf_every = s->hf_every;
     A.TJ = s->TJ;
     A.Np = s->Np;
     A.mcap = s->mcap;
@@ -996,7 +1014,7 @@ static bool run_fused(ms2_system s, long long m, long long s0) {
     A.timing = s->timing ? 1 : 0;
     A.tmax = (unsigned long long *)(cnt + 56);  // 3 x 8 bytes at byte 224 of the counter block (zero at entry)
     if (s->timing) cudaEventRecord(s->ev[0], s->stream);
-    const cudaError_t e = ms2_launch_step(s->step_fn, s->step_grid, smem, s->stream, s->dP, s->d, A);
+    const cudaError_t e = ms2_launch_step(fn, s->step_grid, smem, s->stream, s->dP, s->d, A);
     if (e != cudaSuccess) {  // e.g. co-residency refused: the per-phase kernels from now on
         cudaGetLastError();
         s->step_fn = nullptr;
@@ -1476,6 +1494,85 @@ extern "C" ms2_status ms2_conductivity(ms2_system s, double *sigma, double *acf,
         } else {  // e^2 (A/fs)^2 fs / (A^3 kB K) -> S/m
             const double e = 1.602176634e-19, kB = 1.380649e-23;
             *sigma = integral * e * e * 1e-5 / (3.0 * s->hp.V * 1e-30 * kB * s->hp.T0);
+        }
+    }
+    return MS2_OK;
+}
+
+// ------------------------------------------ Green-Kubo thermal conductivity
+extern "C" ms2_status ms2_heat_setup(ms2_system s, int every, int n_lags, const double *h) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (every < 1 || n_lags < 2 || n_lags > (1 << 20))
+        return ms2_fail(MS2_EINVAL, "need every >= 1 and 2 <= n_lags <= 2^20");
+    if (s->hp.elec == ELEC_EWALD) return ms2_fail(MS2_EINVAL, "heat flux: pairwise interactions only (no Ewald)");
+    void *hfn = s->fp64 ? nullptr : ms2_pick_heat_kernel(s->ns, s->ljm, s->qm, s->dm, s->hp.elec, s->multi_used, s->pair_fn);
+    if (!hfn) return ms2_fail(MS2_EINVAL, "heat flux: no heat-flux kernel for this system (FP64 or 8-slot models)");
+    for (int m = 0; h && m < s->hp.n_species; ++m)
+        if (!std::isfinite(h[m])) return ms2_fail(MS2_EINVAL, "partial molar enthalpy %d is not finite", m);
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    MS2_CUDA_OK(cudaFuncSetAttribute((const void *)hfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)std::max<size_t>(s->pair_smem, 48 * 1024)));
+    if (!s->d.hpart) MS2_CUDA_OK(s->al.alloc((void **)&s->d.hpart, sizeof(float) * 3 * (size_t)s->jsplit * s->N));
+    if (!s->d.hf || s->d.hf_lags != n_lags) {
+        double *g = nullptr;
+        MS2_CUDA_OK(s->al.alloc((void **)&g, sizeof(double) * (4 + 4 * (size_t)n_lags)));
+        s->d.hf = g;  // a previous buffer stays with the system until it is destroyed
+        s->d.hf_lags = n_lags;
+    }
+    MS2_CUDA_OK(cudaMemsetAsync(s->d.hf, 0, sizeof(double) * (4 + 4 * (size_t)n_lags), s->stream));
+    for (int m = 0; m < MS2_MAXSP; ++m) s->hp.henth[m] = (h && m < s->hp.n_species) ? h[m] : 0.0;
+    MS2_CUDA_OK(cudaMemcpyAsync(s->dP, &s->hp, sizeof(SysParams), cudaMemcpyHostToDevice, s->stream));
+    // the fused variant with the heat pass, on the same decomposition
+    s->step_heat_fn = nullptr;
+    if (s->fuse_fn && s->step_fn) {
+        void *fn = ms2_pick_step_kernel(s->ns, s->ljm, s->qm, s->dm, s->hp.elec, false, s->hp.massieu != 0, true);
+        int nb = 0;
+        const size_t base = ms2_step_smem_bytes(s->ns, s->dmu, false, s->Np, s->mcap, s->jsplit, 0);
+        if (fn && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->step_smem_max) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ms2_step_threads(), base) == cudaSuccess && nb >= 1)
+            s->step_heat_fn = fn;
+        cudaGetLastError();
+    }
+    s->heat_fn = hfn;
+    s->hf_every = every;
+    destroy_graphs(s);
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_heat_flux(ms2_system s, double J[3]) {
+    if (!s || !J) return ms2_fail(MS2_EINVAL, "null argument");
+    if (s->hf_every <= 0) return ms2_fail(MS2_ESTATE, "heat-flux sampling is off (ms2_heat_setup)");
+    double sc[SC_COUNT_];
+    ms2_status st = read_scalars(s, sc);
+    if (st != MS2_OK) return st;
+    for (int k = 0; k < 3; ++k) J[k] = sc[SC_HX + k];
+    return MS2_OK;
+}
+
+extern "C" ms2_status ms2_thermal_conductivity(ms2_system s, double *lambda, double *acf, long long *n_samples) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (s->hf_every <= 0) return ms2_fail(MS2_ESTATE, "heat-flux sampling is off (ms2_heat_setup)");
+    const int M = s->d.hf_lags;
+    std::vector<double> g(4 + 4 * (size_t)M);
+    MS2_CUDA_OK(cudaMemcpyAsync(g.data(), s->d.hf, sizeof(double) * g.size(), cudaMemcpyDeviceToHost, s->stream));
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    const long long n = (long long)g[0];
+    if (n_samples) *n_samples = n;
+    const double *sums = g.data() + 4 + 3 * (size_t)M;
+    double integral = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const double c = m < n ? sums[m] / (double)(n - m) : 0.0;
+        if (acf) acf[m] = c;
+        integral += ((m == 0 || m == M - 1) ? 0.5 : 1.0) * c;
+    }
+    integral *= s->hf_every * s->hp.dt;
+    if (lambda) {
+        const double T = s->hp.T0;
+        if (s->reduced) {
+            *lambda = integral / (3.0 * s->hp.V * T * T);
+        } else {  // (K A/fs)^2 fs / (A^3 K^2) with energies in K: kB 1e-5 / 1e-30 -> W/(m K)
+            const double kB = 1.380649e-23;
+            *lambda = integral * kB * 1e-5 / (3.0 * s->hp.V * 1e-30 * T * T);
         }
     }
     return MS2_OK;

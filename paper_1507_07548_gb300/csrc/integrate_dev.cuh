@@ -487,28 +487,33 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
     }
 }
 
+// total of per-unit scalar k over units [0, nvb) by one warp, in reduce_totals'
+// order (lane l sums units l, l + 32, ... in order, then the fixed tree); every lane
+__device__ __forceinline__ double unit_total(const DevSys &S, int nvb, int k, int lane) {
+    double x = 0;
+    for (int b = lane; b < nvb; b += 32) x += __ldcg(S.blk + (size_t)b * MS2_NRED + k);
+    return warp_sum(x);
+}
+
 // Totals of the step scalars over the reduction units, fixed order: warp w
 // takes scalars w, w + nwarps, ...; lane l sums units l, l + 32, ... in order,
 // then a fixed shuffle tree.  Result in tot[0 .. Q_N) (shared memory).
 __device__ __forceinline__ void reduce_totals(const DevSys &S, int nvb, double *tot, int nq = Q_N) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int k = warp; k < nq; k += nw) {
-        double x = 0;
-        for (int b = lane; b < nvb; b += 32) x += __ldcg(S.blk + (size_t)b * MS2_NRED + k);
-        x = warp_sum(x);
+        const double x = unit_total(S, nvb, k, lane);
         if (lane == 0) tot[k] = x;
     }
 }
 
-// One conductivity sample j = tot[Q_N .. Q_N+2] into the flux ring and the lag
-// sums, by a whole warp: sums[m] += j(t).j(t - m) for m < min(samples, lags),
-// each sum in sample order (Sec. 4, Eqs. 3-4; the extended time step is the
-// sampling interval).
-__device__ __forceinline__ void gk_update(const DevSys &S, const double *tot, int lane) {
-    double *g = S.gk, *ring = g + 4, *sums = ring + 3 * (size_t)S.gk_lags;
+// One flux sample j into a flux ring g (layout: [0] samples, [1..3] unused,
+// ring [M][3], lag sums [M]) and its lag sums, by a whole warp:
+// sums[m] += j(t).j(t - m) for m < min(samples, M), each sum in sample order
+// (Sec. 4, Eqs. 3-5; the extended time step is the sampling interval).
+__device__ __forceinline__ void acf_update(double *g, int M, double j0, double j1, double j2, int lane) {
+    double *ring = g + 4, *sums = ring + 3 * (size_t)M;
     const long long n = (long long)g[0];
-    const int M = S.gk_lags, slot = (int)(n % M);
-    const double j0 = tot[Q_N], j1 = tot[Q_N + 1], j2 = tot[Q_N + 2];
+    const int slot = (int)(n % M);
     if (lane == 0) {
         ring[3 * slot] = j0;
         ring[3 * slot + 1] = j1;
@@ -522,6 +527,104 @@ __device__ __forceinline__ void gk_update(const DevSys &S, const double *tot, in
     }
     __syncwarp();
     if (lane == 0) g[0] = (double)(n + 1);
+}
+
+// the electric current flux j = tot[Q_N .. Q_N+2] of one conductivity sample
+__device__ __forceinline__ void gk_update(const DevSys &S, const double *tot, int lane) {
+    acf_update(S.gk, S.gk_lags, tot[Q_N], tot[Q_N + 1], tot[Q_N + 2], lane);
+}
+
+// ------------------------------------------------------------- heat flux
+// Velocity and angular velocity of molecule m (state view sv) at the integer
+// time of the current forces, in FP32 for the heat-flux power pass, the same in
+// every lane: v = v_{n-1/2} + dt/2 F/M, L = L_{n-1/2} + dt/2 tau (space frame,
+// the mean of the two half steps of the leapfrog without the thermostat factor),
+// w = A I^-1 A^T L.  Velocity Verlet (integrator 0, point molecules): its
+// reduction already left v at the integer time.
+__device__ __forceinline__ double half_kick(const SysParams *__restrict__ P, int sp) {
+    return P->integrator == 0 ? 0.0 : 0.5 * P->kick[sp];
+}
+
+template <bool SH>
+__device__ __forceinline__ void heat_velocities(const SysParams *__restrict__ P, const StateView &sv, int m, float v[3],
+                                                float w[3]) {
+    const int ld = sv.ld, sp = sv.spc[m];
+    const double hk = half_kick(P, sp), hd = 0.5 * P->dtk;
+    float L[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        v[k] = d2f(fma(hk, ldv<SH>(sv.F + k * ld + m), ldv<SH>(sv.v + k * ld + m)));
+        L[k] = d2f(fma(hd, ldv<SH>(sv.tau + k * ld + m), ldv<SH>(sv.L + k * ld + m)));
+    }
+    const float q0 = d2f(ldv<SH>(sv.q + m)), q1 = d2f(ldv<SH>(sv.q + ld + m)), q2 = d2f(ldv<SH>(sv.q + 2 * ld + m)),
+                q3 = d2f(ldv<SH>(sv.q + 3 * ld + m));
+    // A (body -> space) of the unit quaternion (w, x, y, z)
+    const float A00 = 1.f - 2.f * (q2 * q2 + q3 * q3), A01 = 2.f * (q1 * q2 - q0 * q3), A02 = 2.f * (q1 * q3 + q0 * q2);
+    const float A10 = 2.f * (q1 * q2 + q0 * q3), A11 = 1.f - 2.f * (q1 * q1 + q3 * q3), A12 = 2.f * (q2 * q3 - q0 * q1);
+    const float A20 = 2.f * (q1 * q3 - q0 * q2), A21 = 2.f * (q2 * q3 + q0 * q1), A22 = 1.f - 2.f * (q1 * q1 + q2 * q2);
+    const float b0 = d2f(P->Iinv[sp][0]) * (A00 * L[0] + A10 * L[1] + A20 * L[2]);
+    const float b1 = d2f(P->Iinv[sp][1]) * (A01 * L[0] + A11 * L[1] + A21 * L[2]);
+    const float b2 = d2f(P->Iinv[sp][2]) * (A02 * L[0] + A12 * L[1] + A22 * L[2]);
+    w[0] = A00 * b0 + A01 * b1 + A02 * b2;
+    w[1] = A10 * b0 + A11 * b1 + A12 * b2;
+    w[2] = A20 * b0 + A21 * b1 + A22 * b2;
+}
+
+// Heat-flux reduction unit u of U (the molecules of reduce_unit's unit u, a
+// quad per molecule): lane c forms component c of
+//   E_k v_k - 1/2 sum_p hp[p][c][m],   E_k = K_k + 1/2 sum_l u_kl - h_k
+// (Sec. 4, Eq. 6 with the pair partials sum_l d_kl P_kl, d_kl = R_l - R_k) at the
+// velocities of heat_velocities in FP64; per-molecule energies from Ui.  The
+// warp's three sums go to blk[u][Q_N + 3 ..].
+template <bool SH>
+__device__ __forceinline__ void heat_unit(const SysParams *__restrict__ P, const DevSys &S, const float *hp, int hld,
+                                          const StateView &sv, const double *Ui, int uld, int i0, int u, int U,
+                                          int lane) {
+    const unsigned F = 0xffffffffu, qb = lane & 28;
+    const int N = S.N, c = lane & 3, cc = c < 3 ? c : 2;
+    const int i_lo = (int)((long long)N * u / U), i_hi = (int)((long long)N * (u + 1) / U);
+    const int ld = sv.ld;
+    double jr = 0.0;
+    for (int base = i_lo; base < i_hi; base += 8) {
+        const int i = base + (lane >> 2);
+        const bool on = i < i_hi;
+        const int m = (on ? i : i_lo) - i0;
+        const int sp = sv.spc[m];
+        double jc = 0.0;
+        for (int p = 0; p < S.jsplit; ++p) jc += f2d(ldv<SH>(hp + ((size_t)p * 3 + cc) * hld + m));
+        const double v = fma(half_kick(P, sp), ldv<SH>(sv.F + cc * ld + m), ldv<SH>(sv.v + cc * ld + m));
+        const double Lc = fma(0.5 * P->dtk, ldv<SH>(sv.tau + cc * ld + m), ldv<SH>(sv.L + cc * ld + m));
+        double L[3], col[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) L[k] = __shfl_sync(F, Lc, qb | k);
+        const double q[4] = {ldv<SH>(sv.q + m), ldv<SH>(sv.q + ld + m), ldv<SH>(sv.q + 2 * ld + m),
+                             ldv<SH>(sv.q + 3 * ld + m)};
+        rot_column(q, cc, col);
+        const double lb = col[0] * L[0] + col[1] * L[1] + col[2] * L[2];
+        double ke = c < 3 ? P->half_mass[sp] * v * v + P->half_Iinv[sp][cc] * lb * lb : 0.0;
+        ke += __shfl_xor_sync(F, ke, 1);
+        ke += __shfl_xor_sync(F, ke, 2);
+        const double uk = ldv<SH>(Ui + m) + ldv<SH>(Ui + uld + m) + ldv<SH>(Ui + 2 * uld + m);
+        const double E = ke * P->inv_kconv + 0.5 * uk - P->henth[sp];
+        const double x = (c < 3 && on) ? E * v - 0.5 * jc : 0.0;
+        jr = (base == i_lo) ? x : jr + x;
+    }
+    double y[4] = {(lane & 3) == 0 ? jr : 0.0, (lane & 3) == 1 ? jr : 0.0, (lane & 3) == 2 ? jr : 0.0, 0.0};
+    const double t = warp_sum4(y, lane);
+    const int k = (lane >> 3) & 3;
+    if ((lane & 7) == 0 && k < 3) S.blk[(size_t)u * MS2_NRED + Q_N + 3 + k] = t;
+}
+
+// one heat-flux sample from the heat units: SC_HX.. and the heat-flux ring
+__device__ __forceinline__ void heat_record(const DevSys &S, int nvb, int lane) {
+    const double j0 = unit_total(S, nvb, Q_N + 3, lane), j1 = unit_total(S, nvb, Q_N + 4, lane),
+                 j2 = unit_total(S, nvb, Q_N + 5, lane);
+    if (lane == 0) {
+        S.scal[SC_HX] = j0;
+        S.scal[SC_HY] = j1;
+        S.scal[SC_HZ] = j2;
+    }
+    acf_update(S.hf, S.hf_lags, j0, j1, j2, lane);
 }
 
 // isokinetic factor sqrt(T0 / T') from the kicked kinetic energy (as finish_step)

@@ -55,6 +55,25 @@ __global__ void __launch_bounds__(128) k_reduce(const SysParams *__restrict__ P,
     if ((mode & RED_GK) && threadIdx.x < 32) gk_update(S, tot, threadIdx.x);
 }
 
+// Heat flux of a sampled step (after k_reduce and the power pass k_heat): one
+// warp per reduction unit (integ::heat_unit); the last block records the sample.
+__global__ void __launch_bounds__(128) k_heat_reduce(const SysParams *__restrict__ P, DevSys S) {
+    const int lane = threadIdx.x & 31, u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (u < S.nunits) heat_unit<false>(P, S, S.hpart, S.N, global_view(S), S.Ui, S.N, 0, u, S.nunits, lane);
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(S.counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < 32) heat_record(S, S.nunits, threadIdx.x);
+    __syncthreads();
+    if (threadIdx.x == 0) *S.counter = 0u;
+}
+
 // On-demand breakdown of the current configuration (single block, fixed order):
 // out[0..5] = sums of U_lj, U_qq, U_dd, W_pair (owner-doubled), partner counts,
 // and the reciprocal molecular-virial correction sum_s F_s.s_s.

@@ -23,6 +23,7 @@
 // range order, so results are bitwise reproducible.
 #include "ms2_internal.cuh"
 
+#include "integrate_dev.cuh"
 #include "pair_engine.cuh"
 
 using namespace pair_engine;
@@ -67,6 +68,45 @@ __global__ void __launch_bounds__(256) k_pair(const SysParams *__restrict__ P, D
         q[PV_NP * N] = (float)o.np;
         q[PV_VV * N] = o.vv;
     }
+}
+
+// Heat-flux power pass (Sec. 4, Eq. 6) after the reduction of a sampled step:
+// the decomposition of k_pair, each warp's molecule i moving with its
+// integer-time velocities (integ::heat_velocities); one FP32 partial
+// sum_l d_kl P_kl per (j-range, i, component) into hpart.
+template <int NS, unsigned LJM, unsigned QM, unsigned DM, int ELEC, bool MULTI>
+__global__ void __launch_bounds__(256) k_heat(const SysParams *__restrict__ P, DevSys S, int TJ) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using Eng = PairWarp<NS, LJM, QM, DM, ELEC, MULTI>;
+    const int N = S.N;
+    const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * wpb + warp;
+    const int JS = gridDim.y, p = blockIdx.y;
+    const int j0 = (int)(((long long)N * p) / JS), j1 = (int)(((long long)N * (p + 1)) / JS);
+    Smem sm = carve<NS, Eng::DMU, MULTI>(smem_raw, TJ, wpb);
+    int *wq = sm.queue + warp * 64;
+    load_tables<MULTI>(P, sm);
+    Eng e;
+    e.setup(P);
+    const bool active = i < N;
+    const int ii = active ? i : 0;
+    e.begin(P, S, ii);
+    float v[3], w[3];
+    integ::heat_velocities<false>(P, integ::global_view(S), ii, v, w);
+    e.begin_heat(v, w);
+    for (int t0 = j0; t0 < j1; t0 += TJ) {
+        const int tn = min(TJ, j1 - t0);
+        __syncthreads();
+        stage_tile<NS, Eng::DMU, MULTI>(sm, S, t0, tn, TJ, Eng::MOLD && e.rfq);
+        __syncthreads();
+        if (active) e.template scan<true>(sm, TJ, t0, tn, wq, lane);
+    }
+    if (!active) return;
+    float jh[3];
+    e.finish_heat(jh);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) S.hpart[((size_t)p * 3 + k) * N + i] = jh[k];
 }
 
 // FP64 variant for point LJ molecules (site-pair arithmetic in FP64 too):
@@ -162,20 +202,25 @@ struct PairVariant {
     bool multi;
     void (*fn)(const SysParams *, DevSys, int);
     void (*mass)(const SysParams *, DevSys, int);  // variant that also sums d2U/dV2, or null
+    void (*heat)(const SysParams *, DevSys, int);  // heat-flux power pass, or null (Ewald)
 };
 
-#define V(NS, LJM, QM, DM, E, M) {NS, LJM, QM, DM, E, M, &k_pair<NS, LJM, QM, DM, E, M>, nullptr}
-#define VM(NS, LJM, QM, DM, E, M) \
-    {NS, LJM, QM, DM, E, M, &k_pair<NS, LJM, QM, DM, E, M>, &k_pair<NS, LJM, QM, DM, E, M, true>}
+#define V(NS, LJM, QM, DM, E, M) {NS, LJM, QM, DM, E, M, &k_pair<NS, LJM, QM, DM, E, M>, nullptr, nullptr}
+#define VH(NS, LJM, QM, DM, E, M) \
+    {NS, LJM, QM, DM, E, M, &k_pair<NS, LJM, QM, DM, E, M>, nullptr, &k_heat<NS, LJM, QM, DM, E, M>}
+#define VMH(NS, LJM, QM, DM, E, M)                                                                   \
+    {NS, LJM, QM, DM, E, M, &k_pair<NS, LJM, QM, DM, E, M>, &k_pair<NS, LJM, QM, DM, E, M, true>, \
+     &k_heat<NS, LJM, QM, DM, E, M>}
 static const PairVariant kVariants[] = {
-    VM(1, 1u, 0u, 0u, ELEC_NONE, false),     // point LJ
-    VM(3, 1u, 7u, 0u, ELEC_RF, false),       // 3-site water, reaction field
+    VMH(1, 1u, 0u, 0u, ELEC_NONE, false),    // point LJ
+    VMH(3, 1u, 7u, 0u, ELEC_RF, false),      // 3-site water, reaction field
     V(3, 1u, 7u, 0u, ELEC_EWALD, false),     // 3-site water, Ewald
     V(3, 1u, 7u, 0u, ELEC_EWALD, true),      // water + single-site ions, Ewald
-    V(3, 3u, 0u, 4u, ELEC_RF, false),        // 2 LJ + dipole (Stockmayer-like)
+    VH(3, 3u, 0u, 4u, ELEC_RF, false),       // 2 LJ + dipole (Stockmayer-like)
 };
 #undef V
-#undef VM
+#undef VH
+#undef VMH
 
 // generic fallbacks: runtime electrostatics, all slots may carry everything
 static void (*const kGeneric[2][2])(const SysParams *, DevSys, int) = {
@@ -183,6 +228,22 @@ static void (*const kGeneric[2][2])(const SysParams *, DevSys, int) = {
     {&k_pair<8, 0xFFu, 0xFFu, 0u, -1, true>, &k_pair<8, 0xFFu, 0xFFu, 0xFFu, -1, true>},
 };
 static void (*const kGenericMass)(const SysParams *, DevSys, int) = &k_pair<4, 0xFu, 0xFu, 0u, -1, true, true>;
+static void (*const kGenericHeat[2])(const SysParams *, DevSys, int) = {&k_heat<4, 0xFu, 0xFu, 0u, -1, true>,
+                                                                        &k_heat<4, 0xFu, 0xFu, 0xFu, -1, true>};
+
+// The heat-flux pass matching the pair kernel ms2_pick_pair_kernel returned for
+// the same arguments (same slot padding and decomposition), or null (Ewald, FP64
+// path, 8 site slots).
+void *ms2_pick_heat_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, const void *pair_fn) {
+    if (elec == ELEC_EWALD) return nullptr;
+    for (const PairVariant &v : kVariants)
+        if ((const void *)v.fn == pair_fn || (const void *)v.mass == pair_fn) return (void *)v.heat;
+    for (int d = 0; d < 2; ++d)
+        if ((const void *)kGeneric[0][d] == pair_fn) return (void *)kGenericHeat[d];
+    if ((const void *)kGenericMass == pair_fn) return (void *)kGenericHeat[0];
+    (void)ns; (void)ljm; (void)qm; (void)dm; (void)multi;
+    return nullptr;
+}
 
 // Picks the kernel for a system's slot pattern.  Returns the padded slot count
 // the kernel expects in *ns_used (the site arrays must be laid out with it).

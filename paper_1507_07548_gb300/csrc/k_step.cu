@@ -134,13 +134,18 @@ __device__ __forceinline__ bool gk_step(const StepArgs &A, int k) {
     return A.gk_every > 0 && ((A.s0 + k + 1) % A.gk_every) == 0;
 }
 
+// step k of the launch samples the heat flux
+__device__ __forceinline__ bool hf_step(const StepArgs &A, int k) {
+    return A.hf_every > 0 && ((A.s0 + k + 1) % A.hf_every) == 0;
+}
+
 }  // namespace
 
 static_assert(sizeof(SysParams) % 16 == 0, "the parameter copy moves 16-byte words");
 
 // per-block region after the staged system: parameters, own state and partials
 struct OwnLayout {
-    size_t params, state, ui, np, sp, part, hist, end;  // byte offsets from the region start
+    size_t params, state, ui, np, sp, part, hpart, hist, end;  // byte offsets from the region start
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -153,12 +158,17 @@ __host__ __device__ inline OwnLayout own_layout(int mcap, int js, int rdf_cells)
     o.np = al16(o.ui + sizeof(double) * 4 * (size_t)mcap);            // 1 int per slot
     o.sp = al16(o.np + sizeof(int) * (size_t)mcap);                   // species, 1 int per slot
     o.part = al16(o.sp + sizeof(int) * (size_t)mcap);                 // [js][NPV][mcap] floats
-    o.hist = al16(o.part + sizeof(float) * MS2_NPV * (size_t)js * mcap);
+    o.hpart = al16(o.part + sizeof(float) * MS2_NPV * (size_t)js * mcap);  // [js][3][mcap] heat partials
+    o.hist = al16(o.hpart + sizeof(float) * 3 * (size_t)js * mcap);
     o.end = al16(o.hist + sizeof(unsigned) * (size_t)rdf_cells);
     return o;
 }
 
-template <int NS, unsigned LJM, unsigned QM, unsigned DM, int ELEC, bool MULTI, bool MASS = false>
+// HEAT: the variant that also runs the heat-flux power pass and heat unit of
+// k_heat / k_heat_reduce on the sampled steps (after the totals, before the next
+// drift); their record (block 0) follows at the next step's pair phase, or after
+// one more grid barrier at the end of the launch.
+template <int NS, unsigned LJM, unsigned QM, unsigned DM, int ELEC, bool MULTI, bool MASS = false, bool HEAT = false>
 __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__restrict__ P, DevSys S, StepArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using Eng = PairWarp<NS, LJM, QM, DM, ELEC, MULTI, MASS>;
@@ -183,6 +193,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     // then read no parameter through L2 after a grid barrier
     const SysParams *Ps = (const SysParams *)(own + own_layout(MC, JS, 0).params);
     auto part_at = [&]() { return (float *)(own + own_layout(MC, JS, 0).part); };
+    auto hpart_at = [&]() { return (float *)(own + own_layout(MC, JS, 0).hpart); };
     int *wq = sm.queue + warp * 64;
     // own state into shared memory
     for (int t = threadIdx.x; t < nm; t += blockDim.x) {
@@ -243,6 +254,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
             const int gk = gk_step(A, k - 1) ? RED_GK : 0;
             if (lane == 0) finish_step(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA | gk, tot);
             if (gk) gk_update(S, tot, lane);
+            if (HEAT && hf_step(A, k - 1)) heat_record(S, G, lane);
         }
         for (int t = warp; t < nm * JS; t += STEP_WARPS) {
             const int m = t % nm, p = t / nm, i = lo + m;
@@ -283,6 +295,33 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         __syncthreads();
         if (threadIdx.x == 0) lam_s = lambda_of(Ps, tot);
         __syncthreads();
+        // ---- heat flux of this configuration (sampled steps): power pass over
+        // the staged system, then heat unit b
+        if constexpr (HEAT) {
+            if (hf_step(A, k)) {
+                for (int t = warp; t < nm * JS; t += STEP_WARPS) {
+                    const int m = t % nm, p = t / nm, i = lo + m;
+                    const int j0 = (int)(((long long)N * p) / JS), j1 = (int)(((long long)N * (p + 1)) / JS);
+                    e.begin_tile(Ps, sm, A.Np, i);
+                    float hv[3], hw[3];
+                    heat_velocities<true>(Ps, view(), m, hv, hw);
+                    e.begin_heat(hv, hw);
+                    for (int t0 = j0; t0 < j1; t0 += A.TJ)
+                        e.template scan<true>(shifted(sm, t0), A.Np, t0, min(A.TJ, j1 - t0), wq, lane);
+                    float jh[3];
+                    e.finish_heat(jh);
+                    if (lane == 0)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) hpart_at()[((size_t)p * 3 + c) * MC + m] = jh[c];
+                }
+                __syncthreads();
+                if (warp == 0) {
+                    const OwnLayout ol = own_layout(MC, JS, 0);
+                    heat_unit<true>(Ps, S, hpart_at(), MC, view(), (const double *)(own + ol.ui), MC, lo, b, G, lane);
+                }
+                __syncthreads();
+            }
+        }
         if (tm) {
             const unsigned long long t4 = global_ns();
             const unsigned long long m0 = __ldcg(A.tmax), m1 = __ldcg(A.tmax + 1), m2 = __ldcg(A.tmax + 2);
@@ -305,6 +344,10 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         const int gk = gk_step(A, A.nsteps - 1) ? RED_GK : 0;
         if (lane == 0) finish_step(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA | gk, tot);
         if (gk) gk_update(S, tot, lane);
+    }
+    if (HEAT && A.nsteps > 0 && hf_step(A, A.nsteps - 1)) {  // uniform over the grid
+        grid_sync(A.bar, A.err, target, S.scal);
+        if (b == 0 && warp == 0) heat_record(S, G, lane);
     }
     __syncthreads();
     const OwnLayout ol = own_layout(MC, JS, 0);
@@ -347,18 +390,21 @@ int ms2_step_threads() { return STEP_THREADS; }
 
 // fused-step kernel of a pair-kernel variant, or null where the per-phase
 // kernels are used (Ewald, FP64, 8 site slots)
-void *ms2_pick_step_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, bool mass) {
-    if (elec == ELEC_EWALD) return nullptr;
-    if (!multi) {
-        if (ns == 1 && ljm == 1 && qm == 0 && dm == 0 && elec == ELEC_NONE)
-            return mass ? (void *)&k_step<1, 1u, 0u, 0u, ELEC_NONE, false, true>
-                        : (void *)&k_step<1, 1u, 0u, 0u, ELEC_NONE, false>;
-        if (ns == 3 && ljm == 1 && qm == 7 && dm == 0 && elec == ELEC_RF)
-            return mass ? (void *)&k_step<3, 1u, 7u, 0u, ELEC_RF, false, true>
-                        : (void *)&k_step<3, 1u, 7u, 0u, ELEC_RF, false>;
-        if (ns == 3 && ljm == 3 && qm == 0 && dm == 4 && elec == ELEC_RF && !mass)
-            return (void *)&k_step<3, 3u, 0u, 4u, ELEC_RF, false>;
-    }
+// (heat: the variant with the heat-flux pass; Massieu sampling and heat flux
+// together run on the per-phase kernels)
+void *ms2_pick_step_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, bool mass, bool heat) {
+    if (elec == ELEC_EWALD || multi || (mass && heat)) return nullptr;
+    if (ns == 1 && ljm == 1 && qm == 0 && dm == 0 && elec == ELEC_NONE)
+        return mass ? (void *)&k_step<1, 1u, 0u, 0u, ELEC_NONE, false, true>
+                    : heat ? (void *)&k_step<1, 1u, 0u, 0u, ELEC_NONE, false, false, true>
+                           : (void *)&k_step<1, 1u, 0u, 0u, ELEC_NONE, false>;
+    if (ns == 3 && ljm == 1 && qm == 7 && dm == 0 && elec == ELEC_RF)
+        return mass ? (void *)&k_step<3, 1u, 7u, 0u, ELEC_RF, false, true>
+                    : heat ? (void *)&k_step<3, 1u, 7u, 0u, ELEC_RF, false, false, true>
+                           : (void *)&k_step<3, 1u, 7u, 0u, ELEC_RF, false>;
+    if (ns == 3 && ljm == 3 && qm == 0 && dm == 4 && elec == ELEC_RF && !mass)
+        return heat ? (void *)&k_step<3, 3u, 0u, 4u, ELEC_RF, false, false, true>
+                    : (void *)&k_step<3, 3u, 0u, 4u, ELEC_RF, false>;
     return nullptr;
 }
 

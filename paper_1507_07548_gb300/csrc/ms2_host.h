@@ -46,6 +46,7 @@ struct ms2_system_s {
     // fused step (k_step.cu): null when the per-phase kernels run every step
     void *step_fn = nullptr;
     void *fuse_fn = nullptr;  // the variant when the system is fusable (decides the decomposition)
+    void *step_heat_fn = nullptr;  // the fused variant with the heat-flux pass (heat sampling on), or null
     int step_grid = 0, Np = 0, bar_parity = 0, mcap = 0, nunits = 1;
     size_t step_smem_max = 0;
     int last_launch_steps = 0;
@@ -58,12 +59,14 @@ struct ms2_system_s {
     double uconst = 0, wbg = 0, ulrc = 0, plrc = 0;
     long long step = 0;
     int graph_chunk = 50;
-    std::map<std::tuple<int, int, int, int>, GraphEntry> graphs;  // (steps, RDF, conductivity, residence phase)
+    std::map<std::tuple<int, int, int, int, int>, GraphEntry> graphs;  // (steps, RDF, conductivity, residence, heat phase)
     long long launch_acc = 0;
     // RDF
     int rdf_every = 0, rdf_samples = 0, rdf_cap = 0;
     int gk_every = 0;  // conductivity: extended time step (0: off)
     int res_every = 0;  // residence time: extended time step (0: off)
+    int hf_every = 0;   // thermal conductivity: extended time step (0: off)
+    void *heat_fn = nullptr;  // heat-flux power pass matching pair_fn
     ResArgs res{};
     double rdf_rmax = 0;
     // host staging of the state
@@ -87,6 +90,6 @@ size_t ms2_residence_state_doubles(int M);
 // fused step kernel (k_step.cu)
 size_t ms2_step_smem_bytes(int NS, bool dmu, bool multi, int Np, int mcap, int js, int rdf_cells);
 int ms2_step_threads();
-void *ms2_pick_step_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, bool mass);
+void *ms2_pick_step_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, bool mass, bool heat);
 cudaError_t ms2_launch_step(void *fn, int grid, size_t smem, cudaStream_t st, const SysParams *P, const DevSys &S,
                             const StepArgs &A);

@@ -40,6 +40,7 @@ struct SysParams {
     // the thermostat constant 2 / (kconv ndof T0)
     double dtk, kick[MS2_MAXSP], half_mass[MS2_MAXSP], half_Iinv[MS2_MAXSP][3], lam_c;
     double qmol[MS2_MAXSP];  // net molecular charge of each species (electric current flux)
+    double henth[MS2_MAXSP]; // partial molar enthalpy of each species, energy units (heat flux)
     double lat_scale;          // 2^32 / L  (FP64, exact same value as the host computes)
     unsigned long long rc2;    // lattice cut-off threshold
     float lat_to_len;          // L / 2^32 (FP32 rounding of it)
@@ -76,6 +77,9 @@ struct DevSys {
     float *mum;                        // [3][N] molecular dipole sum_a q_a s_ia (reaction field)
     double *gk;                        // conductivity: [0] samples, [1..3] -, ring [gk_lags][3], lag sums [gk_lags]
     int gk_lags;
+    double *hf;                        // thermal conductivity: the same layout as gk (heat flux J_q)
+    int hf_lags;
+    float *hpart;                      // [jsplit][3][N] heat-flux pair partials sum_l d_kl P_kl
     float *part;                       // [jsplit][NPV][N]
     double *part64;                    // FP64 partials (FP64 pair path)
     double *F, *tau;                   // [3][N]
@@ -112,6 +116,7 @@ enum {
     SC_TPAIR,  // fused step: pair-phase time of the last step of a chunk (ns)
     SC_TPH0, SC_TPH1, SC_TPH2, SC_TPH3, SC_TPH4, SC_TPH5, SC_TPH6, SC_TPH7, SC_TPH8,  // fused step: phase times (ns)
     SC_KERR,   // fused step: a grid-barrier wait timed out (sticky until read)
+    SC_HX, SC_HY, SC_HZ,  // heat flux of the last thermal-conductivity sample
     SC_COUNT_
 };
 // running averages; AC_M*: Massieu-derivative moment sums of x = U - U0, y = U_V - V0, w = U_VV
@@ -144,6 +149,7 @@ struct StepArgs {
     long long s0;          // step counter before the chunk (RDF sampling phase)
     int rdf_every;         // 0: no RDF sampling
     int gk_every;          // 0: no conductivity sampling, else the extended time step in steps
+    int hf_every;          // 0: no heat-flux sampling, else its extended time step
     int TJ;                // j tile segmentation of the per-phase pair kernel
     int Np;                // stride of the staged system
     int mcap;              // molecules a block owns at most: ceil(N / gridDim.x)

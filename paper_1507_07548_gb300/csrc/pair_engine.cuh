@@ -146,6 +146,9 @@ struct PairWarp {
     // lane accumulators
     float fa[NS][3], ea[NS][3], ulj, uqq, udd, w, vv, erf_[3];
     int np;
+    // heat-flux power pass (HP): site velocities v_i + w_i x s_ia, w_i x mu_ia,
+    // w_i x mu_i (reaction field) and the lane sums of d_kl P_kl
+    float vs[NS][3], wmu[NS][3], wmd[3], jh[3];
 
     __device__ __forceinline__ void setup(const SysParams *__restrict__ P) {
         elec = ELEC >= 0 ? ELEC : P->elec;
@@ -232,7 +235,31 @@ struct PairWarp {
         np = 0;
     }
 
-    // one partner, tile-local index jl, into this lane's accumulators
+    // Heat-flux power pass (Sec. 4, Eqs. 5-6) of molecule i, after begin or
+    // begin_tile: v and w are its velocity and angular velocity.  The pass sums,
+    // over partners l, d_kl P_kl with P_kl = F_kl.v_k + tau_kl.w_k, taken per site
+    // as sum_a f_a.(v + w x s_a) + e_a.(w x mu_a) (the dipole torque mu_a x e_a)
+    // + 2 C k_RF mu_l.(w x mu_i) (the reaction-field molecular torque); the site
+    // forces are those of the force pass, term for term.
+    __device__ __forceinline__ void begin_heat(const float v[3], const float wv[3]) {
+#pragma unroll
+        for (int a = 0; a < NS; ++a) {
+            vs[a][0] = v[0] + (wv[1] * si[a][2] - wv[2] * si[a][1]);
+            vs[a][1] = v[1] + (wv[2] * si[a][0] - wv[0] * si[a][2]);
+            vs[a][2] = v[2] + (wv[0] * si[a][1] - wv[1] * si[a][0]);
+            wmu[a][0] = wv[1] * mui[a][2] - wv[2] * mui[a][1];
+            wmu[a][1] = wv[2] * mui[a][0] - wv[0] * mui[a][2];
+            wmu[a][2] = wv[0] * mui[a][1] - wv[1] * mui[a][0];
+        }
+        wmd[0] = wv[1] * mdi[2] - wv[2] * mdi[1];
+        wmd[1] = wv[2] * mdi[0] - wv[0] * mdi[2];
+        wmd[2] = wv[0] * mdi[1] - wv[1] * mdi[0];
+        jh[0] = jh[1] = jh[2] = 0.f;
+    }
+
+    // one partner, tile-local index jl, into this lane's accumulators (HP: the
+    // heat-flux power pass; the force-pass accumulators are then dead)
+    template <bool HP = false>
     __device__ __forceinline__ void interact(const Smem &sm, int TJ, int jl) {
     const int dxi = (int)(sm.tX[jl] - Xi), dyi = (int)(sm.tY[jl] - Yi), dzi = (int)(sm.tZ[jl] - Zi);
     // lattice difference -> length with the scale split in two floats, so the
@@ -254,7 +281,7 @@ struct PairWarp {
     // Molecular virial, owner share: the site-pair part -sum_ab f_ab.r_ab here
     // (short levers, no FP32 force sum meets the long lever d), the
     // intramolecular part -2 sum_a s_ia.F_ia once per molecule in finish().
-    float wsite = 0.f, wvv = 0.f;
+    float wsite = 0.f, wvv = 0.f, pw = 0.f;  // pw: the power P_kl (HP)
     const float dd2 = MASS ? dx * dx + dy * dy + dz * dz : 0.f;
 #pragma unroll
     for (int a = 0; a < NS; ++a) {
@@ -334,12 +361,18 @@ struct PairWarp {
                 fa[a][0] += fx; fa[a][1] += fy; fa[a][2] += fz;
                 wsite -= fx * rx + fy * ry + fz * rz;
                 const float ce = 3.f * C * mbr * rinv5, cm = -C * (rinv3 - kd);
-                ea[a][0] += ce * rx + cm * muj[b][0];
-                ea[a][1] += ce * ry + cm * muj[b][1];
-                ea[a][2] += ce * rz + cm * muj[b][2];
+                const float ex = ce * rx + cm * muj[b][0], ey = ce * ry + cm * muj[b][1], ez = ce * rz + cm * muj[b][2];
+                ea[a][0] += ex;
+                ea[a][1] += ey;
+                ea[a][2] += ez;
+                if (HP) {
+                    pw += fx * vs[a][0] + fy * vs[a][1] + fz * vs[a][2];
+                    pw += ex * wmu[a][0] + ey * wmu[a][1] + ez * wmu[a][2];
+                }
             }
             fa[a][0] = fmaf(g, rx, fa[a][0]); fa[a][1] = fmaf(g, ry, fa[a][1]); fa[a][2] = fmaf(g, rz, fa[a][2]);
             wsite = fmaf(-g, r2, wsite);
+            if (HP) pw = fmaf(g, rx * vs[a][0] + ry * vs[a][1] + rz * vs[a][2], pw);
             if (MASS) {
                 const float rd = rx * dx + ry * dy + rz * dz;
                 wvv += fmaf(hh * rd, rd, g * (dd2 - 2.f * rd));
@@ -352,11 +385,18 @@ struct PairWarp {
         erf_[0] += sm.tmd[jl];
         erf_[1] += sm.tmd[TJ + jl];
         erf_[2] += sm.tmd[2 * TJ + jl];
+        if (HP) pw += 2.f * C * krf * (sm.tmd[jl] * wmd[0] + sm.tmd[TJ + jl] * wmd[1] + sm.tmd[2 * TJ + jl] * wmd[2]);
+    }
+    if (HP) {
+        jh[0] = fmaf(dx, pw, jh[0]);
+        jh[1] = fmaf(dy, pw, jh[1]);
+        jh[2] = fmaf(dz, pw, jh[2]);
     }
     ++np;
     }
 
     // scan tile slots [0, tn) (global index of slot 0: t0), partners in batches of 32
+    template <bool HP = false>
     __device__ __forceinline__ void scan(const Smem &sm, int TJ, int t0, int tn, int *wq, int lane) {
         int qn = 0;
         for (int base = 0; base < tn; base += 32) {
@@ -371,7 +411,7 @@ struct PairWarp {
             qn += __popc(m);
             __syncwarp();
             if (qn >= 32) {
-                interact(sm, TJ, wq[lane]);
+                interact<HP>(sm, TJ, wq[lane]);
                 __syncwarp();
                 qn -= 32;
                 if (lane < qn) wq[lane] = wq[32 + lane];
@@ -379,9 +419,15 @@ struct PairWarp {
             }
         }
         if (qn > 0) {
-            if (lane < qn) interact(sm, TJ, wq[lane]);
+            if (lane < qn) interact<HP>(sm, TJ, wq[lane]);
             __syncwarp();
         }
+    }
+
+    // heat pass: the warp's sum_l d_kl P_kl (fixed tree, every lane)
+    __device__ __forceinline__ void finish_heat(float out[3]) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) out[k] = warp_sum(jh[k]);
     }
 
     // fixed-tree warp reduction; the result is valid in lane 0

@@ -103,6 +103,9 @@ SIGNATURES = {
     "ms2_conductivity_setup": (C.c_int, [_vp, C.c_int, C.c_int]),
     "ms2_current": (C.c_int, [_vp, _d]),
     "ms2_conductivity": (C.c_int, [_vp, _d, _d, _P(C.c_longlong)]),
+    "ms2_heat_setup": (C.c_int, [_vp, C.c_int, C.c_int, _d]),
+    "ms2_heat_flux": (C.c_int, [_vp, _d]),
+    "ms2_thermal_conductivity": (C.c_int, [_vp, _d, _d, _P(C.c_longlong)]),
     "ms2_residence_setup": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int]),
     "ms2_residence": (C.c_int, [_vp, _d, _d, _d, _P(C.c_longlong)]),
     "ms2_step_kernel": (C.c_int, [_vp, _P(C.c_int)]),
@@ -339,6 +342,27 @@ class System:
         n = C.c_longlong()
         check(lib().ms2_conductivity(self.h, C.byref(sig), _dp(acf), C.byref(n)))
         return sig.value, acf, n.value
+
+    def heat_setup(self, every, n_lags, h=None):
+        """Sample the heat flux J_q every `every` steps into an ACF of n_lags lags;
+        h: partial molar enthalpy per species (energy units per molecule), default 0."""
+        hh = None if h is None else np.ascontiguousarray(h, dtype=np.float64)
+        check(lib().ms2_heat_setup(self.h, every, n_lags, None if hh is None else _dp(hh)))
+        self._hf_lags = n_lags
+
+    def heat_flux(self):
+        """Heat flux J_q of the last sample (K A/fs, energies in K)."""
+        j = np.zeros(3)
+        check(lib().ms2_heat_flux(self.h, _dp(j)))
+        return j
+
+    def thermal_conductivity(self):
+        """(lambda in W/(m K), the heat-flux ACF, number of samples)."""
+        lam = C.c_double()
+        acf = np.zeros(getattr(self, "_hf_lags", 1))
+        n = C.c_longlong()
+        check(lib().ms2_thermal_conductivity(self.h, C.byref(lam), _dp(acf), C.byref(n)))
+        return lam.value, acf, n.value
 
     MASSIEU_NAMES = ("A10", "A01", "A20", "A11", "A02", "A30", "A21", "A12")
 

@@ -265,6 +265,26 @@ def ionic_solution(n_water=1000, n_ion_pairs=20, rc=14.0, T=298.0, seed=3, dt=2.
                     alpha=alpha, kmax=tuple(kmax), seed=seed)
 
 
+def water_argon(n_water=800, n_argon=200, rc=14.0, T=298.0, seed=6, dt=2.0) -> Workload:
+    """Binary mixture of rigid water and argon-like LJ atoms (reaction field) at
+    water number density: molecules on simple-cubic lattice points (a seeded
+    choice of which hold argon), numbered species by species, waters randomly
+    oriented (the multi-component heat flux of Sec. 4)."""
+    N = n_water + n_argon
+    L = (N / WATER_NUMBER_DENSITY) ** (1 / 3)
+    rng = np.random.default_rng(seed)
+    models = [water(), argon()]
+    R = sc_lattice(N, L) + rng.uniform(-0.05, 0.05, size=(N, 3))
+    sp = np.zeros(N, np.int32)
+    sp[rng.permutation(N)[:n_argon]] = 1
+    order = np.argsort(sp, kind="stable")
+    sp, R = sp[order], R[order]
+    q = random_quaternions(N, rng)
+    q[sp != 0] = [1.0, 0, 0, 0]
+    v, Ls = thermal_velocities(models, sp, q, T, KCONV, rng)
+    return Workload("water_argon_N%d" % N, models, sp, L, rc, 1, T, dt, False, R, q, v, Ls, seed=seed)
+
+
 def stockmayer_fluid(N=500, rho=0.012, T=300.0, rc=17.5, seed=4, dt=2.0) -> Workload:
     L = (N / rho) ** (1 / 3)
     rng = np.random.default_rng(seed)
