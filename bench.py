@@ -282,6 +282,7 @@ def gpu_arm(args, rank, world, local_rank):
     if not args.no_extra and rank == 0:
         extra["ewald_ionic"] = ewald_sub(args, stream)
         extra["massieu"] = massieu_sub(args, stream, flush)
+        extra["thermal"] = thermal_sub(args, stream, flush)
         extra["batch"] = batch_sub(args, flush)
         extra["serve"] = serve_sub(args, extra["batch"]["batched"]["value"])
 
@@ -444,6 +445,45 @@ def massieu_sub(args, stream, flush):
             "A_r": {k: float(v) for k, v in A.items()},
             "note": "%d samples after %d relaxation steps: a short run, the values illustrate the output "
                     "rather than converged properties" % (n, RELAX_STEPS)}
+
+
+def thermal_sub(args, stream, flush):
+    """The headline water workload sampling the Green-Kubo heat flux (Eqs. 5-6):
+    every step, timed like the headline (L2 flushed, one step per interval), then
+    every 5 steps in chunks as a production run would, for lambda."""
+    import torch
+    import paper_1507_07548_gb300.ms2 as ms2
+    from paper_1507_07548_gb300 import workloads as W
+    wl = W.water_box(N=N_WATER, rc=RC, seed=SEED)
+    s = ms2.System.from_workload(wl, stream=stream.cuda_stream)
+    s.step(RELAX_STEPS)
+    s.heat_setup(every=1, n_lags=8)
+    fused = s.fused_step() == 1
+    t = []
+    for k in range(MASSIEU_STEPS + args.warmup):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            t.append(e0.elapsed_time(e1))
+    s.heat_setup(every=5, n_lags=100)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(GK_STEPS)
+    e1.record(stream)
+    e1.synchronize()
+    lam, acf, nsamp = s.thermal_conductivity()
+    s.close()
+    return {"workload": "rigid 3-site water N=1000, reaction field, rc=14 A, 298 K, heat flux J_q sampled",
+            "fused": fused, "ms_per_step_sampled_every_step": statistics.mean(t),
+            "ms_per_step_in_chunks": e0.elapsed_time(e1) / GK_STEPS, "steps": GK_STEPS, "extended_step": 5,
+            "lags": 100, "samples": nsamp, "lambda_W_per_mK": lam,
+            "note": "partial molar enthalpy 0, isokinetic thermostat on (J_q uses the unscaled half-step mean); "
+                    "short run: lambda illustrates the output, it is not converged"}
 
 
 def ewald_sub(args, stream):

@@ -743,40 +743,47 @@ def test_heat_flux_is_the_time_derivative_of_the_energy_moment():
     """Without the enthalpy term, J_q = d/dt sum_k R_k E_k for Newtonian dynamics of
     an isolated cluster (E_k = kinetic energies + half the pair energies of k).
     Leapfrog NVE from the oracle; integer-time velocities as half-step means;
-    central differences of the moment against J_q at the middle step."""
+    central differences of the moment against J_q at the middle step.  The
+    mismatch is the O(dt^2) of the differences: it falls ~4x per halving of dt
+    (a dropped or mis-signed term would leave an O(1) part)."""
     rng = np.random.default_rng(41)
     n, L = 8, 60.0
     models = [W.water()]
     sp = np.zeros(n, np.int32)
-    R = 30.0 + 3.1 * np.array([[x, y, z] for x in (0, 1) for y in (0, 1) for z in (0, 1)], float)
-    R += rng.normal(0, 0.1, R.shape)
-    q = W.random_quaternions(n, rng)
+    R0 = 30.0 + 3.1 * np.array([[x, y, z] for x in (0, 1) for y in (0, 1) for z in (0, 1)], float)
+    R0 += rng.normal(0, 0.1, R0.shape)
+    q0 = W.random_quaternions(n, rng)
     o = Oracle(models, sp, L, 25.0, elec=1, lrc=0)
-    v, Lg = W.thermal_velocities(models, sp, q, 30.0, o.s.kconv, rng)
-    dt = 0.25
-    states = [(R, q, v, Lg)]
-    for _ in range(3):
-        R, q, v, Lg, _, _ = o.run_leapfrog(R, q, v, Lg, dt, 1, T0=0.0)
-        states.append((R, q, v, Lg))
-    # state k holds R_k, q_k and the velocities v_{k-1/2}, L_{k-1/2}
+    v0, L0 = W.thermal_velocities(models, sp, q0, 30.0, o.s.kconv, rng)
     M = sum(s.mass for s in models[0].sites)
     Iinv = 1.0 / W.principal_moments(models[0])
 
-    def moment(k):
-        Rk, qk = states[k][0], states[k][1]
-        vk = 0.5 * (states[k][2] + states[k + 1][2])
-        Lk = 0.5 * (states[k][3] + states[k + 1][3])
-        A = W.quat_to_matrix(qk)
-        Lb = np.einsum("nij,ni->nj", A, Lk)
-        ke = (0.5 * M * (vk * vk).sum(1) + 0.5 * (Iinv * Lb * Lb).sum(1)) / o.s.kconv
-        u = o.molecule_terms(Rk, qk)[:, :3].sum(1)          # half of each pair energy per molecule
-        return ((ke + u)[:, None] * Rk).sum(0), (Rk, qk, vk, Lk)
+    def mismatch(dt):
+        states = [(R0, q0, v0, L0)]
+        R, q, v, Lg = R0, q0, v0, L0
+        for _ in range(3):
+            R, q, v, Lg, _, _ = o.run_leapfrog(R, q, v, Lg, dt, 1, T0=0.0)
+            states.append((R, q, v, Lg))
 
-    D0, _ = moment(0)
-    D2, _ = moment(2)
-    _, mid = moment(1)
-    J = o.heat_flux(*mid, h=[0.0])
-    np.testing.assert_allclose((D2 - D0) / (2 * dt), J, rtol=2e-3, atol=2e-3 * np.abs(J).max())
+        # state k holds R_k, q_k and the velocities v_{k-1/2}, L_{k-1/2}
+        def moment(k):
+            Rk, qk = states[k][0], states[k][1]
+            vk = 0.5 * (states[k][2] + states[k + 1][2])
+            Lk = 0.5 * (states[k][3] + states[k + 1][3])
+            A = W.quat_to_matrix(qk)
+            Lb = np.einsum("nij,ni->nj", A, Lk)
+            ke = (0.5 * M * (vk * vk).sum(1) + 0.5 * (Iinv * Lb * Lb).sum(1)) / o.s.kconv
+            u = o.molecule_terms(Rk, qk)[:, :3].sum(1)      # half of each pair energy per molecule
+            return ((ke + u)[:, None] * Rk).sum(0), (Rk, qk, vk, Lk)
+
+        D0, _ = moment(0)
+        D2, _ = moment(2)
+        J = o.heat_flux(*moment(1)[1], h=[0.0])
+        return np.abs((D2 - D0) / (2 * dt) - J).max() / np.abs(J).max()
+
+    e1, e2 = mismatch(0.125), mismatch(0.0625)
+    assert e2 < 1e-4
+    assert 3.0 < e1 / e2 < 5.0, (e1, e2)
 
 
 def test_heat_flux_enthalpy_term_and_units():
