@@ -1,18 +1,27 @@
-// Batched systems: persistent kernels that advance many independent systems,
-// one thread block per system for a whole chunk of steps (drift + rotation +
-// site build, optional RDF sample, partner search + site-pair forces, fixed-
-// order reduction with the isokinetic factor), taking the next system from a
-// longest-first work list when done.  A step needs only __syncthreads(): no
-// grid-wide barrier.  Each model kind (slot pattern) has its own kernel, so each
-// keeps its own register budget; the kinds run concurrently on forked streams.
+// Batched systems: many independent systems advanced together by one
+// cooperative persistent kernel per model kind (slot pattern), one 512-thread
+// block per SM, for a chunk of steps.  Each step runs the phases of the
+// single-system path over all systems of the kind at once, with a bounded grid
+// barrier between phases:
+//   drift      groups of 8 molecules (a quad per molecule), round-robin over all warps
+//   pair       molecule items split into equal-cost contiguous ranges, one per
+//              block; a block stages each system of its range in shared memory
+//              and its warps take that system's items (owner warp per molecule,
+//              the whole system as one j-range); RDF samples on the same tile
+//   reduction  units of ~32 molecules, round-robin over all warps
+//   totals     one warp per system: fixed-order unit totals, the step record and
+//              the thermostat factor of the next drift
+// So work is balanced over the whole GPU at molecule granularity whatever the
+// mix of sizes (no system waits on one block), and the kinds run one after the
+// other on the batch stream.
 //
-// Every per-system result depends only on the system and its fixed tile (the
-// whole system in one shared-memory tile): warps take molecules round-robin,
-// and the system sums are taken over fixed chunks of 32 molecules in chunk
-// order.  A system therefore gives bit-identical results alone, in any batch,
-// and with any block size the autotuner picks.
+// Every per-system result depends only on the system: its pair items, its
+// reduction units and their orders are fixed by the system alone, not by the
+// batch, the grid or the block size.  A system therefore gives bit-identical
+// results alone, in any batch, and with any shape the autotuner picks.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -25,6 +34,7 @@
 
 #include <sys/stat.h>
 
+#include "grid_dev.cuh"
 #include "integrate_dev.cuh"
 #include "ms2_host.h"
 #include "pair_engine.cuh"
@@ -37,209 +47,131 @@ namespace {
 enum Kind { K_LJ1 = 0, K_W3RF, K_ST3RF, K_G4, K_G4D, K_COUNT };
 const char *kKindName[K_COUNT] = {"lj1", "water3_rf", "stockmayer3_rf", "generic4", "generic4_dipole"};
 
+constexpr int MS_THREADS = 512;   // largest block shape (the autotuner may take 256)
+constexpr int UNIT = 32;          // molecules per reduction unit
+constexpr int RDF_SMEM_MAX = 4096;  // histogram cells staged in shared memory
+
 struct BatchEntry {
     const SysParams *P;
-    DevSys S;
-    int TJ;
+    DevSys S;         // the system's arrays, with jsplit = 1 and blk -> the batch's unit partials
+    int units;        // reduction units: ceil(N / UNIT)
     int rdf_every;
     long long step0;  // step counter of the system before this launch
-    double *chunk;    // [ceil(N/32)][Q_N] partial sums of the fixed-order reduction
 };
 
-constexpr int RDF_SMEM_MAX = 4096;  // histogram cells staged in shared memory
+// launch arguments of one kind (device tables built on the host)
+struct MsArgs {
+    const BatchEntry *tab;
+    int n_sys;
+    const int2 *drift;     // drift groups (entry, first molecule), 8 molecules each
+    int n_drift;
+    const int4 *seg;       // pair segments (entry, first molecule, end, 0) ...
+    const int *seg_off;    // ... of block b: seg[seg_off[b] .. seg_off[b + 1])
+    const int2 *unit;      // reduction units (entry, unit)
+    int n_unit;
+    int Np;                // stride of the staged tile (largest N of the kind, multiple of 4)
+    int nsteps;
+    unsigned *bar, *err;   // barrier counter (zero at entry) and sticky timeout flag
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 }  // namespace
 
-// ------------------------------------------------------------------ phases
-// drift: one quad of lanes per molecule (lanes 0-2 components, lane 3 rotation)
-__device__ __forceinline__ void batch_drift(const SysParams *__restrict__ P, const DevSys &S) {
-    const int N = S.N, c = threadIdx.x & 3;
-    const double dt = P->dt, lam = S.scal[SC_LAMBDA];
-    for (int base = 0; base < N; base += blockDim.x >> 2) {
-        const int i = base + (threadIdx.x >> 2);
-        const bool on = i < N;
-        const int ii = on ? i : 0, sp = S.species[ii];
-        double q[4] = {S.q[ii], S.q[N + ii], S.q[2 * N + ii], S.q[3 * N + ii]};
-        if (c < 3) {
-            if (on) {
-                const double v = lam * (S.v[c * N + i] + dt * P->kconv * P->inv_mass[sp] * S.F[c * N + i]);
-                S.v[c * N + i] = v;
-                S.R[c * N + i] += dt * v;
-            }
-        } else {
-            const double ct = dt * P->kconv;
-            double L[3];
-            for (int k = 0; k < 3; ++k) {
-                L[k] = lam * (S.Lm[k * N + ii] + ct * S.tau[k * N + ii]);
-                if (on) S.Lm[k * N + i] = L[k];
-            }
-            const double *Ii = P->Iinv[sp];
-            if (Ii[0] != 0.0 || Ii[1] != 0.0 || Ii[2] != 0.0) {
-                double q1[4];
-                rotate_q(Ii, q, L, dt, P->quat_iters, q1);
-                for (int k = 0; k < 4; ++k) {
-                    q[k] = q1[k];
-                    if (on) S.q[k * N + i] = q1[k];
-                }
-            }
-        }
-        for (int k = 0; k < 4; ++k) q[k] = __shfl_sync(0xffffffffu, q[k], (threadIdx.x & 28) | 3);
-        if (c < 3 && on) build_row(P, S, i, c, q, S.R[c * N + i], S.species[i]);
-    }
-}
-
-// RDF sample of the current configuration into a shared-memory histogram
-__device__ void batch_rdf(const SysParams *__restrict__ P, const DevSys &S, unsigned *hist) {
-    const int N = S.N, NS = S.ns, nb = S.rdf_bins, rows = S.rdf_rows, T = P->n_ljt;
-    for (int k = threadIdx.x; k < rows * nb; k += blockDim.x) hist[k] = 0u;
-    __syncthreads();
-    const float l2l = P->lat_to_len, l2 = P->len_to_lat, rmax2 = S.rdf_rmax2, inv_dr = S.rdf_inv_dr;
-    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = warp; i < N; i += nw) {
-        const int spi = S.species[i];
-        for (int a = 0; a < NS; ++a) {
-            const int ta = S.rdf_kind[spi * MS2_MAXS + a];
-            if (ta < 0) continue;
-            uint32_t Xa[3];
-            for (int c = 0; c < 3; ++c)
-                Xa[c] = S.X[c * N + i] + (uint32_t)__float2int_rn(S.s[(c * NS + a) * N + i] * l2);
-            for (int j = i + 1 + lane; j < N; j += 32) {
-                const int spj = S.species[j];
-                for (int b = 0; b < NS; ++b) {
-                    const int tb = S.rdf_kind[spj * MS2_MAXS + b];
-                    if (tb < 0) continue;
-                    float r2 = 0.f;
-                    for (int c = 0; c < 3; ++c) {
-                        const uint32_t Xb = S.X[c * N + j] + (uint32_t)__float2int_rn(S.s[(c * NS + b) * N + j] * l2);
-                        const float d = (float)(int)(Xb - Xa[c]) * l2l;
-                        r2 += d * d;
-                    }
-                    if (!(r2 < rmax2)) continue;
-                    const int bin = (int)(sqrtf(r2) * inv_dr);
-                    if (bin >= nb) continue;
-                    const int t1 = min(ta, tb), t2 = max(ta, tb);
-                    atomicAdd(&hist[(t1 * T - t1 * (t1 - 1) / 2 + (t2 - t1)) * nb + bin], 1u);
-                }
-            }
-        }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < rows * nb; k += blockDim.x)
-        if (hist[k]) atomicAdd(&S.rdf[k], (unsigned long long)hist[k]);
-}
-
-// reduction: lane = molecule within a chunk of 32, chunks round-robin over the
-// warps, chunk sums in a fixed shuffle tree, then chunk order; the step scalars
-// and the isokinetic factor for the next drift
-__device__ void batch_reduce(const SysParams *__restrict__ P, const DevSys &S, double *chunk) {
-    const int N = S.N, nch = (N + 31) >> 5;
-    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const double dt = P->dt, kc = P->kconv;
-    for (int ch = warp; ch < nch; ch += nw) {
-        const int i = ch * 32 + lane;
-        double r[Q_N] = {0, 0, 0, 0, 0, 0};
-        if (i < N) {
-            const int sp = S.species[i];
-            const double M = P->mass[sp];
-            const double q[4] = {S.q[i], S.q[N + i], S.q[2 * N + i], S.q[3 * N + i]};
-            double fm = 0;
-            for (int c = 0; c < 3; ++c) {
-                double col[3];
-                rot_column(q, c, col);
-                const double F = S.F[c * N + i], v = S.v[c * N + i];
-                fm = fmax(fm, fabs(F));
-                const double L0 = S.Lm[i], L1 = S.Lm[N + i], L2 = S.Lm[2 * N + i];
-                const double t0 = S.tau[i], t1 = S.tau[N + i], t2 = S.tau[2 * N + i];
-                const double lb = col[0] * L0 + col[1] * L1 + col[2] * L2;
-                const double lb1 = lb + dt * kc * (col[0] * t0 + col[1] * t1 + col[2] * t2);
-                const double Ii = P->Iinv[sp][c];
-                const double v1 = v + dt * kc * P->inv_mass[sp] * F;
-                r[Q_KTR] += 0.5 * M * v * v;
-                r[Q_KROT] += 0.5 * Ii * lb * lb;
-                r[Q_K1] += 0.5 * M * v1 * v1 + 0.5 * Ii * lb1 * lb1;
-            }
-            r[Q_U] = S.Ui[i] + S.Ui[N + i] + S.Ui[2 * N + i];
-            r[Q_W] = S.Ui[3 * N + i];
-            r[Q_BAD] = fm < 1e30 ? 0.0 : 1.0;
-        }
-        for (int k = 0; k < Q_N; ++k) {
-            const double x = warp_sum(r[k]);
-            if (lane == 0) chunk[ch * Q_N + k] = x;
-        }
-    }
-    __syncthreads();
-    __shared__ double tot[Q_N];
-    if (warp == 0) {
-        for (int k = 0; k < Q_N; ++k) {
-            double x = 0;
-            for (int ch = lane; ch < nch; ch += 32) x += chunk[ch * Q_N + k];
-            x = warp_sum(x);
-            if (lane == 0) tot[k] = x;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) finish_step(P, S, RED_SUM | RED_RECORD | RED_LAMBDA, tot);
-    __syncthreads();
-}
-
+// ------------------------------------------------------------------ kernel
 template <int NS, unsigned LJM, unsigned QM, unsigned DM, int ELEC, bool MULTI>
-__global__ void __launch_bounds__(256) k_batch(const BatchEntry *__restrict__ tab, const int *__restrict__ order,
-                                               int n, unsigned int *next, int nsteps) {
+__global__ void __launch_bounds__(MS_THREADS, 1) k_mstep(MsArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using Eng = PairWarp<NS, LJM, QM, DM, ELEC, MULTI>;
-    __shared__ int cur;
+    __shared__ double wtot[MS_THREADS / 32][MS2_NRED];
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) cur = (int)atomicAdd(next, 1u);
-        __syncthreads();
-        if (cur >= n) return;
-        const BatchEntry &e = tab[order[cur]];
-        const SysParams *P = e.P;
-        const DevSys S = e.S;
-        const int N = S.N, TJ = e.TJ;
-        Smem sm = carve<NS, Eng::DMU, MULTI>(smem_raw, TJ, nw);
-        unsigned *hist = (unsigned *)(smem_raw + pair_engine::smem_bytes(NS, Eng::DMU, MULTI, TJ, nw));
-        int *wq = sm.queue + warp * 64;
-        load_tables<MULTI>(P, sm);
-        Eng eng;
-        eng.setup(P);
-        for (int st = 0; st < nsteps; ++st) {
-            batch_drift(P, S);
-            __syncthreads();
-            if (S.rdf && e.rdf_every > 0 && ((e.step0 + st + 1) % e.rdf_every) == 0) batch_rdf(P, S, hist);
-            stage_tile<NS, Eng::DMU, MULTI>(sm, S, 0, N, TJ, Eng::MOLD && eng.rfq);
-            __syncthreads();
-            for (int i = warp; i < N; i += nw) {
-                eng.begin(P, S, i);
-                eng.scan(sm, TJ, 0, N, wq, lane);
-                const PairOut o = eng.finish(lane);
-                if (lane == 0) {
-                    for (int k = 0; k < 3; ++k) {
-                        S.F[k * N + i] = (double)o.F[k];
-                        S.tau[k * N + i] = (double)o.T[k];
-                    }
-                    S.Ui[i] = o.ulj;
-                    S.Ui[N + i] = o.uqq;
-                    S.Ui[2 * N + i] = o.udd;
-                    S.Ui[3 * N + i] = o.w;
-                    S.npart[i] = o.np;
-                }
-            }
-            __syncthreads();
-            batch_reduce(P, S, e.chunk);
+    const int gw = blockIdx.x * nw + warp, W = gridDim.x * nw;
+    const Smem sm = carve<NS, Eng::DMU, MULTI>(smem_raw, A.Np, nw);
+    unsigned *hist = (unsigned *)(smem_raw + al16(pair_engine::smem_bytes(NS, Eng::DMU, MULTI, A.Np, nw)));
+    int *wq = sm.queue + warp * 64;
+    unsigned target = 0;
+    auto on_timeout = [&]() {
+        for (int e = 0; e < A.n_sys; ++e) A.tab[e].S.scal[SC_KERR] = 1.0;
+    };
+    using grid_dev::grid_sync;
+    for (int k = 0; k < A.nsteps; ++k) {
+        // ---- drift + site build: kick with the last forces and thermostat factor
+        for (int g = gw; g < A.n_drift; g += W) {
+            const int2 d = A.drift[g];
+            const BatchEntry &en = A.tab[d.x];
+            const int i = d.y + (lane >> 2);
+            const bool on = i < en.S.N;
+            const double lam = __ldcg(en.S.scal + SC_LAMBDA);
+            drift_quad<false>(en.P, en.S, global_view(en.S), i, i, on, lane & 3, false, lam);
         }
+        grid_sync(A.bar, A.err, target, on_timeout);
+        // ---- pair items of this block, system by system (and RDF samples)
+        for (int sg = A.seg_off[blockIdx.x]; sg < A.seg_off[blockIdx.x + 1]; ++sg) {
+            const int4 g = A.seg[sg];
+            const BatchEntry &en = A.tab[g.x];
+            const SysParams *P = en.P;
+            const DevSys &S = en.S;
+            const int N = S.N;
+            const bool rdf = S.rdf && en.rdf_every > 0 && ((en.step0 + k + 1) % en.rdf_every) == 0;
+            Eng e;
+            e.setup(P);
+            __syncthreads();  // the previous segment's tile is no longer read
+            load_tables<MULTI>(P, sm);
+            stage_tile<NS, Eng::DMU, MULTI>(sm, S, 0, N, A.Np, Eng::MOLD && e.rfq);
+            if (rdf)
+                for (int c = threadIdx.x; c < S.rdf_rows * S.rdf_bins; c += blockDim.x) hist[c] = 0u;
+            __syncthreads();
+            for (int i = g.y + warp; i < g.z; i += nw) {
+                e.begin_tile(P, sm, A.Np, i);
+                e.scan(sm, A.Np, 0, N, wq, lane);
+                const PairOut o = e.finish(lane);
+                if (lane == 0) {
+                    float *q = S.part + i;
+                    q[PV_FX * N] = o.F[0]; q[PV_FY * N] = o.F[1]; q[PV_FZ * N] = o.F[2];
+                    q[PV_TX * N] = o.T[0]; q[PV_TY * N] = o.T[1]; q[PV_TZ * N] = o.T[2];
+                    q[PV_ULJ * N] = o.ulj; q[PV_UQQ * N] = o.uqq; q[PV_UDD * N] = o.udd; q[PV_W * N] = o.w;
+                    q[PV_NP * N] = (float)o.np;
+                    q[PV_VV * N] = o.vv;
+                }
+                if (rdf) rdf_molecule<NS, MULTI>(P, S, sm, A.Np, i, i + 1 + lane, 32, N, hist);
+            }
+            if (rdf) {  // uniform over the block
+                __syncthreads();
+                for (int c = threadIdx.x; c < S.rdf_rows * S.rdf_bins; c += blockDim.x)
+                    if (hist[c]) atomicAdd(&S.rdf[c], (unsigned long long)hist[c]);
+            }
+        }
+        grid_sync(A.bar, A.err, target, on_timeout);
+        // ---- reduction units: F, tau, energies, kinetic energies (before and after the kick)
+        for (int g = gw; g < A.n_unit; g += W) {
+            const int2 u = A.unit[g];
+            const BatchEntry &en = A.tab[u.x];
+            reduce_unit<false>(en.P, en.S, global_io(en.S), RED_SUM | RED_LAMBDA, u.y, en.units, lane);
+        }
+        grid_sync(A.bar, A.err, target, on_timeout);
+        // ---- per system: totals in unit order, the record, the next thermostat factor
+        for (int s = gw; s < A.n_sys; s += W) {
+            const BatchEntry &en = A.tab[s];
+            for (int q = 0; q < Q_N; ++q) {
+                const double x = unit_total(en.S, en.units, q, lane);
+                if (lane == 0) wtot[warp][q] = x;
+            }
+            __syncwarp();
+            if (lane == 0) finish_step(en.P, en.S, RED_SUM | RED_RECORD | RED_LAMBDA, wtot[warp]);
+            __syncwarp();
+        }
+        grid_sync(A.bar, A.err, target, on_timeout);
     }
 }
 
 namespace {
-typedef void (*BatchFn)(const BatchEntry *, const int *, int, unsigned int *, int);
+typedef void (*BatchFn)(MsArgs);
 const BatchFn kBatchFn[K_COUNT] = {
-    &k_batch<1, 1u, 0u, 0u, ELEC_NONE, false>,
-    &k_batch<3, 1u, 7u, 0u, ELEC_RF, false>,
-    &k_batch<3, 3u, 0u, 4u, ELEC_RF, false>,
-    &k_batch<4, 0xFu, 0xFu, 0u, -1, true>,
-    &k_batch<4, 0xFu, 0xFu, 0xFu, -1, true>,
+    &k_mstep<1, 1u, 0u, 0u, ELEC_NONE, false>,
+    &k_mstep<3, 1u, 7u, 0u, ELEC_RF, false>,
+    &k_mstep<3, 3u, 0u, 4u, ELEC_RF, false>,
+    &k_mstep<4, 0xFu, 0xFu, 0u, -1, true>,
+    &k_mstep<4, 0xFu, 0xFu, 0xFu, -1, true>,
 };
 const int kKindNS[K_COUNT] = {1, 3, 3, 4, 4};
 const bool kKindDMU[K_COUNT] = {false, false, true, false, true};
@@ -250,13 +182,27 @@ int kind_of(ms2_system s) {
     if (P.ns == 1 && s->ljm == 1u && s->qm == 0 && s->dm == 0 && P.elec == ELEC_NONE && !P.multi) return K_LJ1;
     if (P.ns == 3 && s->ljm == 1u && s->qm == 7u && s->dm == 0 && P.elec == ELEC_RF && !P.multi) return K_W3RF;
     if (P.ns == 3 && s->ljm == 3u && s->qm == 0 && s->dm == 4u && P.elec == ELEC_RF && !P.multi) return K_ST3RF;
-    if (P.ns <= 4) return s->dm ? K_G4D : K_G4;
+    if (P.ns == 4) return s->dm ? K_G4D : K_G4;
     return -1;
 }
 
-size_t batch_smem(int kind, int N, int threads, int rdf_cells) {
-    return pair_engine::smem_bytes(kKindNS[kind], kKindDMU[kind], kKindMulti[kind], N, threads / 32) +
+size_t batch_smem(int kind, int Np, int threads, int rdf_cells) {
+    return al16(pair_engine::smem_bytes(kKindNS[kind], kKindDMU[kind], kKindMulti[kind], Np, threads / 32)) +
            sizeof(unsigned) * (size_t)std::max(rdf_cells, 1);
+}
+
+// relative cost of one pair item of system s (warp instructions, rough): the
+// candidate scan over all N molecules plus the expected partners times the
+// site pairs each evaluates
+double item_cost(ms2_system s) {
+    const double L = s->hp.L, rc = s->rc;
+    const double frac = std::min(1.0, 4.0 / 3.0 * M_PI * rc * rc * rc / (L * L * L));
+    int sp = 0;
+    for (int a = 0; a < 8; ++a)
+        for (int c = 0; c < 8; ++c)
+            if ((((s->ljm >> a) & (s->ljm >> c)) | ((s->qm >> a) & (s->qm >> c)) | ((s->dm >> a) & (s->dm >> c))) & 1u)
+                ++sp;
+    return (double)s->N * (20.0 + frac * (25.0 * sp + 30.0));
 }
 
 // ---------------------------------------------------------- autotune cache
@@ -299,39 +245,68 @@ struct ms2_batch_s {
     std::vector<ms2_system> sys;
     cudaStream_t stream = nullptr;
     DevAlloc al;
-    BatchEntry *dtab = nullptr;
-    std::vector<BatchEntry> htab;
-    int *dorder[K_COUNT] = {nullptr};
-    std::vector<int> order[K_COUNT];
-    unsigned *dnext = nullptr;  // one counter per kind
-    int threads[K_COUNT] = {0};
+    std::vector<int> order[K_COUNT];       // member systems of each kind, in creation order
+    std::vector<BatchEntry> htab[K_COUNT];
+    BatchEntry *dtab[K_COUNT] = {nullptr};
+    int2 *ddrift[K_COUNT] = {nullptr}, *dunit[K_COUNT] = {nullptr};
+    int n_drift[K_COUNT] = {0}, n_unit[K_COUNT] = {0};
+    int4 *dseg[K_COUNT] = {nullptr};
+    int *dsegoff[K_COUNT] = {nullptr};
+    int Np[K_COUNT] = {0}, rdf_cells[K_COUNT] = {0};
+    int threads[K_COUNT] = {0}, grid[K_COUNT] = {0};
     size_t smem[K_COUNT] = {0};
-    int grid[K_COUNT] = {0};
-    cudaStream_t ks[K_COUNT] = {nullptr};
-    cudaEvent_t ev_fork = nullptr, ev_join[K_COUNT] = {nullptr};
+    unsigned *dbar = nullptr;  // [K_COUNT][2]: barrier counter, timeout flag
     int chunk = 100;
 };
 
 // trial = autotuner run: no RDF samples, no step counters
+static ms2_status set_shape(ms2_batch b, int k, int threads);
+
 static ms2_status batch_launch(ms2_batch b, int nsteps, bool trial = false) {
-    for (size_t k = 0; k < b->sys.size(); ++k) {
-        b->htab[k].step0 = b->sys[k]->step;
-        b->htab[k].rdf_every = (!trial && b->sys[k]->d.rdf) ? b->sys[k]->rdf_every : 0;
-        b->htab[k].S = b->sys[k]->d;
-    }
-    MS2_CUDA_OK(cudaMemcpyAsync(b->dtab, b->htab.data(), sizeof(BatchEntry) * b->htab.size(), cudaMemcpyHostToDevice,
-                                b->stream));
-    MS2_CUDA_OK(cudaMemsetAsync(b->dnext, 0, sizeof(unsigned) * K_COUNT, b->stream));
-    MS2_CUDA_OK(cudaEventRecord(b->ev_fork, b->stream));
     for (int k = 0; k < K_COUNT; ++k) {
         if (b->order[k].empty()) continue;
-        MS2_CUDA_OK(cudaStreamWaitEvent(b->ks[k], b->ev_fork, 0));
-        kBatchFn[k]<<<b->grid[k], b->threads[k], b->smem[k], b->ks[k]>>>(b->dtab, b->dorder[k], (int)b->order[k].size(),
-                                                                         b->dnext + k, nsteps);
+        std::vector<BatchEntry> &t = b->htab[k];
+        int cells = b->rdf_cells[k];
+        for (size_t e = 0; e < t.size(); ++e) {
+            ms2_system s = b->sys[b->order[k][e]];
+            // the system's current arrays (an RDF set up after the batch was made),
+            // with the batch's own decomposition
+            double *ublk = t[e].S.blk;
+            t[e].S = s->d;
+            t[e].S.jsplit = 1;
+            t[e].S.nunits = t[e].units;
+            t[e].S.blk = ublk;
+            t[e].step0 = s->step;
+            t[e].rdf_every = (!trial && s->d.rdf) ? s->rdf_every : 0;
+            if (s->d.rdf) cells = std::max(cells, s->d.rdf_rows * s->d.rdf_bins);
+        }
+        if (cells > b->rdf_cells[k]) {  // a larger histogram than the shape reserves
+            if (cells > RDF_SMEM_MAX) return ms2_fail(MS2_EINVAL, "RDF histogram too large for a batch");
+            b->rdf_cells[k] = cells;
+            ms2_status st = set_shape(b, k, b->threads[k]);
+            if (st != MS2_OK) st = set_shape(b, k, 256);
+            if (st != MS2_OK) return st;
+        }
+        MS2_CUDA_OK(cudaMemcpyAsync(b->dtab[k], t.data(), sizeof(BatchEntry) * t.size(), cudaMemcpyHostToDevice,
+                                    b->stream));
+        MS2_CUDA_OK(cudaMemsetAsync(b->dbar + 2 * k, 0, 2 * sizeof(unsigned), b->stream));
+        MsArgs A;
+        A.tab = b->dtab[k];
+        A.n_sys = (int)t.size();
+        A.drift = b->ddrift[k];
+        A.n_drift = b->n_drift[k];
+        A.seg = b->dseg[k];
+        A.seg_off = b->dsegoff[k];
+        A.unit = b->dunit[k];
+        A.n_unit = b->n_unit[k];
+        A.Np = b->Np[k];
+        A.nsteps = nsteps;
+        A.bar = b->dbar + 2 * k;
+        A.err = b->dbar + 2 * k + 1;
+        void *args[] = {(void *)&A};
+        MS2_CUDA_OK(cudaLaunchCooperativeKernel((const void *)kBatchFn[k], b->grid[k], b->threads[k], args, b->smem[k],
+                                                b->stream));
         ms2_count_launches(1);
-        MS2_CUDA_OK(cudaGetLastError());
-        MS2_CUDA_OK(cudaEventRecord(b->ev_join[k], b->ks[k]));
-        MS2_CUDA_OK(cudaStreamWaitEvent(b->stream, b->ev_join[k], 0));
     }
     if (trial) return MS2_OK;
     for (ms2_system s : b->sys) {
@@ -342,23 +317,55 @@ static ms2_status batch_launch(ms2_batch b, int nsteps, bool trial = false) {
     return MS2_OK;
 }
 
+// block shape of kind k and the pair segments of each block: the kind's items
+// (molecules, system by system) cut into grid ranges of equal estimated cost
 static ms2_status set_shape(ms2_batch b, int k, int threads) {
-    int maxN = 0, rdf = 0;
-    for (int idx : b->order[k]) {
-        maxN = std::max(maxN, b->sys[idx]->N);
-        rdf = std::max(rdf, b->sys[idx]->d.rdf ? b->sys[idx]->d.rdf_rows * b->sys[idx]->d.rdf_bins : 0);
-    }
     b->threads[k] = threads;
-    b->smem[k] = batch_smem(k, maxN, threads, rdf);
+    b->smem[k] = batch_smem(k, b->Np[k], threads, b->rdf_cells[k]);
     MS2_CUDA_OK(cudaFuncSetAttribute((const void *)kBatchFn[k], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)std::max<size_t>(b->smem[k], 48 * 1024)));
-    int per_sm = 0;
+    int per_sm = 0, sms = 0, dev = 0, coop = 0;
     MS2_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kBatchFn[k], threads, b->smem[k]));
-    if (per_sm < 1) return ms2_fail(MS2_EINVAL, "batch kind %s: %d threads do not fit one SM", kKindName[k], threads);
-    int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    b->grid[k] = std::min((int)b->order[k].size(), per_sm * sms);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (per_sm < 1 || !coop)
+        return ms2_fail(MS2_EINVAL, "batch kind %s: %d threads with %zu B of shared memory do not fit one SM",
+                        kKindName[k], threads, b->smem[k]);
+    const int G = per_sm * sms;
+    b->grid[k] = G;
+    double total = 0;
+    std::vector<double> cost;
+    for (int idx : b->order[k]) {
+        cost.push_back(item_cost(b->sys[idx]));
+        total += cost.back() * b->sys[idx]->N;
+    }
+    std::vector<int4> seg;
+    std::vector<int> off(G + 1, 0);
+    double acc = 0;
+    int blk = 0;
+    for (size_t e = 0; e < b->order[k].size(); ++e) {
+        const int N = b->sys[b->order[k][e]]->N;
+        int first = 0;
+        for (int i = 0; i < N; ++i) {
+            const double mid = acc + (i + 0.5) * cost[e];
+            const int bi = std::min(G - 1, (int)(mid * G / total));
+            if (bi != blk) {
+                if (i > first) seg.push_back(make_int4((int)e, first, i, 0));
+                for (int q = blk + 1; q <= bi; ++q) off[q] = (int)seg.size();
+                blk = bi;
+                first = i;
+            }
+        }
+        if (N > first) seg.push_back(make_int4((int)e, first, N, 0));
+        acc += cost[e] * N;
+    }
+    for (int q = blk + 1; q <= G; ++q) off[q] = (int)seg.size();
+    MS2_CUDA_OK(b->al.alloc((void **)&b->dseg[k], sizeof(int4) * std::max<size_t>(seg.size(), 1)));
+    MS2_CUDA_OK(b->al.alloc((void **)&b->dsegoff[k], sizeof(int) * (G + 1)));
+    MS2_CUDA_OK(cudaMemcpyAsync(b->dseg[k], seg.data(), sizeof(int4) * seg.size(), cudaMemcpyHostToDevice, b->stream));
+    MS2_CUDA_OK(cudaMemcpyAsync(b->dsegoff[k], off.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, b->stream));
+    MS2_CUDA_OK(cudaStreamSynchronize(b->stream));  // the host vectors go out of scope
     return MS2_OK;
 }
 
@@ -407,8 +414,10 @@ static ms2_status snapshot_state(ms2_batch b, std::vector<void *> &buf, bool sav
     return MS2_OK;
 }
 
-// Autotuner: per model kind, the block size (128 or 256 threads) that runs one
-// step of this batch fastest; results cached on disk by (kind, size bucket).
+// Autotuner: per model kind, the block shape (256 threads, two blocks per SM
+// where they fit, or 512 threads, one block per SM) that runs one step of this
+// batch fastest; results cached on disk by (kind, size bucket, count bucket).
+// The shape changes only the work split, never a system's results.
 static ms2_status tune(ms2_batch b) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     std::map<std::string, int> cache = load_tune();
@@ -424,7 +433,7 @@ static ms2_status tune(ms2_batch b) {
         int cnt = 1;
         while (cnt < (int)ns.size()) cnt <<= 1;
         std::ostringstream os;
-        os << "v1/" << kKindName[k] << "/N" << bucket << "/S" << cnt;
+        os << "v2/" << kKindName[k] << "/N" << bucket << "/S" << cnt;
         key[k] = os.str();
         auto it = cache.find(key[k]);
         if (it != cache.end() && set_shape(b, k, it->second) == MS2_OK) continue;
@@ -440,8 +449,8 @@ static ms2_status tune(ms2_batch b) {
     for (int k = 0; k < K_COUNT; ++k) {
         if (b->order[k].empty() || cache.count(key[k])) continue;
         float best = 1e30f;
-        int best_t = 256;
-        for (int t : {128, 256}) {
+        int best_t = MS_THREADS;
+        for (int t : {256, MS_THREADS}) {
             if (set_shape(b, k, t) != MS2_OK) continue;
             // only kind k runs in a trial
             std::vector<int> keep[K_COUNT];
@@ -483,7 +492,7 @@ bool ms2_batch_accepts(ms2_system s) {
     if (kind < 0) return false;
     const int rdf = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
     if (rdf > RDF_SMEM_MAX) return false;
-    return batch_smem(kind, s->N, 128, rdf) <= 227 * 1024;
+    return batch_smem(kind, (s->N + 3) & ~3, 256, rdf) <= 227 * 1024;
 }
 
 extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_batch *out) {
@@ -505,50 +514,56 @@ extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_bat
         if (kind < 0) { delete b; return ms2_fail(MS2_EINVAL, "system %d: more than 4 site slots", k); }
         const int rdf = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
         if (rdf > RDF_SMEM_MAX) { delete b; return ms2_fail(MS2_EINVAL, "system %d: RDF histogram too large for a batch", k); }
-        if (batch_smem(kind, s->N, 128, rdf) > 227 * 1024) {
+        if (batch_smem(kind, (s->N + 3) & ~3, 256, rdf) > 227 * 1024) {
             delete b;
             return ms2_fail(MS2_EINVAL, "system %d: %d molecules do not fit one block's shared memory", k, s->N);
         }
         b->sys.push_back(s);
         b->order[kind].push_back(k);
     }
-    // longest first: cost ~ N^2 (all pairs are tested; partners ~ N * const)
-    for (int k = 0; k < K_COUNT; ++k)
-        std::stable_sort(b->order[k].begin(), b->order[k].end(),
-                         [&](int x, int y) { return b->sys[x]->N > b->sys[y]->N; });
-    b->htab.resize(n);
     ms2_status st = MS2_OK;
     auto fail = [&](ms2_status s2) { ms2_batch_destroy(b); return s2; };
     {
         cudaError_t e0 = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
         if (e0 != cudaSuccess) return fail(ms2_fail_cuda(e0, "batch stream", __FILE__, __LINE__));
     }
-    for (int k = 0; k < n; ++k) {
-        ms2_system s = b->sys[k];
-        BatchEntry &e = b->htab[k];
-        e.P = s->dP;
-        e.S = s->d;
-        e.TJ = s->N;
-        e.rdf_every = 0;
-        e.step0 = s->step;
-        cudaError_t ce = b->al.alloc((void **)&e.chunk, sizeof(double) * Q_N * ((s->N + 31) / 32));
-        if (ce != cudaSuccess) return fail(ms2_fail_cuda(ce, "batch scratch", __FILE__, __LINE__));
-    }
-    cudaError_t ce = b->al.alloc((void **)&b->dtab, sizeof(BatchEntry) * n);
-    if (ce == cudaSuccess) ce = b->al.alloc((void **)&b->dnext, sizeof(unsigned) * K_COUNT);
+    cudaError_t ce = b->al.alloc((void **)&b->dbar, sizeof(unsigned) * 2 * K_COUNT);
     for (int k = 0; k < K_COUNT && ce == cudaSuccess; ++k) {
         if (b->order[k].empty()) continue;
-        ce = b->al.alloc((void **)&b->dorder[k], sizeof(int) * b->order[k].size());
+        std::vector<int2> drift, unit;
+        for (size_t e = 0; e < b->order[k].size() && ce == cudaSuccess; ++e) {
+            ms2_system s = b->sys[b->order[k][e]];
+            const int N = s->N;
+            BatchEntry en;
+            memset(&en, 0, sizeof en);
+            en.P = s->dP;
+            en.S = s->d;
+            en.S.jsplit = 1;
+            en.units = (N + UNIT - 1) / UNIT;
+            en.S.nunits = en.units;
+            ce = b->al.alloc((void **)&en.S.blk, sizeof(double) * MS2_NRED * en.units);
+            en.step0 = s->step;
+            b->htab[k].push_back(en);
+            for (int m = 0; m < N; m += 8) drift.push_back(make_int2((int)e, m));
+            for (int u = 0; u < en.units; ++u) unit.push_back(make_int2((int)e, u));
+            b->Np[k] = std::max(b->Np[k], (N + 3) & ~3);
+            b->rdf_cells[k] = std::max(b->rdf_cells[k], s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0);
+        }
+        if (ce == cudaSuccess) ce = b->al.alloc((void **)&b->dtab[k], sizeof(BatchEntry) * b->htab[k].size());
+        if (ce == cudaSuccess) ce = b->al.alloc((void **)&b->ddrift[k], sizeof(int2) * drift.size());
+        if (ce == cudaSuccess) ce = b->al.alloc((void **)&b->dunit[k], sizeof(int2) * unit.size());
         if (ce == cudaSuccess)
-            ce = cudaMemcpyAsync(b->dorder[k], b->order[k].data(), sizeof(int) * b->order[k].size(),
-                                 cudaMemcpyHostToDevice, b->stream);
-        if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&b->ks[k], cudaStreamNonBlocking);
-        if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
+            ce = cudaMemcpyAsync(b->ddrift[k], drift.data(), sizeof(int2) * drift.size(), cudaMemcpyHostToDevice, b->stream);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(b->dunit[k], unit.data(), sizeof(int2) * unit.size(), cudaMemcpyHostToDevice, b->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);  // the host vectors go out of scope
+        b->n_drift[k] = (int)drift.size();
+        b->n_unit[k] = (int)unit.size();
     }
-    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
     if (ce != cudaSuccess) return fail(ms2_fail_cuda(ce, "batch set-up", __FILE__, __LINE__));
     for (int k = 0; k < K_COUNT; ++k)
-        if (!b->order[k].empty() && (st = set_shape(b, k, 256)) != MS2_OK) return fail(st);
+        if (!b->order[k].empty() && set_shape(b, k, MS_THREADS) != MS2_OK && (st = set_shape(b, k, 256)) != MS2_OK)
+            return fail(st);
     // the systems' own queued work comes first
     for (ms2_system s : b->sys)
         if (s->stream != b->stream) {
@@ -585,11 +600,6 @@ extern "C" ms2_status ms2_batch_step(ms2_batch b, long long n) {
 extern "C" ms2_status ms2_batch_destroy(ms2_batch b) {
     if (!b) return MS2_OK;
     if (b->stream) cudaStreamSynchronize(b->stream);
-    for (int k = 0; k < K_COUNT; ++k) {
-        if (b->ks[k]) cudaStreamDestroy(b->ks[k]);
-        if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
-    }
-    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     b->al.release_all();
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;

@@ -35,97 +35,29 @@
 // reports MS2_ETIMEOUT at its next read.
 #include "ms2_internal.cuh"
 
+#include "grid_dev.cuh"
 #include "integrate_dev.cuh"
 #include "pair_engine.cuh"
 
 using namespace pair_engine;
 using namespace integ;
+using grid_dev::global_ns;
 
 namespace {
 
 constexpr int STEP_THREADS = 512;
 constexpr int STEP_WARPS = STEP_THREADS / 32;
-constexpr unsigned long long WAIT_NS = 2000000000ull;
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void red_release_u32(unsigned *p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// monotone-counter grid barrier: the k-th barrier of a launch waits for
-// count >= k * gridDim.x.  Ordering: the block's writes happen before thread 0's
-// arrival (bar.sync), which is a gpu-scope release; thread 0's polling load is a
-// gpu-scope acquire, and the closing bar.sync orders the block's later reads
-// after it (release/acquire are cumulative in the PTX memory model).
-__device__ __forceinline__ void grid_sync(unsigned *count, unsigned *err, unsigned &target, double *scal) {
-    __syncthreads();
-    target += gridDim.x;
-    if (threadIdx.x == 0) {
-        red_release_u32(count, 1u);
-        const unsigned long long t0 = global_ns();
-        while (ld_acquire_u32(count) < target) {
-            if (ld_acquire_u32(err) != 0u) break;  // another block gave up
-            if (global_ns() - t0 > WAIT_NS) {
-                atomicExch(err, 1u);
-                scal[SC_KERR] = 1.0;
-                break;
-            }
-        }
-    }
-    __syncthreads();
-}
-
 // site-site RDF of the staged configuration (the k_rdf arithmetic, reading
 // the shared-memory tile): molecules i = block, block + grid, ...; threads over j > i
 template <int NS, bool MULTI>
 __device__ void rdf_tile(const SysParams *__restrict__ P, const DevSys &S, const Smem &sm, int TJ, unsigned *hist) {
-    const int N = S.N, nb = S.rdf_bins, rows = S.rdf_rows, T = P->n_ljt;
-    for (int k = threadIdx.x; k < rows * nb; k += blockDim.x) hist[k] = 0u;
+    const int N = S.N, cells = S.rdf_rows * S.rdf_bins;
+    for (int k = threadIdx.x; k < cells; k += blockDim.x) hist[k] = 0u;
     __syncthreads();
-    const float l2l = P->lat_to_len, l2 = P->len_to_lat;
-    const float rmax2 = S.rdf_rmax2, inv_dr = S.rdf_inv_dr;
-    const uint32_t *tx[3] = {sm.tX, sm.tY, sm.tZ};
-    for (int i = blockIdx.x; i < N; i += gridDim.x) {
-        const int spi = MULTI ? sm.tsp[i] : 0;
-        for (int a = 0; a < NS; ++a) {
-            const int ta = S.rdf_kind[spi * MS2_MAXS + a];
-            if (ta < 0) continue;
-            uint32_t Xa[3];
-            for (int c = 0; c < 3; ++c) Xa[c] = tx[c][i] + (uint32_t)__float2int_rn(sm.ts[(c * NS + a) * TJ + i] * l2);
-            for (int j = i + 1 + threadIdx.x; j < N; j += blockDim.x) {
-                const int spj = MULTI ? sm.tsp[j] : 0;
-                for (int b = 0; b < NS; ++b) {
-                    const int tb = S.rdf_kind[spj * MS2_MAXS + b];
-                    if (tb < 0) continue;
-                    float r2 = 0.f;
-                    for (int c = 0; c < 3; ++c) {
-                        const uint32_t Xb = tx[c][j] + (uint32_t)__float2int_rn(sm.ts[(c * NS + b) * TJ + j] * l2);
-                        const float d = (float)(int)(Xb - Xa[c]) * l2l;
-                        r2 += d * d;
-                    }
-                    if (!(r2 < rmax2)) continue;
-                    const int bin = (int)(sqrtf(r2) * inv_dr);
-                    if (bin >= nb) continue;
-                    const int t1 = min(ta, tb), t2 = max(ta, tb);
-                    const int row = t1 * T - t1 * (t1 - 1) / 2 + (t2 - t1);
-                    atomicAdd(&hist[row * nb + bin], 1u);
-                }
-            }
-        }
-    }
+    for (int i = blockIdx.x; i < N; i += gridDim.x)
+        rdf_molecule<NS, MULTI>(P, S, sm, TJ, i, i + 1 + threadIdx.x, blockDim.x, N, hist);
     __syncthreads();
-    for (int k = threadIdx.x; k < rows * nb; k += blockDim.x)
+    for (int k = threadIdx.x; k < cells; k += blockDim.x)
         if (hist[k]) atomicAdd(&S.rdf[k], (unsigned long long)hist[k]);
 }
 
@@ -221,6 +153,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     e.setup(P);
     if (b == 0 && threadIdx.x == 0) *A.bar_next = 0u;
     unsigned target = 0;
+    auto on_timeout = [&]() { S.scal[SC_KERR] = 1.0; };
+    using grid_dev::grid_sync;
     const bool rfq = Eng::MOLD && e.rfq;
     const bool rec = A.timing && b == 0 && threadIdx.x == 0;
     // timing of the last step: every block marks the end of its compute phases
@@ -242,7 +176,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
                 drift_quad<true>(Ps, S, view(), m, lo + m, m < nm, lane & 3, false, lam_s);
             }
         mark(k, 0);
-        grid_sync(A.bar, A.err, target, S.scal);
+        grid_sync(A.bar, A.err, target, on_timeout);
         if (tm) tph[1] = global_ns();
         // ---- stage the whole system; pair items of the own molecules; RDF
         stage_tile<NS, Eng::DMU, MULTI>(sm, S, 0, N, A.Np, rfq);
@@ -288,7 +222,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
             reduce_unit<true>(Ps, S, io, RED_SUM | RED_LAMBDA | (gk_step(A, k) ? RED_GK : 0), b, G, lane);
         }
         mark(k, 2);
-        grid_sync(A.bar, A.err, target, S.scal);
+        grid_sync(A.bar, A.err, target, on_timeout);
         if (tm) tph[3] = global_ns();
         // ---- totals in every block; thermostat factor for the next drift
         reduce_totals(S, G, tot, gk_step(A, k) ? Q_N + 3 : Q_N);
@@ -346,7 +280,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         if (gk) gk_update(S, tot, lane);
     }
     if (HEAT && A.nsteps > 0 && hf_step(A, A.nsteps - 1)) {  // uniform over the grid
-        grid_sync(A.bar, A.err, target, S.scal);
+        grid_sync(A.bar, A.err, target, on_timeout);
         if (b == 0 && warp == 0) heat_record(S, G, lane);
     }
     __syncthreads();

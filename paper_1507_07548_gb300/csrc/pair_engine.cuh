@@ -110,6 +110,45 @@ __device__ __forceinline__ Smem shifted(const Smem &m, int t0) {
     return v;
 }
 
+// Site-site RDF counts (Sec. 3, Eq. 2) of tile molecule i against tile molecules
+// j = j0, j0 + jstep, ... < n (the caller picks j > i so that every pair counts
+// once): LJ-site kinds, site positions on the integer lattice (site minimum
+// image), bins of width 1/inv_dr below r_max; integer shared-memory atomics.
+template <int NS, bool MULTI>
+__device__ __forceinline__ void rdf_molecule(const SysParams *__restrict__ P, const DevSys &S, const Smem &sm, int TJ,
+                                             int i, int j0, int jstep, int n, unsigned *hist) {
+    const int nb = S.rdf_bins, T = P->n_ljt;
+    const float l2l = P->lat_to_len, l2 = P->len_to_lat;
+    const float rmax2 = S.rdf_rmax2, inv_dr = S.rdf_inv_dr;
+    const uint32_t *tx[3] = {sm.tX, sm.tY, sm.tZ};
+    const int spi = MULTI ? sm.tsp[i] : 0;
+    for (int a = 0; a < NS; ++a) {
+        const int ta = S.rdf_kind[spi * MS2_MAXS + a];
+        if (ta < 0) continue;
+        uint32_t Xa[3];
+        for (int c = 0; c < 3; ++c) Xa[c] = tx[c][i] + (uint32_t)__float2int_rn(sm.ts[(c * NS + a) * TJ + i] * l2);
+        for (int j = j0; j < n; j += jstep) {
+            const int spj = MULTI ? sm.tsp[j] : 0;
+            for (int b = 0; b < NS; ++b) {
+                const int tb = S.rdf_kind[spj * MS2_MAXS + b];
+                if (tb < 0) continue;
+                float r2 = 0.f;
+                for (int c = 0; c < 3; ++c) {
+                    const uint32_t Xb = tx[c][j] + (uint32_t)__float2int_rn(sm.ts[(c * NS + b) * TJ + j] * l2);
+                    const float d = (float)(int)(Xb - Xa[c]) * l2l;
+                    r2 += d * d;
+                }
+                if (!(r2 < rmax2)) continue;
+                const int bin = (int)(sqrtf(r2) * inv_dr);
+                if (bin >= nb) continue;
+                const int t1 = min(ta, tb), t2 = max(ta, tb);
+                const int row = t1 * T - t1 * (t1 - 1) / 2 + (t2 - t1);
+                atomicAdd(&hist[row * nb + bin], 1u);
+            }
+        }
+    }
+}
+
 // result of one molecule (valid in lane 0): F, tau, U_lj, U_qq, U_dd, W,
 // the second-volume-derivative sum vv (MASS) and the partner count
 struct PairOut {
