@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--impl", default="ms2", choices=["ms2", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle CPU-baseline sample length")
     ap.add_argument("--no-extra", action="store_true", help="skip the Ewald sub-benchmark")
+    ap.add_argument("--uniform-batch", type=int, default=0, metavar="S",
+                    help="only time one batch of S copies of the water workload (single steps; the ncu case "
+                         "of the multi-system step kernel)")
     a = ap.parse_args()
     a.warmup = max(a.warmup, 3)
     return a
@@ -178,7 +181,8 @@ def reference_arm(args, rank, world):
 # ---------------------------------------------------------------- GPU arm
 # kernel sources a stored DRAM-traffic figure describes (it is void once they change)
 TRAFFIC_SOURCES = {"pair_water_rf": ("k_pair.cu", "pair_engine.cuh", "ms2_internal.cuh"),
-                   "step_water_rf": ("k_step.cu", "pair_engine.cuh", "integrate_dev.cuh", "ms2_internal.cuh")}
+                   "step_water_rf": ("k_step.cu", "pair_engine.cuh", "integrate_dev.cuh", "grid_dev.cuh",
+                                     "ms2_internal.cuh")}
 
 
 def traffic_record(kernel):
@@ -336,7 +340,7 @@ def batch_sub(args, flush):
     """The same work -- BATCH_SYSTEMS independent systems of the LJ / Stockmayer /
     water mix, BATCH_STEPS steps each -- run one system at a time on one stream
     (each on its best single-system path: the fused step kernel) and as one
-    persistent batch (one block per system per chunk).  Host wall time between
+    batch (one cooperative multi-system step kernel per model kind).  Host wall time between
     device synchronisations (each run is far longer than a launch), L2 flushed
     before each run."""
     import torch
@@ -380,7 +384,7 @@ def batch_sub(args, flush):
             "unit": "molecule-steps/s",
             "plain": {"value": work / t_plain, "seconds": t_plain, "path": "one system at a time, %d of %d fused"
                       % (fused, len(plain))},
-            "batched": {"value": work / t_batch, "seconds": t_batch, "path": "persistent batch kernels"},
+            "batched": {"value": work / t_batch, "seconds": t_batch, "path": "multi-system step kernels (one per model kind)"},
             "speedup": t_plain / t_batch}
 
 
@@ -533,8 +537,38 @@ def ewald_sub(args, stream):
                              "note": "short run: sigma illustrates the output, it is not converged"}}
 
 
+def uniform_batch(args):
+    """S copies of the headline water system in one batch: `warmup` then `steps`
+    single-step batch launches, CUDA events around each, L2 flushed between."""
+    import torch
+    import paper_1507_07548_gb300.ms2 as ms2
+    from paper_1507_07548_gb300 import workloads as W
+    wl = W.water_box(N=N_WATER, rc=RC, seed=SEED)
+    ss = [ms2.System.from_workload(wl) for _ in range(args.uniform_batch)]
+    b = ms2.Batch(ss)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    t = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.step(1)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            t.append(time.perf_counter() - t0)
+    pairs = sum(s.energy_terms()["n_pairs"] for s in ss)
+    ms = 1e3 * statistics.mean(t)
+    print(json.dumps({"workload": "%d x rigid 3-site water N=%d, reaction field, rc=%g A, one batch" % (
+        len(ss), N_WATER, RC), "ms_per_step": ms, "pair_interactions_per_s": pairs / (ms * 1e-3),
+        "molecule_steps_per_s": len(ss) * N_WATER / (ms * 1e-3), "steps": args.steps}), flush=True)
+    b.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.uniform_batch > 0:
+        return uniform_batch(args)
     rank, world, local_rank = dist_env()
     if world > 1:
         import torch.distributed as tdist

@@ -202,12 +202,18 @@ MS2_API ms2_status ms2_averages(ms2_system sys, double out[5], long long *n_step
 MS2_API ms2_status ms2_reset_averages(ms2_system sys);
 
 /* ----------------------------------------------------------------- batch */
-/* A batch advances many independent systems in ONE persistent kernel per
- * chunk of steps: each thread block owns one system for the whole chunk
- * (partner search, forces, integration, thermostat) and takes the next system
- * from a longest-first work list when it finishes.  The systems must be
- * reaction-field or non-electrostatic leapfrog systems with at most 4096
- * molecules; tile shapes come from the autotuner cache.  The systems stay
+/* A batch advances many independent systems together: per chunk of steps, one
+ * cooperative persistent kernel per model kind (slot pattern) runs every phase
+ * of a step (drift and site build, partner search and site-pair forces, RDF
+ * samples, reduction, thermostat, record) over all of the kind's systems at
+ * once, spread over the whole GPU at molecule granularity, with a bounded grid
+ * barrier between phases.  A system's results depend only on the system (bit
+ * for bit the same alone or in any batch).  The systems must be
+ * reaction-field or non-electrostatic leapfrog systems whose whole
+ * configuration fits one block's shared memory (about 3700 three-site
+ * molecules); the block shape comes from the autotuner cache.  A barrier wait
+ * that runs out (2 s) marks every system of the kind so that its next
+ * ms2_energy_virial returns MS2_ETIMEOUT.  The systems stay
  * usable on their own: the batch runs on a stream of its own, waits for work
  * already queued on the systems' streams and makes their later work wait for
  * it.  Destroy a batch before any of its systems. */
@@ -246,7 +252,7 @@ typedef struct {
  * device memory; a scheduler thread admits eligible jobs in arrival order as
  * budget and slots free up, advances all resident jobs together chunk by chunk
  * (continuous batching), and retires finished ones.  max_slots <= 1024.  A job's
- * path is fixed at admission: with 64 or more jobs resident, jobs the batch
+ * path is fixed at admission: with 8 or more jobs resident, jobs the batch
  * kernels take join the batch; otherwise a job steps with its own
  * single-system kernels.  All the server's systems share one stream.  Results
  * are reproducible for a given arrival sequence; the two paths agree within the

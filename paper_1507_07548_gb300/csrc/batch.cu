@@ -8,7 +8,7 @@
 //              block; a block stages each system of its range in shared memory
 //              and its warps take that system's items (owner warp per molecule,
 //              the whole system as one j-range); RDF samples on the same tile
-//   reduction  units of ~32 molecules, round-robin over all warps
+//   reduction  units of 8 molecules, round-robin over all warps
 //   totals     one warp per system: fixed-order unit totals, the step record and
 //              the thermostat factor of the next drift
 // So work is balanced over the whole GPU at molecule granularity whatever the
@@ -48,7 +48,7 @@ enum Kind { K_LJ1 = 0, K_W3RF, K_ST3RF, K_G4, K_G4D, K_COUNT };
 const char *kKindName[K_COUNT] = {"lj1", "water3_rf", "stockmayer3_rf", "generic4", "generic4_dipole"};
 
 constexpr int MS_THREADS = 512;   // largest block shape (the autotuner may take 256)
-constexpr int UNIT = 32;          // molecules per reduction unit
+constexpr int UNIT = 8;           // molecules per reduction unit (one quad pass of a warp)
 constexpr int RDF_SMEM_MAX = 4096;  // histogram cells staged in shared memory
 
 struct BatchEntry {
@@ -149,13 +149,16 @@ __global__ void __launch_bounds__(MS_THREADS, 1) k_mstep(MsArgs A) {
             reduce_unit<false>(en.P, en.S, global_io(en.S), RED_SUM | RED_LAMBDA, u.y, en.units, lane);
         }
         grid_sync(A.bar, A.err, target, on_timeout);
-        // ---- per system: totals in unit order, the record, the next thermostat factor
+        // ---- per system: totals (lane l sums units l, l + 32, ... in order, then
+        // one fixed 8-value tree), the record, the next thermostat factor
         for (int s = gw; s < A.n_sys; s += W) {
             const BatchEntry &en = A.tab[s];
-            for (int q = 0; q < Q_N; ++q) {
-                const double x = unit_total(en.S, en.units, q, lane);
-                if (lane == 0) wtot[warp][q] = x;
-            }
+            double x[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int u = lane; u < en.units; u += 32)
+#pragma unroll
+                for (int q = 0; q < Q_N; ++q) x[q] += __ldcg(en.S.blk + (size_t)u * MS2_NRED + q);
+            const double t = warp_sum8(x, lane);
+            if ((lane & 3) == 0 && (lane >> 2) < Q_N) wtot[warp][lane >> 2] = t;
             __syncwarp();
             if (lane == 0) finish_step(en.P, en.S, RED_SUM | RED_RECORD | RED_LAMBDA, wtot[warp]);
             __syncwarp();

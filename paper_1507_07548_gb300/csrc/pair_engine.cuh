@@ -337,7 +337,10 @@ struct PairWarp {
             float rinv = rsqrtf(r2);
             rinv = fmaf(rinv, fmaf(-0.5f * r2 * rinv, rinv, 0.5f), rinv);
             const float rinv2 = rinv * rinv;
-            float g = 0.f, hh = 0.f;  // u'/r and (u'' - u'/r)/r^2 (MASS)
+            // g = u'/r of the site pair; gv the part of it whose virial -gv r^2 is
+            // summed here (bare reaction-field Coulomb has -g r^2 = its energy term,
+            // summed as U_qq); hh = (u'' - u'/r)/r^2 (MASS)
+            float g = 0.f, gv = 0.f, hh = 0.f;
             if (mlj) {
                 float c6, c12, c6l, c12l;
                 if (MULTI) {
@@ -358,6 +361,7 @@ struct PairWarp {
                 const float t6 = fmaf(c6, r6, c6l * r6), t12 = fmaf(c12, r12, c12l * r12);
                 ulj += t12 - t6;
                 g += (6.f * t6 - 12.f * t12) * rinv2;
+                gv = g;
                 if (MASS) hh += (168.f * t12 - 48.f * t6) * (rinv2 * rinv2);
             }
             if (mq && elec != ELEC_NONE) {
@@ -370,18 +374,19 @@ struct PairWarp {
                     cqq = hq[a][b];
                     cql = hql[a][b];
                 }
-                float bu, bg;  // energy and force brackets
-                if (elec == ELEC_RF) {  // bare Coulomb; the RF part is a molecular term
-                    bu = rinv;
-                    bg = -rinv * rinv2;
+                float gq;
+                if (elec == ELEC_RF) {  // bare Coulomb (the RF part is a molecular term): g = -E / r^2
+                    const float eq = fmaf(cqq, rinv, cql * rinv);
+                    uqq += eq;
+                    gq = -eq * rinv2;
                 } else {
                     const float ar = alpha * r2 * rinv;
                     const float ec = erfcf(ar), ex = expf(-ar * ar);
-                    bu = ec * rinv;
-                    bg = -(ec * rinv + tasp * ex) * rinv2;
+                    const float bu = ec * rinv, bg = -(ec * rinv + tasp * ex) * rinv2;
+                    uqq += fmaf(cqq, bu, cql * bu);
+                    gq = fmaf(cqq, bg, cql * bg);
+                    gv += gq;
                 }
-                uqq += fmaf(cqq, bu, cql * bu);
-                const float gq = fmaf(cqq, bg, cql * bg);
                 g += gq;
                 if (MASS) hh -= 3.f * gq * rinv2;  // bare Coulomb: h = 3 C q q / r^5
             }
@@ -410,7 +415,7 @@ struct PairWarp {
                 }
             }
             fa[a][0] = fmaf(g, rx, fa[a][0]); fa[a][1] = fmaf(g, ry, fa[a][1]); fa[a][2] = fmaf(g, rz, fa[a][2]);
-            wsite = fmaf(-g, r2, wsite);
+            if (mlj || (mq && elec == ELEC_EWALD)) wsite = fmaf(-gv, r2, wsite);
             if (HP) pw = fmaf(g, rx * vs[a][0] + ry * vs[a][1] + rz * vs[a][2], pw);
             if (MASS) {
                 const float rd = rx * dx + ry * dy + rz * dz;
@@ -486,6 +491,7 @@ struct PairWarp {
         o.uqq = warp_sum(uqq);
         o.udd = warp_sum(udd);
         o.w = warp_sum(w);
+        if (elec == ELEC_RF) o.w += o.uqq;  // the bare-Coulomb site virials (before the molecular RF term)
         o.vv = MASS ? warp_sum(vv) : 0.f;
         o.np = warp_sum(np);
         o.F[0] = o.F[1] = o.F[2] = o.T[0] = o.T[1] = o.T[2] = 0.f;

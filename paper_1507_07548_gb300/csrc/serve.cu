@@ -9,8 +9,9 @@
 // Jobs that arrive while others run are admitted at the next chunk boundary
 // (continuous batching).  A job's path is fixed at admission: while at least
 // BATCH_MIN_RESIDENT jobs are resident, a job the batch kernels take goes into
-// the batch (one block per system, efficient once the systems outnumber the
-// SMs); otherwise it steps with its own single-system kernels (the fused step
+// the batch (the multi-system step kernels, ahead of stepping the systems one
+// by one from about 4 systems on); otherwise it steps with its own
+// single-system kernels (the fused step
 // where the system allows, each chunk on the whole GPU).  All systems of a
 // server share one stream, so cooperative fused launches never overlap each
 // other or the batch.  Results are reproducible for a given arrival sequence;
@@ -30,7 +31,7 @@ bool ms2_batch_accepts(ms2_system s);  // batch.cu
 
 namespace {
 
-constexpr int BATCH_MIN_RESIDENT = 64;  // resident jobs from which new jobs join the batch
+constexpr int BATCH_MIN_RESIDENT = 8;  // resident jobs from which new jobs join the batch
 
 struct JobSpec {
     long long id = 0;

@@ -403,7 +403,7 @@ class System:
 
 
 class Batch:
-    """Many systems advanced together by the persistent batch kernels."""
+    """Many systems advanced together by the multi-system step kernels (ms2_batch_*)."""
 
     def __init__(self, systems):
         self.systems = list(systems)

@@ -1,4 +1,4 @@
-"""Batched systems (ms2_batch_*): one block per system for a whole chunk of steps.
+"""Batched systems (ms2_batch_*): one cooperative kernel per model kind steps all systems.
 
 Checks: one batched step against the FP64 oracle (same tolerances as the
 single-system path), bit-identical results for a system alone and inside a
