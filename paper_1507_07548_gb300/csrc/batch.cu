@@ -581,6 +581,8 @@ extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_bat
 extern "C" ms2_status ms2_batch_step(ms2_batch b, long long n) {
     if (!b) return ms2_fail(MS2_EINVAL, "null batch");
     if (n < 0) return ms2_fail(MS2_EINVAL, "negative step count");
+    for (ms2_system s : b->sys)  // forces of a state set since the last step
+        if (ms2_status e = ms2_ensure_forces(s)) return e;
     for (ms2_system s : b->sys)
         if (s->stream != b->stream) cudaStreamSynchronize(s->stream);
     long long done = 0;

@@ -737,15 +737,21 @@ static void initial_state(ms2_system s, const ms2_model *models, double T, unsig
 }
 
 static ms2_status ensure_pinned(ms2_system s) {
-    if (!s->pinned) MS2_CUDA_OK(cudaMallocHost((void **)&s->pinned, sizeof(double) * 13 * s->N));
+    if (!s->pinned) MS2_CUDA_OK(cudaMallocHost((void **)&s->pinned, sizeof(double) * 30 * s->N));
+    for (int k = 0; k < 2; ++k)
+        if (!s->up_ev[k]) MS2_CUDA_OK(cudaEventCreateWithFlags(&s->up_ev[k], cudaEventDisableTiming));
     return MS2_OK;
 }
 
+// host state -> device, through the upload buffer whose previous copy has ended;
+// returns without waiting for this copy
 static ms2_status upload_state(ms2_system s) {
     const int N = s->N;
     ms2_status st = ensure_pinned(s);
     if (st != MS2_OK) return st;
-    double *buf = s->pinned;
+    const int k = s->up_k;
+    MS2_CUDA_OK(cudaEventSynchronize(s->up_ev[k]));
+    double *buf = s->pinned + (size_t)13 * N * k;
     size_t off = 0;
     auto put = [&](double *dst, const std::vector<double> &src, int nc) -> cudaError_t {
         double *b = buf + off;
@@ -758,8 +764,17 @@ static ms2_status upload_state(ms2_system s) {
     MS2_CUDA_OK(put(s->d.q, s->hq, 4));
     MS2_CUDA_OK(put(s->d.v, s->hv, 3));
     MS2_CUDA_OK(put(s->d.Lm, s->hL, 3));
-    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));  // the pinned buffer is reused
+    MS2_CUDA_OK(cudaEventRecord(s->up_ev[k], s->stream));
+    s->up_k = 1 - k;
     return MS2_OK;
+}
+
+// forces, energies and site build of the current state (after ms2_set_state)
+ms2_status ms2_ensure_forces(ms2_system s) {
+    if (!s->stale) return MS2_OK;
+    ms2_status st = ms2_eval_forces(s);
+    if (st == MS2_OK) s->stale = false;
+    return st;
 }
 
 static ms2_status setup_ewald(ms2_system s, double alpha, int kx, int ky, int kz) {
@@ -974,6 +989,8 @@ extern "C" ms2_status ms2_destroy_system(ms2_system s) {
     for (int k = 0; k < 5; ++k)
         if (s->ev[k]) cudaEventDestroy(s->ev[k]);
     if (s->pinned) cudaFreeHost(s->pinned);
+    for (int k = 0; k < 2; ++k)
+        if (s->up_ev[k]) cudaEventDestroy(s->up_ev[k]);
     s->al.release_all();
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
@@ -1012,6 +1029,7 @@ static bool run_fused(ms2_system s, long long m, long long s0) {
     A.bar_next = cnt + 16 + 16 * (1 - s->bar_parity);
     A.err = cnt + 48;
     A.timing = s->timing ? 1 : 0;
+    A.init = s->stale ? 1 : 0;
     A.tmax = (unsigned long long *)(cnt + 56);  // 3 x 8 bytes at byte 224 of the counter block (zero at entry)
     if (s->timing) cudaEventRecord(s->ev[0], s->stream);
     const cudaError_t e = ms2_launch_step(fn, s->step_grid, smem, s->stream, s->dP, s->d, A);
@@ -1022,6 +1040,7 @@ static bool run_fused(ms2_system s, long long m, long long s0) {
     }
     if (s->timing) cudaEventRecord(s->ev[4], s->stream);
     s->bar_parity ^= 1;
+    s->stale = false;
     s->last_launch_steps = (int)m;
     s->last_fused = true;
     ms2_count_launches(1);
@@ -1036,7 +1055,8 @@ extern "C" ms2_status ms2_step(ms2_system s, long long n) {
     while (done < n) {
         const long long m = std::min(chunk, n - done);
         if (!run_fused(s, m, s->step + done)) {
-            ms2_status st = run_graph(s, m, s->step + done);
+            ms2_status st = ms2_ensure_forces(s);
+            if (st == MS2_OK) st = run_graph(s, m, s->step + done);
             if (st != MS2_OK) return st;
             s->last_fused = false;
         }
@@ -1054,6 +1074,7 @@ extern "C" ms2_status ms2_step(ms2_system s, long long n) {
 
 extern "C" ms2_status ms2_energy_virial(ms2_system s, double *U, double *W, double *T_inst, double *P) {
     if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (ms2_status e = ms2_ensure_forces(s)) return e;
     double sc[SC_COUNT_];
     ms2_status st = read_scalars(s, sc);
     if (st != MS2_OK) return st;
@@ -1075,6 +1096,7 @@ extern "C" ms2_status ms2_energy_virial(ms2_system s, double *U, double *W, doub
 
 extern "C" ms2_status ms2_energy_terms(ms2_system s, double terms[16]) {
     if (!s || !terms) return ms2_fail(MS2_EINVAL, "null argument");
+    if (ms2_status e = ms2_ensure_forces(s)) return e;
     double sc[SC_COUNT_];
     ms2_status st = read_scalars(s, sc);
     if (st != MS2_OK) return st;
@@ -1124,7 +1146,7 @@ static ms2_status get_soa(ms2_system s, const double *src, int nc, double *dst) 
     const int N = s->N;
     ms2_status st = ensure_pinned(s);
     if (st != MS2_OK) return st;
-    double *buf = s->pinned;
+    double *buf = s->pinned + (size_t)26 * N;  // the download buffer
     MS2_CUDA_OK(cudaMemcpyAsync(buf, src, sizeof(double) * nc * N, cudaMemcpyDeviceToHost, s->stream));
     MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
     for (int i = 0; i < N; ++i)
@@ -1134,7 +1156,7 @@ static ms2_status get_soa(ms2_system s, const double *src, int nc, double *dst) 
 
 extern "C" ms2_status ms2_forces_torques(ms2_system s, double *F, double *tau) {
     if (!s) return ms2_fail(MS2_EINVAL, "null system");
-    ms2_status st = MS2_OK;
+    ms2_status st = ms2_ensure_forces(s);
     if (F) st = get_soa(s, s->d.F, 3, F);
     if (st == MS2_OK && tau) st = get_soa(s, s->d.tau, 3, tau);
     return st;
@@ -1148,6 +1170,7 @@ __global__ void k_aos3(const double *src, double *dst, int N) {
 
 extern "C" ms2_status ms2_forces_torques_dev(ms2_system s, double *F_dev, double *tau_dev) {
     if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (ms2_status e = ms2_ensure_forces(s)) return e;
     if (F_dev) k_aos3<<<(s->N + 127) / 128, 128, 0, s->stream>>>(s->d.F, F_dev, s->N);
     if (tau_dev) k_aos3<<<(s->N + 127) / 128, 128, 0, s->stream>>>(s->d.tau, tau_dev, s->N);
     ms2_count_launches((F_dev ? 1 : 0) + (tau_dev ? 1 : 0));
@@ -1165,6 +1188,7 @@ extern "C" ms2_status ms2_ewald_params(ms2_system s, double alpha, int kx, int k
     ms2_status st = setup_ewald(s, alpha, kx, ky, kz);
     if (st == MS2_OK) st = upload_params(s);
     if (st == MS2_OK) st = ms2_eval_forces(s);
+    if (st == MS2_OK) s->stale = false;
     return st;
 }
 
@@ -1182,7 +1206,6 @@ extern "C" ms2_status ms2_get_state(ms2_system s, double *R, double *q, double *
 extern "C" ms2_status ms2_set_state(ms2_system s, const double *R, const double *q, const double *v,
                                     const double *Lang) {
     if (!s) return ms2_fail(MS2_EINVAL, "null system");
-    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
     const int N = s->N;
     if (R || q || v || Lang) {
         std::vector<double> cur;
@@ -1210,11 +1233,13 @@ extern "C" ms2_status ms2_set_state(ms2_system s, const double *R, const double 
         ms2_status st = upload_state(s);
         if (st != MS2_OK) return st;
     }
-    return ms2_eval_forces(s);
+    s->stale = true;
+    return MS2_OK;
 }
 
 extern "C" ms2_status ms2_partner_counts(ms2_system s, int *counts) {
     if (!s || !counts) return ms2_fail(MS2_EINVAL, "null argument");
+    if (ms2_status e = ms2_ensure_forces(s)) return e;
     MS2_CUDA_OK(cudaMemcpyAsync(counts, s->d.npart, sizeof(int) * s->N, cudaMemcpyDeviceToHost, s->stream));
     MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
     return MS2_OK;
@@ -1222,6 +1247,7 @@ extern "C" ms2_status ms2_partner_counts(ms2_system s, int *counts) {
 
 extern "C" ms2_status ms2_molecule_energies(ms2_system s, double *out) {
     if (!s || !out) return ms2_fail(MS2_EINVAL, "null argument");
+    if (ms2_status e = ms2_ensure_forces(s)) return e;
     ms2_status st = get_soa(s, s->d.Ui, 4, out);
     if (st != MS2_OK) return st;
     for (int k = 0; k < 4 * s->N; ++k) out[k] *= 0.5;
@@ -1230,6 +1256,7 @@ extern "C" ms2_status ms2_molecule_energies(ms2_system s, double *out) {
 
 extern "C" ms2_status ms2_site_offsets(ms2_system s, double *offsets, int *n_site_slots) {
     if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (ms2_status e = ms2_ensure_forces(s)) return e;
     const int N = s->N, NS = s->ns;
     if (n_site_slots) *n_site_slots = NS;
     if (!offsets) return MS2_OK;
@@ -1271,6 +1298,7 @@ extern "C" ms2_status ms2_rdf_setup(ms2_system s, double r_max, int n_bins, int 
 extern "C" ms2_status ms2_rdf_sample(ms2_system s) {
     if (!s) return ms2_fail(MS2_EINVAL, "null system");
     if (!s->d.rdf) return ms2_fail(MS2_ESTATE, "call ms2_rdf_setup first");
+    if (ms2_status e = ms2_ensure_forces(s)) return e;
     launch_rdf(s);
     flush_launches(s);
     MS2_CUDA_OK(cudaGetLastError());
@@ -1337,6 +1365,7 @@ extern "C" ms2_status ms2_averages(ms2_system s, double out[5], long long *n_ste
 
 extern "C" ms2_status ms2_volume_derivatives(ms2_system s, double *dUdV, double *d2UdV2) {
     if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (ms2_status e = ms2_ensure_forces(s)) return e;
     if (!s->hp.massieu) return ms2_fail(MS2_ESTATE, "created without ms2_options.massieu");
     double sc[SC_COUNT_];
     ms2_status st = read_scalars(s, sc);

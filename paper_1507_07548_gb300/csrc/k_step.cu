@@ -166,14 +166,25 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     };
     if (threadIdx.x == 0) lam_s = __ldcg(S.scal + SC_LAMBDA);
     __syncthreads();
-    for (int k = 0; k < A.nsteps; ++k) {
+    // k = -1 (after ms2_set_state): the state as set is evaluated first -- site
+    // build instead of the drift, then partner search, forces, unit reduction,
+    // totals and the configuration's scalars (ms2_eval_forces' k_build, k_pair
+    // and k_reduce on the same decomposition), no record and no sampling
+    for (int k = A.init ? -1 : 0; k < A.nsteps; ++k) {
+        const bool ev = k < 0;
         const bool tm = rec && k == A.nsteps - 1;
         if (tm) tph[0] = global_ns();
-        // ---- drift + site build of the own molecules
+        // ---- drift + site build of the own molecules (k = -1: the site build alone, as k_build)
         if (warp >= 1)
             for (int m0 = 8 * (warp - 1); m0 < nm; m0 += 8 * (STEP_WARPS - 1)) {
-                const int m = m0 + (lane >> 2);
-                drift_quad<true>(Ps, S, view(), m, lo + m, m < nm, lane & 3, false, lam_s);
+                const int m = m0 + (lane >> 2), c = lane & 3;
+                if (!ev) {
+                    drift_quad<true>(Ps, S, view(), m, lo + m, m < nm, c, false, lam_s);
+                } else if (m < nm && c < 3) {
+                    const StateView sv = view();
+                    const double q[4] = {sv.q[m], sv.q[MC + m], sv.q[2 * MC + m], sv.q[3 * MC + m]};
+                    build_row(Ps, S, lo + m, c, q, sv.R[c * MC + m], sv.spc[m]);
+                }
             }
         mark(k, 0);
         grid_sync(A.bar, A.err, target, on_timeout);
@@ -205,7 +216,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
                 q[PV_VV * MC] = o.vv;
             }
         }
-        if (A.rdf_every > 0 && ((A.s0 + k + 1) % A.rdf_every) == 0) {
+        if (!ev && A.rdf_every > 0 && ((A.s0 + k + 1) % A.rdf_every) == 0) {
             __syncthreads();
             rdf_tile<NS, MULTI>(Ps, S, sm, A.Np, (unsigned *)(own + own_layout(MC, JS, 0).hist));
         }
@@ -219,20 +230,23 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         if (warp == 0) {
             const OwnLayout ol = own_layout(MC, JS, 0);
             const RedIO io{part_at(), nullptr, MC, view(), (double *)(own + ol.ui), (int *)(own + ol.np), MC, lo};
-            reduce_unit<true>(Ps, S, io, RED_SUM | RED_LAMBDA | (gk_step(A, k) ? RED_GK : 0), b, G, lane);
+            reduce_unit<true>(Ps, S, io, RED_SUM | RED_LAMBDA | (!ev && gk_step(A, k) ? RED_GK : 0), b, G, lane);
         }
         mark(k, 2);
         grid_sync(A.bar, A.err, target, on_timeout);
         if (tm) tph[3] = global_ns();
         // ---- totals in every block; thermostat factor for the next drift
-        reduce_totals(S, G, tot, gk_step(A, k) ? Q_N + 3 : Q_N);
+        reduce_totals(S, G, tot, !ev && gk_step(A, k) ? Q_N + 3 : Q_N);
         __syncthreads();
-        if (threadIdx.x == 0) lam_s = lambda_of(Ps, tot);
+        if (threadIdx.x == 0) {
+            lam_s = lambda_of(Ps, tot);
+            if (ev && b == 0) finish_step(Ps, S, RED_SUM | RED_LAMBDA, tot);  // the scalars of the state as set
+        }
         __syncthreads();
         // ---- heat flux of this configuration (sampled steps): power pass over
         // the staged system, then heat unit b
         if constexpr (HEAT) {
-            if (hf_step(A, k)) {
+            if (!ev && hf_step(A, k)) {
                 for (int t = warp; t < nm * JS; t += STEP_WARPS) {
                     const int m = t % nm, p = t / nm, i = lo + m;
                     const int j0 = (int)(((long long)N * p) / JS), j1 = (int)(((long long)N * (p + 1)) / JS);

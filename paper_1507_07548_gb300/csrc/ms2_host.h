@@ -71,7 +71,14 @@ struct ms2_system_s {
     double rdf_rmax = 0;
     // host staging of the state
     std::vector<double> hR, hq, hv, hL;
-    double *pinned = nullptr;  // page-locked staging for state transfers (4N doubles)
+    // page-locked staging: two upload buffers of 13N doubles (used alternately,
+    // each guarded by the event of its last copy) and one download buffer of 4N
+    double *pinned = nullptr;
+    cudaEvent_t up_ev[2] = {nullptr, nullptr};
+    int up_k = 0;
+    // set_state leaves forces, energies and site build stale; the next query
+    // evaluates them, or the next fused step does it in its prologue
+    bool stale = false;
     // timing events: [0] step start, [1] before pair, [2] after pair, [3] after Ewald, [4] step end
     bool timing = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -83,6 +90,7 @@ ms2_status ms2_fail(ms2_status st, const char *fmt, ...);
 ms2_status ms2_fail_cuda(cudaError_t e, const char *what, const char *file, int line);
 void ms2_unit_constants(bool reduced, double *coulomb, double *kconv);
 ms2_status ms2_eval_forces(ms2_system s);
+ms2_status ms2_ensure_forces(ms2_system s);  // evaluates after ms2_set_state, else nothing
 ms2_status ms2_validate_models(const ms2_model *models, int n_models, ms2_elec elec);
 // residence-time sampling (k_residence.cu)
 void ms2_launch_residence(cudaStream_t st, const SysParams *P, const DevSys &S, const ResArgs &a);

@@ -157,6 +157,7 @@ struct StepArgs {
     unsigned *bar_next;    // the next launch's counter, zeroed by this launch
     unsigned *err;         // sticky timeout flag
     int timing;            // record the phase times of the last step (SC_TPAIR, SC_TPH*, ns)
+    int init;              // first evaluate the state as set (site build, forces, energies): after ms2_set_state
     unsigned long long *tmax;  // timing: [3] latest compute-end times over blocks (zero at entry, re-zeroed after use)
 };
 
