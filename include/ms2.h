@@ -170,8 +170,13 @@ MS2_API ms2_status ms2_ewald_params(ms2_system sys, double alpha, int kx, int ky
  * (w, x, y, z), body -> space), centre velocities v (N x 3) and space-frame
  * angular momenta Lang (N x 3, g/mol*A^2/fs) — for the leapfrog these are the
  * values half a step behind R and q — and the step counter.  Any pointer may be
- * NULL.  set_state recomputes forces; it renormalises a q whose squared norm
- * differs from 1 by more than 1e-13 and takes the others bit for bit. */
+ * NULL.  set_state renormalises a q whose squared norm differs from 1 by more
+ * than 1e-13 and takes the others bit for bit.  It validates and stages the
+ * state on the host, queues the copy and returns without waiting for it; the
+ * forces, energies and site build of the new state are evaluated by the next
+ * call that reads them (energies, forces, terms, partner counts, offsets, an RDF
+ * sample, a batch step) or by the next ms2_step, whose fused kernel evaluates
+ * the state first.  Results are the same either way, bit for bit. */
 MS2_API ms2_status ms2_get_state(ms2_system sys, double *R, double *q, double *v, double *Lang, long long *step);
 MS2_API ms2_status ms2_set_state(ms2_system sys, const double *R, const double *q, const double *v, const double *Lang);
 
