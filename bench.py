@@ -125,26 +125,29 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------- CPU baseline
-def oracle_rate(seconds, nsteps=None):
+def oracle_rate(seconds, nsteps=None, threads=0):
     """The FP64 oracle (as it stands) stepping the same workload on the host
-    cores; returns (pair interactions/s, steps, seconds, cores)."""
+    cores (all of them, or `threads`); returns (pair interactions/s, steps,
+    seconds, threads used)."""
     from oracle import Oracle
     from paper_1507_07548_gb300 import workloads as W
     wl = W.water_box(N=N_WATER, rc=RC, seed=SEED)
     o = Oracle.from_workload(wl)
     cores = len(os.sched_getaffinity(0))
     R, q, v, L = wl.R, wl.q, wl.v, wl.Lang
+    Oracle.set_threads(threads if threads else cores)
     t0 = time.perf_counter()
     R, q, v, L, th, _ = o.run_leapfrog(R, q, v, L, wl.dt, 1, T0=wl.T)
     t1 = time.perf_counter() - t0
     n = nsteps if nsteps else max(1, int(seconds / max(t1, 1e-6)))
-    pairs = 0
-    t0 = time.perf_counter()
-    for _ in range(n):
+    pairs, dt = 0.0, 0.0
+    for _ in range(n):  # only the steps are timed; the pairs are counted outside
+        t0 = time.perf_counter()
         R, q, v, L, th, _ = o.run_leapfrog(R, q, v, L, wl.dt, 1, T0=wl.T)
-        pairs += o.forces(R, q)[2]["n_pairs"] if False else o.partner_counts(R).sum() / 2
-    dt = time.perf_counter() - t0
-    return pairs / dt, n, dt, cores
+        dt += time.perf_counter() - t0
+        pairs += o.partner_counts(R).sum() / 2
+    Oracle.set_threads(cores)
+    return pairs / dt, n, dt, (threads if threads else cores)
 
 
 def reference_arm(args, rank, world):
@@ -301,6 +304,7 @@ def gpu_arm(args, rank, world, local_rank):
     achieved = flops / (sum(kern_ms) * 1e-3) / 1e12
     traffic = traffic_record("step_water_rf" if fused else "pair_water_rf")
     cpu_val, cpu_n, cpu_dt, cores = oracle_rate(args.cpu_seconds)
+    cpu1_val, cpu1_n, cpu1_dt, _ = oracle_rate(max(1.0, args.cpu_seconds / 4), threads=1)
     value = pairs_all / (tot_ms_max * 1e-3)
     line = {
         "metric": "pair interactions/s", "value": value, "unit": "pair interactions/s", "n_gpus": world,
@@ -321,7 +325,9 @@ def gpu_arm(args, rank, world, local_rank):
                      "pair_phase_ms": statistics.mean(t_pair),
                      "algorithmic_flops_per_launch": FLOPS_PER_WATER_PAIR * statistics.mean(pairs)},
         "cpu_baseline": {"value": cpu_val, "unit": "pair interactions/s", "cores": cores, "kind": "oracle",
-                         "sample": "%d MD steps of the same workload, %.1f s" % (cpu_n, cpu_dt)},
+                         "sample": "%d MD steps of the same workload, %.1f s" % (cpu_n, cpu_dt),
+                         "single_thread": {"value": cpu1_val, "cores": 1,
+                                           "sample": "%d MD steps, %.1f s" % (cpu1_n, cpu1_dt)}},
         "e2e": {"value": e2e_pairs / e2e_t, "unit": "pair interactions/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,

@@ -82,6 +82,7 @@ def _load():
             "or_heat_flux": [P(_Sys), d, d, d, d, d, d],
             "or_thermal_conductivity": [d, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int],
             "or_conductivity": [d, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int],
+            "or_set_threads": [C.c_int],
         }
         for name, args in sig.items():
             getattr(_lib, name).argtypes = args
@@ -210,6 +211,11 @@ class Oracle:
         f = lambda a: _p(np.ascontiguousarray(a, np.float64))
         self.lib.or_heat_flux(self.ref, f(R), f(q), f(v), f(Lang), _p(hh), _p(J))
         return J
+
+    @staticmethod
+    def set_threads(n):
+        """Host threads of the oracle's OpenMP loops (timing; results do not depend on it)."""
+        _load().or_set_threads(C.c_int(int(n)))
 
     @staticmethod
     def thermal_conductivity(acf, dt_ext, V, T, reduced=False):

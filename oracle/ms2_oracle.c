@@ -45,6 +45,18 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* host threads of the OpenMP loops (timing only; the arithmetic does not depend on it) */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
 
 #define OR_MAXSP 4
 #define OR_MAXS 8

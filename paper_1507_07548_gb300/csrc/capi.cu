@@ -347,10 +347,11 @@ static ms2_status sys_alloc(ms2_system s) {
     d.jsplit = s->jsplit;
     auto A = [&](void **p, size_t n) { return s->al.alloc(p, n); };
     MS2_CUDA_OK(A((void **)&s->dP, sizeof(SysParams)));
-    MS2_CUDA_OK(A((void **)&d.R, sizeof(double) * 3 * N));
-    MS2_CUDA_OK(A((void **)&d.v, sizeof(double) * 3 * N));
-    MS2_CUDA_OK(A((void **)&d.q, sizeof(double) * 4 * N));
-    MS2_CUDA_OK(A((void **)&d.Lm, sizeof(double) * 3 * N));
+    // R, q, v, Lm back to back: a state upload is one copy
+    MS2_CUDA_OK(A((void **)&d.R, sizeof(double) * 13 * N));
+    d.q = d.R + 3 * (size_t)N;
+    d.v = d.q + 4 * (size_t)N;
+    d.Lm = d.v + 3 * (size_t)N;
     MS2_CUDA_OK(A((void **)&d.species, sizeof(int) * N));
     MS2_CUDA_OK(A((void **)&d.X, sizeof(uint32_t) * 3 * N));
     MS2_CUDA_OK(A((void **)&d.s, sizeof(float) * 3 * NS * N));
@@ -737,7 +738,7 @@ static void initial_state(ms2_system s, const ms2_model *models, double T, unsig
 }
 
 static ms2_status ensure_pinned(ms2_system s) {
-    if (!s->pinned) MS2_CUDA_OK(cudaMallocHost((void **)&s->pinned, sizeof(double) * 30 * s->N));
+    if (!s->pinned) MS2_CUDA_OK(cudaMallocHost((void **)&s->pinned, sizeof(double) * 39 * s->N));
     for (int k = 0; k < 2; ++k)
         if (!s->up_ev[k]) MS2_CUDA_OK(cudaEventCreateWithFlags(&s->up_ev[k], cudaEventDisableTiming));
     return MS2_OK;
@@ -753,17 +754,18 @@ static ms2_status upload_state(ms2_system s) {
     MS2_CUDA_OK(cudaEventSynchronize(s->up_ev[k]));
     double *buf = s->pinned + (size_t)13 * N * k;
     size_t off = 0;
-    auto put = [&](double *dst, const std::vector<double> &src, int nc) -> cudaError_t {
+    auto put = [&](const std::vector<double> &src, int nc) {  // AoS -> the device SoA order
         double *b = buf + off;
         for (int i = 0; i < N; ++i)
             for (int k = 0; k < nc; ++k) b[k * N + i] = src[nc * i + k];
         off += (size_t)nc * N;
-        return cudaMemcpyAsync(dst, b, sizeof(double) * nc * N, cudaMemcpyHostToDevice, s->stream);
     };
-    MS2_CUDA_OK(put(s->d.R, s->hR, 3));
-    MS2_CUDA_OK(put(s->d.q, s->hq, 4));
-    MS2_CUDA_OK(put(s->d.v, s->hv, 3));
-    MS2_CUDA_OK(put(s->d.Lm, s->hL, 3));
+    put(s->hR, 3);
+    put(s->hq, 4);
+    put(s->hv, 3);
+    put(s->hL, 3);
+    // the device arrays R, q, v, Lm are contiguous in this order (sys_alloc)
+    MS2_CUDA_OK(cudaMemcpyAsync(s->d.R, buf, sizeof(double) * 13 * N, cudaMemcpyHostToDevice, s->stream));
     MS2_CUDA_OK(cudaEventRecord(s->up_ev[k], s->stream));
     s->up_k = 1 - k;
     return MS2_OK;
@@ -1194,13 +1196,25 @@ extern "C" ms2_status ms2_ewald_params(ms2_system s, double alpha, int kx, int k
 
 extern "C" ms2_status ms2_get_state(ms2_system s, double *R, double *q, double *v, double *Lang, long long *step) {
     if (!s) return ms2_fail(MS2_EINVAL, "null system");
-    ms2_status st = MS2_OK;
-    if (R) st = get_soa(s, s->d.R, 3, R);
-    if (st == MS2_OK && q) st = get_soa(s, s->d.q, 4, q);
-    if (st == MS2_OK && v) st = get_soa(s, s->d.v, 3, v);
-    if (st == MS2_OK && Lang) st = get_soa(s, s->d.Lm, 3, Lang);
     if (step) *step = s->step;
-    return st;
+    if (!R && !q && !v && !Lang) return MS2_OK;
+    ms2_status st = ensure_pinned(s);
+    if (st != MS2_OK) return st;
+    // one copy of the contiguous R, q, v, Lm (sys_alloc) into the download buffer
+    const int N = s->N;
+    double *buf = s->pinned + (size_t)26 * N;
+    MS2_CUDA_OK(cudaMemcpyAsync(buf, s->d.R, sizeof(double) * 13 * N, cudaMemcpyDeviceToHost, s->stream));
+    MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    auto out = [&](double *dst, size_t off, int nc) {
+        if (dst)
+            for (int i = 0; i < N; ++i)
+                for (int k = 0; k < nc; ++k) dst[nc * i + k] = buf[off + (size_t)k * N + i];
+    };
+    out(R, 0, 3);
+    out(q, (size_t)3 * N, 4);
+    out(v, (size_t)7 * N, 3);
+    out(Lang, (size_t)10 * N, 3);
+    return MS2_OK;
 }
 
 extern "C" ms2_status ms2_set_state(ms2_system s, const double *R, const double *q, const double *v,

@@ -72,7 +72,7 @@ struct ms2_system_s {
     // host staging of the state
     std::vector<double> hR, hq, hv, hL;
     // page-locked staging: two upload buffers of 13N doubles (used alternately,
-    // each guarded by the event of its last copy) and one download buffer of 4N
+    // each guarded by the event of its last copy) and one download buffer of 13N
     double *pinned = nullptr;
     cudaEvent_t up_ev[2] = {nullptr, nullptr};
     int up_k = 0;
