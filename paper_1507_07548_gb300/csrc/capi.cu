@@ -46,10 +46,14 @@ __global__ void k_reduce(const SysParams *, DevSys, int);
 __global__ void k_heat_reduce(const SysParams *, DevSys);
 __global__ void k_drift(const SysParams *, DevSys, int);
 __global__ void k_pair_lj64(const SysParams *, DevSys, int);
-__global__ void k_ewald_prep(const SysParams *, DevSys);
-__global__ void k_ewald_sk(const SysParams *, DevSys, float2 *);
-__global__ void k_ewald_energy(const SysParams *, DevSys, int);
-__global__ void k_ewald_force(const SysParams *, DevSys, const float2 *, int);
+__global__ void k_ewald_skp(const SysParams *, DevSys);
+__global__ void k_ewald_sksum(const SysParams *, DevSys, float2 *, int);
+void *ms2_ewald_force_kernel(int kx);
+__global__ void k_ewald_fsum(const SysParams *, DevSys);
+size_t ms2_ewald_skp_smem(int kx, int ky, int kz);
+int ms2_ewald_skp_blocks(int M);
+int ms2_ewald_sksum_blocks(int K);
+size_t ms2_ewald_force_smem(int kx, int kz, int ny_per_chunk);
 __global__ void k_rdf(const SysParams *, DevSys);
 __global__ void k_terms(const SysParams *, DevSys, double *);
 size_t ms2_pair_smem_bytes(int NS, bool dmu, bool multi, int TJ, int wpb);
@@ -511,11 +515,16 @@ ms2_status launch_pair(ms2_system s) {
 ms2_status launch_ewald(ms2_system s) {
     if (s->hp.elec != ELEC_EWALD) return MS2_OK;
     DevSys &d = s->d;
-    k_ewald_prep<<<(d.nsite_q + 127) / 128, 128, 0, s->stream>>>(s->dP, d);
-    const int cols = (2 * d.ky + 1) * (2 * d.kz + 1), ych = (d.kx + 1 + 7) / 8;
-    k_ewald_sk<<<dim3(cols, ych), 256, 0, s->stream>>>(s->dP, d, s->AS);
-    k_ewald_energy<<<1, 256, 0, s->stream>>>(s->dP, d, cols * ych);
-    k_ewald_force<<<dim3((d.nsite_q + 127) / 128, d.kchunks), 128, 0, s->stream>>>(s->dP, d, s->AS, s->ny_per_chunk);
+    const int K = (2 * d.ky + 1) * (2 * d.kz + 1) * (d.kx + 1), nb = ms2_ewald_skp_blocks(d.nsite_q);
+    k_ewald_skp<<<nb, 320, ms2_ewald_skp_smem(d.kx, d.ky, d.kz), s->stream>>>(s->dP, d);
+    k_ewald_sksum<<<ms2_ewald_sksum_blocks(K), 1024, 0, s->stream>>>(s->dP, d, s->AS, nb);
+    {
+        void (*fk)(const SysParams *, DevSys, const float2 *, int) =
+            (void (*)(const SysParams *, DevSys, const float2 *, int))ms2_ewald_force_kernel(d.kx);
+        fk<<<dim3((d.nsite_q + 127) / 128, d.kchunks), 128, ms2_ewald_force_smem(d.kx, d.kz, s->ny_per_chunk),
+             s->stream>>>(s->dP, d, s->AS, s->ny_per_chunk);
+    }
+    k_ewald_fsum<<<(3 * d.nsite_q + 127) / 128, 128, 0, s->stream>>>(s->dP, d);
     s->launch_acc += 4;
     return MS2_OK;
 }
@@ -791,15 +800,39 @@ static ms2_status setup_ewald(ms2_system s, double alpha, int kx, int ky, int kz
     const int M = d.nsite_q, kst = std::max(kx, std::max(ky, kz)) + 1;
     d.kchunks = 2 * ky + 1;
     s->ny_per_chunk = 1;
-    const int cols = (2 * ky + 1) * (2 * kz + 1), ych = (kx + 1 + 7) / 8;
+    const int cols = (2 * ky + 1) * (2 * kz + 1), K = cols * (kx + 1);
     auto A = [&](void **p, size_t n) { return s->al.alloc(p, n); };
     // (re)allocation: old buffers stay owned by the allocator list until destroy
-    MS2_CUDA_OK(A((void **)&d.Xs, sizeof(uint32_t) * 3 * M));
     MS2_CUDA_OK(A((void **)&d.qs, sizeof(float) * M));
     MS2_CUDA_OK(A((void **)&d.eik, sizeof(float2) * 3 * kst * M));
     MS2_CUDA_OK(A((void **)&d.frec, sizeof(float) * d.kchunks * 3 * M));
-    MS2_CUDA_OK(A((void **)&d.kblk, sizeof(double) * 2 * cols * ych));
-    MS2_CUDA_OK(A((void **)&s->AS, sizeof(float2) * cols * (kx + 1)));
+    MS2_CUDA_OK(A((void **)&d.skpart, sizeof(float2) * (size_t)ms2_ewald_skp_blocks(M) * K));
+    MS2_CUDA_OK(A((void **)&d.kblk, sizeof(double) * 2 * ms2_ewald_sksum_blocks(K)));
+    MS2_CUDA_OK(A((void **)&s->AS, sizeof(float2) * K));
+    {  // the k-space tables of this box and alpha (k = (col, nx) with col = (ny + ky)(2 kz + 1) + nz + kz)
+        std::vector<double> Ak(K), Bk(K);
+        const double tw = 2.0 * M_PI / s->hp.L, ia2 = 1.0 / ((double)s->hp.alpha * (double)s->hp.alpha);
+        for (int k = 0; k < K; ++k) {
+            const int col = k / (kx + 1), nx = k % (kx + 1);
+            const int ny = col / (2 * kz + 1) - ky, nz = col % (2 * kz + 1) - kz;
+            const bool on = nx > 0 || ny > 0 || (ny == 0 && nz > 0);  // the half space
+            const double kk = tw * tw * ((double)nx * nx + (double)ny * ny + (double)nz * nz);
+            Ak[k] = on ? std::exp(-0.25 * kk * ia2) / kk : 0.0;
+            Bk[k] = Ak[k] * (1.0 - 0.5 * kk * ia2);
+        }
+        MS2_CUDA_OK(A((void **)&d.Ak, sizeof(double) * K));
+        MS2_CUDA_OK(A((void **)&d.Bk, sizeof(double) * K));
+        MS2_CUDA_OK(cudaMemcpyAsync(d.Ak, Ak.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s->stream));
+        MS2_CUDA_OK(cudaMemcpyAsync(d.Bk, Bk.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s->stream));
+        MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    }
+    {
+        const size_t sm = ms2_ewald_skp_smem(kx, ky, kz), fm = ms2_ewald_force_smem(kx, kz, s->ny_per_chunk);
+        MS2_CUDA_OK(cudaFuncSetAttribute((const void *)k_ewald_skp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)std::max<size_t>(sm, 48 * 1024)));
+        MS2_CUDA_OK(cudaFuncSetAttribute(ms2_ewald_force_kernel(kx), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)std::max<size_t>(fm, 48 * 1024)));
+    }
     double coulomb, kconv;
     ms2_unit_constants(s->reduced, &coulomb, &kconv);
     ms2_energy_constants(s->hp, s->species, alpha, s->rc, s->lrc, coulomb, &s->uconst, &s->wbg, &s->ulrc, &s->plrc);

@@ -401,13 +401,11 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
             x[Q_U] = c == 0 ? ulj + uqq + udd : 0.0;
             x[Q_W] = c == 0 ? w : 0.0;
             x[Q_VV] = c == 0 ? vvm : 0.0;
-            if (!SH && (mode & RED_EWALD)) {  // reciprocal-space site forces, summed over k chunks (global layout)
+            if (!SH && (mode & RED_EWALD)) {  // reciprocal-space site forces (summed over k chunks by k_ewald_fsum)
                 const int NS = S.ns, M = S.nsite_q, c1 = (cc + 1) % 3, c2 = (cc + 2) % 3;
                 double wc = 0;  // -F_s.s_s molecular-virial correction, component c
                 for (int a2 = 0; a2 < NS; ++a2) {
-                    double f = 0;
-                    for (int ch = 0; ch < S.kchunks; ++ch)
-                        f += f2d(__ldcg(S.frec + ((size_t)ch * 3 + cc) * M + a2 * N + ii));
+                    const double f = f2d(__ldcg(S.frec + (size_t)cc * M + a2 * N + ii));
                     const double f1 = __shfl_sync(F, f, qb | c1), f2 = __shfl_sync(F, f, qb | c2);
                     const double o1 = f2d(S.s[(c1 * NS + a2) * N + ii]), o2 = f2d(S.s[(c2 * NS + a2) * N + ii]);
                     const double oc = f2d(S.s[(cc * NS + a2) * N + ii]);

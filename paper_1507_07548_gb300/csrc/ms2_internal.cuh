@@ -93,11 +93,12 @@ struct DevSys {
     double *acc;                       // running averages (see AC_* below)
     // Ewald
     int nk, kx, ky, kz, nsite_q, kchunks;
-    uint32_t *Xs;                      // [3][nsite_q] site lattice coordinates
     float *qs;                         // [nsite_q] site charges
     float2 *eik;                       // [3][kmax+1][nsite_q] e^{i n theta}
     double *Sk;                        // [nk][4]: A*Re S, A*Im S, |S|^2 A part, ... (scaled)
     float *frec;                       // [kchunks][3][nsite_q] partial site forces
+    float2 *skpart;                    // [site blocks][k] partial structure factors
+    double *Ak, *Bk;                   // [k] A(k) = exp(-k^2/4a^2)/k^2 on the half space (else 0), A (1 - k^2/2a^2)
     double *kblk;                      // per-block energy/virial partials of S(k)
     // RDF
     unsigned long long *rdf;           // [rows][nbins]
