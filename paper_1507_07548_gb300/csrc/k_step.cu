@@ -297,11 +297,12 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         grid_sync(A.bar, A.err, target, on_timeout);
         if (b == 0 && warp == 0) heat_record(S, G, lane);
     }
-    __syncthreads();
+    // the write-back starts at warp 1, so that block 0's record (warp 0) runs
+    // beside it; it reads only block-held data the last barrier ordered
     const OwnLayout ol = own_layout(MC, JS, 0);
     const double *ui_s = (const double *)(own + ol.ui);
     const int *np_s = (const int *)(own + ol.np);
-    for (int t = threadIdx.x; t < nm; t += blockDim.x) {
+    for (int t = (threadIdx.x + STEP_THREADS - 32) % STEP_THREADS; t < nm; t += blockDim.x) {
         const StateView sv = view();
         const int i = lo + t;
 #pragma unroll

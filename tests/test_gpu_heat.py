@@ -166,3 +166,17 @@ def test_setup_checks_arguments_and_ewald_is_refused():
     e = ms2.System.from_workload(snapshot(wl, "ionic_N1040"))
     with pytest.raises(ms2.Ms2Error, match="EINVAL"):
         e.heat_setup(every=1, n_lags=8)
+
+
+def test_heat_flux_ragged_system_fused():
+    """1003 molecules (a ragged last block of the fused decomposition)."""
+    wl = W.water_box(N=1003, rc=14.0, seed=21)
+    wl.dt = 0.5
+    s = ms2.System.from_workload(wl)
+    s.heat_setup(every=1, n_lags=4, h=[100.0])
+    assert s.fused_step() == 1
+    s.step(2)
+    o = Oracle.from_workload(wl)
+    R, q, v, L = integer_time_velocities(wl, o, s)
+    Jo = o.heat_flux(R, q, v, L, h=[100.0])
+    assert rel(s.heat_flux(), Jo) <= TOL_J
