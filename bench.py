@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--impl", default="ms2", choices=["ms2", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle CPU-baseline sample length")
     ap.add_argument("--no-extra", action="store_true", help="skip the Ewald sub-benchmark")
+    ap.add_argument("--only", choices=["ewald", "massieu", "thermal", "batch"], default=None,
+                    help="run one sub-benchmark alone and print its JSON object")
     ap.add_argument("--uniform-batch", type=int, default=0, metavar="S",
                     help="only time one batch of S copies of the water workload (single steps; the ncu case "
                          "of the multi-system step kernel)")
@@ -571,10 +573,24 @@ def uniform_batch(args):
     return 0
 
 
+def only_sub(args):
+    """One sub-benchmark of the default run, alone (e.g. the ncu case of its kernels)."""
+    import torch
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    fn = {"ewald": lambda: ewald_sub(args, stream), "massieu": lambda: massieu_sub(args, stream, flush),
+          "thermal": lambda: thermal_sub(args, stream, flush), "batch": lambda: batch_sub(args, flush)}[args.only]
+    print(json.dumps({args.only: fn()}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.uniform_batch > 0:
         return uniform_batch(args)
+    if args.only:
+        return only_sub(args)
     rank, world, local_rank = dist_env()
     if world > 1:
         import torch.distributed as tdist
