@@ -1254,6 +1254,33 @@ extern "C" ms2_status ms2_set_state(ms2_system s, const double *R, const double 
                                     const double *Lang) {
     if (!s) return ms2_fail(MS2_EINVAL, "null system");
     const int N = s->N;
+    if (R && q && v && Lang) {  // the whole state: validated and staged in one pass, straight into pinned memory
+        ms2_status st = ensure_pinned(s);
+        if (st != MS2_OK) return st;
+        const int k = s->up_k;
+        MS2_CUDA_OK(cudaEventSynchronize(s->up_ev[k]));
+        double *b = s->pinned + (size_t)13 * N * k;  // R, q, v, Lm in the device order (sys_alloc)
+        for (int i = 0; i < N; ++i) {
+            for (int c = 0; c < 3; ++c) {
+                const double x = R[3 * i + c], y = v[3 * i + c], z = Lang[3 * i + c];
+                if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z))
+                    return ms2_fail(MS2_EINVAL, "non-finite state value for molecule %d", i);
+                b[(size_t)c * N + i] = x;
+                b[(size_t)(7 + c) * N + i] = y;
+                b[(size_t)(10 + c) * N + i] = z;
+            }
+            double n2 = 0;
+            for (int c = 0; c < 4; ++c) n2 += q[4 * i + c] * q[4 * i + c];
+            if (!(n2 > 0) || !std::isfinite(n2)) return ms2_fail(MS2_EINVAL, "quaternion %d has zero norm", i);
+            const double inv = std::fabs(n2 - 1.0) > 1e-13 ? 1.0 / std::sqrt(n2) : 1.0;  // unit ones bit for bit
+            for (int c = 0; c < 4; ++c) b[(size_t)(3 + c) * N + i] = inv == 1.0 ? q[4 * i + c] : q[4 * i + c] * inv;
+        }
+        MS2_CUDA_OK(cudaMemcpyAsync(s->d.R, b, sizeof(double) * 13 * N, cudaMemcpyHostToDevice, s->stream));
+        MS2_CUDA_OK(cudaEventRecord(s->up_ev[k], s->stream));
+        s->up_k = 1 - k;
+        s->stale = true;
+        return MS2_OK;
+    }
     if (R || q || v || Lang) {
         std::vector<double> cur;
         // fetch what is not replaced

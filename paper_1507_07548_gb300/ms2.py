@@ -79,8 +79,8 @@ SIGNATURES = {
     "ms2_forces_torques": (C.c_int, [_vp, _d, _d]),
     "ms2_forces_torques_dev": (C.c_int, [_vp, _vp, _vp]),
     "ms2_ewald_params": (C.c_int, [_vp, C.c_double, C.c_int, C.c_int, C.c_int]),
-    "ms2_get_state": (C.c_int, [_vp, _d, _d, _d, _d, _P(C.c_longlong)]),
-    "ms2_set_state": (C.c_int, [_vp, _d, _d, _d, _d]),
+    "ms2_get_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _P(C.c_longlong)]),
+    "ms2_set_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "ms2_partner_counts": (C.c_int, [_vp, _P(C.c_int)]),
     "ms2_site_offsets": (C.c_int, [_vp, _d, _P(C.c_int)]),
     "ms2_molecule_energies": (C.c_int, [_vp, _d]),
@@ -261,15 +261,13 @@ class System:
     def get_state(self):
         R, q, v, Lg = np.zeros((self.N, 3)), np.zeros((self.N, 4)), np.zeros((self.N, 3)), np.zeros((self.N, 3))
         st = C.c_longlong()
-        check(lib().ms2_get_state(self.h, _dp(R), _dp(q), _dp(v), _dp(Lg), C.byref(st)))
+        check(lib().ms2_get_state(self.h, R.ctypes.data, q.ctypes.data, v.ctypes.data, Lg.ctypes.data, C.byref(st)))
         return R, q, v, Lg, st.value
 
     def set_state(self, R=None, q=None, v=None, Lang=None):
         N = self.N
-        args = []
-        for a, n in ((R, 3), (q, 4), (v, 3), (Lang, 3)):
-            args.append(None if a is None else _f64(a, (N, n)))
-        check(lib().ms2_set_state(self.h, *[None if a is None else _dp(a) for a in args]))
+        keep = [None if a is None else _f64(a, (N, n)) for a, n in ((R, 3), (q, 4), (v, 3), (Lang, 3))]
+        check(lib().ms2_set_state(self.h, *[None if a is None else a.ctypes.data for a in keep]))
 
     def partner_counts(self):
         c = np.zeros(self.N, np.int32)
