@@ -374,9 +374,12 @@ MS2_API ms2_status ms2_step_kernel(ms2_system sys, int *fused);
  * and RDF, [3] unit reduction (each until the slowest block is done), [1] and
  * [4] the grid barriers after [0] and [3], [5] totals and thermostat factor,
  * [6] kernel entry to that last step, [7] the whole last step, [8] its end to
- * the kernel's exit (write-back of the block-held state).  MS2_ESTATE if timing
+ * the kernel's exit (write-back of the block-held state); Ewald systems (whose
+ * reciprocal-space tasks run between [2] and the reduction, inside [3]):
+ * [9] structure-factor tasks, [10] sum tasks, [11] force tasks, each until the
+ * grid barrier after it ends (block 0's clock), else 0.  MS2_ESTATE if timing
  * is off or the last chunk ran as per-phase kernels. */
-MS2_API ms2_status ms2_last_step_phases(ms2_system sys, double out[9]);
+MS2_API ms2_status ms2_last_step_phases(ms2_system sys, double out[12]);
 MS2_API ms2_status ms2_last_step_times(ms2_system sys, double out[4]);
 
 /* ------------------------------------------------------- allocation-free */

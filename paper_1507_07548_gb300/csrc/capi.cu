@@ -48,10 +48,10 @@ __global__ void k_drift(const SysParams *, DevSys, int);
 __global__ void k_pair_lj64(const SysParams *, DevSys, int);
 __global__ void k_ewald_skp(const SysParams *, DevSys);
 __global__ void k_ewald_sksum(const SysParams *, DevSys, float2 *, int);
-void *ms2_ewald_force_kernel(int kx);
-__global__ void k_ewald_fsum(const SysParams *, DevSys);
-size_t ms2_ewald_skp_smem(int kx, int ky, int kz);
-int ms2_ewald_skp_blocks(int M);
+void *ms2_ewald_force_kernel(int kx, int kz);
+size_t ms2_ewald_skp_smem(int kx, int ky, int kz, int skc);
+int ms2_ewald_sk_sites(int M, int G);
+int ms2_ewald_skp_blocks(int M, int skc);
 int ms2_ewald_sksum_blocks(int K);
 size_t ms2_ewald_force_smem(int kx, int kz, int ny_per_chunk);
 __global__ void k_rdf(const SysParams *, DevSys);
@@ -455,6 +455,11 @@ static ms2_status size_pair_tiles(ms2_system s) {
     return MS2_OK;
 }
 
+// reciprocal-space scratch of a fused block for the system's current k range (0 without Ewald)
+static size_t step_ews(ms2_system s) {
+    return s->hp.elec == ELEC_EWALD ? ms2_step_ewald_scratch(s->d.kx, s->d.ky, s->d.kz, s->ny_per_chunk, s->d.sk_sites) : 0;
+}
+
 // fused step: a system is fusable where a variant exists, the device launches
 // cooperative kernels, every block owns at most 16 molecules (one pair item per
 // warp for j-split >= 1) and the whole system plus the own region fits one
@@ -464,8 +469,8 @@ static ms2_status size_pair_tiles(ms2_system s) {
 // only chooses which path runs.
 static void setup_fused(ms2_system s, const ms2_options &o) {
     s->fuse_fn = s->step_fn = nullptr;
-    if (s->fp64 || s->hp.integrator == MS2_INT_VERLET || s->hp.elec == ELEC_EWALD || s->multi_used) return;
-    void *fn = ms2_pick_step_kernel(s->ns, s->ljm, s->qm, s->dm, s->hp.elec, false, s->hp.massieu != 0, false);
+    if (s->fp64 || s->hp.integrator == MS2_INT_VERLET) return;
+    void *fn = ms2_pick_step_kernel(s->ns, s->ljm, s->qm, s->dm, s->hp.elec, s->multi_used, s->hp.massieu != 0, false);
     if (!fn) return;
     int coop = 0, sms = 0, optin = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device) != cudaSuccess || !coop) return;
@@ -481,7 +486,10 @@ static void setup_fused(ms2_system s, const ms2_options &o) {
     const int js = std::max(1, std::min(8, 16 / mcap));
     const int Np = (s->N + 3) & ~3;
     const size_t maxdyn = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
-    const size_t base = ms2_step_smem_bytes(s->ns, s->dmu, false, Np, mcap, js, 0);
+    // Ewald: the reciprocal-space scratch of the default |n| <= 8 (ms2_ewald_params may change it later;
+    // a launch that then does not fit takes the per-phase kernels)
+    const size_t ews = s->hp.elec == ELEC_EWALD ? ms2_step_ewald_scratch(8, 8, 8, 1, ms2_ewald_sk_sites(s->N * s->ns, sms)) : 0;
+    const size_t base = ms2_step_smem_bytes(s->ns, s->dmu, s->multi_used, Np, mcap, js, 0, ews);
     int nb = 0;
     if (base > maxdyn || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxdyn) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ms2_step_threads(), base) != cudaSuccess || nb < 1) {
@@ -515,17 +523,16 @@ ms2_status launch_pair(ms2_system s) {
 ms2_status launch_ewald(ms2_system s) {
     if (s->hp.elec != ELEC_EWALD) return MS2_OK;
     DevSys &d = s->d;
-    const int K = (2 * d.ky + 1) * (2 * d.kz + 1) * (d.kx + 1), nb = ms2_ewald_skp_blocks(d.nsite_q);
-    k_ewald_skp<<<nb, 320, ms2_ewald_skp_smem(d.kx, d.ky, d.kz), s->stream>>>(s->dP, d);
+    const int K = (2 * d.ky + 1) * (2 * d.kz + 1) * (d.kx + 1), nb = ms2_ewald_skp_blocks(d.nsite_q, d.sk_sites);
+    k_ewald_skp<<<nb, 576, ms2_ewald_skp_smem(d.kx, d.ky, d.kz, d.sk_sites), s->stream>>>(s->dP, d);
     k_ewald_sksum<<<ms2_ewald_sksum_blocks(K), 1024, 0, s->stream>>>(s->dP, d, s->AS, nb);
     {
         void (*fk)(const SysParams *, DevSys, const float2 *, int) =
-            (void (*)(const SysParams *, DevSys, const float2 *, int))ms2_ewald_force_kernel(d.kx);
+            (void (*)(const SysParams *, DevSys, const float2 *, int))ms2_ewald_force_kernel(d.kx, d.kz);
         fk<<<dim3((d.nsite_q + 127) / 128, d.kchunks), 128, ms2_ewald_force_smem(d.kx, d.kz, s->ny_per_chunk),
              s->stream>>>(s->dP, d, s->AS, s->ny_per_chunk);
     }
-    k_ewald_fsum<<<(3 * d.nsite_q + 127) / 128, 128, 0, s->stream>>>(s->dP, d);
-    s->launch_acc += 4;
+    s->launch_acc += 3;
     return MS2_OK;
 }
 
@@ -806,7 +813,9 @@ static ms2_status setup_ewald(ms2_system s, double alpha, int kx, int ky, int kz
     MS2_CUDA_OK(A((void **)&d.qs, sizeof(float) * M));
     MS2_CUDA_OK(A((void **)&d.eik, sizeof(float2) * 3 * kst * M));
     MS2_CUDA_OK(A((void **)&d.frec, sizeof(float) * d.kchunks * 3 * M));
-    MS2_CUDA_OK(A((void **)&d.skpart, sizeof(float2) * (size_t)ms2_ewald_skp_blocks(M) * K));
+    // sites per structure-factor task: one round over the fused grid (the same on both paths)
+    d.sk_sites = ms2_ewald_sk_sites(M, s->step_grid > 0 ? s->step_grid : 152);
+    MS2_CUDA_OK(A((void **)&d.skpart, sizeof(float2) * (size_t)ms2_ewald_skp_blocks(M, d.sk_sites) * K));
     MS2_CUDA_OK(A((void **)&d.kblk, sizeof(double) * 2 * ms2_ewald_sksum_blocks(K)));
     MS2_CUDA_OK(A((void **)&s->AS, sizeof(float2) * K));
     {  // the k-space tables of this box and alpha (k = (col, nx) with col = (ny + ky)(2 kz + 1) + nz + kz)
@@ -827,10 +836,10 @@ static ms2_status setup_ewald(ms2_system s, double alpha, int kx, int ky, int kz
         MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
     }
     {
-        const size_t sm = ms2_ewald_skp_smem(kx, ky, kz), fm = ms2_ewald_force_smem(kx, kz, s->ny_per_chunk);
+        const size_t sm = ms2_ewald_skp_smem(kx, ky, kz, d.sk_sites), fm = ms2_ewald_force_smem(kx, kz, s->ny_per_chunk);
         MS2_CUDA_OK(cudaFuncSetAttribute((const void *)k_ewald_skp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)std::max<size_t>(sm, 48 * 1024)));
-        MS2_CUDA_OK(cudaFuncSetAttribute(ms2_ewald_force_kernel(kx), cudaFuncAttributeMaxDynamicSharedMemorySize,
+        MS2_CUDA_OK(cudaFuncSetAttribute(ms2_ewald_force_kernel(kx, kz), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)std::max<size_t>(fm, 48 * 1024)));
     }
     double coulomb, kconv;
@@ -971,7 +980,8 @@ extern "C" ms2_status ms2_step_kernel(ms2_system s, int *fused) {
     if (!s || !fused) return ms2_fail(MS2_EINVAL, "null argument");
     const int cells = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
     *fused = s->step_fn && s->res_every == 0 && (s->hf_every == 0 || s->step_heat_fn) &&
-                     ms2_step_smem_bytes(s->ns, s->dmu, false, s->Np, s->mcap, s->jsplit, cells) <= s->step_smem_max
+                     ms2_step_smem_bytes(s->ns, s->dmu, s->multi_used, s->Np, s->mcap, s->jsplit, cells, step_ews(s)) <=
+                         s->step_smem_max
                  ? 1 : 0;
     return MS2_OK;
 }
@@ -982,13 +992,14 @@ static ms2_status read_scalars(ms2_system s, double *sc) {
     return MS2_OK;
 }
 
-extern "C" ms2_status ms2_last_step_phases(ms2_system s, double out[9]) {
+extern "C" ms2_status ms2_last_step_phases(ms2_system s, double out[12]) {
     if (!s || !out) return ms2_fail(MS2_EINVAL, "null argument");
     if (!s->timing || !s->last_fused) return ms2_fail(MS2_ESTATE, "no timed fused chunk (timing off or per-phase kernels)");
     double sc[SC_COUNT_];
     ms2_status st = read_scalars(s, sc);
     if (st != MS2_OK) return st;
-    for (int k = 0; k < 9; ++k) out[k] = sc[SC_TPH0 + k] * 1e-6;
+    for (int k = 0; k < 12; ++k) out[k] = sc[SC_TPH0 + k] * 1e-6;
+    if (s->hp.elec != ELEC_EWALD) out[9] = out[10] = out[11] = 0.0;
     return MS2_OK;
 }
 
@@ -1048,7 +1059,7 @@ static bool run_fused(ms2_system s, long long m, long long s0) {
     void *fn = s->hf_every > 0 ? s->step_heat_fn : s->step_fn;
     if (!fn) return false;
     const int cells = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
-    const size_t smem = ms2_step_smem_bytes(s->ns, s->dmu, false, s->Np, s->mcap, s->jsplit, cells);
+    const size_t smem = ms2_step_smem_bytes(s->ns, s->dmu, s->multi_used, s->Np, s->mcap, s->jsplit, cells, step_ews(s));
     if (smem > s->step_smem_max) return false;
     unsigned *cnt = s->d.counter;
     StepArgs A;
@@ -1065,6 +1076,9 @@ static bool run_fused(ms2_system s, long long m, long long s0) {
     A.err = cnt + 48;
     A.timing = s->timing ? 1 : 0;
     A.init = s->stale ? 1 : 0;
+    A.AS = s->AS;
+    A.ny_per_chunk = s->ny_per_chunk;
+    A.ews = (int)step_ews(s);
     A.tmax = (unsigned long long *)(cnt + 56);  // 3 x 8 bytes at byte 224 of the counter block (zero at entry)
     if (s->timing) cudaEventRecord(s->ev[0], s->stream);
     const cudaError_t e = ms2_launch_step(fn, s->step_grid, smem, s->stream, s->dP, s->d, A);
@@ -1630,7 +1644,7 @@ extern "C" ms2_status ms2_heat_setup(ms2_system s, int every, int n_lags, const 
     if (s->fuse_fn && s->step_fn) {
         void *fn = ms2_pick_step_kernel(s->ns, s->ljm, s->qm, s->dm, s->hp.elec, false, s->hp.massieu != 0, true);
         int nb = 0;
-        const size_t base = ms2_step_smem_bytes(s->ns, s->dmu, false, s->Np, s->mcap, s->jsplit, 0);
+        const size_t base = ms2_step_smem_bytes(s->ns, s->dmu, s->multi_used, s->Np, s->mcap, s->jsplit, 0, 0);
         if (fn && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->step_smem_max) == cudaSuccess &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ms2_step_threads(), base) == cudaSuccess && nb >= 1)
             s->step_heat_fn = fn;

@@ -401,14 +401,26 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
             x[Q_U] = c == 0 ? ulj + uqq + udd : 0.0;
             x[Q_W] = c == 0 ? w : 0.0;
             x[Q_VV] = c == 0 ? vvm : 0.0;
-            if (!SH && (mode & RED_EWALD)) {  // reciprocal-space site forces (summed over k chunks by k_ewald_fsum)
+            if (mode & RED_EWALD) {  // reciprocal-space site forces: the k chunks summed in order (FP32)
                 const int NS = S.ns, M = S.nsite_q, c1 = (cc + 1) % 3, c2 = (cc + 2) % 3;
                 double wc = 0;  // -F_s.s_s molecular-virial correction, component c
                 for (int a2 = 0; a2 < NS; ++a2) {
-                    const double f = f2d(__ldcg(S.frec + (size_t)cc * M + a2 * N + ii));
+                    float fs = 0.f;
+                    const float *fr = S.frec + (size_t)cc * M + a2 * N + ii;
+                    int ch = 0;
+                    for (; ch + 8 <= S.kchunks; ch += 8) {  // 8 loads in flight, then the adds in order
+                        float p[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) p[u] = __ldcg(fr + (size_t)(ch + u) * 3 * M);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) fs += p[u];
+                    }
+                    for (; ch < S.kchunks; ++ch) fs += __ldcg(fr + (size_t)ch * 3 * M);
+                    const double f = f2d(fs);
                     const double f1 = __shfl_sync(F, f, qb | c1), f2 = __shfl_sync(F, f, qb | c2);
-                    const double o1 = f2d(S.s[(c1 * NS + a2) * N + ii]), o2 = f2d(S.s[(c2 * NS + a2) * N + ii]);
-                    const double oc = f2d(S.s[(cc * NS + a2) * N + ii]);
+                    const double o1 = f2d(__ldcg(S.s + (c1 * NS + a2) * N + ii)),
+                                 o2 = f2d(__ldcg(S.s + (c2 * NS + a2) * N + ii));
+                    const double oc = f2d(__ldcg(S.s + (cc * NS + a2) * N + ii));
                     Fc += f;
                     Tc += o1 * f2 - o2 * f1;
                     wc += oc * f;

@@ -33,8 +33,11 @@
 // up sets a sticky flag that ends every other wait at once and marks the system
 // (SC_KERR); the kernel then runs to its end without waiting and the host
 // reports MS2_ETIMEOUT at its next read.
+#include <algorithm>
+
 #include "ms2_internal.cuh"
 
+#include "ewald_dev.cuh"
 #include "grid_dev.cuh"
 #include "integrate_dev.cuh"
 #include "pair_engine.cuh"
@@ -77,12 +80,14 @@ static_assert(sizeof(SysParams) % 16 == 0, "the parameter copy moves 16-byte wor
 
 // per-block region after the staged system: parameters, own state and partials
 struct OwnLayout {
-    size_t params, state, ui, np, sp, part, hpart, hist, end;  // byte offsets from the region start
+    size_t params, state, ui, np, sp, part, hpart, ews, hist;  // byte offsets from the region start
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline OwnLayout own_layout(int mcap, int js, int rdf_cells) {
+// (ews: bytes of the reciprocal-space task scratch, Ewald systems; the RDF
+// histogram follows)
+__host__ __device__ inline OwnLayout own_layout(int mcap, int js, size_t ews) {
     OwnLayout o;
     o.params = 0;                                                     // a copy of the system parameters
     o.state = al16(o.params + sizeof(SysParams));                     // 19 doubles per slot
@@ -91,8 +96,8 @@ __host__ __device__ inline OwnLayout own_layout(int mcap, int js, int rdf_cells)
     o.sp = al16(o.np + sizeof(int) * (size_t)mcap);                   // species, 1 int per slot
     o.part = al16(o.sp + sizeof(int) * (size_t)mcap);                 // [js][NPV][mcap] floats
     o.hpart = al16(o.part + sizeof(float) * MS2_NPV * (size_t)js * mcap);  // [js][3][mcap] heat partials
-    o.hist = al16(o.hpart + sizeof(float) * 3 * (size_t)js * mcap);
-    o.end = al16(o.hist + sizeof(unsigned) * (size_t)rdf_cells);
+    o.ews = al16(o.hpart + sizeof(float) * 3 * (size_t)js * mcap);
+    o.hist = al16(o.ews + ews);
     return o;
 }
 
@@ -104,6 +109,7 @@ template <int NS, unsigned LJM, unsigned QM, unsigned DM, int ELEC, bool MULTI, 
 __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__restrict__ P, DevSys S, StepArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using Eng = PairWarp<NS, LJM, QM, DM, ELEC, MULTI, MASS>;
+    constexpr int EWM = ELEC == ELEC_EWALD ? RED_EWALD : 0;  // reduction mode bit of the reciprocal space
     __shared__ double tot[MS2_NRED];
     __shared__ double lam_s;                    // thermostat factor for the next drift
     __shared__ unsigned long long tph[6];       // timing: entry, then the phase marks of the last step
@@ -116,16 +122,16 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     // the own region's arrays, rebuilt where needed (short live ranges: the
     // pair loop keeps its registers)
     auto view = [&]() {
-        const OwnLayout l = own_layout(MC, JS, 0);
+        const OwnLayout l = own_layout(MC, JS, (size_t)A.ews);
         double *st = (double *)(own + l.state);
         return StateView{st, st + 3 * MC, st + 6 * MC, st + 10 * MC, st + 13 * MC, st + 16 * MC,
                          (const int *)(own + l.sp), MC};
     };
     // the system parameters, copied into shared memory once: the per-step phases
     // then read no parameter through L2 after a grid barrier
-    const SysParams *Ps = (const SysParams *)(own + own_layout(MC, JS, 0).params);
-    auto part_at = [&]() { return (float *)(own + own_layout(MC, JS, 0).part); };
-    auto hpart_at = [&]() { return (float *)(own + own_layout(MC, JS, 0).hpart); };
+    const SysParams *Ps = (const SysParams *)(own + own_layout(MC, JS, (size_t)A.ews).params);
+    auto part_at = [&]() { return (float *)(own + own_layout(MC, JS, (size_t)A.ews).part); };
+    auto hpart_at = [&]() { return (float *)(own + own_layout(MC, JS, (size_t)A.ews).hpart); };
     int *wq = sm.queue + warp * 64;
     // own state into shared memory
     for (int t = threadIdx.x; t < nm; t += blockDim.x) {
@@ -145,7 +151,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     }
     {
         const int4 *src = (const int4 *)P;
-        int4 *dst = (int4 *)(own + own_layout(MC, JS, 0).params);
+        int4 *dst = (int4 *)(own + own_layout(MC, JS, (size_t)A.ews).params);
         for (int k = threadIdx.x; k < (int)(sizeof(SysParams) / sizeof(int4)); k += blockDim.x) dst[k] = src[k];
     }
     load_tables<MULTI>(P, sm);
@@ -197,7 +203,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         // item unless 16 are due
         if (k > 0 && b == 0 && warp == STEP_WARPS - 1) {
             const int gk = gk_step(A, k - 1) ? RED_GK : 0;
-            if (lane == 0) finish_step(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA | gk, tot);
+            if (lane == 0) finish_step(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA | EWM | gk, tot);
             if (gk) gk_update(S, tot, lane);
             if (HEAT && hf_step(A, k - 1)) heat_record(S, G, lane);
         }
@@ -218,7 +224,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         }
         if (!ev && A.rdf_every > 0 && ((A.s0 + k + 1) % A.rdf_every) == 0) {
             __syncthreads();
-            rdf_tile<NS, MULTI>(Ps, S, sm, A.Np, (unsigned *)(own + own_layout(MC, JS, 0).hist));
+            rdf_tile<NS, MULTI>(Ps, S, sm, A.Np, (unsigned *)(own + own_layout(MC, JS, (size_t)A.ews).hist));
         }
         __syncthreads();
         mark(k, 1);
@@ -226,11 +232,39 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
             tph[2] = global_ns();
             S.scal[SC_TPAIR] = (double)(tph[2] - tph[1]);
         }
+        // ---- Ewald reciprocal space: the tasks of the per-phase kernels, spread
+        // over the blocks (structure-factor tasks, sum tasks, force tasks), a grid
+        // barrier after each kind; the reduction then sums the force chunks
+        if constexpr (ELEC == ELEC_EWALD) {
+            unsigned char *ews = own + own_layout(MC, JS, (size_t)A.ews).ews;
+            const int M = S.nsite_q, nsb = ewald::n_site_tasks(M, S.sk_sites);
+            const int nkc = ewald::n_sum_tasks(ewald::n_k(S.kx, S.ky, S.kz));
+            unsigned long long te = tm ? global_ns() : 0ull;  // timing (block 0): each phase until its barrier ends
+            for (int sb = b; sb < nsb; sb += G) ewald::sk_task(Ps, S, sb, ews, threadIdx.x, STEP_THREADS);
+            grid_sync(A.bar, A.err, target, on_timeout);
+            if (tm) { const unsigned long long t = global_ns(); S.scal[SC_TPH9] = (double)(t - te); te = t; }
+            for (int kc = b; kc < nkc; kc += G) ewald::sum_task(S, A.AS, kc, nsb, ews, threadIdx.x, STEP_THREADS);
+            grid_sync(A.bar, A.err, target, on_timeout);
+            if (tm) { const unsigned long long t = global_ns(); S.scal[SC_TPH10] = (double)(t - te); te = t; }
+            const int ng = (M + STEP_THREADS - 1) / STEP_THREADS, nft = ng * S.kchunks;
+            // U_rec and W_rec: the last block, which has no force task when there are fewer than G
+            if (b == G - 1 && warp == 0) ewald::sum_finish(Ps, S, nkc, lane);
+            for (int t = b; t < nft; t += G) {
+                if (S.kx == 8)
+                    ewald::force_task<9>(Ps, S, A.AS, (t % ng) * STEP_THREADS, t / ng, A.ny_per_chunk, ews, threadIdx.x,
+                                         STEP_THREADS);
+                else
+                    ewald::force_task<0>(Ps, S, A.AS, (t % ng) * STEP_THREADS, t / ng, A.ny_per_chunk, ews, threadIdx.x,
+                                         STEP_THREADS);
+            }
+            grid_sync(A.bar, A.err, target, on_timeout);
+            if (tm) S.scal[SC_TPH11] = (double)(global_ns() - te);
+        }
         // ---- reduction unit b: the own molecules
         if (warp == 0) {
-            const OwnLayout ol = own_layout(MC, JS, 0);
+            const OwnLayout ol = own_layout(MC, JS, (size_t)A.ews);
             const RedIO io{part_at(), nullptr, MC, view(), (double *)(own + ol.ui), (int *)(own + ol.np), MC, lo};
-            reduce_unit<true>(Ps, S, io, RED_SUM | RED_LAMBDA | (!ev && gk_step(A, k) ? RED_GK : 0), b, G, lane);
+            reduce_unit<true>(Ps, S, io, RED_SUM | RED_LAMBDA | EWM | (!ev && gk_step(A, k) ? RED_GK : 0), b, G, lane);
         }
         mark(k, 2);
         grid_sync(A.bar, A.err, target, on_timeout);
@@ -240,7 +274,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         __syncthreads();
         if (threadIdx.x == 0) {
             lam_s = lambda_of(Ps, tot);
-            if (ev && b == 0) finish_step(Ps, S, RED_SUM | RED_LAMBDA, tot);  // the scalars of the state as set
+            if (ev && b == 0) finish_step(Ps, S, RED_SUM | RED_LAMBDA | EWM, tot);  // the scalars of the state as set
         }
         __syncthreads();
         // ---- heat flux of this configuration (sampled steps): power pass over
@@ -264,7 +298,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
                 }
                 __syncthreads();
                 if (warp == 0) {
-                    const OwnLayout ol = own_layout(MC, JS, 0);
+                    const OwnLayout ol = own_layout(MC, JS, (size_t)A.ews);
                     heat_unit<true>(Ps, S, hpart_at(), MC, view(), (const double *)(own + ol.ui), MC, lo, b, G, lane);
                 }
                 __syncthreads();
@@ -290,7 +324,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     // back to global memory
     if (A.nsteps > 0 && b == 0 && warp == 0) {
         const int gk = gk_step(A, A.nsteps - 1) ? RED_GK : 0;
-        if (lane == 0) finish_step(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA | gk, tot);
+        if (lane == 0) finish_step(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA | EWM | gk, tot);
         if (gk) gk_update(S, tot, lane);
     }
     if (HEAT && A.nsteps > 0 && hf_step(A, A.nsteps - 1)) {  // uniform over the grid
@@ -299,7 +333,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     }
     // the write-back starts at warp 1, so that block 0's record (warp 0) runs
     // beside it; it reads only block-held data the last barrier ordered
-    const OwnLayout ol = own_layout(MC, JS, 0);
+    const OwnLayout ol = own_layout(MC, JS, (size_t)A.ews);
     const double *ui_s = (const double *)(own + ol.ui);
     const int *np_s = (const int *)(own + ol.np);
     for (int t = (threadIdx.x + STEP_THREADS - 32) % STEP_THREADS; t < nm; t += blockDim.x) {
@@ -330,19 +364,25 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
 // shared memory of the fused step: the staged system, the partner queues of 16
 // warps, the parameter tables, then the own region (state and partials of at
 // most mcap molecules, j-split js) and an RDF histogram of rdf_cells counters
-size_t ms2_step_smem_bytes(int NS, bool dmu, bool multi, int Np, int mcap, int js, int rdf_cells) {
-    const size_t own = own_layout(mcap, js, 0).hist;
+size_t ms2_step_smem_bytes(int NS, bool dmu, bool multi, int Np, int mcap, int js, int rdf_cells, size_t ews) {
+    const size_t own = own_layout(mcap, js, ews).hist;
     return al16(pair_engine::smem_bytes(NS, dmu, multi, Np, STEP_WARPS)) + own + sizeof(unsigned) * (size_t)rdf_cells;
 }
 
 int ms2_step_threads() { return STEP_THREADS; }
 
 // fused-step kernel of a pair-kernel variant, or null where the per-phase
-// kernels are used (Ewald, FP64, 8 site slots)
+// kernels are used (FP64, 8 site slots, other mixtures)
 // (heat: the variant with the heat-flux pass; Massieu sampling and heat flux
 // together run on the per-phase kernels)
 void *ms2_pick_step_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, bool mass, bool heat) {
-    if (elec == ELEC_EWALD || multi || (mass && heat)) return nullptr;
+    if (mass && heat) return nullptr;
+    if (elec == ELEC_EWALD) {  // water with single-site ions (several species); no Massieu or heat flux with Ewald
+        if (multi && ns == 3 && ljm == 1 && qm == 7 && dm == 0 && !mass && !heat)
+            return (void *)&k_step<3, 1u, 7u, 0u, ELEC_EWALD, true>;
+        return nullptr;
+    }
+    if (multi) return nullptr;
     if (ns == 1 && ljm == 1 && qm == 0 && dm == 0 && elec == ELEC_NONE)
         return mass ? (void *)&k_step<1, 1u, 0u, 0u, ELEC_NONE, false, true>
                     : heat ? (void *)&k_step<1, 1u, 0u, 0u, ELEC_NONE, false, false, true>
@@ -362,4 +402,10 @@ cudaError_t ms2_launch_step(void *fn, int grid, size_t smem, cudaStream_t st, co
                             const StepArgs &A) {
     void *args[] = {(void *)&P, (void *)&S, (void *)&A};
     return cudaLaunchCooperativeKernel(fn, grid, STEP_THREADS, args, smem, st);
+}
+
+// bytes of the reciprocal-space task scratch of a fused Ewald block
+size_t ms2_step_ewald_scratch(int kx, int ky, int kz, int ny_per_chunk, int skc) {
+    return std::max(std::max(ewald::sk_smem(kx, ky, kz, skc), ewald::sum_smem()),
+                    ewald::force_smem(kx, kz, ny_per_chunk, STEP_THREADS));
 }

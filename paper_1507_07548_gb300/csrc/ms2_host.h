@@ -96,7 +96,8 @@ ms2_status ms2_validate_models(const ms2_model *models, int n_models, ms2_elec e
 void ms2_launch_residence(cudaStream_t st, const SysParams *P, const DevSys &S, const ResArgs &a);
 size_t ms2_residence_state_doubles(int M);
 // fused step kernel (k_step.cu)
-size_t ms2_step_smem_bytes(int NS, bool dmu, bool multi, int Np, int mcap, int js, int rdf_cells);
+size_t ms2_step_smem_bytes(int NS, bool dmu, bool multi, int Np, int mcap, int js, int rdf_cells, size_t ews);
+size_t ms2_step_ewald_scratch(int kx, int ky, int kz, int ny_per_chunk, int skc);
 int ms2_step_threads();
 void *ms2_pick_step_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, bool mass, bool heat);
 cudaError_t ms2_launch_step(void *fn, int grid, size_t smem, cudaStream_t st, const SysParams *P, const DevSys &S,

@@ -93,6 +93,7 @@ struct DevSys {
     double *acc;                       // running averages (see AC_* below)
     // Ewald
     int nk, kx, ky, kz, nsite_q, kchunks;
+    int sk_sites;                      // sites per structure-factor task
     float *qs;                         // [nsite_q] site charges
     float2 *eik;                       // [3][kmax+1][nsite_q] e^{i n theta}
     double *Sk;                        // [nk][4]: A*Re S, A*Im S, |S|^2 A part, ... (scaled)
@@ -116,6 +117,7 @@ enum {
     SC_JX, SC_JY, SC_JZ,  // electric current flux of the last conductivity sample
     SC_TPAIR,  // fused step: pair-phase time of the last step of a chunk (ns)
     SC_TPH0, SC_TPH1, SC_TPH2, SC_TPH3, SC_TPH4, SC_TPH5, SC_TPH6, SC_TPH7, SC_TPH8,  // fused step: phase times (ns)
+    SC_TPH9, SC_TPH10, SC_TPH11,  // fused Ewald step: the structure-factor, sum and force task phases (ns)
     SC_KERR,   // fused step: a grid-barrier wait timed out (sticky until read)
     SC_HX, SC_HY, SC_HZ,  // heat flux of the last thermal-conductivity sample
     SC_COUNT_
@@ -159,6 +161,9 @@ struct StepArgs {
     unsigned *err;         // sticky timeout flag
     int timing;            // record the phase times of the last step (SC_TPAIR, SC_TPH*, ns)
     int init;              // first evaluate the state as set (site build, forces, energies): after ms2_set_state
+    float2 *AS;            // Ewald: A(k) S(k) of the step (the reciprocal-space force tasks read it)
+    int ny_per_chunk;      // Ewald: ny values per force k chunk
+    int ews;               // Ewald: bytes of the block's reciprocal-space task scratch
     unsigned long long *tmax;  // timing: [3] latest compute-end times over blocks (zero at entry, re-zeroed after use)
 };
 

@@ -379,8 +379,9 @@ class System:
 
     def last_step_phases(self):
         """Fused step, timing on, device ms of the last step: drift, barrier, pair, reduction,
-        barrier, totals, kernel entry to the last step, the whole last step, its end to exit."""
-        out = np.zeros(9)
+        barrier, totals, kernel entry to the last step, the whole last step, its end to exit;
+        Ewald: structure-factor, sum and force task phases (else 0)."""
+        out = np.zeros(12)
         check(lib().ms2_last_step_phases(self.h, _dp(out)))
         return out
 

@@ -45,8 +45,12 @@ def lj32():
     return wl
 
 
-CASES = [water1000, water_ragged, stock, lj32]
-IDS = ["water1000", "water1003", "stockmayer", "lj"]
+def ionic():
+    return snapshot(W.ionic_solution(seed=3), "ionic_N1040")
+
+
+CASES = [water1000, water_ragged, stock, lj32, ionic]
+IDS = ["water1000", "water1003", "stockmayer", "lj", "ionic_ewald"]
 
 
 def rms_rel(a, b):
@@ -122,3 +126,25 @@ def test_largest_rdf_histogram_stays_fused_and_exact():
     for x, y in zip(a.get_state(), b.get_state()):
         assert np.array_equal(np.asarray(x), np.asarray(y))
     assert np.array_equal(a.rdf()[0], b.rdf()[0])
+
+
+def test_fused_ewald_step_matches_oracle():
+    """The ionic solution (Ewald, water + ions) as one fused launch: its
+    reciprocal-space tasks run between grid barriers inside the step kernel."""
+    wl = ionic()
+    s = ms2.System.from_workload(wl)
+    assert s.fused_step() == 1
+    s.step(1)
+    R, q, v, L, st = s.get_state()
+    o = Oracle.from_workload(wl)
+    Ro, qo, vo, Lo, th, _ = o.run_leapfrog(wl.R, wl.q, wl.v, wl.Lang, wl.dt, 1, T0=wl.T)
+    dR = Ro - wl.R
+    assert np.abs((R - wl.R) - dR).max() <= 1e-6 * np.abs(dR).max()
+    assert rms_rel(v, vo) <= 1e-6
+    U, Wv, T, P = s.energy_virial()
+    assert abs(U - th[-1, 0]) <= 1e-6 * abs(th[-1, 0])
+    F, tau = s.forces_torques()
+    Fo, To, to = o.forces(R, q)
+    assert rms_rel(F, Fo) <= 1e-5 and rms_rel(tau, To) <= 1e-5
+    t = s.energy_terms()
+    assert t["U_rec"] == pytest.approx(to["U_rec"], rel=1e-6)
