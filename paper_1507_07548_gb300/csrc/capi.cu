@@ -524,7 +524,7 @@ ms2_status launch_ewald(ms2_system s) {
     if (s->hp.elec != ELEC_EWALD) return MS2_OK;
     DevSys &d = s->d;
     const int K = (2 * d.ky + 1) * (2 * d.kz + 1) * (d.kx + 1), nb = ms2_ewald_skp_blocks(d.nsite_q, d.sk_sites);
-    k_ewald_skp<<<nb, 576, ms2_ewald_skp_smem(d.kx, d.ky, d.kz, d.sk_sites), s->stream>>>(s->dP, d);
+    k_ewald_skp<<<nb, 320, ms2_ewald_skp_smem(d.kx, d.ky, d.kz, d.sk_sites), s->stream>>>(s->dP, d);
     k_ewald_sksum<<<ms2_ewald_sksum_blocks(K), 1024, 0, s->stream>>>(s->dP, d, s->AS, nb);
     {
         void (*fk)(const SysParams *, DevSys, const float2 *, int) =
@@ -815,6 +815,7 @@ static ms2_status setup_ewald(ms2_system s, double alpha, int kx, int ky, int kz
     MS2_CUDA_OK(A((void **)&d.frec, sizeof(float) * d.kchunks * 3 * M));
     // sites per structure-factor task: one round over the fused grid (the same on both paths)
     d.sk_sites = ms2_ewald_sk_sites(M, s->step_grid > 0 ? s->step_grid : 152);
+    d.ew_fpre = (float)(8.0 * 3.141592653589793 * (double)s->hp.coulomb / s->hp.V * 2.0 * 3.141592653589793 / s->hp.L);
     MS2_CUDA_OK(A((void **)&d.skpart, sizeof(float2) * (size_t)ms2_ewald_skp_blocks(M, d.sk_sites) * K));
     MS2_CUDA_OK(A((void **)&d.kblk, sizeof(double) * 2 * ms2_ewald_sksum_blocks(K)));
     MS2_CUDA_OK(A((void **)&s->AS, sizeof(float2) * K));

@@ -20,7 +20,7 @@
 namespace ewald {
 
 constexpr int SKC_MIN = 16;  // sites per structure-factor task at least (S.sk_sites: per system)
-constexpr int NXC = 5;       // nx values per structure-factor work item (the grouping of k into work items
+constexpr int NXC = 9;       // nx values per structure-factor work item (the grouping of k into work items
                              // does not change any partial: each is one thread's sum over the task's sites)
 constexpr int KB = 32;     // k vectors per sum task
 constexpr int SLOTS = 32;  // fixed partial-sum slots of a sum task
@@ -259,7 +259,7 @@ __device__ __forceinline__ void force_task(const SysParams *__restrict__ P, cons
                 fz += (float)nz * syz;
             }
         }
-        const float pre = (float)(8.0 * 3.141592653589793 * (double)P->coulomb / P->V * 2.0 * 3.141592653589793 / P->L) * q;
+        const float pre = S.ew_fpre * q;  // 8 pi C / V * 2 pi / L, formed once on the host
         fx *= pre; fy *= pre; fz *= pre;
     }
     if (s < M) {

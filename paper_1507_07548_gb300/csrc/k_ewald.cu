@@ -13,7 +13,7 @@ int ms2_ewald_skp_blocks(int M, int skc) { return n_site_tasks(M, skc); }
 int ms2_ewald_sksum_blocks(int K) { return n_sum_tasks(K); }
 size_t ms2_ewald_force_smem(int kx, int kz, int ny_per_chunk) { return force_smem(kx, kz, ny_per_chunk, 128); }
 
-__global__ void __launch_bounds__(576) k_ewald_skp(const SysParams *__restrict__ P, DevSys S) {
+__global__ void __launch_bounds__(320) k_ewald_skp(const SysParams *__restrict__ P, DevSys S) {
     extern __shared__ __align__(16) unsigned char ew_smem[];
     sk_task(P, S, blockIdx.x, ew_smem, threadIdx.x, blockDim.x);
 }

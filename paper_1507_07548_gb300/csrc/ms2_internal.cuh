@@ -94,6 +94,7 @@ struct DevSys {
     // Ewald
     int nk, kx, ky, kz, nsite_q, kchunks;
     int sk_sites;                      // sites per structure-factor task
+    float ew_fpre;                     // force prefactor 8 pi C / V * 2 pi / L (FP64 on the host, then FP32)
     float *qs;                         // [nsite_q] site charges
     float2 *eik;                       // [3][kmax+1][nsite_q] e^{i n theta}
     double *Sk;                        // [nk][4]: A*Re S, A*Im S, |S|^2 A part, ... (scaled)
