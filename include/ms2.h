@@ -363,7 +363,8 @@ MS2_API ms2_status ms2_thermal_conductivity(ms2_system sys, double *lambda, doub
  * and returns, in ms: [0] pair kernel, [1] Ewald reciprocal kernels, [2] the whole
  * last step, [3] that step minus [0] and [1].  When the last chunk ran as one
  * fused kernel (ms2_options.fused_step), [2] is the chunk's time per step,
- * [0] the pair phase of its last step (device timer) and [1] is 0. */
+ * [0] the pair phase of its last step and [1] its reciprocal-space task phases
+ * (device timer; 0 without Ewald). */
 MS2_API ms2_status ms2_enable_timing(ms2_system sys, int on);
 /* *fused = 1 if the next chunk of steps runs as the fused cooperative kernel
  * (ms2_options.fused_step and a system it takes; an RDF histogram too large for

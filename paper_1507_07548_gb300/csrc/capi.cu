@@ -1010,12 +1010,15 @@ extern "C" ms2_status ms2_last_step_times(ms2_system s, double out[4]) {
     MS2_CUDA_OK(cudaEventSynchronize(s->ev[4]));
     float a, b, c;
     if (s->last_fused) {  // one kernel per chunk: the step is the chunk's mean, the pair phase from %globaltimer
-        double tp = 0;
-        MS2_CUDA_OK(cudaMemcpy(&tp, s->d.scal + SC_TPAIR, sizeof tp, cudaMemcpyDeviceToHost));
+        double tp[SC_TPH11 - SC_TPAIR + 1];
+        MS2_CUDA_OK(cudaMemcpy(tp, s->d.scal + SC_TPAIR, sizeof tp, cudaMemcpyDeviceToHost));
         MS2_CUDA_OK(cudaEventElapsedTime(&c, s->ev[0], s->ev[4]));
         out[2] = c / std::max(1, s->last_launch_steps);
-        out[0] = tp * 1e-6;
-        out[1] = 0.0;
+        out[0] = tp[0] * 1e-6;
+        // the reciprocal-space task phases (structure factor, sums, forces)
+        out[1] = s->hp.elec == ELEC_EWALD
+                     ? (tp[SC_TPH9 - SC_TPAIR] + tp[SC_TPH10 - SC_TPAIR] + tp[SC_TPH11 - SC_TPAIR]) * 1e-6
+                     : 0.0;
         out[3] = out[2] - out[0];
         return MS2_OK;
     }

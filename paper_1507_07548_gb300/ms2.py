@@ -386,7 +386,8 @@ class System:
         return out
 
     def last_step_times(self):
-        """(pair kernel ms, Ewald kernels ms, whole last step ms, rest ms) of the last enqueued step."""
+        """(pair kernel ms, Ewald kernels ms, whole last step ms, rest ms) of the last enqueued step;
+        a fused chunk gives its pair phase and Ewald task phases (device timer) and its mean step."""
         out = np.zeros(4)
         check(lib().ms2_last_step_times(self.h, _dp(out)))
         return out
