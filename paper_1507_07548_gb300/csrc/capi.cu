@@ -281,6 +281,13 @@ void ms2_fill_params(SysParams &P, const ms2_model *models, int n_models, const 
         for (int a = 0; a < models[m].n_sites; ++a)
             if (P.bdip[m][a][0] != 0 || P.bdip[m][a][1] != 0 || P.bdip[m][a][2] != 0) any_d = true;
     P.has_dipole = any_d;
+    for (int m = 0; m < MS2_MAXSP; ++m) {
+        P.rot[m] = m < n_models && (P.Iinv[m][0] != 0 || P.Iinv[m][1] != 0 || P.Iinv[m][2] != 0);
+        bool pt = m < n_models;
+        for (int a = 0; pt && a < models[m].n_sites; ++a)
+            for (int k = 0; k < 3; ++k) pt = pt && P.bpos[m][a][k] == 0.0 && P.bdip[m][a][k] == 0.0;
+        P.point[m] = pt;
+    }
     P.massieu = o.massieu != 0;
 }
 

@@ -29,6 +29,14 @@ __device__ __forceinline__ void build_row(const SysParams *__restrict__ P, const
     const int c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
     const double acc = 1.0 - 2.0 * (v1 * v1 + v2 * v2), ac1 = 2.0 * (vc * v1 - w * v2), ac2 = 2.0 * (vc * v2 + w * v1);
     const int nsp = P->n_sites[sp];
+    if (P->point[sp]) {  // sites and dipoles at the centre: the offsets are zero in every orientation
+        for (int a = 0; a < NS; ++a) {
+            S.s[(c * NS + a) * N + i] = 0.f;
+            if (S.mu) S.mu[(c * NS + a) * N + i] = 0.f;
+        }
+        if (S.mum) S.mum[c * N + i] = 0.f;
+        return;
+    }
     double md = 0.0;
     for (int a = 0; a < NS; ++a) {
         double o = 0.0, m = 0.0;
@@ -269,21 +277,23 @@ __device__ __forceinline__ void drift_quad(const SysParams *__restrict__ P, cons
             sv.R[c * ld + m] = Rc;
             sv.L[c * ld + m] = Lc;
         }
-        double L[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) L[k] = __shfl_sync(0xffffffffu, Lc, qb | k);
-        const double *Ii = P->Iinv[sp];
-        const bool rot = Ii[0] != 0.0 || Ii[1] != 0.0 || Ii[2] != 0.0;
+        const bool rot = P->rot[sp] != 0;
         // quads of one warp may differ in species: every lane takes the same
-        // shuffles, a non-rotating quad just keeps its quaternion
-        const double q1c = rotate_q_quad(Ii, q, L, dt, rot ? P->quat_iters : 0, c);
-        double qn[4];
+        // shuffles, a non-rotating quad just keeps its quaternion (a warp of
+        // non-rotating quads skips the rotation)
+        if (__any_sync(0xffffffffu, rot)) {
+            double L[3];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) qn[k] = __shfl_sync(0xffffffffu, q1c, qb | k);
-        if (rot) {
+            for (int k = 0; k < 3; ++k) L[k] = __shfl_sync(0xffffffffu, Lc, qb | k);
+            const double q1c = rotate_q_quad(P->Iinv[sp], q, L, dt, rot ? P->quat_iters : 0, c);
+            double qn[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) q[k] = qn[k];
-            if (on) sv.q[c * ld + m] = q1c;
+            for (int k = 0; k < 4; ++k) qn[k] = __shfl_sync(0xffffffffu, q1c, qb | k);
+            if (rot) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) q[k] = qn[k];
+                if (on) sv.q[c * ld + m] = q1c;
+            }
         }
     }
     if (c < 3 && on) build_row(P, S, i, c, q, Rc, sp);
@@ -447,22 +457,27 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
         }
         // kinetic energies: lane c takes component c of v and body component c of L.
         // The state may have been written by another block of a persistent kernel: L2 loads.
+        // (a warp of non-rotating molecules has no rotational terms: hI = 0)
         {
             const double hM = P->half_mass[sp], hI = P->half_Iinv[sp][cc];
-            const double q[4] = {ldv<SH>(sv.q + m), ldv<SH>(sv.q + ld + m), ldv<SH>(sv.q + 2 * ld + m),
-                                 ldv<SH>(sv.q + 3 * ld + m)};
-            double col[3], L[3], tq[3];
-            rot_column(q, cc, col);
+            const bool anyrot = __any_sync(F, P->rot[sp] != 0);
+            double col[3] = {0, 0, 0}, tq[3];
+            double lb = 0.0;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                L[k] = ldv<SH>(sv.L + k * ld + m);
-                tq[k] = __shfl_sync(F, Tc, qb | k);
+            for (int k = 0; k < 3; ++k) tq[k] = __shfl_sync(F, Tc, qb | k);
+            if (anyrot) {
+                const double q[4] = {ldv<SH>(sv.q + m), ldv<SH>(sv.q + ld + m), ldv<SH>(sv.q + 2 * ld + m),
+                                     ldv<SH>(sv.q + 3 * ld + m)};
+                double L[3];
+                rot_column(q, cc, col);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) L[k] = ldv<SH>(sv.L + k * ld + m);
+                lb = col[0] * L[0] + col[1] * L[1] + col[2] * L[2];
             }
             double v = ldv<SH>(sv.v + cc * ld + m);
-            const double lb = col[0] * L[0] + col[1] * L[1] + col[2] * L[2];
             if (c < 3) {
                 x[Q_KTR] = hM * v * v;
-                x[Q_KROT] = hI * lb * lb;
+                x[Q_KROT] = anyrot ? hI * lb * lb : 0.0;
             }
             if (mode & RED_HALFKICK) {  // Verlet: velocities at t + dt, recorded
                 v += 0.5 * P->kick[sp] * Fc;
@@ -470,8 +485,12 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
                 if (c < 3) x[Q_KTR] = x[Q_K1] = hM * v * v;
             } else if (mode & RED_LAMBDA) {  // the kinetic energy after the kick
                 v += P->kick[sp] * Fc;
-                const double lb1 = lb + P->dtk * (col[0] * tq[0] + col[1] * tq[1] + col[2] * tq[2]);
-                if (c < 3) x[Q_K1] = hM * v * v + hI * lb1 * lb1;
+                if (anyrot) {
+                    const double lb1 = lb + P->dtk * (col[0] * tq[0] + col[1] * tq[1] + col[2] * tq[2]);
+                    if (c < 3) x[Q_K1] = hM * v * v + hI * lb1 * lb1;
+                } else if (c < 3) {
+                    x[Q_K1] = hM * v * v;
+                }
             }
         }
         if (base == i_lo) {  // first pass: no add

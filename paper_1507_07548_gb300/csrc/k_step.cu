@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     const SysParams *Ps = (const SysParams *)(own + own_layout(MC, JS, (size_t)A.ews).params);
     auto part_at = [&]() { return (float *)(own + own_layout(MC, JS, (size_t)A.ews).part); };
     auto hpart_at = [&]() { return (float *)(own + own_layout(MC, JS, (size_t)A.ews).hpart); };
-    int *wq = sm.queue + warp * 64;
+    int *wq = sm.queue + warp * QCAP;
     // own state into shared memory
     for (int t = threadIdx.x; t < nm; t += blockDim.x) {
         const StateView sv = view();

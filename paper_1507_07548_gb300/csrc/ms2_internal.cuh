@@ -59,6 +59,8 @@ struct SysParams {
     int ljt[MS2_MAXSP][MS2_MAXS];          // LJ kind or -1
     double mass[MS2_MAXSP];                // molecule mass
     double Iinv[MS2_MAXSP][3];             // inverse principal moments (0: free axis)
+    int rot[MS2_MAXSP];                    // 1: some inverse moment is non-zero (the species rotates)
+    int point[MS2_MAXSP];                  // 1: every site and dipole at the centre (no orientation)
     float c6[MS2_MAXT][MS2_MAXT];          // 4 eps sigma^6 (Lorentz-Berthelot), FP32 rounding
     float c12[MS2_MAXT][MS2_MAXT];         // 4 eps sigma^12, FP32 rounding
     float c6lo[MS2_MAXT][MS2_MAXT];        // remainders: c = hi + lo to ~48 bits, so that

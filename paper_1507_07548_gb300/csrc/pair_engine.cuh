@@ -11,6 +11,9 @@
 namespace pair_engine {
 
 constexpr unsigned FULL = 0xffffffffu;
+// partner queue of a warp: a ring of QCAP tile slots (the scan adds up to 64
+// partners to fewer than 32 waiting ones)
+constexpr int QCAP = 128;
 
 struct Smem {
     uint32_t *tX, *tY, *tZ;
@@ -32,7 +35,7 @@ __device__ __forceinline__ Smem carve(unsigned char *base, int TJ, int wpb) {
     m.tmd = m.tmu + (DMU ? 3 * NS * TJ : 0);
     m.tsp = (int *)(m.tmd + 3 * TJ);
     m.queue = m.tsp + (MULTI ? TJ : 0);
-    m.sq = (float *)(m.queue + wpb * 64);
+    m.sq = (float *)(m.queue + wpb * QCAP);
     m.sql = m.sq + MS2_MAXSP * MS2_MAXS;
     m.sljt = (int *)(m.sql + MS2_MAXSP * MS2_MAXS);
     m.sc6 = (float *)(m.sljt + MS2_MAXSP * MS2_MAXS);
@@ -47,7 +50,7 @@ __host__ __device__ inline size_t smem_bytes(int NS, bool dmu, bool multi, int T
     if (dmu) n += sizeof(float) * 3 * NS * TJ;
     n += sizeof(float) * 3 * TJ;  // molecular dipoles (reaction field; reserved always)
     if (multi) n += sizeof(int) * TJ;
-    n += sizeof(int) * wpb * 64;
+    n += sizeof(int) * wpb * QCAP;
     n += 2 * sizeof(float) * MS2_MAXSP * MS2_MAXS + sizeof(int) * MS2_MAXSP * MS2_MAXS;
     n += 4 * sizeof(float) * MS2_MAXT * MS2_MAXT;
     return n;
@@ -439,31 +442,38 @@ struct PairWarp {
     ++np;
     }
 
-    // scan tile slots [0, tn) (global index of slot 0: t0), partners in batches of 32
+    // scan tile slots [0, tn) (global index of slot 0: t0), partners in batches of 32.
+    // Two groups of 32 candidates are tested per pass (independent chains); the
+    // partners enter the ring queue wq in ascending slot order, so the batches are
+    // those of a scan 32 at a time.
     template <bool HP = false>
     __device__ __forceinline__ void scan(const Smem &sm, int TJ, int t0, int tn, int *wq, int lane) {
-        int qn = 0;
-        for (int base = 0; base < tn; base += 32) {
-            const int jl = base + lane;
-            bool partner = false;
-            if (jl < tn && t0 + jl != i) {
-                const int dx = (int)(sm.tX[jl] - Xi), dy = (int)(sm.tY[jl] - Yi), dz = (int)(sm.tZ[jl] - Zi);
-                partner = lattice_d2(dx, dy, dz) < rc2;
-            }
-            const unsigned m = __ballot_sync(FULL, partner);
-            if (partner) wq[qn + __popc(m & ((1u << lane) - 1u))] = jl;
-            qn += __popc(m);
+        const unsigned below = (1u << lane) - 1u;
+        const int il = i - t0;  // the owner's own slot (may lie outside the range)
+        auto partner = [&](int jl) {
+            if (jl >= tn || jl == il) return false;
+            const int dx = (int)(sm.tX[jl] - Xi), dy = (int)(sm.tY[jl] - Yi), dz = (int)(sm.tZ[jl] - Zi);
+            return lattice_d2(dx, dy, dz) < rc2;
+        };
+        int head = 0, qn = 0;  // first waiting partner in the ring, number waiting
+        for (int base = 0; base < tn; base += 64) {
+            const int j0 = base + lane, j1 = base + 32 + lane;
+            const bool p0 = partner(j0), p1 = partner(j1);
+            const unsigned m0 = __ballot_sync(FULL, p0), m1 = __ballot_sync(FULL, p1);
+            const int n0 = __popc(m0);
+            if (p0) wq[(head + qn + __popc(m0 & below)) & (QCAP - 1)] = j0;
+            if (p1) wq[(head + qn + n0 + __popc(m1 & below)) & (QCAP - 1)] = j1;
+            qn += n0 + __popc(m1);
             __syncwarp();
-            if (qn >= 32) {
-                interact<HP>(sm, TJ, wq[lane]);
-                __syncwarp();
+            while (qn >= 32) {
+                interact<HP>(sm, TJ, wq[(head + lane) & (QCAP - 1)]);
+                __syncwarp();  // the batch is read before later passes overwrite its slots
+                head = (head + 32) & (QCAP - 1);
                 qn -= 32;
-                if (lane < qn) wq[lane] = wq[32 + lane];
-                __syncwarp();
             }
         }
         if (qn > 0) {
-            if (lane < qn) interact<HP>(sm, TJ, wq[lane]);
+            if (lane < qn) interact<HP>(sm, TJ, wq[(head + lane) & (QCAP - 1)]);
             __syncwarp();
         }
     }
