@@ -450,10 +450,11 @@ struct PairWarp {
     __device__ __forceinline__ void scan(const Smem &sm, int TJ, int t0, int tn, int *wq, int lane) {
         const unsigned below = (1u << lane) - 1u;
         const int il = i - t0;  // the owner's own slot (may lie outside the range)
+        // branch-free test: a slot past the range reads the last one and is masked
         auto partner = [&](int jl) {
-            if (jl >= tn || jl == il) return false;
-            const int dx = (int)(sm.tX[jl] - Xi), dy = (int)(sm.tY[jl] - Yi), dz = (int)(sm.tZ[jl] - Zi);
-            return lattice_d2(dx, dy, dz) < rc2;
+            const int js = min(jl, tn - 1);
+            const int dx = (int)(sm.tX[js] - Xi), dy = (int)(sm.tY[js] - Yi), dz = (int)(sm.tZ[js] - Zi);
+            return (jl < tn) & (jl != il) & (lattice_d2(dx, dy, dz) < rc2);
         };
         int head = 0, qn = 0;  // first waiting partner in the ring, number waiting
         for (int base = 0; base < tn; base += 64) {
