@@ -15,10 +15,13 @@ constexpr unsigned FULL = 0xffffffffu;
 // partners to fewer than 32 waiting ones)
 constexpr int QCAP = 128;
 
+// Tile arrays: tP[j] = (lattice centre X, Y, Z, species) of tile molecule j
+// (one 16-byte load), site offsets ts[(k NS + b) TJ + j], point dipoles tmu (same
+// layout) and molecular dipoles tmd[k TJ + j].
 struct Smem {
-    uint32_t *tX, *tY, *tZ;
+    uint4 *tP;
     float *ts, *tmu, *tmd;
-    int *tsp, *queue;
+    int *queue;
     float *sq, *sql, *sc6, *sc12, *sc6l, *sc12l;
     int *sljt;
 };
@@ -27,14 +30,11 @@ struct Smem {
 template <int NS, bool DMU, bool MULTI>
 __device__ __forceinline__ Smem carve(unsigned char *base, int TJ, int wpb) {
     Smem m;
-    m.tX = (uint32_t *)base;
-    m.tY = m.tX + TJ;
-    m.tZ = m.tY + TJ;
-    m.ts = (float *)(m.tZ + TJ);
+    m.tP = (uint4 *)base;
+    m.ts = (float *)(m.tP + TJ);
     m.tmu = m.ts + 3 * NS * TJ;
     m.tmd = m.tmu + (DMU ? 3 * NS * TJ : 0);
-    m.tsp = (int *)(m.tmd + 3 * TJ);
-    m.queue = m.tsp + (MULTI ? TJ : 0);
+    m.queue = (int *)(m.tmd + 3 * TJ);
     m.sq = (float *)(m.queue + wpb * QCAP);
     m.sql = m.sq + MS2_MAXSP * MS2_MAXS;
     m.sljt = (int *)(m.sql + MS2_MAXSP * MS2_MAXS);
@@ -46,10 +46,10 @@ __device__ __forceinline__ Smem carve(unsigned char *base, int TJ, int wpb) {
 }
 
 __host__ __device__ inline size_t smem_bytes(int NS, bool dmu, bool multi, int TJ, int wpb) {
-    size_t n = 3 * sizeof(uint32_t) * TJ + sizeof(float) * 3 * NS * TJ;
+    (void)multi;
+    size_t n = sizeof(uint4) * TJ + sizeof(float) * 3 * NS * TJ;
     if (dmu) n += sizeof(float) * 3 * NS * TJ;
     n += sizeof(float) * 3 * TJ;  // molecular dipoles (reaction field; reserved always)
-    if (multi) n += sizeof(int) * TJ;
     n += sizeof(int) * wpb * QCAP;
     n += 2 * sizeof(float) * MS2_MAXSP * MS2_MAXS + sizeof(int) * MS2_MAXSP * MS2_MAXS;
     n += 4 * sizeof(float) * MS2_MAXT * MS2_MAXT;
@@ -81,16 +81,14 @@ __device__ __forceinline__ void stage_tile(const Smem &sm, const DevSys &S, int 
     for (int k = threadIdx.x; k < tn; k += blockDim.x) {
         const int j = t0 + k;
         // L2 loads (the data may come from another block of the same persistent kernel)
-        sm.tX[k] = __ldcg(S.X + j);
-        sm.tY[k] = __ldcg(S.X + N + j);
-        sm.tZ[k] = __ldcg(S.X + 2 * N + j);
+        sm.tP[k] = make_uint4(__ldcg(S.X + j), __ldcg(S.X + N + j), __ldcg(S.X + 2 * N + j),
+                              MULTI ? (uint32_t)S.species[j] : 0u);
 #pragma unroll
         for (int c = 0; c < 3 * NS; ++c) sm.ts[c * TJ + k] = __ldcg(S.s + c * N + j);
         if (DMU) {
 #pragma unroll
             for (int c = 0; c < 3 * NS; ++c) sm.tmu[c * TJ + k] = __ldcg(S.mu + c * N + j);
         }
-        if (MULTI) sm.tsp[k] = S.species[j];
         if (rfq) {
             sm.tmd[k] = __ldcg(S.mum + j);
             sm.tmd[TJ + k] = __ldcg(S.mum + N + j);
@@ -103,13 +101,10 @@ __device__ __forceinline__ void stage_tile(const Smem &sm, const DevSys &S, int 
 // that holds the whole system
 __device__ __forceinline__ Smem shifted(const Smem &m, int t0) {
     Smem v = m;
-    v.tX += t0;
-    v.tY += t0;
-    v.tZ += t0;
+    v.tP += t0;
     v.ts += t0;
     v.tmu += t0;
     v.tmd += t0;
-    v.tsp += t0;
     return v;
 }
 
@@ -123,21 +118,21 @@ __device__ __forceinline__ void rdf_molecule(const SysParams *__restrict__ P, co
     const int nb = S.rdf_bins, T = P->n_ljt;
     const float l2l = P->lat_to_len, l2 = P->len_to_lat;
     const float rmax2 = S.rdf_rmax2, inv_dr = S.rdf_inv_dr;
-    const uint32_t *tx[3] = {sm.tX, sm.tY, sm.tZ};
-    const int spi = MULTI ? sm.tsp[i] : 0;
+    auto coord = [&](int m, int c) { const uint4 p = sm.tP[m]; return c == 0 ? p.x : (c == 1 ? p.y : p.z); };
+    const int spi = MULTI ? (int)sm.tP[i].w : 0;
     for (int a = 0; a < NS; ++a) {
         const int ta = S.rdf_kind[spi * MS2_MAXS + a];
         if (ta < 0) continue;
         uint32_t Xa[3];
-        for (int c = 0; c < 3; ++c) Xa[c] = tx[c][i] + (uint32_t)__float2int_rn(sm.ts[(c * NS + a) * TJ + i] * l2);
+        for (int c = 0; c < 3; ++c) Xa[c] = coord(i, c) + (uint32_t)__float2int_rn(sm.ts[(c * NS + a) * TJ + i] * l2);
         for (int j = j0; j < n; j += jstep) {
-            const int spj = MULTI ? sm.tsp[j] : 0;
+            const int spj = MULTI ? (int)sm.tP[j].w : 0;
             for (int b = 0; b < NS; ++b) {
                 const int tb = S.rdf_kind[spj * MS2_MAXS + b];
                 if (tb < 0) continue;
                 float r2 = 0.f;
                 for (int c = 0; c < 3; ++c) {
-                    const uint32_t Xb = tx[c][j] + (uint32_t)__float2int_rn(sm.ts[(c * NS + b) * TJ + j] * l2);
+                    const uint32_t Xb = coord(j, c) + (uint32_t)__float2int_rn(sm.ts[(c * NS + b) * TJ + j] * l2);
                     const float d = (float)(int)(Xb - Xa[c]) * l2l;
                     r2 += d * d;
                 }
@@ -245,9 +240,10 @@ struct PairWarp {
     // molecule i from a tile that holds the whole system with stride TJ
     __device__ __forceinline__ void begin_tile(const SysParams *__restrict__ P, const Smem &sm, int TJ, int i_) {
         i = i_;
-        Xi = sm.tX[i];
-        Yi = sm.tY[i];
-        Zi = sm.tZ[i];
+        const uint4 p = sm.tP[i];
+        Xi = p.x;
+        Yi = p.y;
+        Zi = p.z;
 #pragma unroll
         for (int a = 0; a < NS; ++a)
 #pragma unroll
@@ -255,7 +251,7 @@ struct PairWarp {
                 si[a][k] = sm.ts[(k * NS + a) * TJ + i];
                 mui[a][k] = DMU && ((DM >> a) & 1) ? sm.tmu[(k * NS + a) * TJ + i] : 0.f;
             }
-        spi = MULTI ? sm.tsp[i] : 0;
+        spi = MULTI ? (int)p.w : 0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) mdi[k] = (MOLD && rfq) ? sm.tmd[k * TJ + i] : 0.f;
         begin_common(P);
@@ -303,13 +299,14 @@ struct PairWarp {
     // heat-flux power pass; the force-pass accumulators are then dead)
     template <bool HP = false>
     __device__ __forceinline__ void interact(const Smem &sm, int TJ, int jl) {
-    const int dxi = (int)(sm.tX[jl] - Xi), dyi = (int)(sm.tY[jl] - Yi), dzi = (int)(sm.tZ[jl] - Zi);
+    const uint4 pjl = sm.tP[jl];
+    const int dxi = (int)(pjl.x - Xi), dyi = (int)(pjl.y - Yi), dzi = (int)(pjl.z - Zi);
     // lattice difference -> length with the scale split in two floats, so the
     // FP32 rounding of L/2^32 does not scale every displacement the same way
     const float fxi = (float)dxi, fyi = (float)dyi, fzi = (float)dzi;
     const float dx = fmaf(fxi, l2l, fxi * l2l_lo), dy = fmaf(fyi, l2l, fyi * l2l_lo),
                 dz = fmaf(fzi, l2l, fzi * l2l_lo);
-    const int spj = MULTI ? sm.tsp[jl] : 0;
+    const int spj = MULTI ? (int)pjl.w : 0;
     float pj[NS][3], muj[NS][3];
 #pragma unroll
     for (int b = 0; b < NS; ++b) {
@@ -453,7 +450,8 @@ struct PairWarp {
         // branch-free test: a slot past the range reads the last one and is masked
         auto partner = [&](int jl) {
             const int js = min(jl, tn - 1);
-            const int dx = (int)(sm.tX[js] - Xi), dy = (int)(sm.tY[js] - Yi), dz = (int)(sm.tZ[js] - Zi);
+            const uint4 p = sm.tP[js];
+            const int dx = (int)(p.x - Xi), dy = (int)(p.y - Yi), dz = (int)(p.z - Zi);
             return (jl < tn) & (jl != il) & (lattice_d2(dx, dy, dz) < rc2);
         };
         int head = 0, qn = 0;  // first waiting partner in the ring, number waiting
