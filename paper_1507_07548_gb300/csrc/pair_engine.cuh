@@ -167,6 +167,21 @@ struct PairWarp {
     static_assert(!MASS || (DM == 0 && ELEC != ELEC_EWALD), "volume derivatives: LJ and point charges, no Ewald");
     static constexpr bool DMU = DM != 0;
     static constexpr bool MOLD = QM != 0 && (ELEC == ELEC_RF || ELEC < 0);  // molecular-dipole RF term
+    // First site PA of an adjacent pair (PA, PA + 1) that meets every partner site
+    // with the same kinds of term (LJ and/or charge, no point dipole), or -1.  In
+    // the force pass of a single-species LJ / reaction-field kernel the two rows of
+    // site pairs are evaluated together in packed FP32x2 arithmetic (PKF).
+    static constexpr int pair_site() {
+        for (int a = 0; a + 1 < NS; ++a) {
+            const unsigned l0 = (LJM >> a) & 1u, l1 = (LJM >> (a + 1)) & 1u;
+            const unsigned q0 = (QM >> a) & 1u, q1 = (QM >> (a + 1)) & 1u;
+            const unsigned d0 = (DM >> a) & 1u, d1 = (DM >> (a + 1)) & 1u;
+            if (l0 == l1 && q0 == q1 && !d0 && !d1 && (l0 || q0)) return a;
+        }
+        return -1;
+    }
+    static constexpr int PA = pair_site(), PB = PA + 1;
+    static constexpr bool PKF = PA >= 0 && !MULTI && !MASS && (ELEC == ELEC_RF || ELEC == ELEC_NONE);
     int elec;
     bool rfq;
     float C, krf, alpha, tasp, l2l, l2l_lo;
@@ -180,6 +195,10 @@ struct PairWarp {
     uint32_t Xi, Yi, Zi;
     float si[NS][3], mui[NS][3], qih[NS], qil[NS], mdi[3];
     int ljti[NS];
+    // the packed pair (PKF): offsets (s_PA, s_PB) per component, coefficients
+    // (PA, b), (PB, b) per partner site b, and the lane sums of the NEGATED site
+    // forces (-f_PA, -f_PB) per component (no sign flips in the packed terms)
+    float2 sp2[3], pq[NS], pql[NS], pc6[NS], pc12[NS], pc6l[NS], pc12l[NS], fp[3];
     // lane accumulators
     float fa[NS][3], ea[NS][3], ulj, uqq, udd, w, vv, erf_[3];
     int np;
@@ -214,6 +233,17 @@ struct PairWarp {
                     hc6l[a][b] = on ? P->c6lo[ia][ib] : 0.f;
                     hc12l[a][b] = on ? P->c12lo[ia][ib] : 0.f;
                 }
+            if constexpr (PKF) {
+#pragma unroll
+                for (int b = 0; b < NS; ++b) {
+                    pq[b] = make_float2(hq[PA][b], hq[PB][b]);
+                    pql[b] = make_float2(hql[PA][b], hql[PB][b]);
+                    pc6[b] = make_float2(hc6[PA][b], hc6[PB][b]);
+                    pc12[b] = make_float2(hc12[PA][b], hc12[PB][b]);
+                    pc6l[b] = make_float2(hc6l[PA][b], hc6l[PB][b]);
+                    pc12l[b] = make_float2(hc12l[PA][b], hc12l[PB][b]);
+                }
+            }
         }
     }
 
@@ -268,6 +298,13 @@ struct PairWarp {
         for (int a = 0; a < NS; ++a)
 #pragma unroll
             for (int k = 0; k < 3; ++k) fa[a][k] = ea[a][k] = 0.f;
+        if constexpr (PKF) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                sp2[k] = make_float2(si[PA][k], si[PB][k]);
+                fp[k] = make_float2(0.f, 0.f);
+            }
+        }
         ulj = uqq = udd = w = vv = 0.f;
         erf_[0] = erf_[1] = erf_[2] = 0.f;
         np = 0;
@@ -322,8 +359,64 @@ struct PairWarp {
     // intramolecular part -2 sum_a s_ia.F_ia once per molecule in finish().
     float wsite = 0.f, wvv = 0.f, pw = 0.f;  // pw: the power P_kl (HP)
     const float dd2 = MASS ? dx * dx + dy * dy + dz * dz : 0.f;
+    constexpr bool PK = PKF && !HP;
 #pragma unroll
     for (int a = 0; a < NS; ++a) {
+        if (PK && a == PB) continue;
+        if (PK && a == PA) {
+            // rows PA and PB together (FP32x2, lane .x = PA, .y = PB): the scalar
+            // operations below term by term, the force factor negated; row PB's
+            // energy and virial terms are added after row PA's, in partner-site order
+            const float2 m1 = make_float2(-1.f, -1.f);
+            float dl[NS], dq[NS], dgv[NS], dr2[NS];
+#pragma unroll
+            for (int b = 0; b < NS; ++b) {
+                const bool mlj = (LJM >> PA) & (LJM >> b) & 1u;
+                const bool mq = ((QM >> PA) & (QM >> b) & 1u) && elec != ELEC_NONE;
+                if (!(mlj || mq)) continue;
+                const float2 rx = __ffma2_rn(sp2[0], m1, make_float2(pj[b][0], pj[b][0]));
+                const float2 ry = __ffma2_rn(sp2[1], m1, make_float2(pj[b][1], pj[b][1]));
+                const float2 rz = __ffma2_rn(sp2[2], m1, make_float2(pj[b][2], pj[b][2]));
+                const float2 r2 = __ffma2_rn(rz, rz, __ffma2_rn(ry, ry, __fmul2_rn(rx, rx)));
+                float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                const float2 nt = __fmul2_rn(__fmul2_rn(make_float2(-0.5f, -0.5f), r2), rinv);
+                rinv = __ffma2_rn(rinv, __ffma2_rn(nt, rinv, make_float2(0.5f, 0.5f)), rinv);
+                const float2 rinv2 = __fmul2_rn(rinv, rinv);
+                float2 ng = make_float2(0.f, 0.f);  // -g
+                if (mlj) {
+                    const float2 r6 = __fmul2_rn(__fmul2_rn(rinv2, rinv2), rinv2), r12 = __fmul2_rn(r6, r6);
+                    const float2 t6 = __ffma2_rn(pc6[b], r6, __fmul2_rn(pc6l[b], r6));
+                    const float2 t12 = __ffma2_rn(pc12[b], r12, __fmul2_rn(pc12l[b], r12));
+                    const float2 tl = __ffma2_rn(t6, m1, t12);
+                    ulj += tl.x;
+                    dl[b] = tl.y;
+                    ng = __fmul2_rn(__ffma2_rn(make_float2(12.f, 12.f), t12, __fmul2_rn(make_float2(-6.f, -6.f), t6)),
+                                    rinv2);
+                    wsite = fmaf(ng.x, r2.x, wsite);
+                    dgv[b] = ng.y;
+                    dr2[b] = r2.y;
+                }
+                if (mq) {  // bare Coulomb (reaction field)
+                    const float2 eq = __ffma2_rn(pq[b], rinv, __fmul2_rn(pql[b], rinv));
+                    uqq += eq.x;
+                    dq[b] = eq.y;
+                    const float2 ngq = __fmul2_rn(eq, rinv2);
+                    ng = mlj ? __fadd2_rn(ng, ngq) : ngq;
+                }
+                fp[0] = __ffma2_rn(ng, rx, fp[0]);
+                fp[1] = __ffma2_rn(ng, ry, fp[1]);
+                fp[2] = __ffma2_rn(ng, rz, fp[2]);
+            }
+#pragma unroll
+            for (int b = 0; b < NS; ++b) {
+                const bool mlj = (LJM >> PA) & (LJM >> b) & 1u;
+                const bool mq = ((QM >> PA) & (QM >> b) & 1u) && elec != ELEC_NONE;
+                if (mlj) ulj += dl[b];
+                if (mq) uqq += dq[b];
+                if (mlj) wsite = fmaf(dgv[b], dr2[b], wsite);
+            }
+            continue;
+        }
 #pragma unroll
         for (int b = 0; b < NS; ++b) {
             const bool mlj = (LJM >> a) & (LJM >> b) & 1u;
@@ -331,7 +424,8 @@ struct PairWarp {
             const bool md = (DM >> a) & (DM >> b) & 1u;
             if (!(mlj || (mq && elec != ELEC_NONE) || (md && elec != ELEC_NONE))) continue;
             const float rx = pj[b][0] - si[a][0], ry = pj[b][1] - si[a][1], rz = pj[b][2] - si[a][2];
-            float r2 = rx * rx + ry * ry + rz * rz;
+            // (explicit operation order, shared with the packed rows above)
+            float r2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
             if (MULTI) r2 = fmaxf(r2, 1e-12f);
             // rsqrt approximation + one Newton step: unbiased to ~1 ulp
             float rinv = rsqrtf(r2);
@@ -360,7 +454,7 @@ struct PairWarp {
                 const float r6 = rinv2 * rinv2 * rinv2, r12 = r6 * r6;
                 const float t6 = fmaf(c6, r6, c6l * r6), t12 = fmaf(c12, r12, c12l * r12);
                 ulj += t12 - t6;
-                g += (6.f * t6 - 12.f * t12) * rinv2;
+                g = fmaf(-12.f, t12, 6.f * t6) * rinv2;
                 gv = g;
                 if (MASS) hh += (168.f * t12 - 48.f * t6) * (rinv2 * rinv2);
             }
@@ -385,9 +479,9 @@ struct PairWarp {
                     const float bu = ec * rinv, bg = -(ec * rinv + tasp * ex) * rinv2;
                     uqq += fmaf(cqq, bu, cql * bu);
                     gq = fmaf(cqq, bg, cql * bg);
-                    gv += gq;
+                    gv = mlj ? gv + gq : gq;
                 }
-                g += gq;
+                g = mlj ? g + gq : gq;
                 if (MASS) hh -= 3.f * gq * rinv2;  // bare Coulomb: h = 3 C q q / r^5
             }
             if (md && elec != ELEC_NONE) {
@@ -485,6 +579,13 @@ struct PairWarp {
 
     // fixed-tree warp reduction; the result is valid in lane 0
     __device__ __forceinline__ PairOut finish(int lane) {
+        if constexpr (PKF) {  // the packed rows' negated sums
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                fa[PA][k] = 0.f - fp[k].x;
+                fa[PB][k] = 0.f - fp[k].y;
+            }
+        }
 #pragma unroll
         for (int a = 0; a < NS; ++a)
 #pragma unroll
