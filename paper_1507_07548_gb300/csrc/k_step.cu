@@ -133,6 +133,16 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     auto part_at = [&]() { return (float *)(own + own_layout(MC, JS, (size_t)A.ews).part); };
     auto hpart_at = [&]() { return (float *)(own + own_layout(MC, JS, (size_t)A.ews).hpart); };
     int *wq = sm.queue + warp * QCAP;
+    // prologue: every load is issued before anything waits on one (after an L2
+    // flush each dependent round trip goes to DRAM): the thermostat factor, the
+    // parameter copy and the own state; the tables then come from the copy
+    double lam0 = 0.0;
+    if (threadIdx.x == 0) lam0 = __ldcg(S.scal + SC_LAMBDA);
+    {
+        const int4 *src = (const int4 *)P;
+        int4 *dst = (int4 *)(own + own_layout(MC, JS, (size_t)A.ews).params);
+        for (int k = threadIdx.x; k < (int)(sizeof(SysParams) / sizeof(int4)); k += blockDim.x) dst[k] = src[k];
+    }
     // own state into shared memory
     for (int t = threadIdx.x; t < nm; t += blockDim.x) {
         const StateView sv = view();
@@ -149,14 +159,10 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         for (int c = 0; c < 4; ++c) sv.q[c * MC + t] = __ldcg(S.q + c * N + i);
         ((int *)sv.spc)[t] = S.species[i];
     }
-    {
-        const int4 *src = (const int4 *)P;
-        int4 *dst = (int4 *)(own + own_layout(MC, JS, (size_t)A.ews).params);
-        for (int k = threadIdx.x; k < (int)(sizeof(SysParams) / sizeof(int4)); k += blockDim.x) dst[k] = src[k];
-    }
-    load_tables<MULTI>(P, sm);
+    __syncthreads();
+    load_tables<MULTI>(Ps, sm);
     Eng e;
-    e.setup(P);
+    e.setup(Ps);
     if (b == 0 && threadIdx.x == 0) *A.bar_next = 0u;
     unsigned target = 0;
     auto on_timeout = [&]() { S.scal[SC_KERR] = 1.0; };
@@ -170,7 +176,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
             if (threadIdx.x == 0) atomicMax(A.tmax + slot, global_ns());
         }
     };
-    if (threadIdx.x == 0) lam_s = __ldcg(S.scal + SC_LAMBDA);
+    if (threadIdx.x == 0) lam_s = lam0;
     __syncthreads();
     // k = -1 (after ms2_set_state): the state as set is evaluated first -- site
     // build instead of the drift, then partner search, forces, unit reduction,
