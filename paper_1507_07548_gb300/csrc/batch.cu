@@ -160,7 +160,8 @@ __global__ void __launch_bounds__(BT, 1) k_mstep(MsArgs A) {
             const double t = warp_sum8(x, lane);
             if ((lane & 3) == 0 && (lane >> 2) < Q_N) wtot[warp][lane >> 2] = t;
             __syncwarp();
-            if (lane == 0) finish_step(en.P, en.S, RED_SUM | RED_RECORD | RED_LAMBDA, wtot[warp]);
+            finish_step_warp(en.P, en.S, RED_SUM | RED_RECORD | RED_LAMBDA, wtot[warp], lane, en.S.acc,
+                             global_consts(en.S));
             __syncwarp();
         }
         grid_sync(A.bar, A.err, target, on_timeout);

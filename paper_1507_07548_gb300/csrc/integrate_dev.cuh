@@ -150,71 +150,119 @@ __device__ __forceinline__ void rot_column(const double q[4], int c, double col[
 // rotation), kinetic energy after the kick, non-finite force flag
 enum { Q_U = 0, Q_W, Q_KTR, Q_KROT, Q_K1, Q_BAD, Q_VV, Q_N };  // Q_VV: d2U/dV2 owner sums
 
-// final fixed-order scalars of a step; run by the last block
-__device__ __forceinline__ void finish_step(const SysParams *__restrict__ P, const DevSys &S, int mode, const double *tot) {
+// Final fixed-order scalars of a step (potential energy, virial, T, P, the
+// running averages, the next thermostat factor), by a whole warp: every lane
+// calls it.  The scalars are formed on one instruction stream with
+// lane-selected operands, so that independent values share FP64 instructions
+// (an FP64 warp instruction costs an SMSP the same for one active lane or 32):
+// lanes 0-3 form U, W and the kinetic energies, lanes 0-1 T and P, and lane
+// k < AC_COUNT_ updates running sum k as acc_k + f_k g_k.  Every path calls
+// this one function, so they agree to the bit.  acc holds the running sums and
+// kc the launch constants (U_const, U_lrc, W_bg, P_lrc): S.acc and global_consts
+// on the per-phase paths, a block's shared-memory copies in the fused step.
+struct StepConsts {
+    double uconst, ulrc, wbg, plrc;
+};
+__device__ __forceinline__ StepConsts global_consts(const DevSys &S) {
+    return StepConsts{S.scal[SC_UCONST], S.scal[SC_ULRC], S.scal[SC_WBG], S.scal[SC_PLRC]};
+}
+__device__ __forceinline__ void finish_step_warp(const SysParams *__restrict__ P, const DevSys &S, int mode,
+                                                 const double *tot, int lane, double *acc, const StepConsts &kc) {
+    const unsigned FM = 0xffffffffu;
     double *sc = S.scal;
-    const double ikc = P->inv_kconv;
-    if (mode & RED_SUM) {
-        const double U = 0.5 * tot[Q_U] + ((mode & RED_EWALD) ? sc[SC_UREC] : 0.0) + sc[SC_UCONST] + sc[SC_ULRC];
-        const double W = 0.5 * tot[Q_W] + ((mode & RED_EWALD) ? sc[SC_WREC_AT] : 0.0) + sc[SC_WBG];
-        sc[SC_UTOT] = U;
-        sc[SC_WTOT] = W;
-        sc[SC_UNSTABLE] = tot[Q_BAD] > 0 ? 1.0 : 0.0;
+    const bool sum = mode & RED_SUM, ew = mode & RED_EWALD, ms = sum && P->massieu, rec = mode & RED_RECORD;
+    const double plrc = kc.plrc;
+    // U = 0.5 t_U + urec + uconst + ulrc,  W = 0.5 t_W + wrec + wbg,  K = t_K / kconv
+    double m = 0.0, t = 0.0, p = 0.0, q = 0.0, r = 0.0;
+    if (lane == 0) { m = 0.5; t = tot[Q_U]; p = ew ? sc[SC_UREC] : 0.0; q = kc.uconst; r = kc.ulrc; }
+    if (lane == 1) { m = 0.5; t = tot[Q_W]; p = ew ? sc[SC_WREC_AT] : 0.0; q = kc.wbg; }
+    if (lane == 2) { m = tot[Q_KTR]; t = P->inv_kconv; }
+    if (lane == 3) { m = tot[Q_KROT]; t = P->inv_kconv; }
+    double v = (fma(m, t, p) + q) + r;
+    double U = __shfl_sync(FM, v, 0), W = __shfl_sync(FM, v, 1);
+    const double ketr = __shfl_sync(FM, v, 2), kerot = __shfl_sync(FM, v, 3);
+    if (!sum) {  // the stored configuration scalars
+        U = sc[SC_UTOT];
+        W = sc[SC_WTOT];
     }
-    if ((mode & RED_SUM) && P->massieu) {  // volume derivatives of this configuration (Sec. 2, Eq. 1)
-        sc[SC_UV] = -sc[SC_WTOT] * (1.0 / 3.0) * P->inv_V - sc[SC_PLRC];
-        sc[SC_UVV] = 0.5 * tot[Q_VV] * (1.0 / 9.0) * P->inv_V * P->inv_V + 2.0 * sc[SC_PLRC] * P->inv_V;
+    // T = (2 (K_tr + K_rot)) / ndof on lane 0, P = (2 K_tr + W) / (3 V) + P_lrc on lane 1
+    const double c1 = lane == 1 ? 2.0 : 1.0, c2 = lane == 1 ? W : kerot;
+    const double k1 = lane == 1 ? (1.0 / 3.0) : 2.0, k2 = lane == 1 ? P->inv_V : P->inv_ndof, k3 = lane == 1 ? plrc : 0.0;
+    const double tp = fma(k1 * fma(c1, ketr, c2), k2, k3);
+    const double T = __shfl_sync(FM, tp, 0), Pr = __shfl_sync(FM, tp, 1);
+    double UV = 0.0, UVV = 0.0;
+    if (ms) {  // volume derivatives of this configuration (Sec. 2, Eq. 1)
+        UV = fma(-W * (1.0 / 3.0), P->inv_V, -plrc);
+        UVV = fma(0.5 * tot[Q_VV] * (1.0 / 9.0) * P->inv_V, P->inv_V, 2.0 * plrc * P->inv_V);
+    } else if (rec && P->massieu) {
+        UV = sc[SC_UV];
+        UVV = sc[SC_UVV];
     }
-    if (mode & RED_GK) {
-        sc[SC_JX] = tot[Q_N];
-        sc[SC_JY] = tot[Q_N + 1];
-        sc[SC_JZ] = tot[Q_N + 2];
-    }
-    const double ketr = tot[Q_KTR] * ikc, kerot = tot[Q_KROT] * ikc;
-    sc[SC_KETR_NOW] = ketr;
-    sc[SC_KEROT_NOW] = kerot;
-    sc[SC_T] = 2.0 * (ketr + kerot) * P->inv_ndof;
-    sc[SC_P] = (2.0 * ketr + sc[SC_WTOT]) * (1.0 / 3.0) * P->inv_V + sc[SC_PLRC];
-    if (mode & RED_RECORD) {
-        double *ac = S.acc;
-        ac[AC_N] += 1.0;
-        ac[AC_U] += sc[SC_UTOT];
-        ac[AC_P] += sc[SC_P];
-        ac[AC_T] += sc[SC_T];
-        ac[AC_BN] += 1.0;
-        ac[AC_BU] += sc[SC_UTOT];
-        ac[AC_BP] += sc[SC_P];
-        if (P->massieu) {  // Massieu-derivative moments, shifted by the first sample
-            if (ac[AC_MN] == 0.0) {
-                ac[AC_MU0] = sc[SC_UTOT];
-                ac[AC_MV0] = sc[SC_UV];
-            }
-            const double x = sc[SC_UTOT] - ac[AC_MU0], y = sc[SC_UV] - ac[AC_MV0], w = sc[SC_UVV];
-            ac[AC_MN] += 1.0;
-            ac[AC_MX] += x;
-            ac[AC_MX2] += x * x;
-            ac[AC_MX3] += x * x * x;
-            ac[AC_MY] += y;
-            ac[AC_MY2] += y * y;
-            ac[AC_MXY] += x * y;
-            ac[AC_MX2Y] += x * x * y;
-            ac[AC_MXY2] += x * y * y;
-            ac[AC_MW] += w;
-            ac[AC_MXW] += x * w;
-        }
-        if (ac[AC_BN] >= 100.0) {  // close a block of 100 steps
-            const double bu = ac[AC_BU] * 0.01, bp = ac[AC_BP] * 0.01;
-            ac[AC_NB] += 1.0;
-            ac[AC_SBU] += bu;
-            ac[AC_SBU2] += bu * bu;
-            ac[AC_SBP] += bp;
-            ac[AC_SBP2] += bp * bp;
-            ac[AC_BN] = ac[AC_BU] = ac[AC_BP] = 0.0;
-        }
-    }
+    double lam = 1.0;
     if (mode & RED_LAMBDA) {  // isokinetic factor sqrt(T0 / T') for the next drift (as lambda_of)
         const double x = P->lam_c * tot[Q_K1];
-        sc[SC_LAMBDA] = (P->thermostat && x > 0) ? rsqrt_fp64(x) : 1.0;
+        lam = (P->thermostat && x > 0) ? rsqrt_fp64(x) : 1.0;
+    }
+    if (rec) {
+        double a = lane < AC_COUNT_ ? acc[lane] : 0.0;
+        double f = 0.0, g = 0.0;
+        if (lane == AC_N || lane == AC_BN) { f = 1.0; g = 1.0; }
+        if (lane == AC_U || lane == AC_BU) { f = 1.0; g = U; }
+        if (lane == AC_P || lane == AC_BP) { f = 1.0; g = Pr; }
+        if (lane == AC_T) { f = 1.0; g = T; }
+        if (P->massieu) {  // Massieu-derivative moments, shifted by the first sample
+            const double mn = __shfl_sync(FM, a, AC_MN);
+            const double mu0 = mn == 0.0 ? U : __shfl_sync(FM, a, AC_MU0);
+            const double mv0 = mn == 0.0 ? UV : __shfl_sync(FM, a, AC_MV0);
+            if (lane == AC_MU0) a = mu0;
+            if (lane == AC_MV0) a = mv0;
+            const double x = U - mu0, y = UV - mv0, w = UVV, xx = x * x, xy = x * y;
+            if (lane == AC_MN) { f = 1.0; g = 1.0; }
+            if (lane == AC_MX) { f = 1.0; g = x; }
+            if (lane == AC_MX2) { f = x; g = x; }
+            if (lane == AC_MX3) { f = xx; g = x; }
+            if (lane == AC_MY) { f = 1.0; g = y; }
+            if (lane == AC_MY2) { f = y; g = y; }
+            if (lane == AC_MXY) { f = x; g = y; }
+            if (lane == AC_MX2Y) { f = xx; g = y; }
+            if (lane == AC_MXY2) { f = xy; g = y; }
+            if (lane == AC_MW) { f = 1.0; g = w; }
+            if (lane == AC_MXW) { f = x; g = w; }
+        }
+        a = fma(f, g, a);
+        if (__shfl_sync(FM, a, AC_BN) >= 100.0) {  // close a block of 100 steps
+            const double bu = __shfl_sync(FM, a, AC_BU) * 0.01, bp = __shfl_sync(FM, a, AC_BP) * 0.01;
+            double f2 = 0.0, g2 = 0.0;
+            if (lane == AC_NB) { f2 = 1.0; g2 = 1.0; }
+            if (lane == AC_SBU) { f2 = 1.0; g2 = bu; }
+            if (lane == AC_SBU2) { f2 = bu; g2 = bu; }
+            if (lane == AC_SBP) { f2 = 1.0; g2 = bp; }
+            if (lane == AC_SBP2) { f2 = bp; g2 = bp; }
+            a = fma(f2, g2, a);
+            if (lane == AC_BN || lane == AC_BU || lane == AC_BP) a = 0.0;
+        }
+        if (lane < AC_COUNT_) acc[lane] = a;
+    }
+    if (lane == 0) {
+        if (sum) {
+            sc[SC_UTOT] = U;
+            sc[SC_WTOT] = W;
+            sc[SC_UNSTABLE] = tot[Q_BAD] > 0 ? 1.0 : 0.0;
+        }
+        if (ms) {
+            sc[SC_UV] = UV;
+            sc[SC_UVV] = UVV;
+        }
+        if (mode & RED_GK) {
+            sc[SC_JX] = tot[Q_N];
+            sc[SC_JY] = tot[Q_N + 1];
+            sc[SC_JZ] = tot[Q_N + 2];
+        }
+        sc[SC_KETR_NOW] = ketr;
+        sc[SC_KEROT_NOW] = kerot;
+        sc[SC_T] = T;
+        sc[SC_P] = Pr;
+        if (mode & RED_LAMBDA) sc[SC_LAMBDA] = lam;
     }
 }
 
@@ -656,7 +704,7 @@ __device__ __forceinline__ void heat_record(const DevSys &S, int nvb, int lane) 
     acf_update(S.hf, S.hf_lags, j0, j1, j2, lane);
 }
 
-// isokinetic factor sqrt(T0 / T') from the kicked kinetic energy (as finish_step)
+// isokinetic factor sqrt(T0 / T') from the kicked kinetic energy (as finish_step_warp)
 __device__ __forceinline__ double lambda_of(const SysParams *__restrict__ P, const double *tot) {
     const double x = P->lam_c * tot[Q_K1];  // T' / T0
     return (P->thermostat && x > 0) ? rsqrt_fp64(x) : 1.0;

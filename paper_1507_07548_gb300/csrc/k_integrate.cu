@@ -48,10 +48,8 @@ __global__ void __launch_bounds__(128) k_reduce(const SysParams *__restrict__ P,
     __shared__ double tot[MS2_NRED];
     reduce_totals(S, S.nunits, tot, (mode & RED_GK) ? Q_N + 3 : Q_N);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        finish_step(P, S, mode, tot);
-        *S.counter = 0u;
-    }
+    if (threadIdx.x < 32) finish_step_warp(P, S, mode, tot, threadIdx.x, S.acc, global_consts(S));
+    if (threadIdx.x == 0) *S.counter = 0u;
     if ((mode & RED_GK) && threadIdx.x < 32) gk_update(S, tot, threadIdx.x);
 }
 

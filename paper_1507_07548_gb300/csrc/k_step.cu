@@ -21,7 +21,7 @@
 //   -- grid barrier --
 //
 // The phases are the device functions of the per-phase kernels (drift_quad,
-// PairWarp, reduce_unit, reduce_totals, finish_step) and the per-phase path of a
+// PairWarp, reduce_unit, reduce_totals, finish_step_warp) and the per-phase path of a
 // fusable system uses the same decomposition (j-ranges, tile segmentation,
 // reduction units = the G block ranges), so a chunk run here is bitwise
 // identical to the same chunk run as separate kernels.  What the fusion saves
@@ -138,6 +138,14 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     // parameter copy and the own state; the tables then come from the copy
     double lam0 = 0.0;
     if (threadIdx.x == 0) lam0 = __ldcg(S.scal + SC_LAMBDA);
+    // block 0 records the steps: its running sums and the launch constants stay
+    // in shared memory for the launch (written back at the end)
+    __shared__ double acc_s[AC_COUNT_];
+    __shared__ StepConsts kc_s;
+    if (b == 0) {
+        if (threadIdx.x < AC_COUNT_) acc_s[threadIdx.x] = __ldcg(S.acc + threadIdx.x);
+        if (threadIdx.x == 32) kc_s = global_consts(S);
+    }
     {
         const int4 *src = (const int4 *)P;
         int4 *dst = (int4 *)(own + own_layout(MC, JS, (size_t)A.ews).params);
@@ -209,7 +217,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         // item unless 16 are due
         if (k > 0 && b == 0 && warp == STEP_WARPS - 1) {
             const int gk = gk_step(A, k - 1) ? RED_GK : 0;
-            if (lane == 0) finish_step(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA | EWM | gk, tot);
+            finish_step_warp(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA | EWM | gk, tot, lane, acc_s, kc_s);
             if (gk) gk_update(S, tot, lane);
             if (HEAT && hf_step(A, k - 1)) heat_record(S, G, lane);
         }
@@ -278,9 +286,9 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         // ---- totals in every block; thermostat factor for the next drift
         reduce_totals(S, G, tot, !ev && gk_step(A, k) ? Q_N + 3 : Q_N);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            lam_s = lambda_of(Ps, tot);
-            if (ev && b == 0) finish_step(Ps, S, RED_SUM | RED_LAMBDA | EWM, tot);  // the scalars of the state as set
+        if (warp == 0) {
+            if (lane == 0) lam_s = lambda_of(Ps, tot);
+            if (ev && b == 0) finish_step_warp(Ps, S, RED_SUM | RED_LAMBDA | EWM, tot, lane, acc_s, kc_s);  // the scalars of the state as set
         }
         __syncthreads();
         // ---- heat flux of this configuration (sampled steps): power pass over
@@ -330,9 +338,10 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     // back to global memory
     if (A.nsteps > 0 && b == 0 && warp == 0) {
         const int gk = gk_step(A, A.nsteps - 1) ? RED_GK : 0;
-        if (lane == 0) finish_step(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA | EWM | gk, tot);
+        finish_step_warp(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA | EWM | gk, tot, lane, acc_s, kc_s);
         if (gk) gk_update(S, tot, lane);
     }
+    if (b == 0 && warp == 0 && lane < AC_COUNT_) S.acc[lane] = acc_s[lane];  // the launch's running sums
     if (HEAT && A.nsteps > 0 && hf_step(A, A.nsteps - 1)) {  // uniform over the grid
         grid_sync(A.bar, A.err, target, on_timeout);
         if (b == 0 && warp == 0) heat_record(S, G, lane);
