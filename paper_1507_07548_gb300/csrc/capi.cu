@@ -994,9 +994,13 @@ extern "C" ms2_status ms2_step_kernel(ms2_system s, int *fused) {
     return MS2_OK;
 }
 
+// the system scalars, through a page-locked buffer (a copy into pageable memory
+// takes the driver's staged path)
 static ms2_status read_scalars(ms2_system s, double *sc) {
-    MS2_CUDA_OK(cudaMemcpyAsync(sc, s->d.scal, sizeof(double) * SC_COUNT_, cudaMemcpyDeviceToHost, s->stream));
+    if (!s->hscal) MS2_CUDA_OK(cudaMallocHost((void **)&s->hscal, sizeof(double) * SC_COUNT_));
+    MS2_CUDA_OK(cudaMemcpyAsync(s->hscal, s->d.scal, sizeof(double) * SC_COUNT_, cudaMemcpyDeviceToHost, s->stream));
     MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
+    std::memcpy(sc, s->hscal, sizeof(double) * SC_COUNT_);
     return MS2_OK;
 }
 
@@ -1046,6 +1050,7 @@ extern "C" ms2_status ms2_destroy_system(ms2_system s) {
     for (int k = 0; k < 5; ++k)
         if (s->ev[k]) cudaEventDestroy(s->ev[k]);
     if (s->pinned) cudaFreeHost(s->pinned);
+    if (s->hscal) cudaFreeHost(s->hscal);
     for (int k = 0; k < 2; ++k)
         if (s->up_ev[k]) cudaEventDestroy(s->up_ev[k]);
     s->al.release_all();

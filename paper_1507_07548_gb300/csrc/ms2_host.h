@@ -74,6 +74,7 @@ struct ms2_system_s {
     // page-locked staging: two upload buffers of 13N doubles (used alternately,
     // each guarded by the event of its last copy) and one download buffer of 13N
     double *pinned = nullptr;
+    double *hscal = nullptr;   // page-locked copy target of the system scalars
     cudaEvent_t up_ev[2] = {nullptr, nullptr};
     int up_k = 0;
     // set_state leaves forces, energies and site build stale; the next query
