@@ -57,6 +57,17 @@ struct BatchEntry {
     int units;        // reduction units: ceil(N / UNIT)
     int rdf_every;
     long long step0;  // step counter of the system before this launch
+    // Candidate lists with a skin: per molecule, the molecules within r_c + skin
+    // at the last build, in ascending order.  The exact centre test runs on them
+    // each step until some molecule of the system has moved more than skin / 2
+    // since the build (then no other molecule can have come within r_c), so the
+    // partners are those of the full scan, in its order.  lcap = 0: full scans.
+    uint16_t *nl;                 // [N][lcap]
+    int *ncnt;                    // [N] candidates at the build (> lcap: that owner scans all)
+    uint32_t *Xb;                 // [3][N] lattice centres at the build
+    int *nflag;                   // non-zero: rebuild in this step's pair phase
+    int lcap;
+    unsigned long long rs2, sk2;  // (r_c + skin)^2 and (skin / 2)^2, lattice units, with margins
 };
 
 // launch arguments of one kind (device tables built on the host)
@@ -103,6 +114,17 @@ __global__ void __launch_bounds__(BT, 1) k_mstep(MsArgs A) {
             const bool on = i < en.S.N;
             const double lam = __ldcg(en.S.scal + SC_LAMBDA);
             drift_quad<false>(en.P, en.S, global_view(en.S), i, i, on, lane & 3, false, lam);
+            if (en.lcap) {  // displacement since the list build (lane c: component c), summed over the quad
+                const int c = lane & 3;
+                unsigned long long d2 = 0;
+                if (on && c < 3) {
+                    const int d = (int)(en.S.X[c * en.S.N + i] - __ldcg(en.Xb + c * en.S.N + i));
+                    d2 = (unsigned long long)((long long)d * d);
+                }
+                d2 += __shfl_xor_sync(0xffffffffu, d2, 1);
+                d2 += __shfl_xor_sync(0xffffffffu, d2, 2);
+                if (c == 0 && d2 > en.sk2) *en.nflag = 1;
+            }
         }
         grid_sync(A.bar, A.err, target, on_timeout);
         // ---- pair items of this block, system by system (and RDF samples)
@@ -121,9 +143,26 @@ __global__ void __launch_bounds__(BT, 1) k_mstep(MsArgs A) {
             if (rdf)
                 for (int c = threadIdx.x; c < S.rdf_rows * S.rdf_bins; c += blockDim.x) hist[c] = 0u;
             __syncthreads();
+            const bool build = en.lcap && __ldcg(en.nflag) != 0;  // the same in every block this step
             for (int i = g.y + warp; i < g.z; i += nw) {
                 e.begin_tile(P, sm, A.Np, i);
-                e.scan(sm, A.Np, 0, N, wq, lane);
+                if (!en.lcap) {
+                    e.scan(sm, A.Np, 0, N, wq, lane);
+                } else if (build) {
+                    const int nc = e.scan_build(sm, A.Np, N, wq, lane, en.nl + (size_t)i * en.lcap, en.lcap, en.rs2);
+                    if (lane == 0) {
+                        en.ncnt[i] = nc;
+                        en.Xb[i] = e.Xi;
+                        en.Xb[N + i] = e.Yi;
+                        en.Xb[2 * N + i] = e.Zi;
+                    }
+                } else {
+                    const int nc = __ldcg(en.ncnt + i);
+                    if (nc > en.lcap)
+                        e.scan(sm, A.Np, 0, N, wq, lane);
+                    else
+                        e.scan_list(sm, A.Np, en.nl + (size_t)i * en.lcap, nc, wq, lane);
+                }
                 const PairOut o = e.finish(lane);
                 if (lane == 0) {
                     float *q = S.part + i;
@@ -147,6 +186,7 @@ __global__ void __launch_bounds__(BT, 1) k_mstep(MsArgs A) {
             const int2 u = A.unit[g];
             const BatchEntry &en = A.tab[u.x];
             reduce_unit<false>(en.P, en.S, global_io(en.S), RED_SUM | RED_LAMBDA, u.y, en.units, lane);
+            if (u.y == 0 && lane == 0 && en.lcap) *en.nflag = 0;  // the pair phase has read it
         }
         grid_sync(A.bar, A.err, target, on_timeout);
         // ---- per system: totals (lane l sums units l, l + 32, ... in order, then
@@ -203,7 +243,9 @@ size_t batch_smem(int kind, int Np, int threads, int rdf_cells) {
 // relative cost of one pair item of system s (warp instructions, rough): the
 // candidate scan over all N molecules plus the expected partners times the
 // site pairs each evaluates
-double item_cost(ms2_system s) {
+// (with candidate lists: the list, ~1.52 x the partners, at a higher cost per
+// entry, plus a full scan about every 16 steps)
+double item_cost(ms2_system s, bool lists) {
     const double L = s->hp.L, rc = s->rc;
     const double frac = std::min(1.0, 4.0 / 3.0 * M_PI * rc * rc * rc / (L * L * L));
     int sp = 0;
@@ -211,7 +253,8 @@ double item_cost(ms2_system s) {
         for (int c = 0; c < 8; ++c)
             if ((((s->ljm >> a) & (s->ljm >> c)) | ((s->qm >> a) & (s->qm >> c)) | ((s->dm >> a) & (s->dm >> c))) & 1u)
                 ++sp;
-    return (double)s->N * (20.0 + frac * (25.0 * sp + 30.0));
+    const double scan = lists ? 25.0 * std::min(1.0, 1.52 * frac) + 20.0 / 16.0 : 20.0;
+    return (double)s->N * (scan + frac * (25.0 * sp + 30.0));
 }
 
 // ---------------------------------------------------------- autotune cache
@@ -265,6 +308,7 @@ struct ms2_batch_s {
     int threads[K_COUNT] = {0}, grid[K_COUNT] = {0};
     size_t smem[K_COUNT] = {0};
     unsigned *dbar = nullptr;  // [K_COUNT][2]: barrier counter, timeout flag
+    int *dnflag[K_COUNT] = {nullptr};  // candidate-list rebuild flags, one per system of the kind
     int chunk = 100;
 };
 
@@ -299,6 +343,8 @@ static ms2_status batch_launch(ms2_batch b, int nsteps, bool trial = false) {
         MS2_CUDA_OK(cudaMemcpyAsync(b->dtab[k], t.data(), sizeof(BatchEntry) * t.size(), cudaMemcpyHostToDevice,
                                     b->stream));
         MS2_CUDA_OK(cudaMemsetAsync(b->dbar + 2 * k, 0, 2 * sizeof(unsigned), b->stream));
+        // the lists are rebuilt at the start of every launch (the states may have been set or stepped since)
+        MS2_CUDA_OK(cudaMemsetAsync(b->dnflag[k], 1, sizeof(int) * t.size(), b->stream));
         MsArgs A;
         A.tab = b->dtab[k];
         A.n_sys = (int)t.size();
@@ -347,8 +393,9 @@ static ms2_status set_shape(ms2_batch b, int k, int threads) {
     b->grid[k] = G;
     double total = 0;
     std::vector<double> cost;
-    for (int idx : b->order[k]) {
-        cost.push_back(item_cost(b->sys[idx]));
+    for (size_t e = 0; e < b->order[k].size(); ++e) {
+        const int idx = b->order[k][e];
+        cost.push_back(item_cost(b->sys[idx], b->htab[k][e].lcap > 0));
         total += cost.back() * b->sys[idx]->N;
     }
     std::vector<int4> seg;
@@ -547,6 +594,7 @@ extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_bat
     for (int k = 0; k < K_COUNT && ce == cudaSuccess; ++k) {
         if (b->order[k].empty()) continue;
         std::vector<int2> drift, unit;
+        ce = b->al.alloc((void **)&b->dnflag[k], sizeof(int) * b->order[k].size());
         for (size_t e = 0; e < b->order[k].size() && ce == cudaSuccess; ++e) {
             ms2_system s = b->sys[b->order[k][e]];
             const int N = s->N;
@@ -558,6 +606,22 @@ extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_bat
             en.units = (N + UNIT - 1) / UNIT;
             en.S.nunits = en.units;
             ce = b->al.alloc((void **)&en.S.blk, sizeof(double) * MS2_NRED * en.units);
+            // candidate lists: skin 0.15 r_c, capacity 1.3 x the ideal-gas count within r_c + skin
+            {
+                const double L = s->hp.L, rc = s->rc, skin = 0.15 * rc, sc = s->hp.lat_scale;
+                const double frac = std::min(1.0, 4.18879020478639098 * std::pow(rc + skin, 3.0) / (L * L * L));  // 4 pi / 3
+                const int lcap = ((int)std::ceil(1.3 * frac * N + 32.0) + 31) & ~31;
+                if (ce == cudaSuccess && N <= 65535 && lcap < (3 * N) / 4) {
+                    ce = b->al.alloc((void **)&en.nl, sizeof(uint16_t) * (size_t)N * lcap);
+                    if (ce == cudaSuccess) ce = b->al.alloc((void **)&en.ncnt, sizeof(int) * N);
+                    if (ce == cudaSuccess) ce = b->al.alloc((void **)&en.Xb, sizeof(uint32_t) * 3 * N);
+                    const double rl = (rc + skin) * sc + 2.0, hl = std::max(0.0, 0.5 * skin * sc - 2.0);
+                    en.rs2 = (unsigned long long)std::ceil(rl * rl);
+                    en.sk2 = (unsigned long long)std::floor(hl * hl);
+                    en.lcap = lcap;
+                }
+            }
+            en.nflag = b->dnflag[k] + e;
             en.step0 = s->step;
             b->htab[k].push_back(en);
             for (int m = 0; m < N; m += 8) drift.push_back(make_int2((int)e, m));

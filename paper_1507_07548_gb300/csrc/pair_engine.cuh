@@ -571,6 +571,92 @@ struct PairWarp {
         }
     }
 
+    // The full scan of a whole-system tile (slots [0, tn)) that also lists, in
+    // ascending slot order, the candidates within the list radius (lattice
+    // rs2 >= rc2) into nl[0, lcap); returns how many there are (> lcap: the list
+    // is incomplete).  The partners and their batches are those of scan().
+    __device__ __forceinline__ int scan_build(const Smem &sm, int TJ, int tn, int *wq, int lane, uint16_t *nl,
+                                              int lcap, unsigned long long rs2) {
+        const unsigned below = (1u << lane) - 1u;
+        auto test = [&](int jl, bool &listed) {
+            const int js = min(jl, tn - 1);
+            const uint4 p = sm.tP[js];
+            const int dx = (int)(p.x - Xi), dy = (int)(p.y - Yi), dz = (int)(p.z - Zi);
+            const unsigned long long d2 = lattice_d2(dx, dy, dz);
+            const bool in = (jl < tn) & (jl != i);
+            listed = in & (d2 < rs2);
+            return in & (d2 < rc2);
+        };
+        int head = 0, qn = 0, nc = 0;
+        for (int base = 0; base < tn; base += 64) {
+            const int j0 = base + lane, j1 = base + 32 + lane;
+            bool l0, l1;
+            const bool p0 = test(j0, l0), p1 = test(j1, l1);
+            const unsigned a0 = __ballot_sync(FULL, l0), a1 = __ballot_sync(FULL, l1);
+            const int c0 = nc + __popc(a0 & below), c1 = nc + __popc(a0) + __popc(a1 & below);
+            if (l0 && c0 < lcap) nl[c0] = (uint16_t)j0;
+            if (l1 && c1 < lcap) nl[c1] = (uint16_t)j1;
+            nc += __popc(a0) + __popc(a1);
+            const unsigned m0 = __ballot_sync(FULL, p0), m1 = __ballot_sync(FULL, p1);
+            const int n0 = __popc(m0);
+            if (p0) wq[(head + qn + __popc(m0 & below)) & (QCAP - 1)] = j0;
+            if (p1) wq[(head + qn + n0 + __popc(m1 & below)) & (QCAP - 1)] = j1;
+            qn += n0 + __popc(m1);
+            __syncwarp();
+            while (qn >= 32) {
+                interact(sm, TJ, wq[(head + lane) & (QCAP - 1)]);
+                __syncwarp();
+                head = (head + 32) & (QCAP - 1);
+                qn -= 32;
+            }
+        }
+        if (qn > 0) {
+            if (lane < qn) interact(sm, TJ, wq[(head + lane) & (QCAP - 1)]);
+            __syncwarp();
+        }
+        return nc;
+    }
+
+    // The scan of a complete candidate list nl[0, cnt) (ascending slots of a
+    // whole-system tile, the owner excluded): the exact centre test on each, the
+    // partners in the order and batches of scan().
+    __device__ __forceinline__ void scan_list(const Smem &sm, int TJ, const uint16_t *nl, int cnt, int *wq, int lane) {
+        const unsigned below = (1u << lane) - 1u;
+        auto test = [&](int k, int jl) {
+            const uint4 p = sm.tP[jl];
+            const int dx = (int)(p.x - Xi), dy = (int)(p.y - Yi), dz = (int)(p.z - Zi);
+            return (k < cnt) & (lattice_d2(dx, dy, dz) < rc2);
+        };
+        // the list entries of the next pass are loaded while this pass runs
+        const int last = cnt - 1;
+        int n0 = cnt > 0 ? __ldcg(nl + min(lane, last)) : 0, n1 = cnt > 0 ? __ldcg(nl + min(lane + 32, last)) : 0;
+        int head = 0, qn = 0;
+        for (int base = 0; base < cnt; base += 64) {
+            const int j0 = n0, j1 = n1;
+            if (base + 64 < cnt) {
+                n0 = __ldcg(nl + min(base + 64 + lane, last));
+                n1 = __ldcg(nl + min(base + 96 + lane, last));
+            }
+            const bool p0 = test(base + lane, j0), p1 = test(base + 32 + lane, j1);
+            const unsigned m0 = __ballot_sync(FULL, p0), m1 = __ballot_sync(FULL, p1);
+            const int n0 = __popc(m0);
+            if (p0) wq[(head + qn + __popc(m0 & below)) & (QCAP - 1)] = j0;
+            if (p1) wq[(head + qn + n0 + __popc(m1 & below)) & (QCAP - 1)] = j1;
+            qn += n0 + __popc(m1);
+            __syncwarp();
+            while (qn >= 32) {
+                interact(sm, TJ, wq[(head + lane) & (QCAP - 1)]);
+                __syncwarp();
+                head = (head + 32) & (QCAP - 1);
+                qn -= 32;
+            }
+        }
+        if (qn > 0) {
+            if (lane < qn) interact(sm, TJ, wq[(head + lane) & (QCAP - 1)]);
+            __syncwarp();
+        }
+    }
+
     // heat pass: the warp's sum_l d_kl P_kl (fixed tree, every lane)
     __device__ __forceinline__ void finish_heat(float out[3]) {
 #pragma unroll
