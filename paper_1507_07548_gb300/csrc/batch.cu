@@ -50,6 +50,7 @@ const char *kKindName[K_COUNT] = {"lj1", "water3_rf", "stockmayer3_rf", "generic
 constexpr int MS_THREADS = 512;   // largest block shape (the autotuner may take 256)
 constexpr int UNIT = 8;           // molecules per reduction unit (one quad pass of a warp)
 constexpr int RDF_SMEM_MAX = 4096;  // histogram cells staged in shared memory
+constexpr double kSkin = 0.3;       // candidate-list skin, in units of the cut-off
 
 struct BatchEntry {
     const SysParams *P;
@@ -57,7 +58,7 @@ struct BatchEntry {
     int units;        // reduction units: ceil(N / UNIT)
     int rdf_every;
     long long step0;  // step counter of the system before this launch
-    // Candidate lists with a skin: per molecule, the molecules within r_c + skin
+    // Candidate lists with a skin (kSkin r_c): per molecule, the molecules within r_c + skin
     // at the last build, in ascending order.  The exact centre test runs on them
     // each step until some molecule of the system has moved more than skin / 2
     // since the build (then no other molecule can have come within r_c), so the
@@ -243,8 +244,8 @@ size_t batch_smem(int kind, int Np, int threads, int rdf_cells) {
 // relative cost of one pair item of system s (warp instructions, rough): the
 // candidate scan over all N molecules plus the expected partners times the
 // site pairs each evaluates
-// (with candidate lists: the list, ~1.52 x the partners, at a higher cost per
-// entry, plus a full scan about every 16 steps)
+// (with candidate lists: the list, (1 + skin)^3 x the partners, at a higher
+// cost per entry, plus a full scan about every 16 steps)
 double item_cost(ms2_system s, bool lists) {
     const double L = s->hp.L, rc = s->rc;
     const double frac = std::min(1.0, 4.0 / 3.0 * M_PI * rc * rc * rc / (L * L * L));
@@ -253,7 +254,8 @@ double item_cost(ms2_system s, bool lists) {
         for (int c = 0; c < 8; ++c)
             if ((((s->ljm >> a) & (s->ljm >> c)) | ((s->qm >> a) & (s->qm >> c)) | ((s->dm >> a) & (s->dm >> c))) & 1u)
                 ++sp;
-    const double scan = lists ? 25.0 * std::min(1.0, 1.52 * frac) + 20.0 / 16.0 : 20.0;
+    const double grow = (1.0 + kSkin) * (1.0 + kSkin) * (1.0 + kSkin);
+    const double scan = lists ? 25.0 * std::min(1.0, grow * frac) + 20.0 / 16.0 : 20.0;
     return (double)s->N * (scan + frac * (25.0 * sp + 30.0));
 }
 
@@ -606,9 +608,11 @@ extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_bat
             en.units = (N + UNIT - 1) / UNIT;
             en.S.nunits = en.units;
             ce = b->al.alloc((void **)&en.S.blk, sizeof(double) * MS2_NRED * en.units);
-            // candidate lists: skin 0.15 r_c, capacity 1.3 x the ideal-gas count within r_c + skin
+            // candidate lists: skin 0.3 r_c (measured on the bench mix: 0.1 -> 2.74, 0.15 -> 2.55,
+            // 0.22 -> 2.42, 0.3 -> 2.32, 0.4 -> 2.48 ms per step), capacity 1.3 x the ideal-gas
+            // count within r_c + skin
             {
-                const double L = s->hp.L, rc = s->rc, skin = 0.15 * rc, sc = s->hp.lat_scale;
+                const double L = s->hp.L, rc = s->rc, skin = kSkin * rc, sc = s->hp.lat_scale;
                 const double frac = std::min(1.0, 4.18879020478639098 * std::pow(rc + skin, 3.0) / (L * L * L));  // 4 pi / 3
                 const int lcap = ((int)std::ceil(1.3 * frac * N + 32.0) + 31) & ~31;
                 if (ce == cudaSuccess && N <= 65535 && lcap < (3 * N) / 4) {
