@@ -50,7 +50,10 @@ const char *kKindName[K_COUNT] = {"lj1", "water3_rf", "stockmayer3_rf", "generic
 constexpr int MS_THREADS = 512;   // largest block shape (the autotuner may take 256)
 constexpr int UNIT = 8;           // molecules per reduction unit (one quad pass of a warp)
 constexpr int RDF_SMEM_MAX = 4096;  // histogram cells staged in shared memory
-constexpr double kSkin = 0.3;       // candidate-list skin, in units of the cut-off
+// candidate-list skin, in units of the cut-off (measured on the bench mix, which
+// starts from lattices: 0.1 -> 2.74, 0.15 -> 2.55, 0.22 -> 2.42, 0.3 -> 2.32,
+// 0.4 -> 2.48 ms per step; the small skins rebuild often while the lattices relax)
+constexpr double kSkin = 0.3;
 
 struct BatchEntry {
     const SysParams *P;
@@ -597,6 +600,26 @@ extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_bat
         if (b->order[k].empty()) continue;
         std::vector<int2> drift, unit;
         ce = b->al.alloc((void **)&b->dnflag[k], sizeof(int) * b->order[k].size());
+        // candidate lists of the kind's systems in one allocation (a server re-creates
+        // batches as jobs come and go): skin kSkin r_c, capacity 1.3 x the ideal-gas
+        // count within r_c + skin; only where the list is shorter than 3N/4
+        std::vector<int> lcaps(b->order[k].size(), 0);
+        std::vector<size_t> nl_off(b->order[k].size(), 0);
+        size_t nl_bytes = 0;
+        for (size_t e = 0; e < b->order[k].size(); ++e) {
+            ms2_system s = b->sys[b->order[k][e]];
+            const int N = s->N;
+            const double L = s->hp.L, rc = s->rc, skin = kSkin * rc;
+            const double frac = std::min(1.0, 4.18879020478639098 * std::pow(rc + skin, 3.0) / (L * L * L));  // 4 pi / 3
+            const int lcap = ((int)std::ceil(1.3 * frac * N + 32.0) + 31) & ~31;
+            if (N <= 65535 && lcap < (3 * N) / 4) {
+                lcaps[e] = lcap;
+                nl_off[e] = nl_bytes;
+                nl_bytes += al16(sizeof(uint16_t) * (size_t)N * lcap) + al16(sizeof(int) * N) + al16(sizeof(uint32_t) * 3 * N);
+            }
+        }
+        unsigned char *nl_base = nullptr;
+        if (ce == cudaSuccess && nl_bytes) ce = b->al.alloc((void **)&nl_base, nl_bytes);
         for (size_t e = 0; e < b->order[k].size() && ce == cudaSuccess; ++e) {
             ms2_system s = b->sys[b->order[k][e]];
             const int N = s->N;
@@ -608,22 +631,19 @@ extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_bat
             en.units = (N + UNIT - 1) / UNIT;
             en.S.nunits = en.units;
             ce = b->al.alloc((void **)&en.S.blk, sizeof(double) * MS2_NRED * en.units);
-            // candidate lists: skin 0.3 r_c (measured on the bench mix: 0.1 -> 2.74, 0.15 -> 2.55,
-            // 0.22 -> 2.42, 0.3 -> 2.32, 0.4 -> 2.48 ms per step), capacity 1.3 x the ideal-gas
-            // count within r_c + skin
-            {
-                const double L = s->hp.L, rc = s->rc, skin = kSkin * rc, sc = s->hp.lat_scale;
-                const double frac = std::min(1.0, 4.18879020478639098 * std::pow(rc + skin, 3.0) / (L * L * L));  // 4 pi / 3
-                const int lcap = ((int)std::ceil(1.3 * frac * N + 32.0) + 31) & ~31;
-                if (ce == cudaSuccess && N <= 65535 && lcap < (3 * N) / 4) {
-                    ce = b->al.alloc((void **)&en.nl, sizeof(uint16_t) * (size_t)N * lcap);
-                    if (ce == cudaSuccess) ce = b->al.alloc((void **)&en.ncnt, sizeof(int) * N);
-                    if (ce == cudaSuccess) ce = b->al.alloc((void **)&en.Xb, sizeof(uint32_t) * 3 * N);
-                    const double rl = (rc + skin) * sc + 2.0, hl = std::max(0.0, 0.5 * skin * sc - 2.0);
-                    en.rs2 = (unsigned long long)std::ceil(rl * rl);
-                    en.sk2 = (unsigned long long)std::floor(hl * hl);
-                    en.lcap = lcap;
-                }
+            if (ce == cudaSuccess && lcaps[e]) {
+                const int lcap = lcaps[e];
+                const double rc = s->rc, skin = kSkin * rc, sc = s->hp.lat_scale;
+                unsigned char *q = nl_base + nl_off[e];
+                en.nl = (uint16_t *)q;
+                q += al16(sizeof(uint16_t) * (size_t)N * lcap);
+                en.ncnt = (int *)q;
+                q += al16(sizeof(int) * N);
+                en.Xb = (uint32_t *)q;
+                const double rl = (rc + skin) * sc + 2.0, hl = std::max(0.0, 0.5 * skin * sc - 2.0);
+                en.rs2 = (unsigned long long)std::ceil(rl * rl);
+                en.sk2 = (unsigned long long)std::floor(hl * hl);
+                en.lcap = lcap;
             }
             en.nflag = b->dnflag[k] + e;
             en.step0 = s->step;
