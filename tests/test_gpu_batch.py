@@ -67,6 +67,39 @@ def test_one_batched_step_matches_oracle(make):
     assert rms_rel(F, Fo) <= 1e-5
 
 
+def dilute_lj():
+    wl = W.lj_fluid(N=1372, rho=0.3, rc=3.0, T=1.5, seed=17)
+    wl.integrator = 1
+    return wl
+
+
+def dilute_water():
+    return W.water_box(N=1000, rc=14.0, seed=19, density=0.5 * W.WATER_NUMBER_DENSITY)
+
+
+@pytest.mark.parametrize("make", [dilute_lj, dilute_water], ids=["lj", "water"])
+def test_candidate_lists_find_every_partner(make):
+    """Dilute systems take candidate lists in a batch (the list within r_c + skin
+    holds 5 % and 42 % of the molecules).  After 150 batched steps in two launches
+    (list builds at each launch and whenever a molecule has moved half the skin,
+    list scans in between), each molecule's partner count equals that of a full
+    evaluation of the same state, and the forces are the oracle's."""
+    wl = make()
+    s = ms2.System.from_workload(wl)
+    b = ms2.Batch([s])
+    b.step(150)
+    R, q, v, L, _ = s.get_state()
+    c = ms2.System.from_workload(wl)
+    c.set_state(R, q, v, L)
+    assert np.array_equal(np.asarray(s.partner_counts()), np.asarray(c.partner_counts()))
+    F, tau = s.forces_torques()
+    Fo, To, _ = Oracle.from_workload(wl).forces(R, q)
+    assert rms_rel(F, Fo) <= 1e-5
+    if np.linalg.norm(To) > 0:
+        assert rms_rel(tau, To) <= 1e-5
+    b.close()
+
+
 def test_system_alone_and_in_a_mixed_batch_is_bitwise_identical():
     alone = ms2.System.from_workload(water())
     b1 = ms2.Batch([alone])
