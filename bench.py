@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the Ewald sub-benchmark")
     ap.add_argument("--only", choices=["ewald", "massieu", "thermal", "batch"], default=None,
                     help="run one sub-benchmark alone and print its JSON object")
+    ap.add_argument("--batch-kinds", default=None, metavar="K[,K]",
+                    help="batch leg: only the systems of these model kinds of the mix (lj, stockmayer, water)")
     ap.add_argument("--uniform-batch", type=int, default=0, metavar="S",
                     help="only time one batch of S copies of the water workload (single steps; the ncu case "
                          "of the multi-system step kernel)")
@@ -355,6 +357,8 @@ def batch_sub(args, flush):
     import paper_1507_07548_gb300.ms2 as ms2
     from paper_1507_07548_gb300 import workloads as W
     specs = W.system_mix(BATCH_SYSTEMS, seed=4)
+    if args.batch_kinds:  # a sub-mix (profiling one kind's kernel)
+        specs = [sp for sp in specs if sp["name"] in args.batch_kinds.split(",")]
     one = torch.cuda.Stream()
 
     def make(**kw):
