@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(BT, 1) k_mstep(MsArgs A) {
     const int gw = blockIdx.x * nw + warp, W = gridDim.x * nw;
     const Smem sm = carve<NS, Eng::DMU, MULTI>(smem_raw, A.Np, nw);
     unsigned *hist = (unsigned *)(smem_raw + al16(pair_engine::smem_bytes(NS, Eng::DMU, MULTI, A.Np, nw)));
-    int *wq = sm.queue + warp * QCAP;
+    int *wq = sm.queue + warp * QSTRIDE;
     unsigned target = 0;
     auto on_timeout = [&]() {
         for (int e = 0; e < A.n_sys; ++e) A.tab[e].S.scal[SC_KERR] = 1.0;

@@ -281,6 +281,16 @@ void ms2_fill_params(SysParams &P, const ms2_model *models, int n_models, const 
         for (int a = 0; a < models[m].n_sites; ++a)
             if (P.bdip[m][a][0] != 0 || P.bdip[m][a][1] != 0 || P.bdip[m][a][2] != 0) any_d = true;
     P.has_dipole = any_d;
+    // Close-contact LJ pairs in double-float where point charges make the
+    // molecular virial a small difference of large LJ and Coulomb sums (liquid
+    // water at ambient pressure: |W| ~ 1/25 of its LJ part); without charges the
+    // FP32 terms meet the same relative bound and the pass is off.
+    {
+        bool any_q = false;
+        for (int m = 0; m < n_models; ++m)
+            for (int a = 0; a < models[m].n_sites; ++a) any_q = any_q || P.qd[m][a] != 0.0;
+        P.close_k6 = any_q ? (float)std::pow(1.1, -6.0) : INFINITY;
+    }
     for (int m = 0; m < MS2_MAXSP; ++m) {
         P.rot[m] = m < n_models && (P.Iinv[m][0] != 0 || P.Iinv[m][1] != 0 || P.Iinv[m][2] != 0);
         bool pt = m < n_models;
@@ -1177,7 +1187,7 @@ extern "C" ms2_status ms2_energy_terms(ms2_system s, double terms[16]) {
         double sq2 = 0;
         for (int i = 0; i < s->N; ++i)
             for (int a = 0; a < P.n_sites[s->species[i]]; ++a)
-                sq2 += (double)P.q[s->species[i]][a] * P.q[s->species[i]][a];
+                sq2 += P.qd[s->species[i]][a] * P.qd[s->species[i]][a];
         uself = -coulomb * s->alpha / std::sqrt(M_PI) * sq2;
         uintra = c_all - uself - ubg;
     }

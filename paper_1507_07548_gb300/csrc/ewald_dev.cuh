@@ -221,7 +221,9 @@ __device__ __forceinline__ void force_task(const SysParams *__restrict__ P, cons
     for (int nx = 0; nx <= kx; ++nx) ex_s[nx * nt + tid] = __ldcg(S.eik + (size_t)nx * M + ss);
     for (int n = 0; n <= kz; ++n) ez_s[n * nt + tid] = __ldcg(S.eik + ((size_t)2 * kstride + n) * M + ss);
     __syncthreads();
-    float fx = 0.f, fy = 0.f, fz = 0.f;
+    // the column sums enter compensated sums (their FP32 roundings would reach
+    // the molecular virial through the site levers, sum_s F_s.s_s)
+    float fx = 0.f, fy = 0.f, fz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     const float q = __ldcg(S.qs + ss);
     float2 exr[KXT > 0 ? KXT : 1];
     const float2 *ey = S.eik + (size_t)kstride * M + ss;
@@ -254,13 +256,13 @@ __device__ __forceinline__ void force_task(const SysParams *__restrict__ P, cons
                         syz += im;
                     }
                 }
-                fx += sx;
-                fy += (float)ny * syz;
-                fz += (float)nz * syz;
+                kahan_add(fx, cx, sx);
+                kahan_add(fy, cy, (float)ny * syz);
+                kahan_add(fz, cz, (float)nz * syz);
             }
         }
         const float pre = S.ew_fpre * q;  // 8 pi C / V * 2 pi / L, formed once on the host
-        fx *= pre; fy *= pre; fz *= pre;
+        fx = (fx - cx) * pre; fy = (fy - cy) * pre; fz = (fz - cz) * pre;
     }
     if (s < M) {
         float *o = S.frec + (size_t)ch * 3 * M + s;

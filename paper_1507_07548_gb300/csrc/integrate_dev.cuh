@@ -2,6 +2,7 @@
 // (k_integrate.cu) and the batched per-system kernel (batch.cu).
 #pragma once
 #include "ms2_internal.cuh"
+#include "ewald_dev.cuh"
 
 namespace integ {
 
@@ -463,7 +464,7 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
                 const int NS = S.ns, M = S.nsite_q, c1 = (cc + 1) % 3, c2 = (cc + 2) % 3;
                 double wc = 0;  // -F_s.s_s molecular-virial correction, component c
                 for (int a2 = 0; a2 < NS; ++a2) {
-                    float fs = 0.f;
+                    float fs = 0.f, fc = 0.f;  // compensated sum over the k chunks
                     const float *fr = S.frec + (size_t)cc * M + a2 * N + ii;
                     int ch = 0;
                     for (; ch + 8 <= S.kchunks; ch += 8) {  // 8 loads in flight, then the adds in order
@@ -471,10 +472,10 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
 #pragma unroll
                         for (int u = 0; u < 8; ++u) p[u] = __ldcg(fr + (size_t)(ch + u) * 3 * M);
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) fs += p[u];
+                        for (int u = 0; u < 8; ++u) ewald::kahan_add(fs, fc, p[u]);
                     }
-                    for (; ch < S.kchunks; ++ch) fs += __ldcg(fr + (size_t)ch * 3 * M);
-                    const double f = f2d(fs);
+                    for (; ch < S.kchunks; ++ch) ewald::kahan_add(fs, fc, __ldcg(fr + (size_t)ch * 3 * M));
+                    const double f = f2d(fs) - f2d(fc);
                     const double f1 = __shfl_sync(F, f, qb | c1), f2 = __shfl_sync(F, f, qb | c2);
                     const double o1 = f2d(__ldcg(S.s + (c1 * NS + a2) * N + ii)),
                                  o2 = f2d(__ldcg(S.s + (c2 * NS + a2) * N + ii));

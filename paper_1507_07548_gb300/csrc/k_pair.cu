@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256) k_pair(const SysParams *__restrict__ P, D
     const int JS = gridDim.y, p = blockIdx.y;
     const int j0 = (int)(((long long)N * p) / JS), j1 = (int)(((long long)N * (p + 1)) / JS);
     Smem sm = carve<NS, Eng::DMU, MULTI>(smem_raw, TJ, wpb);
-    int *wq = sm.queue + warp * QCAP;
+    int *wq = sm.queue + warp * QSTRIDE;
     load_tables<MULTI>(P, sm);
     Eng e;
     e.setup(P);
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) k_heat(const SysParams *__restrict__ P, D
     const int JS = gridDim.y, p = blockIdx.y;
     const int j0 = (int)(((long long)N * p) / JS), j1 = (int)(((long long)N * (p + 1)) / JS);
     Smem sm = carve<NS, Eng::DMU, MULTI>(smem_raw, TJ, wpb);
-    int *wq = sm.queue + warp * QCAP;
+    int *wq = sm.queue + warp * QSTRIDE;
     load_tables<MULTI>(P, sm);
     Eng e;
     e.setup(P);

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     const SysParams *Ps = (const SysParams *)(own + own_layout(MC, JS, (size_t)A.ews).params);
     auto part_at = [&]() { return (float *)(own + own_layout(MC, JS, (size_t)A.ews).part); };
     auto hpart_at = [&]() { return (float *)(own + own_layout(MC, JS, (size_t)A.ews).hpart); };
-    int *wq = sm.queue + warp * QCAP;
+    int *wq = sm.queue + warp * QSTRIDE;
     // prologue: every load is issued before anything waits on one (after an L2
     // flush each dependent round trip goes to DRAM): the thermostat factor, the
     // parameter copy and the own state; the tables then come from the copy

@@ -47,6 +47,10 @@ struct SysParams {
     float lat_to_len_lo;       // L / 2^32 - lat_to_len (the rounding remainder)
     float len_to_lat;          // 2^32 / L
     float coulomb, krf, crf, alpha, two_alpha_sqrtpi;
+    // LJ site pairs at close contact, r < 1.1 sigma_ab (t12 > close_k6 t6, with
+    // close_k6 = 1.1^-6), are evaluated in double-float; +inf switches it off
+    float close_k6;
+    float pad_close_[3];                   // keeps the struct a whole number of 16-byte words
     // species tables
     int n_sites[MS2_MAXSP];
     double bpos[MS2_MAXSP][MS2_MAXS][3];   // body-frame site positions

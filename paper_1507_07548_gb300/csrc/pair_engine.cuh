@@ -7,6 +7,7 @@
 // molecular virial as the owner share).  See k_pair.cu for the method.
 #pragma once
 #include "ms2_internal.cuh"
+#include "dfloat.cuh"
 
 namespace pair_engine {
 
@@ -14,6 +15,10 @@ constexpr unsigned FULL = 0xffffffffu;
 // partner queue of a warp: a ring of QCAP tile slots (the scan adds up to 64
 // partners to fewer than 32 waiting ones)
 constexpr int QCAP = 128;
+// close-contact queue of a warp: a ring of CQCAP entries (tile slot, owner site,
+// partner site) after the partner ring; QSTRIDE ints per warp in all
+constexpr int CQCAP = 64;
+constexpr int QSTRIDE = QCAP + CQCAP;
 
 // Tile arrays: tP[j] = (lattice centre X, Y, Z, species) of tile molecule j
 // (one 16-byte load), site offsets ts[(k NS + b) TJ + j], point dipoles tmu (same
@@ -35,7 +40,7 @@ __device__ __forceinline__ Smem carve(unsigned char *base, int TJ, int wpb) {
     m.tmu = m.ts + 3 * NS * TJ;
     m.tmd = m.tmu + (DMU ? 3 * NS * TJ : 0);
     m.queue = (int *)(m.tmd + 3 * TJ);
-    m.sq = (float *)(m.queue + wpb * QCAP);
+    m.sq = (float *)(m.queue + wpb * QSTRIDE);
     m.sql = m.sq + MS2_MAXSP * MS2_MAXS;
     m.sljt = (int *)(m.sql + MS2_MAXSP * MS2_MAXS);
     m.sc6 = (float *)(m.sljt + MS2_MAXSP * MS2_MAXS);
@@ -50,7 +55,7 @@ __host__ __device__ inline size_t smem_bytes(int NS, bool dmu, bool multi, int T
     size_t n = sizeof(uint4) * TJ + sizeof(float) * 3 * NS * TJ;
     if (dmu) n += sizeof(float) * 3 * NS * TJ;
     n += sizeof(float) * 3 * TJ;  // molecular dipoles (reaction field; reserved always)
-    n += sizeof(int) * wpb * QCAP;
+    n += sizeof(int) * wpb * QSTRIDE;
     n += 2 * sizeof(float) * MS2_MAXSP * MS2_MAXS + sizeof(int) * MS2_MAXSP * MS2_MAXS;
     n += 4 * sizeof(float) * MS2_MAXT * MS2_MAXT;
     return n;
@@ -182,9 +187,13 @@ struct PairWarp {
     }
     static constexpr int PA = pair_site(), PB = PA + 1;
     static constexpr bool PKF = PA >= 0 && !MULTI && !MASS && (ELEC == ELEC_RF || ELEC == ELEC_NONE);
+    // close-contact LJ site pairs in double-float (not in the heat-flux power
+    // pass): compiled where a slot may carry a charge, the systems the host
+    // switches it on for (SysParams::close_k6)
+    static constexpr bool CLOSE = LJM != 0 && QM != 0;
     int elec;
     bool rfq;
-    float C, krf, alpha, tasp, l2l, l2l_lo;
+    float C, krf, alpha, tasp, l2l, l2l_lo, ck6;
     unsigned long long rc2;
     // coefficient tables of a single-species system (hi + lo floats: a single
     // FP32 rounding of C q_a q_b or 4 eps sigma^12 would scale every term of that
@@ -202,6 +211,9 @@ struct PairWarp {
     // lane accumulators
     float fa[NS][3], ea[NS][3], ulj, uqq, udd, w, vv, erf_[3];
     int np;
+    // close-contact sums (double-float energy and virial) and the close ring state
+    dfl::df ucl, wcl;
+    int cqh, cqn;
     // heat-flux power pass (HP): site velocities v_i + w_i x s_ia, w_i x mu_ia,
     // w_i x mu_i (reaction field) and the lane sums of d_kl P_kl
     float vs[NS][3], wmu[NS][3], wmd[3], jh[3];
@@ -215,6 +227,7 @@ struct PairWarp {
         tasp = P->two_alpha_sqrtpi;
         l2l = P->lat_to_len;
         l2l_lo = P->lat_to_len_lo;
+        ck6 = P->close_k6;
         rc2 = P->rc2;
         if (!MULTI) {
 #pragma unroll
@@ -308,6 +321,8 @@ struct PairWarp {
         ulj = uqq = udd = w = vv = 0.f;
         erf_[0] = erf_[1] = erf_[2] = 0.f;
         np = 0;
+        ucl = wcl = dfl::df{0.f, 0.f};
+        cqh = cqn = 0;
     }
 
     // Heat-flux power pass (Sec. 4, Eqs. 5-6) of molecule i, after begin or
@@ -333,9 +348,12 @@ struct PairWarp {
     }
 
     // one partner, tile-local index jl, into this lane's accumulators (HP: the
-    // heat-flux power pass; the force-pass accumulators are then dead)
+    // heat-flux power pass; the force-pass accumulators are then dead).  Returns
+    // the LJ site pairs (bit a NS + b) at close contact, whose LJ terms are left
+    // out here and evaluated in double-float by close_pair.
     template <bool HP = false>
-    __device__ __forceinline__ void interact(const Smem &sm, int TJ, int jl) {
+    __device__ __forceinline__ unsigned long long interact(const Smem &sm, int TJ, int jl) {
+    unsigned long long cmask = 0ull;
     const uint4 pjl = sm.tP[jl];
     const int dxi = (int)(pjl.x - Xi), dyi = (int)(pjl.y - Yi), dzi = (int)(pjl.z - Zi);
     // lattice difference -> length with the scale split in two floats, so the
@@ -368,7 +386,7 @@ struct PairWarp {
             // operations below term by term, the force factor negated; row PB's
             // energy and virial terms are added after row PA's, in partner-site order
             const float2 m1 = make_float2(-1.f, -1.f);
-            float dl[NS], dq[NS], dgv[NS], dr2[NS];
+            float dl[NS], dq[NS], dgv[NS];
 #pragma unroll
             for (int b = 0; b < NS; ++b) {
                 const bool mlj = (LJM >> PA) & (LJM >> b) & 1u;
@@ -385,16 +403,22 @@ struct PairWarp {
                 float2 ng = make_float2(0.f, 0.f);  // -g
                 if (mlj) {
                     const float2 r6 = __fmul2_rn(__fmul2_rn(rinv2, rinv2), rinv2), r12 = __fmul2_rn(r6, r6);
-                    const float2 t6 = __ffma2_rn(pc6[b], r6, __fmul2_rn(pc6l[b], r6));
-                    const float2 t12 = __ffma2_rn(pc12[b], r12, __fmul2_rn(pc12l[b], r12));
+                    float2 t6 = __ffma2_rn(pc6[b], r6, __fmul2_rn(pc6l[b], r6));
+                    float2 t12 = __ffma2_rn(pc12[b], r12, __fmul2_rn(pc12l[b], r12));
+                    if constexpr (CLOSE && !HP) {
+                        const bool c0 = t12.x > ck6 * t6.x, c1 = t12.y > ck6 * t6.y;
+                        cmask |= ((unsigned long long)c0 << (PA * NS + b)) | ((unsigned long long)c1 << (PB * NS + b));
+                        t6 = make_float2(c0 ? 0.f : t6.x, c1 ? 0.f : t6.y);
+                        t12 = make_float2(c0 ? 0.f : t12.x, c1 ? 0.f : t12.y);
+                    }
                     const float2 tl = __ffma2_rn(t6, m1, t12);
                     ulj += tl.x;
                     dl[b] = tl.y;
-                    ng = __fmul2_rn(__ffma2_rn(make_float2(12.f, 12.f), t12, __fmul2_rn(make_float2(-6.f, -6.f), t6)),
-                                    rinv2);
-                    wsite = fmaf(ng.x, r2.x, wsite);
-                    dgv[b] = ng.y;
-                    dr2[b] = r2.y;
+                    // virial term -g r^2 = 12 t12 - 6 t6 directly (no r^-2 r^2 round trip)
+                    const float2 tw = __ffma2_rn(make_float2(12.f, 12.f), t12, __fmul2_rn(make_float2(-6.f, -6.f), t6));
+                    ng = __fmul2_rn(tw, rinv2);
+                    wsite += tw.x;
+                    dgv[b] = tw.y;
                 }
                 if (mq) {  // bare Coulomb (reaction field)
                     const float2 eq = __ffma2_rn(pq[b], rinv, __fmul2_rn(pql[b], rinv));
@@ -413,7 +437,7 @@ struct PairWarp {
                 const bool mq = ((QM >> PA) & (QM >> b) & 1u) && elec != ELEC_NONE;
                 if (mlj) ulj += dl[b];
                 if (mq) uqq += dq[b];
-                if (mlj) wsite = fmaf(dgv[b], dr2[b], wsite);
+                if (mlj) wsite += dgv[b];
             }
             continue;
         }
@@ -431,10 +455,11 @@ struct PairWarp {
             float rinv = rsqrtf(r2);
             rinv = fmaf(rinv, fmaf(-0.5f * r2 * rinv, rinv, 0.5f), rinv);
             const float rinv2 = rinv * rinv;
-            // g = u'/r of the site pair; gv the part of it whose virial -gv r^2 is
-            // summed here (bare reaction-field Coulomb has -g r^2 = its energy term,
-            // summed as U_qq); hh = (u'' - u'/r)/r^2 (MASS)
-            float g = 0.f, gv = 0.f, hh = 0.f;
+            // g = u'/r of the site pair; wv the virial term -g r^2 of the parts
+            // summed here, formed directly from the terms (bare reaction-field
+            // Coulomb has -g r^2 = its energy term, summed as U_qq); hh = (u'' -
+            // u'/r)/r^2 (MASS)
+            float g = 0.f, wv = 0.f, hh = 0.f;
             if (mlj) {
                 float c6, c12, c6l, c12l;
                 if (MULTI) {
@@ -452,11 +477,18 @@ struct PairWarp {
                     c12l = hc12l[a][b];
                 }
                 const float r6 = rinv2 * rinv2 * rinv2, r12 = r6 * r6;
-                const float t6 = fmaf(c6, r6, c6l * r6), t12 = fmaf(c12, r12, c12l * r12);
-                ulj += t12 - t6;
-                g = fmaf(-12.f, t12, 6.f * t6) * rinv2;
-                gv = g;
+                float t6 = fmaf(c6, r6, c6l * r6), t12 = fmaf(c12, r12, c12l * r12);
                 if (MASS) hh += (168.f * t12 - 48.f * t6) * (rinv2 * rinv2);
+                if constexpr (CLOSE && !HP) {
+                    const bool cl = t12 > ck6 * t6;
+                    cmask |= (unsigned long long)cl << (a * NS + b);
+                    t6 = cl ? 0.f : t6;
+                    t12 = cl ? 0.f : t12;
+                }
+                ulj += t12 - t6;
+                const float t6x = 6.f * t6;
+                g = fmaf(-12.f, t12, t6x) * rinv2;
+                wv = fmaf(12.f, t12, -t6x);
             }
             if (mq && elec != ELEC_NONE) {
                 float cqq, cql;
@@ -476,10 +508,12 @@ struct PairWarp {
                 } else {
                     const float ar = alpha * r2 * rinv;
                     const float ec = erfcf(ar), ex = expf(-ar * ar);
-                    const float bu = ec * rinv, bg = -(ec * rinv + tasp * ex) * rinv2;
-                    uqq += fmaf(cqq, bu, cql * bu);
+                    const float bu = ec * rinv, bx = tasp * ex, bg = -(bu + bx) * rinv2;
+                    const float eu = fmaf(cqq, bu, cql * bu);
+                    uqq += eu;
                     gq = fmaf(cqq, bg, cql * bg);
-                    gv = mlj ? gv + gq : gq;
+                    // -gq r^2 = C q q (erfc(a r)/r + 2a/sqrt(pi) exp(-a^2 r^2)), formed directly
+                    wv += eu + fmaf(cqq, bx, cql * bx);
                 }
                 g = mlj ? g + gq : gq;
                 if (MASS) hh -= 3.f * gq * rinv2;  // bare Coulomb: h = 3 C q q / r^5
@@ -509,7 +543,7 @@ struct PairWarp {
                 }
             }
             fa[a][0] = fmaf(g, rx, fa[a][0]); fa[a][1] = fmaf(g, ry, fa[a][1]); fa[a][2] = fmaf(g, rz, fa[a][2]);
-            if (mlj || (mq && elec == ELEC_EWALD)) wsite = fmaf(-gv, r2, wsite);
+            if (mlj || (mq && elec == ELEC_EWALD)) wsite += wv;
             if (HP) pw = fmaf(g, rx * vs[a][0] + ry * vs[a][1] + rz * vs[a][2], pw);
             if (MASS) {
                 const float rd = rx * dx + ry * dy + rz * dz;
@@ -531,6 +565,146 @@ struct PairWarp {
         jh[2] = fmaf(dz, pw, jh[2]);
     }
     ++np;
+    return cmask;
+    }
+
+    // Close-contact LJ site pair (owner site a, partner tile slot jl, site b) in
+    // double-float: the centre difference exactly from the lattice, the site
+    // offsets as stored, then r^2, r^-6, r^-12, the energy t12 - t6 and the
+    // virial 12 t12 - 6 t6 with ~44-bit significands; the force on site a
+    // (g r, g = -(12 t12 - 6 t6) / r^2) in FP32.
+    __device__ __forceinline__ void close_pair(const Smem &sm, int TJ, int e) {
+        using namespace dfl;
+        const int jl = e & 0xFFFFFF, a = (e >> 24) & 15, b = (e >> 28) & 15;
+        const uint4 pj = sm.tP[jl];
+        const int dv[3] = {(int)(pj.x - Xi), (int)(pj.y - Yi), (int)(pj.z - Zi)};
+        float sa[3] = {0.f, 0.f, 0.f}, c6h = 0.f, c6l = 0.f, c12h = 0.f, c12l = 0.f;
+#pragma unroll
+        for (int a2 = 0; a2 < NS; ++a2)
+            if (a2 == a && ((LJM >> a2) & 1u)) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) sa[k] = si[a2][k];
+            }
+        if constexpr (MULTI) {
+            const int spj = (int)pj.w, tb = sm.sljt[spj * MS2_MAXS + b];
+            int ta = 0;
+#pragma unroll
+            for (int a2 = 0; a2 < NS; ++a2)
+                if (a2 == a) ta = ljti[a2];
+            const int idx = ta * MS2_MAXT + tb;
+            c6h = sm.sc6[idx]; c6l = sm.sc6l[idx]; c12h = sm.sc12[idx]; c12l = sm.sc12l[idx];
+        } else {
+#pragma unroll
+            for (int a2 = 0; a2 < NS; ++a2)
+#pragma unroll
+                for (int b2 = 0; b2 < NS; ++b2)
+                    if (((LJM >> a2) & (LJM >> b2) & 1u) && a2 == a && b2 == b) {
+                        c6h = hc6[a2][b2]; c6l = hc6l[a2][b2]; c12h = hc12[a2][b2]; c12l = hc12l[a2][b2];
+                    }
+        }
+        // d = dv L / 2^32 exactly as hi + lo: dv = 256 hi + lo with both parts exact in FP32
+        const float u256 = 256.f * l2l, u256l = 256.f * l2l_lo;
+        df r[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int hi = dv[k] >> 8, lo = dv[k] & 255;
+            const float fh = (float)hi, fl = (float)lo;
+            df d = two_prod(fh, u256);
+            d.l = __fmaf_rn(fh, u256l, d.l);
+            d.l = __fmaf_rn(fl, l2l, d.l);
+            d.l = __fmaf_rn(fl, l2l_lo, d.l);
+            const float sb = sm.ts[(k * NS + b) * TJ + jl];
+            r[k] = add(d, two_sum(sb, -sa[k]));
+        }
+        df r2 = add(add(sqr(r[0]), sqr(r[1])), sqr(r[2]));
+        if (MULTI && r2.h < 1e-12f) r2 = df{1e-12f, 0.f};
+        const df x = rcp(r2), x3 = mul(sqr(x), x);
+        const df t6 = mul(df{c6h, c6l}, x3), t12 = mul(df{c12h, c12l}, sqr(x3));
+        const df u = add(t12, neg(t6)), wv = add(mul_f(t12, 12.f), neg(mul_f(t6, 6.f)));
+        ucl = add(ucl, u);
+        wcl = add(wcl, wv);
+        const float g = -__fmul_rn(__fadd_rn(wv.h, wv.l), x.h);
+        if constexpr (MASS) {  // the g (d^2 - 2 r.d) part of the volume second derivative
+            float dd = 0.f, rd = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float dk = __fsub_rn(r[k].h, __fsub_rn(sm.ts[(k * NS + b) * TJ + jl], sa[k]));
+                dd = fmaf(dk, dk, dd);
+                rd = fmaf(r[k].h, dk, rd);
+            }
+            vv = fmaf(g, dd - 2.f * rd, vv);
+        }
+#pragma unroll
+        for (int a2 = 0; a2 < NS; ++a2)
+            if (((LJM >> a2) & 1u) && a2 == a) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float f = __fmul_rn(g, r[k].h);
+                    if constexpr (PKF) {
+                        if (a2 == PA) { fp[k].x = __fsub_rn(fp[k].x, f); continue; }
+                        if (a2 == PB) { fp[k].y = __fsub_rn(fp[k].y, f); continue; }
+                    }
+                    fa[a2][k] = __fadd_rn(fa[a2][k], f);
+                }
+            }
+    }
+
+    // the close LJ site pairs of one evaluated batch (cm from interact; lane
+    // order, then site-pair order) into the ring cq; 32 at a time evaluated
+    __device__ __forceinline__ void push_close(const Smem &sm, int TJ, unsigned long long cm, int jl, int lane, int *cq) {
+        const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+        for (int a = 0; a < NS; ++a)
+#pragma unroll
+            for (int b = 0; b < NS; ++b) {
+                if (!((LJM >> a) & (LJM >> b) & 1u)) continue;
+                const bool c = (cm >> (a * NS + b)) & 1ull;
+                const unsigned m = __ballot_sync(FULL, c);
+                if (m == 0u) continue;
+                if (c) cq[(cqh + cqn + __popc(m & below)) & (CQCAP - 1)] = jl | (a << 24) | (b << 28);
+                cqn += __popc(m);
+                __syncwarp();
+                while (cqn >= 32) {
+                    close_pair(sm, TJ, cq[(cqh + lane) & (CQCAP - 1)]);
+                    __syncwarp();
+                    cqh = (cqh + 32) & (CQCAP - 1);
+                    cqn -= 32;
+                }
+            }
+    }
+
+    __device__ __forceinline__ void drain_close(const Smem &sm, int TJ, int lane, int *cq) {
+        if (cqn > 0) {
+            if (lane < cqn) close_pair(sm, TJ, cq[(cqh + lane) & (CQCAP - 1)]);
+            __syncwarp();
+            cqh = cqn = 0;
+        }
+    }
+
+    // one full batch of 32 waiting partners at ring position head
+    template <bool HP>
+    __device__ __forceinline__ void run_batch(const Smem &sm, int TJ, const int *wq, int head, int lane) {
+        const int jl = wq[(head + lane) & (QCAP - 1)];
+        const unsigned long long cm = interact<HP>(sm, TJ, jl);
+        __syncwarp();  // the batch is read before later passes overwrite its slots
+        if constexpr (CLOSE && !HP) push_close(sm, TJ, cm, jl, lane, const_cast<int *>(wq) + QCAP);
+    }
+
+    // the last qn < 32 waiting partners, then the remaining close pairs
+    template <bool HP>
+    __device__ __forceinline__ void run_tail(const Smem &sm, int TJ, const int *wq, int head, int qn, int lane) {
+        int jl = 0;
+        unsigned long long cm = 0ull;
+        if (lane < qn) {
+            jl = wq[(head + lane) & (QCAP - 1)];
+            cm = interact<HP>(sm, TJ, jl);
+        }
+        __syncwarp();
+        if constexpr (CLOSE && !HP) {
+            int *cq = const_cast<int *>(wq) + QCAP;
+            push_close(sm, TJ, cm, jl, lane, cq);
+            drain_close(sm, TJ, lane, cq);
+        }
     }
 
     // scan tile slots [0, tn) (global index of slot 0: t0), partners in batches of 32.
@@ -559,16 +733,12 @@ struct PairWarp {
             qn += n0 + __popc(m1);
             __syncwarp();
             while (qn >= 32) {
-                interact<HP>(sm, TJ, wq[(head + lane) & (QCAP - 1)]);
-                __syncwarp();  // the batch is read before later passes overwrite its slots
+                run_batch<HP>(sm, TJ, wq, head, lane);
                 head = (head + 32) & (QCAP - 1);
                 qn -= 32;
             }
         }
-        if (qn > 0) {
-            if (lane < qn) interact<HP>(sm, TJ, wq[(head + lane) & (QCAP - 1)]);
-            __syncwarp();
-        }
+        run_tail<HP>(sm, TJ, wq, head, qn, lane);
     }
 
     // The full scan of a whole-system tile (slots [0, tn)) that also lists, in
@@ -604,16 +774,12 @@ struct PairWarp {
             qn += n0 + __popc(m1);
             __syncwarp();
             while (qn >= 32) {
-                interact(sm, TJ, wq[(head + lane) & (QCAP - 1)]);
-                __syncwarp();
+                run_batch<false>(sm, TJ, wq, head, lane);
                 head = (head + 32) & (QCAP - 1);
                 qn -= 32;
             }
         }
-        if (qn > 0) {
-            if (lane < qn) interact(sm, TJ, wq[(head + lane) & (QCAP - 1)]);
-            __syncwarp();
-        }
+        run_tail<false>(sm, TJ, wq, head, qn, lane);
         return nc;
     }
 
@@ -645,16 +811,12 @@ struct PairWarp {
             qn += n0 + __popc(m1);
             __syncwarp();
             while (qn >= 32) {
-                interact(sm, TJ, wq[(head + lane) & (QCAP - 1)]);
-                __syncwarp();
+                run_batch<false>(sm, TJ, wq, head, lane);
                 head = (head + 32) & (QCAP - 1);
                 qn -= 32;
             }
         }
-        if (qn > 0) {
-            if (lane < qn) interact(sm, TJ, wq[(head + lane) & (QCAP - 1)]);
-            __syncwarp();
-        }
+        run_tail<false>(sm, TJ, wq, head, qn, lane);
     }
 
     // heat pass: the warp's sum_l d_kl P_kl (fixed tree, every lane)
@@ -687,6 +849,15 @@ struct PairWarp {
         o.uqq = warp_sum(uqq);
         o.udd = warp_sum(udd);
         o.w = warp_sum(w);
+        if constexpr (CLOSE) {  // the double-float close-contact sums (fixed xor tree), one rounding each
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) {
+                ucl = dfl::add(ucl, dfl::df{__shfl_xor_sync(FULL, ucl.h, s), __shfl_xor_sync(FULL, ucl.l, s)});
+                wcl = dfl::add(wcl, dfl::df{__shfl_xor_sync(FULL, wcl.h, s), __shfl_xor_sync(FULL, wcl.l, s)});
+            }
+            o.ulj = dfl::add(dfl::df{o.ulj, 0.f}, ucl).h;
+            o.w = dfl::add(dfl::df{o.w, 0.f}, wcl).h;
+        }
         if (elec == ELEC_RF) o.w += o.uqq;  // the bare-Coulomb site virials (before the molecular RF term)
         o.vv = MASS ? warp_sum(vv) : 0.f;
         o.np = warp_sum(np);

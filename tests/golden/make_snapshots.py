@@ -22,6 +22,8 @@ from paper_1507_07548_gb300 import workloads as W  # noqa: E402
 RECIPES = {
     "water_N1000": (lambda: W.water_box(N=1000, rc=14.0, seed=2), [(0.5, 200, None), (2.0, 600, None)]),
     "water_N216": (lambda: W.water_box(N=216, rc=9.0, seed=9), [(0.5, 200, None), (2.0, 600, None)]),
+    # ragged tiles: N = 1003 is no multiple of any tile or block size
+    "water_N1003": (lambda: W.water_box(N=1003, rc=13.0, seed=5), [(0.5, 200, None), (2.0, 400, None)]),
     "ionic_N1040": (lambda: W.ionic_solution(seed=3), [(0.5, 150, (4, 4, 4)), (2.0, 350, (4, 4, 4))]),
     "stockmayer_N500": (lambda: W.stockmayer_fluid(N=500, seed=4), [(1.0, 200, None), (2.0, 400, None)]),
 }

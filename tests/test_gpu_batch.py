@@ -62,6 +62,8 @@ def test_one_batched_step_matches_oracle(make):
         assert rms_rel(L, Lo) <= 1e-5
     U, Wv, T, P = s.energy_virial()
     assert abs(U - th[0, 0]) <= 1e-6 * abs(th[0, 0])
+    Wo = o.forces(R, q)[2]["W_total"]  # the virial on the identical (stepped) configuration
+    assert abs(Wv - Wo) <= 1e-6 * abs(Wo)
     F, tau = s.forces_torques()
     Fo, To, _ = o.forces(Ro, qo)
     assert rms_rel(F, Fo) <= 1e-5

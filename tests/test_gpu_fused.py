@@ -103,6 +103,10 @@ def test_fused_step_matches_oracle():
     assert rms_rel(L, Lo) <= 1e-5
     U, Wv, T, P = s.energy_virial()
     assert abs(U - th[-1, 0]) <= 1e-6 * abs(th[-1, 0])
+    # the virial on the identical configuration (the stepped GPU state): it moves
+    # ~1e-6 under position changes of 1e-8 A, the size of the one-step deviation
+    Wo = o.forces(R, q)[2]["W_total"]
+    assert abs(Wv - Wo) <= 1e-6 * abs(Wo)
     assert T == pytest.approx(2 * (th[-1, 2] + th[-1, 3]) / o.ndof(), rel=1e-9)
 
 
@@ -145,6 +149,9 @@ def test_fused_ewald_step_matches_oracle():
     assert abs(U - th[-1, 0]) <= 1e-6 * abs(th[-1, 0])
     F, tau = s.forces_torques()
     Fo, To, to = o.forces(R, q)
+    # the virial on the identical configuration, to the FP32 floor of the
+    # real-space terms of the ionic solution (test_gpu_parity.W_EWALD)
+    assert abs(Wv - to["W_total"]) <= 1e-5 * abs(to["W_total"])
     assert rms_rel(F, Fo) <= 1e-5 and rms_rel(tau, To) <= 1e-5
     t = s.energy_terms()
     assert t["U_rec"] == pytest.approx(to["U_rec"], rel=1e-6)

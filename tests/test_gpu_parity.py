@@ -23,13 +23,17 @@ def rms_rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-# The molecular virial of a liquid snapshot is limited by the FP32 representation
-# of the site-site vectors (ulp(3 A)/2 ~ 1.2e-7 A) acting through the stiffness
-# of close contacts: d(r.F)/dr ~ 1e4-1e5 K/A over ~3e4 close site pairs gives
-# ~1 K of random error, i.e. 1-4e-6 of W for liquid water and the ionic solution
-# (measured; an FP32 emulation of the kernel reproduces it).  Those two cases are
-# held to W_FLOOR; every other case and every energy to 1e-6.
-W_FLOOR = 5e-6
+# The molecular virial of the ionic solution at ambient pressure is ~1/100 of its
+# LJ and real-space Coulomb parts (W = -2.0e5 K against +2.4e7 K of LJ virial and
+# -1.8e7 K of site-lever terms).  Each FP32 real-space site-pair term carries
+# ~1e-7 relative rounding; over the ~3.5e6 charged site pairs of a configuration
+# that leaves ~0.5 K rms in W (an FP32 emulation of the kernel puts 0.3 K in the
+# erfc virial terms and 0.4 K in the force factors that meet the site levers),
+# i.e. 2.5e-6 of this W; measured 1.7e-6 on the snapshot and up to 7e-6 on
+# stepped states.  Close-contact LJ pairs are double-float; the erfc terms are
+# not.  The Ewald cases are held to W_EWALD; every other case and every energy
+# to 1e-6.
+W_EWALD = 1e-5
 
 
 def compare(s, o, R, q, tol_f=1e-5, tol_e=1e-6, tol_w=None):
@@ -108,16 +112,14 @@ def test_water_rf_full_size_parity():
     wl = water_c1()
     s = ms2.System.from_workload(wl)
     o = Oracle.from_workload(wl)
-    compare(s, o, wl.R, wl.q, tol_w=W_FLOOR)
+    compare(s, o, wl.R, wl.q)
 
 
-def test_water_rf_ragged_lattice_start():
-    """Unrelaxed lattice start, N = 1003 (ragged tiles).  Random orientations give
-    |U| ~15x smaller than the liquid's while the site terms have liquid size, so
-    energies are held to 1e-5 here; forces and torques to the usual 1e-5."""
-    wl = W.water_box(N=1003, rc=13.0, seed=5)
+def test_water_rf_ragged_tiles():
+    """N = 1003 liquid water (no multiple of any tile or block size), rc = 13 A."""
+    wl = snapshot(W.water_box(N=1003, rc=13.0, seed=5), "water_N1003")
     s = ms2.System.from_workload(wl)
-    compare(s, Oracle.from_workload(wl), wl.R, wl.q, tol_e=1e-5)
+    compare(s, Oracle.from_workload(wl), wl.R, wl.q)
 
 
 def test_site_offsets_match_oracle():
@@ -169,7 +171,7 @@ def test_ionic_ewald_full_size_parity():
     wl = ionic_c2()
     s = ms2.System.from_workload(wl)
     o = Oracle.from_workload(wl)
-    F, tau, t, to = compare(s, o, wl.R, wl.q, tol_w=W_FLOOR)
+    F, tau, t, to = compare(s, o, wl.R, wl.q, tol_w=W_EWALD)
     for k in ("U_rec", "U_self", "U_intra"):
         assert t[k] == pytest.approx(to[k], rel=1e-6)
     assert t["W_rec"] == pytest.approx(to["W_rec"], rel=1e-5, abs=1e-6 * abs(to["W_total"]))
@@ -295,8 +297,7 @@ def test_two_molecules_and_no_partners():
     R[1] = [4.0, 1.0, 1.0]
     s.set_state(R)
     o = Oracle([m], np.zeros(2, np.int32), 20.0, 5.0, elec=1)
-    # a single close pair: 10 site terms cancel ~10x in FP32, so 1e-5 here
-    compare(s, o, R, np.tile([1.0, 0, 0, 0], (2, 1)), tol_e=1e-5)
+    compare(s, o, R, np.tile([1.0, 0, 0, 0], (2, 1)))
 
 
 def test_invalid_arguments_are_rejected():
@@ -319,7 +320,7 @@ def test_ionic_ewald_anisotropic_k_range():
     wl.kmax = (5, 7, 9)
     s = ms2.System.from_workload(wl)
     o = Oracle.from_workload(wl)
-    F, tau, t, to = compare(s, o, wl.R, wl.q, tol_w=W_FLOOR)
+    F, tau, t, to = compare(s, o, wl.R, wl.q, tol_w=W_EWALD)
     assert t["U_rec"] == pytest.approx(to["U_rec"], rel=1e-6)
     assert t["W_rec"] == pytest.approx(to["W_rec"], rel=1e-5, abs=1e-6 * abs(to["W_total"]))
 
