@@ -234,7 +234,10 @@ MS2_API ms2_status ms2_batch_destroy(ms2_batch b);
 /* A simulation job: model mix entry, size and state point, steps, outputs.
  * The server builds the system itself (ms2_create_system defaults with this
  * seed).  arrival_time (s, on the server's clock, which starts at
- * ms2_serve_open) is when the job becomes eligible. */
+ * ms2_serve_open) is when the job becomes eligible.  R0 (N x 3) and q0 (N x 4),
+ * if not NULL, replace the lattice start's centres and orientations (a restart
+ * from a checkpoint); they are copied at submit and checked at admission as by
+ * ms2_set_state (a failure retires the job with that status). */
 typedef struct {
     const ms2_model *models;
     const int *N_per_model;
@@ -246,6 +249,8 @@ typedef struct {
     unsigned long long seed;
     int rdf_bins;         /* 0: no RDF output */
     int rdf_every;
+    const double *R0;     /* optional start: centres, N x 3 */
+    const double *q0;     /* optional start: unit quaternions, N x 4 */
 } ms2_job;
 
 typedef struct {
@@ -386,6 +391,19 @@ MS2_API ms2_status ms2_step_kernel(ms2_system sys, int *fused);
  * is off or the last chunk ran as per-phase kernels. */
 MS2_API ms2_status ms2_last_step_phases(ms2_system sys, double out[12]);
 MS2_API ms2_status ms2_last_step_times(ms2_system sys, double out[4]);
+
+/* Fault-path hook (tests of failure detection; no counterpart in the paper).
+ * what = MS2_FAULT_BARRIER: the next fused launch of sys (ms2_step) limits each
+ * grid-barrier wait to wait_s seconds (1e-6 <= wait_s <= 2) and makes its first
+ * barrier wait for one arrival more than the grid has.  That wait runs out, the
+ * kernel raises its sticky timeout flag, every other wait ends at once and the
+ * launch returns; the next ms2_energy_virial reports MS2_ETIMEOUT, clears the
+ * flag, and the state is unspecified until ms2_set_state.  No wait is
+ * unbounded and no memory access leaves its buffer.  MS2_EINVAL for another
+ * `what` or wait_s out of range; MS2_ESTATE if the system has no fused kernel
+ * (ms2_step_kernel). */
+enum { MS2_FAULT_BARRIER = 1 };
+MS2_API ms2_status ms2_fault_inject(ms2_system sys, int what, double wait_s);
 
 /* ------------------------------------------------------- allocation-free */
 /* Forces, torques, potential energy and molecular virial of ONE configuration

@@ -984,6 +984,16 @@ extern "C" ms2_status ms2_create_system(const ms2_model *models, const int *N_pe
     return MS2_OK;
 }
 
+extern "C" ms2_status ms2_fault_inject(ms2_system s, int what, double wait_s) {
+    if (!s) return ms2_fail(MS2_EINVAL, "null system");
+    if (what != MS2_FAULT_BARRIER) return ms2_fail(MS2_EINVAL, "unknown fault %d", what);
+    if (!(wait_s >= 1e-6 && wait_s <= 2.0)) return ms2_fail(MS2_EINVAL, "wait limit must be 1e-6..2 s");
+    if (!s->step_fn) return ms2_fail(MS2_ESTATE, "the system has no fused step kernel");
+    s->fault_barrier = 1;
+    s->fault_wait_ns = (unsigned long long)(wait_s * 1e9);
+    return MS2_OK;
+}
+
 extern "C" ms2_status ms2_enable_timing(ms2_system s, int on) {
     if (!s) return ms2_fail(MS2_EINVAL, "null system");
     MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
@@ -1106,6 +1116,9 @@ static bool run_fused(ms2_system s, long long m, long long s0) {
     A.ny_per_chunk = s->ny_per_chunk;
     A.ews = (int)step_ews(s);
     A.tmax = (unsigned long long *)(cnt + 56);  // 3 x 8 bytes at byte 224 of the counter block (zero at entry)
+    A.wait_ns = s->fault_barrier ? s->fault_wait_ns : 2000000000ull;  // 2 s (grid_dev::WAIT_NS)
+    A.bar_extra = s->fault_barrier ? 1u : 0u;
+    s->fault_barrier = 0;  // one launch
     if (s->timing) cudaEventRecord(s->ev[0], s->stream);
     const cudaError_t e = ms2_launch_step(fn, s->step_grid, smem, s->stream, s->dP, s->d, A);
     if (e != cudaSuccess) {  // e.g. co-residency refused: the per-phase kernels from now on

@@ -28,11 +28,13 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // block's writes happen before thread 0's arrival (bar.sync), which is a
 // gpu-scope release; thread 0's polling load is a gpu-scope acquire, and the
 // closing bar.sync orders the block's later reads after it (release/acquire are
-// cumulative in the PTX memory model).  A block that waits longer than WAIT_NS
-// sets the sticky flag *err, which ends every other wait at once, and calls
-// on_timeout() (thread 0); the kernel then runs on without waiting.
+// cumulative in the PTX memory model).  A block that waits longer than wait_ns
+// (WAIT_NS unless a test shortens it) sets the sticky flag *err, which ends
+// every other wait at once, and calls on_timeout() (thread 0); the kernel then
+// runs on without waiting.
 template <class OnTimeout>
-__device__ __forceinline__ void grid_sync(unsigned *count, unsigned *err, unsigned &target, OnTimeout on_timeout) {
+__device__ __forceinline__ void grid_sync(unsigned *count, unsigned *err, unsigned &target, OnTimeout on_timeout,
+                                          unsigned long long wait_ns = WAIT_NS) {
     __syncthreads();
     target += gridDim.x;
     if (threadIdx.x == 0) {
@@ -40,7 +42,7 @@ __device__ __forceinline__ void grid_sync(unsigned *count, unsigned *err, unsign
         const unsigned long long t0 = global_ns();
         while (ld_acquire_u32(count) < target) {
             if (ld_acquire_u32(err) != 0u) break;  // another block gave up
-            if (global_ns() - t0 > WAIT_NS) {
+            if (global_ns() - t0 > wait_ns) {
                 atomicExch(err, 1u);
                 on_timeout();
                 break;

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     Eng e;
     e.setup(Ps);
     if (b == 0 && threadIdx.x == 0) *A.bar_next = 0u;
-    unsigned target = 0;
+    unsigned target = A.bar_extra;
     auto on_timeout = [&]() { S.scal[SC_KERR] = 1.0; };
     using grid_dev::grid_sync;
     const bool rfq = Eng::MOLD && e.rfq;
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
                 }
             }
         mark(k, 0);
-        grid_sync(A.bar, A.err, target, on_timeout);
+        grid_sync(A.bar, A.err, target, on_timeout, A.wait_ns);
         if (tm) tph[1] = global_ns();
         // ---- stage the whole system; pair items of the own molecules; RDF
         stage_tile<NS, Eng::DMU, MULTI>(sm, S, 0, N, A.Np, rfq);
@@ -255,10 +255,10 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
             const int nkc = ewald::n_sum_tasks(ewald::n_k(S.kx, S.ky, S.kz));
             unsigned long long te = tm ? global_ns() : 0ull;  // timing (block 0): each phase until its barrier ends
             for (int sb = b; sb < nsb; sb += G) ewald::sk_task(Ps, S, sb, ews, threadIdx.x, STEP_THREADS);
-            grid_sync(A.bar, A.err, target, on_timeout);
+            grid_sync(A.bar, A.err, target, on_timeout, A.wait_ns);
             if (tm) { const unsigned long long t = global_ns(); S.scal[SC_TPH9] = (double)(t - te); te = t; }
             for (int kc = b; kc < nkc; kc += G) ewald::sum_task(S, A.AS, kc, nsb, ews, threadIdx.x, STEP_THREADS);
-            grid_sync(A.bar, A.err, target, on_timeout);
+            grid_sync(A.bar, A.err, target, on_timeout, A.wait_ns);
             if (tm) { const unsigned long long t = global_ns(); S.scal[SC_TPH10] = (double)(t - te); te = t; }
             const int ng = (M + STEP_THREADS - 1) / STEP_THREADS, nft = ng * S.kchunks;
             // U_rec and W_rec: the last block, which has no force task when there are fewer than G
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
                     ewald::force_task<0>(Ps, S, A.AS, (t % ng) * STEP_THREADS, t / ng, A.ny_per_chunk, ews, threadIdx.x,
                                          STEP_THREADS);
             }
-            grid_sync(A.bar, A.err, target, on_timeout);
+            grid_sync(A.bar, A.err, target, on_timeout, A.wait_ns);
             if (tm) S.scal[SC_TPH11] = (double)(global_ns() - te);
         }
         // ---- reduction unit b: the own molecules
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
             reduce_unit<true>(Ps, S, io, RED_SUM | RED_LAMBDA | EWM | (!ev && gk_step(A, k) ? RED_GK : 0), b, G, lane);
         }
         mark(k, 2);
-        grid_sync(A.bar, A.err, target, on_timeout);
+        grid_sync(A.bar, A.err, target, on_timeout, A.wait_ns);
         if (tm) tph[3] = global_ns();
         // ---- totals in every block; thermostat factor for the next drift
         reduce_totals(S, G, tot, !ev && gk_step(A, k) ? Q_N + 3 : Q_N);
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     }
     if (b == 0 && warp == 0 && lane < AC_COUNT_) S.acc[lane] = acc_s[lane];  // the launch's running sums
     if (HEAT && A.nsteps > 0 && hf_step(A, A.nsteps - 1)) {  // uniform over the grid
-        grid_sync(A.bar, A.err, target, on_timeout);
+        grid_sync(A.bar, A.err, target, on_timeout, A.wait_ns);
         if (b == 0 && warp == 0) heat_record(S, G, lane);
     }
     // the write-back starts at warp 1, so that block 0's record (warp 0) runs

@@ -80,6 +80,10 @@ struct ms2_system_s {
     // set_state leaves forces, energies and site build stale; the next query
     // evaluates them, or the next fused step does it in its prologue
     bool stale = false;
+    // fault-path test: the next fused launch's first grid barrier waits for one
+    // arrival more than the grid has, each wait limited to fault_wait_ns
+    int fault_barrier = 0;
+    unsigned long long fault_wait_ns = 0;
     // timing events: [0] step start, [1] before pair, [2] after pair, [3] after Ewald, [4] step end
     bool timing = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};

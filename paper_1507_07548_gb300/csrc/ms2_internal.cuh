@@ -172,6 +172,8 @@ struct StepArgs {
     int ny_per_chunk;      // Ewald: ny values per force k chunk
     int ews;               // Ewald: bytes of the block's reciprocal-space task scratch
     unsigned long long *tmax;  // timing: [3] latest compute-end times over blocks (zero at entry, re-zeroed after use)
+    unsigned long long wait_ns;  // limit of each grid-barrier wait
+    unsigned bar_extra;          // arrivals the first barrier waits for beyond the grid (0; 1: a fault-path test)
 };
 
 // ------------------------------------------------------------ helpers

@@ -42,6 +42,7 @@ struct JobSpec {
     long long steps = 0;
     unsigned long long seed = 1;
     int rdf_bins = 0, rdf_every = 0;
+    std::vector<double> R0, q0;  // optional start (empty: the lattice start)
     size_t bytes = 0;
 };
 
@@ -163,6 +164,9 @@ static void admit(ms2_server S) {
         o.stream = (void *)S->stream;
         ms2_status st = ms2_create_system(models.data(), j.counts.data(), (int)models.size(), 0.0, j.T, j.rho,
                                           j.cutoff, j.elec, &o, &sl.sys);
+        if (st == MS2_OK && (!j.R0.empty() || !j.q0.empty()))
+            st = ms2_set_state(sl.sys, j.R0.empty() ? nullptr : j.R0.data(), j.q0.empty() ? nullptr : j.q0.data(),
+                               nullptr, nullptr);
         if (st == MS2_OK && j.rdf_bins > 0) {
             int N = 0;
             double box = 0, rc = 0;
@@ -310,6 +314,12 @@ extern "C" ms2_status ms2_serve_submit(ms2_server S, const ms2_job *job, long lo
     j.seed = job->seed;
     j.rdf_bins = job->rdf_bins;
     j.rdf_every = job->rdf_every;
+    {
+        long long N = 0;
+        for (int c : j.counts) N += c;
+        if (job->R0) j.R0.assign(job->R0, job->R0 + 3 * N);
+        if (job->q0) j.q0.assign(job->q0, job->q0 + 4 * N);
+    }
     j.bytes = estimate_bytes(j);
     if (j.bytes > S->budget)
         return ms2_fail(MS2_EBUDGET, "job needs ~%zu bytes of device memory, budget is %zu", j.bytes, S->budget);

@@ -54,7 +54,8 @@ class ms2_job(C.Structure):
     _fields_ = [("models", C.POINTER(ms2_model)), ("N_per_model", C.POINTER(C.c_int)), ("n_models", C.c_int),
                 ("T", C.c_double), ("rho", C.c_double), ("cutoff", C.c_double), ("elec", C.c_int),
                 ("steps", C.c_longlong), ("arrival_time", C.c_double), ("seed", C.c_ulonglong),
-                ("rdf_bins", C.c_int), ("rdf_every", C.c_int)]
+                ("rdf_bins", C.c_int), ("rdf_every", C.c_int), ("R0", C.POINTER(C.c_double)),
+                ("q0", C.POINTER(C.c_double))]
 
 
 class ms2_job_result(C.Structure):
@@ -111,6 +112,7 @@ SIGNATURES = {
     "ms2_step_kernel": (C.c_int, [_vp, _P(C.c_int)]),
     "ms2_last_step_phases": (C.c_int, [_vp, _d]),
     "ms2_last_step_times": (C.c_int, [_vp, _d]),
+    "ms2_fault_inject": (C.c_int, [_vp, C.c_int, C.c_double]),
     "ms2_forces_noalloc": (C.c_int, [_P(ms2_model), _P(C.c_int), C.c_int, C.c_double, C.c_double, C.c_int,
                                      _P(ms2_options), _vp, _vp, _vp, _vp, _vp, _vp]),
     "ms2_noalloc_scratch_bytes": (C.c_size_t, []),
@@ -304,6 +306,11 @@ class System:
     def enable_timing(self, on=True):
         check(lib().ms2_enable_timing(self.h, int(on)))
 
+    def fault_inject_barrier(self, wait_s):
+        """The next fused launch's first grid barrier waits for one arrival more than
+        the grid has, each wait limited to wait_s (a fault-path test)."""
+        check(lib().ms2_fault_inject(self.h, 1, float(wait_s)))
+
     def volume_derivatives(self):
         """(dU/dV, d2U/dV2) of the current configuration (needs massieu=1 at creation)."""
         a, b = C.c_double(), C.c_double()
@@ -438,13 +445,18 @@ class Server:
         self.h = h
         self._keep = []
 
-    def submit(self, models, counts, T, rho, cutoff, elec, steps, arrival=0.0, seed=1, rdf_bins=0, rdf_every=10):
+    def submit(self, models, counts, T, rho, cutoff, elec, steps, arrival=0.0, seed=1, rdf_bins=0, rdf_every=10,
+               R0=None, q0=None):
         m, keep = make_models(models)
         cnt = (C.c_int * len(counts))(*[int(c) for c in counts])
-        self._keep.append((m, keep, cnt))
+        n = int(sum(counts))
+        R0 = None if R0 is None else np.ascontiguousarray(R0, np.float64).reshape(n, 3)
+        q0 = None if q0 is None else np.ascontiguousarray(q0, np.float64).reshape(n, 4)
+        self._keep.append((m, keep, cnt, R0, q0))
         j = ms2_job(models=C.cast(m, C.POINTER(ms2_model)), N_per_model=C.cast(cnt, C.POINTER(C.c_int)),
                     n_models=len(models), T=T, rho=rho, cutoff=cutoff, elec=elec, steps=steps,
-                    arrival_time=arrival, seed=seed, rdf_bins=rdf_bins, rdf_every=rdf_every)
+                    arrival_time=arrival, seed=seed, rdf_bins=rdf_bins, rdf_every=rdf_every,
+                    R0=None if R0 is None else _dp(R0), q0=None if q0 is None else _dp(q0))
         jid = C.c_longlong()
         check(lib().ms2_serve_submit(self.h, C.byref(j), C.byref(jid)))
         return jid.value
