@@ -7,8 +7,11 @@ quaternion integration, dt = 2 fs, FP32 site-pair arithmetic with FP64 state
 and sums.  One benchmark step = one MD time step: partner search + site-pair
 energies/forces/torques (pair kernel), reduction + thermostat kick, drift +
 quaternion rotation + site build.  The RDF (every 10 steps) is sampled as well.
-Synthetic input: simple-cubic lattice start with seeded random orientations and
-Maxwell-Boltzmann velocities, relaxed by untimed MD steps before warm-up.
+Synthetic input: the liquid snapshot tests/golden/water_N1000.npz (a seeded
+simple-cubic lattice start with random orientations and Maxwell-Boltzmann
+velocities, relaxed by FP64 NVT leapfrog steps; written by
+tests/golden/make_snapshots.py).  The GPU arm, the CPU baseline and the
+reference arm all start from it.
 
 The L2 cache (129 MB; the whole system is ~0.1 MB) is flushed by writing a
 256 MiB buffer between timed steps, outside the timed interval.  Each step is
@@ -36,12 +39,23 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_WATER, RC, SEED = 1000, 14.0, 2
-RELAX_STEPS = 300
+SNAPSHOT = os.path.join(ROOT, "tests", "golden", "water_N1000.npz")
 RDF_EVERY = 10
 # algorithmic FP32 flops per unique water molecule pair (reaction field):
 # 9 charge site pairs x 22 + the O-O LJ extra 10 + pair set-up/virial 22
 FLOPS_PER_WATER_PAIR = 9 * 22 + 10 + 22
-SMS, FP32_LANES = 152, 128
+FP32_LANES = 128   # FP32 FMA lanes per SM (Blackwell)
+
+
+def workload():
+    """The benchmark system: 1000 water at 997 kg/m^3, rc = 14 A, in the relaxed
+    liquid state of the committed snapshot."""
+    import numpy as np
+    from paper_1507_07548_gb300 import workloads as W
+    wl = W.water_box(N=N_WATER, rc=RC, seed=SEED)
+    z = np.load(SNAPSHOT)
+    wl.R, wl.q, wl.v, wl.Lang = z["R"], z["q"], z["v"], z["Lang"]
+    return wl
 
 
 def parse():
@@ -134,8 +148,7 @@ def oracle_rate(seconds, nsteps=None, threads=0):
     cores (all of them, or `threads`); returns (pair interactions/s, steps,
     seconds, threads used)."""
     from oracle import Oracle
-    from paper_1507_07548_gb300 import workloads as W
-    wl = W.water_box(N=N_WATER, rc=RC, seed=SEED)
+    wl = workload()
     o = Oracle.from_workload(wl)
     cores = len(os.sched_getaffinity(0))
     R, q, v, L = wl.R, wl.q, wl.v, wl.Lang
@@ -158,8 +171,7 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return 0
     from oracle import Oracle
-    from paper_1507_07548_gb300 import workloads as W
-    wl = W.water_box(N=N_WATER, rc=RC, seed=SEED)
+    wl = workload()
     o = Oracle.from_workload(wl)
     cores = len(os.sched_getaffinity(0))
     R, q, v, L = wl.R, wl.q, wl.v, wl.Lang
@@ -176,7 +188,8 @@ def reference_arm(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": "rigid 3-site water N=1000, reaction field, rc=14 A, 298 K, dt=2 fs",
+            "config": {"workload": "rigid 3-site water N=1000, reaction field, rc=14 A, 298 K, dt=2 fs, leapfrog+quaternion",
+                       "molecules": N_WATER, "start": "relaxed liquid snapshot (tests/golden/water_N1000.npz)",
                        "parallelism": "host cores (OpenMP owner loop)"},
             "cpu_baseline": {"value": val, "unit": "pair interactions/s", "cores": cores, "kind": "oracle",
                              "sample": "%d full MD steps of the workload" % args.steps},
@@ -235,9 +248,8 @@ def gpu_arm(args, rank, world, local_rank):
 
     stream = torch.cuda.Stream()               # a real stream handle shared with the library
     torch.cuda.set_stream(stream)
-    wl = W.water_box(N=N_WATER, rc=RC, seed=SEED)
+    wl = workload()
     s = ms2.System.from_workload(wl, stream=stream.cuda_stream)
-    s.step(RELAX_STEPS)                              # relax the lattice start (untimed)
     s.rdf_setup(min(RC, 0.5 * s.L), 280, every=RDF_EVERY)
     s.enable_timing(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -301,7 +313,8 @@ def gpu_arm(args, rank, world, local_rank):
         return 0
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    peak_tflops = sms * FP32_LANES * 2 * sm_max * 1e6 / 1e12
     flops = FLOPS_PER_WATER_PAIR * sum(pairs)
     # dominant kernel: the fused step kernel (one launch per step) or, per phase, the pair kernel
     kern_ms = t_kern if fused else t_pair
@@ -316,6 +329,7 @@ def gpu_arm(args, rank, world, local_rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "rigid 3-site water N=1000, reaction field, rc=14 A, 298 K, dt=2 fs, leapfrog+quaternion",
                    "molecules": N_WATER, "l2": "flushed between steps (256 MiB write)",
+                   "start": "relaxed liquid snapshot (tests/golden/water_N1000.npz)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "state": "FP64 positions/integrator/sums, FP32 site pairs"},
         "molecule_steps_per_s": N_WATER * args.steps * world / (tot_ms_max * 1e-3),
@@ -324,7 +338,8 @@ def gpu_arm(args, rank, world, local_rank):
                      "kernel": "k_step<3,1,7,0,RF> (fused MD step)" if fused else "k_pair<3,1,7,0,RF>",
                      "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (unit counts x max clock)" % sm_max,
+                     "peak_source": "%d SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz max SM clock (unit counts; "
+                                    "MEASURED_PEAKS.json has no FP32 figure)" % (sms, sm_max),
                      "kernel_ms": statistics.mean(kern_ms),
                      "pair_phase_ms": statistics.mean(t_pair),
                      "algorithmic_flops_per_launch": FLOPS_PER_WATER_PAIR * statistics.mean(pairs)},
@@ -440,9 +455,7 @@ def massieu_sub(args, stream, flush):
     import torch
     import paper_1507_07548_gb300.ms2 as ms2
     from paper_1507_07548_gb300 import workloads as W
-    wl = W.water_box(N=N_WATER, rc=RC, seed=SEED)
-    s = ms2.System.from_workload(wl, stream=stream.cuda_stream, massieu=1)
-    s.step(RELAX_STEPS)
+    s = ms2.System.from_workload(workload(), stream=stream.cuda_stream, massieu=1)
     s.reset_averages()
     t = []
     for k in range(MASSIEU_STEPS + args.warmup):
@@ -459,8 +472,8 @@ def massieu_sub(args, stream, flush):
     return {"workload": "rigid 3-site water N=1000, reaction field, rc=14 A, 298 K, Massieu moments every step",
             "ms_per_step": statistics.mean(t), "samples": n,
             "A_r": {k: float(v) for k, v in A.items()},
-            "note": "%d samples after %d relaxation steps: a short run, the values illustrate the output "
-                    "rather than converged properties" % (n, RELAX_STEPS)}
+            "note": "%d samples from the relaxed liquid snapshot: a short run, the values illustrate the output "
+                    "rather than converged properties" % n}
 
 
 def thermal_sub(args, stream, flush):
@@ -470,9 +483,7 @@ def thermal_sub(args, stream, flush):
     import torch
     import paper_1507_07548_gb300.ms2 as ms2
     from paper_1507_07548_gb300 import workloads as W
-    wl = W.water_box(N=N_WATER, rc=RC, seed=SEED)
-    s = ms2.System.from_workload(wl, stream=stream.cuda_stream)
-    s.step(RELAX_STEPS)
+    s = ms2.System.from_workload(workload(), stream=stream.cuda_stream)
     s.heat_setup(every=1, n_lags=8)
     fused = s.fused_step() == 1
     t = []
@@ -507,9 +518,11 @@ def ewald_sub(args, stream):
     import torch
     import paper_1507_07548_gb300.ms2 as ms2
     from paper_1507_07548_gb300 import workloads as W
+    import numpy as np
     wl = W.ionic_solution(seed=3)
+    z = np.load(os.path.join(ROOT, "tests", "golden", "ionic_N1040.npz"))   # relaxed liquid state
+    wl.R, wl.q, wl.v, wl.Lang = z["R"], z["q"], z["v"], z["Lang"]
     s = ms2.System.from_workload(wl, stream=stream.cuda_stream)
-    s.step(RELAX_STEPS)
     s.enable_timing(True)
     fused = s.fused_step()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -557,7 +570,7 @@ def uniform_batch(args):
     import torch
     import paper_1507_07548_gb300.ms2 as ms2
     from paper_1507_07548_gb300 import workloads as W
-    wl = W.water_box(N=N_WATER, rc=RC, seed=SEED)
+    wl = workload()
     ss = [ms2.System.from_workload(wl) for _ in range(args.uniform_batch)]
     b = ms2.Batch(ss)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")

@@ -140,13 +140,24 @@ MS2_API ms2_status ms2_system_info(ms2_system sys, int *N, double *box, double *
 /* Advances n >= 0 time steps (asynchronous).  Each step: interaction partner
  * search, site-pair energies/forces/torques (+ Ewald reciprocal space), then the
  * integrator (velocity Verlet, or leapfrog with the quaternion implicit
- * midpoint rule), with isokinetic scaling when the thermostat is on. */
+ * midpoint rule), with isokinetic scaling when the thermostat is on.  Paper,
+ * Sec. "Hybrid MPI & OpenMP Parallelization": the partner search, the energy
+ * and the force calculation are the loops over molecules that make up an MD
+ * step; the paper names no integrator or thermostat (the leapfrog, quaternion
+ * rule and isokinetic scaling are this library's stated readings).
+ * Errors: MS2_EINVAL (n < 0); failures of the work show at the next read. */
 MS2_API ms2_status ms2_step(ms2_system sys, long long n);
 
 /* Potential energy U (incl. LRC and Ewald constants), molecular virial W
  * (sum over pairs of (R_i - R_j).F_ij, + reciprocal part; excl. LRC), kinetic
  * temperature of the stored velocities and pressure P = (2 KE_tr/3 + W/3)/V + P_LRC,
- * for the current configuration.  Any pointer may be NULL. */
+ * for the current configuration.  Any pointer may be NULL.  Paper, Sec.
+ * "Massieu potential derivatives": U and its volume derivative (W = -3V dU/dV
+ * at fixed scaled centres and orientations) are the NVT ensemble's sampled
+ * quantities; the LRC follows the same section's LRC paragraph.  Synchronises
+ * the system stream.  Errors: MS2_EUNSTABLE (non-finite or exploding forces),
+ * MS2_ETIMEOUT (a bounded wait of the last fused launch ran out; the state is
+ * then unspecified until ms2_set_state), MS2_ECUDA. */
 MS2_API ms2_status ms2_energy_virial(ms2_system sys, double *U, double *W, double *T_inst, double *P);
 
 /* The 16-number breakdown of the current configuration, in this order:
@@ -156,17 +167,24 @@ MS2_API ms2_status ms2_energy_virial(ms2_system sys, double *U, double *W, doubl
 MS2_API ms2_status ms2_energy_terms(ms2_system sys, double terms[16]);
 
 /* Molecule forces F (N x 3) and space-frame torques tau (N x 3) of the current
- * configuration, in K/Angstrom and K. */
+ * configuration, in K/Angstrom and K (paper, Sec. "Hybrid MPI & OpenMP
+ * Parallelization": every pair force acts on both molecules, and the same holds
+ * for torques; here each molecule's owner sums its own, so no write is shared).
+ * Caller-owned host arrays; synchronises the system stream.  Errors as
+ * ms2_energy_virial. */
 MS2_API ms2_status ms2_forces_torques(ms2_system sys, double *F, double *tau);
 /* Same, into device buffers of 3N doubles each, queued on the system stream. */
 MS2_API ms2_status ms2_forces_torques_dev(ms2_system sys, double *F_dev, double *tau_dev);
 
 /* Ewald splitting parameter and k box |n_x| <= kx, |n_y| <= ky, |n_z| <= kz
- * (k = 2 pi n / box).  MS2_EINVAL unless the system uses MS2_ELEC_EWALD or if
+ * (k = 2 pi n / box); paper, Sec. "Algorithmic Developments", paragraph "Ewald
+ * summation" (real-space erfc sum within the cut-off plus the reciprocal sum
+ * over these k vectors, tin-foil boundary).  MS2_EINVAL unless the system uses MS2_ELEC_EWALD or if
  * alpha <= 0 or a kmax is outside 1..64.  Recomputes forces. */
 MS2_API ms2_status ms2_ewald_params(ms2_system sys, double alpha, int kx, int ky, int kz);
 
-/* State for checkpoint/restart: centres R (N x 3), unit quaternions q (N x 4,
+/* State for checkpoint/restart (no counterpart in the paper; the quantities
+ * its MD integrates): centres R (N x 3), unit quaternions q (N x 4,
  * (w, x, y, z), body -> space), centre velocities v (N x 3) and space-frame
  * angular momenta Lang (N x 3, g/mol*A^2/fs) — for the leapfrog these are the
  * values half a step behind R and q — and the step counter.  Any pointer may be
@@ -207,7 +225,16 @@ MS2_API ms2_status ms2_averages(ms2_system sys, double out[5], long long *n_step
 MS2_API ms2_status ms2_reset_averages(ms2_system sys);
 
 /* ----------------------------------------------------------------- batch */
-/* A batch advances many independent systems together: per chunk of steps, one
+/* Paper, Sec. "Introduction": the tool serves high-throughput work, many
+ * independent simulations of ~10^3 molecules (e.g. the state points of a
+ * phase diagram); each system here is one such simulation, and batching them
+ * onto one GPU has no counterpart in the paper.  Arguments: systems[0..n) are
+ * the caller's systems (n >= 1, each in at most one batch; the batch keeps the
+ * handles, not copies); *out receives the batch.  ms2_batch_step advances
+ * every system by n >= 0 steps (asynchronous); read results per system.
+ * Errors: MS2_EINVAL (a system the batch kernels do not take, see below),
+ * MS2_ENOMEM, MS2_ECUDA.
+ * A batch advances many independent systems together: per chunk of steps, one
  * cooperative persistent kernel per model kind (slot pattern) runs every phase
  * of a step (drift and site build, partner search and site-pair forces, RDF
  * samples, reduction, thermostat, record) over all of the kind's systems at
@@ -271,8 +298,13 @@ typedef struct {
  * single-system kernels.  All the server's systems share one stream.  Results
  * are reproducible for a given arrival sequence; the two paths agree within the
  * parity tolerances, not bit for bit. */
+/* (Serving has no counterpart in the paper; each job is one simulation as in
+ * its Sec. "Introduction".)  opt: the defaults of the jobs' systems (NULL:
+ * ms2_default_options); *out receives the server.  Errors: MS2_EINVAL, MS2_ECUDA. */
 MS2_API ms2_status ms2_serve_open(size_t hbm_budget_bytes, int max_slots, const ms2_options *opt, ms2_server *out);
-/* Queues a job (never blocks).  MS2_EBUDGET if it alone exceeds the budget. */
+/* Queues a job (never blocks); the job's arrays are copied, *job_id receives its
+ * id.  MS2_EBUDGET if it alone exceeds the budget; MS2_EINVAL for bad models or
+ * sizes (failures found at admission are reported in the job's result). */
 MS2_API ms2_status ms2_serve_submit(ms2_server s, const ms2_job *job, long long *job_id);
 /* Copies up to max finished results out (oldest first) and removes them. */
 MS2_API ms2_status ms2_serve_poll(ms2_server s, ms2_job_result *out, int max, int *n_done);
@@ -415,7 +447,8 @@ MS2_API ms2_status ms2_fault_inject(ms2_system sys, int what, double wait_s);
  * has no counterpart in the paper.)
  * Inputs (device, row-major FP64): centres R_dev (N x 3), unit quaternions
  * q_dev (N x 4); models/N_per_model/box/cutoff/elec/opt as for
- * ms2_create_system (box > 0 required; MS2_ELEC_NONE or MS2_ELEC_RF only).
+ * ms2_create_system (box > 0 required; MS2_ELEC_NONE or MS2_ELEC_RF only;
+ * opt->fp64 must be 0: the site-pair arithmetic is FP32 here).
  * Outputs (device, FP64): F_dev (N x 3), tau_dev (N x 3), UW_dev[2] = {U, W}
  * (pair energy + LJ long-range correction; molecular pair virial).  All work is
  * queued on `stream` (a cudaStream_t, NULL = default stream); nothing is

@@ -400,13 +400,12 @@ static ms2_status sys_alloc(ms2_system s) {
 
 static void pick_launch_shape(ms2_system s) {
     const int N = s->N;
-    // pair kernel: warps own molecules; split the j loop so that the grid holds
-    // ~32 warps per SM (152 SMs)
-    // ~2 resident blocks of 8 warps per SM: split the j loop only as far as
-    // the grid still fits one wave (a partial second wave costs a whole wave)
+    // pair kernel: warps own molecules; ~2 resident blocks of 8 warps per SM:
+    // split the j loop only as far as the grid still fits one wave (a partial
+    // second wave costs a whole wave)
     s->wpb = 8;
     const int iblocks = (N + s->wpb - 1) / s->wpb;
-    s->jsplit = std::max(1, std::min(8, (152 * 2) / std::max(iblocks, 1)));
+    s->jsplit = std::max(1, std::min(8, (s->sms * 2) / std::max(iblocks, 1)));
     s->nunits = (N + 7) / 8;  // reduction units of 8 molecules
     if (s->fuse_fn) {         // the fused decomposition (see setup_fused)
         s->jsplit = std::max(1, std::min(8, 16 / s->mcap));
@@ -581,7 +580,7 @@ ms2_status launch_drift(ms2_system s) {
 
 ms2_status launch_rdf(ms2_system s) {
     const int rows = s->d.rdf_rows, nb = s->d.rdf_bins;
-    const int blocks = std::min(s->N, 2 * 152);
+    const int blocks = std::min(s->N, 2 * s->sms);
     k_rdf<<<blocks, 256, sizeof(unsigned) * rows * nb, s->stream>>>(s->dP, s->d);
     s->launch_acc += 1;
     return MS2_OK;
@@ -831,7 +830,7 @@ static ms2_status setup_ewald(ms2_system s, double alpha, int kx, int ky, int kz
     MS2_CUDA_OK(A((void **)&d.eik, sizeof(float2) * 3 * kst * M));
     MS2_CUDA_OK(A((void **)&d.frec, sizeof(float) * d.kchunks * 3 * M));
     // sites per structure-factor task: one round over the fused grid (the same on both paths)
-    d.sk_sites = ms2_ewald_sk_sites(M, s->step_grid > 0 ? s->step_grid : 152);
+    d.sk_sites = ms2_ewald_sk_sites(M, s->step_grid > 0 ? s->step_grid : s->sms);
     d.ew_fpre = (float)(8.0 * 3.141592653589793 * (double)s->hp.coulomb / s->hp.V * 2.0 * 3.141592653589793 / s->hp.L);
     MS2_CUDA_OK(A((void **)&d.skpart, sizeof(float2) * (size_t)ms2_ewald_skp_blocks(M, d.sk_sites) * K));
     MS2_CUDA_OK(A((void **)&d.kblk, sizeof(double) * 2 * ms2_ewald_sksum_blocks(K)));
@@ -907,6 +906,8 @@ extern "C" ms2_status ms2_create_system(const ms2_model *models, const int *N_pe
     s->al.ff = o.dev_free;
     s->al.ctx = o.alloc_ctx;
     cudaGetDevice(&s->device);
+    if (cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess || s->sms < 1)
+        s->sms = 1;
     if (o.stream) {
         s->stream = (cudaStream_t)o.stream;
         s->own_stream = false;

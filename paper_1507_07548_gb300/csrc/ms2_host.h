@@ -83,6 +83,7 @@ struct ms2_system_s {
     // fault-path test: the next fused launch's first grid barrier waits for one
     // arrival more than the grid has, each wait limited to fault_wait_ns
     int fault_barrier = 0;
+    int sms = 1;  // multiprocessors of the device (queried at creation)
     unsigned long long fault_wait_ns = 0;
     // timing events: [0] step start, [1] before pair, [2] after pair, [3] after Ewald, [4] step end
     bool timing = false;

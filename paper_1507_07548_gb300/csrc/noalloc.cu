@@ -66,24 +66,63 @@ void ms2_fill_params(SysParams &P, const ms2_model *models, int n_models, const 
 void ms2_energy_constants(const SysParams &P, const std::vector<int> &species, double alpha, double rc, bool lrc,
                           double coulomb, double *uconst, double *wbg, double *ulrc, double *plrc);
 
-// layout of SoA <- row-major conversion of the inputs
-__global__ void k_noalloc_soa(const double *R, const double *q, double *Rs, double *qs, int N) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Everything a call sets up in the scratch, passed by value (no host buffer, so
+// no pageable copy): the system constants, the energy constants, the counts per
+// model.
+struct NaSetup {
+    double uconst, ulrc, plrc, wbg;
+    int counts[MS2_MAXSP];
+    int n_models;
+};
+
+// One thread per molecule: SoA copies of the row-major inputs, the species from
+// the model counts, zero velocities and angular momenta (the reduction reads
+// them: kinetic energy 0).  Block 0 also writes the constants, the scalars and
+// the zeroed last-block counter.
+__global__ void k_noalloc_setup(SysParams P, NaSetup c, DevSys d, SysParams *dP, const double *R, const double *q) {
+    const int N = d.N, i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0) {
+        const int4 *src = (const int4 *)&P;
+        int4 *dst = (int4 *)dP;
+        for (int k = threadIdx.x; k < (int)(sizeof(SysParams) / sizeof(int4)); k += blockDim.x) dst[k] = src[k];
+        for (int k = threadIdx.x; k < SC_COUNT_; k += blockDim.x) d.scal[k] = 0.0;
+        for (int k = threadIdx.x; k < 64; k += blockDim.x) d.counter[k] = 0u;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            d.scal[SC_UCONST] = c.uconst;
+            d.scal[SC_ULRC] = c.ulrc;
+            d.scal[SC_PLRC] = c.plrc;
+            d.scal[SC_WBG] = c.wbg;
+            d.scal[SC_LAMBDA] = 1.0;
+        }
+    }
     if (i >= N) return;
-    for (int k = 0; k < 3; ++k) Rs[(size_t)k * N + i] = R[3 * i + k];
-    for (int k = 0; k < 4; ++k) qs[(size_t)k * N + i] = q[4 * i + k];
+    for (int k = 0; k < 3; ++k) {
+        d.R[(size_t)k * N + i] = R[3 * i + k];
+        d.v[(size_t)k * N + i] = 0.0;
+        d.Lm[(size_t)k * N + i] = 0.0;
+    }
+    for (int k = 0; k < 4; ++k) d.q[(size_t)k * N + i] = q[4 * i + k];
+    int m = 0, end = c.counts[0];
+    while (m + 1 < c.n_models && i >= end) end += c.counts[++m];
+    d.species[i] = m;
 }
 
 namespace {
 struct DeviceScratch {
     bool ready = false;
     unsigned char *base = nullptr;
+    int sms = 0;                 // multiprocessors of the device
+    const void *attr_set[16];    // pair kernels whose shared-memory limit is raised on this device
+    int n_attr = 0;
 };
 std::mutex g_noalloc_mu;
 DeviceScratch g_noalloc_dev[64];
 
-// once per device, with that device current: the device address of the array
-ms2_status scratch_base(unsigned char **out) {
+// once per device, with that device current: the device address of the array,
+// the multiprocessor count; the dynamic shared-memory limit of the pair kernel
+// `fn` raised to 96 KB once per kernel
+ms2_status scratch_base(unsigned char **out, int *sms, const void *fn) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return ms2_fail_cuda(e, "cudaGetDevice", __FILE__, __LINE__);
@@ -95,9 +134,19 @@ ms2_status scratch_base(unsigned char **out) {
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return ms2_fail_cuda(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
         d.base = (unsigned char *)p;
+        e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return ms2_fail_cuda(e, "cudaDeviceGetAttribute", __FILE__, __LINE__);
         d.ready = true;
     }
+    bool set = false;
+    for (int k = 0; k < d.n_attr; ++k) set = set || d.attr_set[k] == fn;
+    if (!set) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        if (e != cudaSuccess) return ms2_fail_cuda(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
+        if (d.n_attr < 16) d.attr_set[d.n_attr++] = fn;
+    }
     *out = d.base;
+    *sms = d.sms;
     return MS2_OK;
 }
 }  // namespace
@@ -130,6 +179,7 @@ extern "C" ms2_status ms2_forces_noalloc(const ms2_model *models, const int *N_p
     ms2_options o;
     ms2_default_options(&o);
     if (opt) o = *opt;
+    if (o.fp64) return ms2_fail(MS2_EINVAL, "ms2_forces_noalloc: FP32 site-pair arithmetic only (opt->fp64 must be 0)");
 
     SysParams hp;
     ms2_fill_params(hp, models, n_models, species, box, cutoff, elec, o, 1.0);
@@ -150,7 +200,8 @@ extern "C" ms2_status ms2_forces_noalloc(const ms2_model *models, const int *N_p
     ms2_energy_constants(hp, species, 1.0, cutoff, o.lrc != 0, coulomb, &uconst, &wbg, &ulrc, &plrc);
 
     unsigned char *base = nullptr;
-    st = scratch_base(&base);
+    int sms = 0;
+    st = scratch_base(&base, &sms, fn);
     if (st != MS2_OK) return st;
     cudaStream_t sm = (cudaStream_t)stream;
 
@@ -159,7 +210,7 @@ extern "C" ms2_status ms2_forces_noalloc(const ms2_model *models, const int *N_p
     d.N = N;
     d.ns = ns;
     const int wpb = 8, iblocks = (N + wpb - 1) / wpb;
-    d.jsplit = std::max(1, std::min(NA_JS, (152 * 2) / std::max(iblocks, 1)));
+    d.jsplit = std::max(1, std::min(NA_JS, (sms * 2) / std::max(iblocks, 1)));
     d.nunits = (N + 7) / 8;
     d.X = (uint32_t *)(base + O_X);
     d.s = (float *)(base + O_S);
@@ -180,30 +231,24 @@ extern "C" ms2_status ms2_forces_noalloc(const ms2_model *models, const int *N_p
     d.Lm = (double *)(base + O_L);
     const SysParams *dP = (const SysParams *)(base + O_PARAMS);
 
-    // inputs; what must start at zero: the last-block counter, the velocities
-    // and angular momenta the reduction reads (kinetic energy 0), the scalars
-    double sc[SC_COUNT_];
-    memset(sc, 0, sizeof sc);
-    sc[SC_UCONST] = uconst;
-    sc[SC_ULRC] = ulrc;
-    sc[SC_PLRC] = plrc;
-    sc[SC_WBG] = wbg;
-    sc[SC_LAMBDA] = 1.0;
-    MS2_CUDA_OK(cudaMemcpyAsync(base + O_PARAMS, &hp, sizeof(SysParams), cudaMemcpyHostToDevice, sm));
-    MS2_CUDA_OK(cudaMemcpyAsync(d.scal, sc, sizeof sc, cudaMemcpyHostToDevice, sm));
-    MS2_CUDA_OK(cudaMemcpyAsync(d.species, species.data(), sizeof(int) * N, cudaMemcpyHostToDevice, sm));
-    MS2_CUDA_OK(cudaMemsetAsync(d.counter, 0, 256, sm));
-    MS2_CUDA_OK(cudaMemsetAsync(d.v, 0, 3 * sizeof(double) * N, sm));
-    MS2_CUDA_OK(cudaMemsetAsync(d.Lm, 0, 3 * sizeof(double) * N, sm));
+    // inputs, and what must start at zero (the last-block counter, the
+    // velocities and angular momenta the reduction reads, the scalars), all set
+    // by one kernel from values passed by value
+    NaSetup c;
+    memset(&c, 0, sizeof c);
+    c.uconst = uconst;
+    c.ulrc = ulrc;
+    c.plrc = plrc;
+    c.wbg = wbg;
+    c.n_models = n_models;
+    for (int m = 0; m < n_models; ++m) c.counts[m] = N_per_model[m];
 
     const int range = (N + d.jsplit - 1) / d.jsplit;
     int TJ = std::max(32, range);
     while (ms2_pair_smem_bytes(ns, dmu, multi, TJ, wpb) > 96 * 1024 && TJ > 64) TJ = (TJ + 1) / 2;
     const size_t smem = ms2_pair_smem_bytes(ns, dmu, multi, TJ, wpb);
-    MS2_CUDA_OK(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)std::max<size_t>(smem, 48 * 1024)));
 
-    k_noalloc_soa<<<(N + 127) / 128, 128, 0, sm>>>(R_dev, q_dev, d.R, d.q, N);
+    k_noalloc_setup<<<(N + 127) / 128, 128, 0, sm>>>(hp, c, d, (SysParams *)(base + O_PARAMS), R_dev, q_dev);
     k_build<<<(4 * N + 127) / 128, 128, 0, sm>>>(dP, d);
     void (*pair)(const SysParams *, DevSys, int) = (void (*)(const SysParams *, DevSys, int))fn;
     pair<<<dim3(iblocks, d.jsplit), wpb * 32, smem, sm>>>(dP, d, TJ);

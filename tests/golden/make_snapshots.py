@@ -26,6 +26,9 @@ RECIPES = {
     "water_N1003": (lambda: W.water_box(N=1003, rc=13.0, seed=5), [(0.5, 200, None), (2.0, 400, None)]),
     "ionic_N1040": (lambda: W.ionic_solution(seed=3), [(0.5, 150, (4, 4, 4)), (2.0, 350, (4, 4, 4))]),
     "stockmayer_N500": (lambda: W.stockmayer_fluid(N=500, seed=4), [(1.0, 200, None), (2.0, 400, None)]),
+    # two models (species numbering): 800 water + 200 argon-like atoms
+    "water_argon_N1000": (lambda: W.water_argon(n_water=800, n_argon=200, rc=14.0, seed=6),
+                          [(0.5, 200, None), (2.0, 400, None)]),
 }
 
 

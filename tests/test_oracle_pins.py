@@ -6,6 +6,7 @@ mistake in the oracle (a dropped term, a wrong sign, index or image, a transpose
 operand) fails at least one of them.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -16,6 +17,7 @@ from oracle import Oracle
 from paper_1507_07548_gb300 import workloads as W
 
 IDQ = np.array([1.0, 0.0, 0.0, 0.0])
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 def qrot_space(q, axis, angle):
@@ -463,6 +465,46 @@ def test_leapfrog_rigid_time_reversible():
     assert np.abs(R2 - R).max() < 1e-8
     sgn = np.sign((q2 * q).sum(1))[:, None]
     assert np.abs(q2 * sgn - q).max() < 1e-8
+
+
+def test_leapfrog_rigid_water_nve_energy_error_scales_as_dt2():
+    """Rigid leapfrog with the quaternion midpoint rule, NVE, on an isolated
+    cluster of 8 waters taken from the liquid snapshot (no pair crosses the
+    cut-off, so the energy is smooth).  The total energy at integer times -- U
+    of (R_k, q_k) plus the kinetic energy of the half-step means of v and L at
+    q_k -- fluctuates boundedly, its fluctuation falls ~4x when dt is halved over
+    the same span, and it does not drift.  A wrong coupling of the torque into
+    the rotation (an axis, a sign, a factor) breaks this at O(1)."""
+    z = np.load(os.path.join(GOLDEN, "water_N216.npz"))
+    L216 = W.water_box(N=216, rc=9.0, seed=9).L
+    d = z["R"] - z["R"][0]
+    d -= L216 * np.rint(d / L216)
+    near = np.argsort((d * d).sum(1))[:8]
+    R0, q0 = 30.0 + d[near], z["q"][near]
+    rng = np.random.default_rng(43)
+    models, sp = [W.water()], np.zeros(8, np.int32)
+    o = Oracle(models, sp, 60.0, 25.0, elec=1, lrc=0)
+    v0, L0 = W.thermal_velocities(models, sp, q0, 150.0, o.s.kconv, rng)
+
+    def energies(dt, span):
+        st = [(R0, q0, v0, L0)]
+        R, q, v, Lg = R0, q0, v0, L0
+        for _ in range(int(round(span / dt)) + 1):
+            R, q, v, Lg, _, _ = o.run_leapfrog(R, q, v, Lg, dt, 1, T0=0.0, thermo=False)
+            st.append((R, q, v, Lg))
+        E = []
+        for k in range(1, len(st) - 1):   # state k: R_k, q_k, v_{k-1/2}, L_{k-1/2}
+            Rk, qk = st[k][0], st[k][1]
+            vk, Lk = 0.5 * (st[k][2] + st[k + 1][2]), 0.5 * (st[k][3] + st[k + 1][3])
+            E.append(o.energy(Rk, qk) + o.kinetic(qk, vk, Lk).sum())
+        return np.array(E)
+
+    e1, e2 = energies(1.0, 200.0), energies(0.5, 200.0)
+    f1, f2 = np.ptp(e1), np.ptp(e2)
+    assert f2 < 2e-3 * abs(e2.mean())                 # bounded
+    assert 3.3 < f1 / f2 < 4.8, (f1, f2)              # ~dt^2
+    q = len(e2) // 4                                  # no secular drift
+    assert abs(e2[-q:].mean() - e2[:q].mean()) < 0.25 * f2
 
 
 @pytest.mark.parametrize("axis", [0, 1, 2])
