@@ -240,10 +240,14 @@ MS2_API ms2_status ms2_reset_averages(ms2_system sys);
  * samples, reduction, thermostat, record) over all of the kind's systems at
  * once, spread over the whole GPU at molecule granularity, with a bounded grid
  * barrier between phases.  A system's results depend only on the system (bit
- * for bit the same alone or in any batch).  The systems must be
- * reaction-field or non-electrostatic leapfrog systems whose whole
- * configuration fits one block's shared memory (about 3700 three-site
- * molecules); the block shape comes from the autotuner cache.  Where it pays
+ * for bit the same alone or in any batch).  The systems must be leapfrog
+ * systems with the reaction field or no electrostatics, or 3-site water (with
+ * or without single-site ions) under Ewald summation, whose whole configuration
+ * fits one block's shared memory (about 3700 three-site molecules).  For the
+ * Ewald kind, the reciprocal-space tasks of the single-system path (structure
+ * factor, sums, forces; paper Sec. "Algorithmic Developments", paragraph "Ewald
+ * summation") run over all its systems between grid barriers after the pair
+ * phase.  The block shape comes from the autotuner cache.  Where it pays
  * (a list shorter than 3N/4), a system also gets device memory for candidate
  * lists: 2 bytes x N x (1.3 x the molecules within 1.3 r_c, + 32), rebuilt at
  * the start of every chunk of steps and whenever a molecule has moved 0.15 r_c;

@@ -34,6 +34,7 @@
 
 #include <sys/stat.h>
 
+#include "ewald_dev.cuh"
 #include "grid_dev.cuh"
 #include "integrate_dev.cuh"
 #include "ms2_host.h"
@@ -44,8 +45,9 @@ using namespace integ;
 
 namespace {
 
-enum Kind { K_LJ1 = 0, K_W3RF, K_ST3RF, K_G4, K_G4D, K_COUNT };
-const char *kKindName[K_COUNT] = {"lj1", "water3_rf", "stockmayer3_rf", "generic4", "generic4_dipole"};
+enum Kind { K_LJ1 = 0, K_W3RF, K_ST3RF, K_G4, K_G4D, K_ION3EW, K_COUNT };
+const char *kKindName[K_COUNT] = {"lj1", "water3_rf", "stockmayer3_rf", "generic4", "generic4_dipole",
+                                  "water_ions3_ewald"};
 
 constexpr int MS_THREADS = 512;   // largest block shape (the autotuner may take 256)
 constexpr int UNIT = 8;           // molecules per reduction unit (one quad pass of a warp)
@@ -72,6 +74,9 @@ struct BatchEntry {
     int *nflag;                   // non-zero: rebuild in this step's pair phase
     int lcap;
     unsigned long long rs2, sk2;  // (r_c + skin)^2 and (skin / 2)^2, lattice units, with margins
+    // Ewald (reciprocal space): A(k) S(k) of the step, structure-factor and sum task counts
+    float2 *AS;
+    int nsb, nkc;
 };
 
 // launch arguments of one kind (device tables built on the host)
@@ -87,6 +92,10 @@ struct MsArgs {
     int Np;                // stride of the staged tile (largest N of the kind, multiple of 4)
     int nsteps;
     unsigned *bar, *err;   // barrier counter (zero at entry) and sticky timeout flag
+    // Ewald kinds: reciprocal-space tasks (entry, task): structure-factor tasks,
+    // sum tasks, force tasks (one k chunk of a system, all its site groups)
+    const int2 *ew_sk, *ew_sum, *ew_force;
+    int n_sk, n_sum, n_force;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -185,11 +194,45 @@ __global__ void __launch_bounds__(BT, 1) k_mstep(MsArgs A) {
             }
         }
         grid_sync(A.bar, A.err, target, on_timeout);
+        // ---- Ewald reciprocal space of every system of the kind: the tasks of
+        // the single-system path (structure factor, sums, forces), each a function
+        // of its system and index alone, a grid barrier after each kind of task
+        constexpr int EWM = ELEC == ELEC_EWALD ? RED_EWALD : 0;
+        if constexpr (ELEC == ELEC_EWALD) {
+            for (int t = blockIdx.x; t < A.n_sk; t += gridDim.x) {
+                const int2 w = A.ew_sk[t];
+                const BatchEntry &en = A.tab[w.x];
+                ewald::sk_task(en.P, en.S, w.y, smem_raw, threadIdx.x, blockDim.x);
+            }
+            grid_sync(A.bar, A.err, target, on_timeout);
+            for (int t = blockIdx.x; t < A.n_sum; t += gridDim.x) {
+                const int2 w = A.ew_sum[t];
+                const BatchEntry &en = A.tab[w.x];
+                ewald::sum_task(en.S, en.AS, w.y, en.nsb, smem_raw, threadIdx.x, blockDim.x);
+            }
+            grid_sync(A.bar, A.err, target, on_timeout);
+            for (int e = gw; e < A.n_sys; e += W) {  // U_rec and W_rec of each system (one warp)
+                const BatchEntry &en = A.tab[e];
+                ewald::sum_finish(en.P, en.S, en.nkc, lane);
+            }
+            for (int t = blockIdx.x; t < A.n_force; t += gridDim.x) {
+                const int2 w = A.ew_force[t];
+                const BatchEntry &en = A.tab[w.x];
+                const int M = en.S.nsite_q;
+                for (int s0 = 0; s0 < M; s0 += blockDim.x) {
+                    if (en.S.kx == 8)
+                        ewald::force_task<9>(en.P, en.S, en.AS, s0, w.y, 1, smem_raw, threadIdx.x, blockDim.x);
+                    else
+                        ewald::force_task<0>(en.P, en.S, en.AS, s0, w.y, 1, smem_raw, threadIdx.x, blockDim.x);
+                }
+            }
+            grid_sync(A.bar, A.err, target, on_timeout);
+        }
         // ---- reduction units: F, tau, energies, kinetic energies (before and after the kick)
         for (int g = gw; g < A.n_unit; g += W) {
             const int2 u = A.unit[g];
             const BatchEntry &en = A.tab[u.x];
-            reduce_unit<false>(en.P, en.S, global_io(en.S), RED_SUM | RED_LAMBDA, u.y, en.units, lane);
+            reduce_unit<false>(en.P, en.S, global_io(en.S), RED_SUM | RED_LAMBDA | EWM, u.y, en.units, lane);
             if (u.y == 0 && lane == 0 && en.lcap) *en.nflag = 0;  // the pair phase has read it
         }
         grid_sync(A.bar, A.err, target, on_timeout);
@@ -204,7 +247,7 @@ __global__ void __launch_bounds__(BT, 1) k_mstep(MsArgs A) {
             const double t = warp_sum8(x, lane);
             if ((lane & 3) == 0 && (lane >> 2) < Q_N) wtot[warp][lane >> 2] = t;
             __syncwarp();
-            finish_step_warp(en.P, en.S, RED_SUM | RED_RECORD | RED_LAMBDA, wtot[warp], lane, en.S.acc,
+            finish_step_warp(en.P, en.S, RED_SUM | RED_RECORD | RED_LAMBDA | EWM, wtot[warp], lane, en.S.acc,
                              global_consts(en.S));
             __syncwarp();
         }
@@ -220,21 +263,24 @@ const BatchFn kBatchFn[K_COUNT] = {
     &k_mstep<3, 3u, 0u, 4u, ELEC_RF, false>,
     &k_mstep<4, 0xFu, 0xFu, 0u, -1, true>,
     &k_mstep<4, 0xFu, 0xFu, 0xFu, -1, true>,
+    &k_mstep<3, 1u, 7u, 0u, ELEC_EWALD, true>,
 };
 // 1024-thread shapes (64 registers a thread) where the pair work needs few
 // registers and the scan's latency wants more warps: the point-LJ kind
 const BatchFn kBatchFnWide[K_COUNT] = {&k_mstep<1, 1u, 0u, 0u, ELEC_NONE, false, 2 * MS_THREADS>, nullptr, nullptr,
-                                       nullptr, nullptr};
+                                       nullptr, nullptr, nullptr};
 BatchFn kernel_of(int kind, int threads) { return threads > MS_THREADS ? kBatchFnWide[kind] : kBatchFn[kind]; }
-const int kKindNS[K_COUNT] = {1, 3, 3, 4, 4};
-const bool kKindDMU[K_COUNT] = {false, false, true, false, true};
-const bool kKindMulti[K_COUNT] = {false, false, false, true, true};
+const int kKindNS[K_COUNT] = {1, 3, 3, 4, 4, 3};
+const bool kKindDMU[K_COUNT] = {false, false, true, false, true, false};
+const bool kKindMulti[K_COUNT] = {false, false, false, true, true, true};
 
 int kind_of(ms2_system s) {
     const SysParams &P = s->hp;
     if (P.ns == 1 && s->ljm == 1u && s->qm == 0 && s->dm == 0 && P.elec == ELEC_NONE && !P.multi) return K_LJ1;
     if (P.ns == 3 && s->ljm == 1u && s->qm == 7u && s->dm == 0 && P.elec == ELEC_RF && !P.multi) return K_W3RF;
     if (P.ns == 3 && s->ljm == 3u && s->qm == 0 && s->dm == 4u && P.elec == ELEC_RF && !P.multi) return K_ST3RF;
+    if (P.elec == ELEC_EWALD)  // water and single-site ions (or water alone), |n| <= kmax per axis
+        return (P.ns == 3 && s->ljm == 1u && s->qm == 7u && s->dm == 0) ? K_ION3EW : -1;
     if (P.ns == 4) return s->dm ? K_G4D : K_G4;
     return -1;
 }
@@ -242,6 +288,15 @@ int kind_of(ms2_system s) {
 size_t batch_smem(int kind, int Np, int threads, int rdf_cells) {
     return al16(pair_engine::smem_bytes(kKindNS[kind], kKindDMU[kind], kKindMulti[kind], Np, threads / 32)) +
            sizeof(unsigned) * (size_t)std::max(rdf_cells, 1);
+}
+
+// scratch of the reciprocal-space tasks of one Ewald system (they reuse the
+// pair tile's shared memory after the pair phase)
+size_t ewald_smem(ms2_system s, int threads) {
+    if (s->hp.elec != ELEC_EWALD) return 0;
+    const DevSys &d = s->d;
+    return std::max({ewald::sk_smem(d.kx, d.ky, d.kz, d.sk_sites), ewald::sum_smem(),
+                     ewald::force_smem(d.kx, d.kz, 1, threads)});
 }
 
 // relative cost of one pair item of system s (warp instructions, rough): the
@@ -310,6 +365,9 @@ struct ms2_batch_s {
     int4 *dseg[K_COUNT] = {nullptr};
     int *dsegoff[K_COUNT] = {nullptr};
     int Np[K_COUNT] = {0}, rdf_cells[K_COUNT] = {0};
+    // Ewald kinds: reciprocal-space task tables
+    int2 *dew_sk[K_COUNT] = {nullptr}, *dew_sum[K_COUNT] = {nullptr}, *dew_force[K_COUNT] = {nullptr};
+    int n_ew_sk[K_COUNT] = {0}, n_ew_sum[K_COUNT] = {0}, n_ew_force[K_COUNT] = {0};
     int threads[K_COUNT] = {0}, grid[K_COUNT] = {0};
     size_t smem[K_COUNT] = {0};
     unsigned *dbar = nullptr;  // [K_COUNT][2]: barrier counter, timeout flag
@@ -363,6 +421,12 @@ static ms2_status batch_launch(ms2_batch b, int nsteps, bool trial = false) {
         A.nsteps = nsteps;
         A.bar = b->dbar + 2 * k;
         A.err = b->dbar + 2 * k + 1;
+        A.ew_sk = b->dew_sk[k];
+        A.ew_sum = b->dew_sum[k];
+        A.ew_force = b->dew_force[k];
+        A.n_sk = b->n_ew_sk[k];
+        A.n_sum = b->n_ew_sum[k];
+        A.n_force = b->n_ew_force[k];
         void *args[] = {(void *)&A};
         MS2_CUDA_OK(cudaLaunchCooperativeKernel((const void *)kernel_of(k, b->threads[k]), b->grid[k], b->threads[k], args, b->smem[k],
                                                 b->stream));
@@ -384,6 +448,7 @@ static ms2_status set_shape(ms2_batch b, int k, int threads) {
     if (!fn) return ms2_fail(MS2_EINVAL, "batch kind %s has no %d-thread shape", kKindName[k], threads);
     b->threads[k] = threads;
     b->smem[k] = batch_smem(k, b->Np[k], threads, b->rdf_cells[k]);
+    for (int idx : b->order[k]) b->smem[k] = std::max(b->smem[k], ewald_smem(b->sys[idx], threads));
     MS2_CUDA_OK(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)std::max<size_t>(b->smem[k], 48 * 1024)));
     int per_sm = 0, sms = 0, dev = 0, coop = 0;
@@ -553,14 +618,14 @@ static ms2_status tune(ms2_batch b) {
 
 // whether the batch kernels take this system (used by the server)
 bool ms2_batch_accepts(ms2_system s) {
-    if (!s || s->hp.integrator != MS2_INT_LEAPFROG_Q || s->fp64 || s->hp.elec == ELEC_EWALD || s->hp.massieu ||
-        s->d.gk || s->res_every > 0 || s->hf_every > 0)
+    if (!s || s->hp.integrator != MS2_INT_LEAPFROG_Q || s->fp64 || s->hp.massieu || s->d.gk || s->res_every > 0 ||
+        s->hf_every > 0)
         return false;
     const int kind = kind_of(s);
     if (kind < 0) return false;
     const int rdf = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
     if (rdf > RDF_SMEM_MAX) return false;
-    return batch_smem(kind, (s->N + 3) & ~3, 256, rdf) <= 227 * 1024;
+    return std::max(batch_smem(kind, (s->N + 3) & ~3, 256, rdf), ewald_smem(s, 256)) <= 227 * 1024;
 }
 
 extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_batch *out) {
@@ -571,18 +636,21 @@ extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_bat
     for (int k = 0; k < n; ++k) {
         ms2_system s = systems[k];
         if (!s) { delete b; return ms2_fail(MS2_EINVAL, "system %d is null", k); }
-        if (s->hp.integrator != MS2_INT_LEAPFROG_Q || s->fp64 || s->hp.elec == ELEC_EWALD || s->hp.massieu || s->d.gk ||
-            s->res_every > 0 || s->hf_every > 0) {
+        if (s->hp.integrator != MS2_INT_LEAPFROG_Q || s->fp64 || s->hp.massieu || s->d.gk || s->res_every > 0 ||
+            s->hf_every > 0) {
             delete b;
-            return ms2_fail(MS2_EINVAL, "system %d: batches take leapfrog systems with FP32 pair arithmetic and "
-                                        "reaction field or no electrostatics, without Massieu, conductivity, "
-                                        "residence or heat-flux sampling", k);
+            return ms2_fail(MS2_EINVAL, "system %d: batches take leapfrog systems with FP32 pair arithmetic, "
+                                        "without Massieu, conductivity, residence or heat-flux sampling", k);
         }
         const int kind = kind_of(s);
-        if (kind < 0) { delete b; return ms2_fail(MS2_EINVAL, "system %d: more than 4 site slots", k); }
+        if (kind < 0) {
+            delete b;
+            return ms2_fail(MS2_EINVAL, "system %d: more than 4 site slots, or an Ewald system other than "
+                                        "3-site water with single-site ions", k);
+        }
         const int rdf = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
         if (rdf > RDF_SMEM_MAX) { delete b; return ms2_fail(MS2_EINVAL, "system %d: RDF histogram too large for a batch", k); }
-        if (batch_smem(kind, (s->N + 3) & ~3, 256, rdf) > 227 * 1024) {
+        if (std::max(batch_smem(kind, (s->N + 3) & ~3, 256, rdf), ewald_smem(s, 256)) > 227 * 1024) {
             delete b;
             return ms2_fail(MS2_EINVAL, "system %d: %d molecules do not fit one block's shared memory", k, s->N);
         }
@@ -598,7 +666,7 @@ extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_bat
     cudaError_t ce = b->al.alloc((void **)&b->dbar, sizeof(unsigned) * 2 * K_COUNT);
     for (int k = 0; k < K_COUNT && ce == cudaSuccess; ++k) {
         if (b->order[k].empty()) continue;
-        std::vector<int2> drift, unit;
+        std::vector<int2> drift, unit, ew_sk, ew_sum, ew_force;
         ce = b->al.alloc((void **)&b->dnflag[k], sizeof(int) * b->order[k].size());
         // candidate lists of the kind's systems in one allocation (a server re-creates
         // batches as jobs come and go): skin kSkin r_c, capacity 1.3 x the ideal-gas
@@ -647,6 +715,14 @@ extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_bat
             }
             en.nflag = b->dnflag[k] + e;
             en.step0 = s->step;
+            if (s->hp.elec == ELEC_EWALD) {
+                en.AS = s->AS;
+                en.nsb = ewald::n_site_tasks(s->d.nsite_q, s->d.sk_sites);
+                en.nkc = ewald::n_sum_tasks(ewald::n_k(s->d.kx, s->d.ky, s->d.kz));
+                for (int t = 0; t < en.nsb; ++t) ew_sk.push_back(make_int2((int)e, t));
+                for (int t = 0; t < en.nkc; ++t) ew_sum.push_back(make_int2((int)e, t));
+                for (int t = 0; t < s->d.kchunks; ++t) ew_force.push_back(make_int2((int)e, t));
+            }
             b->htab[k].push_back(en);
             for (int m = 0; m < N; m += 8) drift.push_back(make_int2((int)e, m));
             for (int u = 0; u < en.units; ++u) unit.push_back(make_int2((int)e, u));
@@ -660,9 +736,21 @@ extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_bat
             ce = cudaMemcpyAsync(b->ddrift[k], drift.data(), sizeof(int2) * drift.size(), cudaMemcpyHostToDevice, b->stream);
         if (ce == cudaSuccess)
             ce = cudaMemcpyAsync(b->dunit[k], unit.data(), sizeof(int2) * unit.size(), cudaMemcpyHostToDevice, b->stream);
+        const std::vector<int2> *ew[3] = {&ew_sk, &ew_sum, &ew_force};
+        int2 **dew[3] = {&b->dew_sk[k], &b->dew_sum[k], &b->dew_force[k]};
+        for (int q = 0; q < 3 && ce == cudaSuccess; ++q)
+            if (!ew[q]->empty()) {
+                ce = b->al.alloc((void **)dew[q], sizeof(int2) * ew[q]->size());
+                if (ce == cudaSuccess)
+                    ce = cudaMemcpyAsync(*dew[q], ew[q]->data(), sizeof(int2) * ew[q]->size(), cudaMemcpyHostToDevice,
+                                         b->stream);
+            }
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);  // the host vectors go out of scope
         b->n_drift[k] = (int)drift.size();
         b->n_unit[k] = (int)unit.size();
+        b->n_ew_sk[k] = (int)ew_sk.size();
+        b->n_ew_sum[k] = (int)ew_sum.size();
+        b->n_ew_force[k] = (int)ew_force.size();
     }
     if (ce != cudaSuccess) return fail(ms2_fail_cuda(ce, "batch set-up", __FILE__, __LINE__));
     for (int k = 0; k < K_COUNT; ++k)

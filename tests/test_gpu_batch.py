@@ -144,10 +144,58 @@ def test_batch_rdf_and_averages_bookkeeping():
     assert av["T"] == pytest.approx(298.0, rel=1e-3)
 
 
-def test_batch_rejects_ewald_and_verlet_systems():
-    ion = ms2.System.from_workload(W.ionic_solution(n_water=200, n_ion_pairs=4, rc=8.0, seed=5))
+def ionic():
+    return snapshot(W.ionic_solution(seed=3), "ionic_N1040")
+
+
+def test_one_batched_ewald_step_matches_oracle():
+    """The ionic solution (water + ions, Ewald) in a batch: the reciprocal-space
+    tasks run between grid barriers of the multi-system kernel."""
+    wl = ionic()
+    s = ms2.System.from_workload(wl)
+    b = ms2.Batch([s])
+    b.step(1)
+    R, q, v, L, st = s.get_state()
+    assert st == 1
+    o = Oracle.from_workload(wl)
+    Ro, qo, vo, Lo, th, _ = o.run_leapfrog(wl.R, wl.q, wl.v, wl.Lang, wl.dt, 1, T0=wl.T)
+    dR = Ro - wl.R
+    assert np.abs((R - wl.R) - dR).max() <= 1e-6 * np.abs(dR).max()
+    assert rms_rel(v, vo) <= 1e-6
+    U, Wv, T, P = s.energy_virial()
+    assert abs(U - th[0, 0]) <= 1e-6 * abs(th[0, 0])
+    F, tau = s.forces_torques()
+    Fo, To, to = o.forces(R, q)                   # the identical (stepped) configuration
+    assert rms_rel(F, Fo) <= 1e-5 and rms_rel(tau, To) <= 1e-5
+    assert abs(Wv - to["W_total"]) <= 1e-5 * abs(to["W_total"])   # W_EWALD of test_gpu_parity
+    t = s.energy_terms()
+    assert t["U_rec"] == pytest.approx(to["U_rec"], rel=1e-6)
+    b.close()
+
+
+def test_ewald_system_alone_and_in_a_mixed_batch_is_bitwise_identical():
+    alone = ms2.System.from_workload(ionic())
+    b1 = ms2.Batch([alone])
+    b1.step(12)
+    ref = alone.get_state()[:4]
+    small = W.ionic_solution(n_water=400, n_ion_pairs=8, rc=9.0, seed=7)
+    mix = [ms2.System.from_workload(w) for w in (water(), small, ionic(), stock())]
+    b2 = ms2.Batch(mix)
+    b2.step(12)
+    got = mix[2].get_state()[:4]
+    for a, c in zip(got, ref):
+        assert np.array_equal(a, c)
+    assert alone.energy_virial() == mix[2].energy_virial()
+
+
+def test_batch_rejects_verlet_and_other_ewald_systems():
+    m = W.water()                     # a TIP4P-like 4-site water: no batch kind takes it under Ewald
+    m.sites[0].charge = 0.0
+    m.sites.append(W.Site((0.0, 0.0, m.sites[0].pos[2] + 0.15), 0.0, charge=-0.8476))
+    ion4 = ms2.System([m, W.cation(), W.anion()], [100, 2, 2], 298.0, 7.0, ms2.ELEC_EWALD,
+                      rho=W.WATER_NUMBER_DENSITY)
     with pytest.raises(ms2.Ms2Error, match="EINVAL"):
-        ms2.Batch([ion])
+        ms2.Batch([ion4])
     wl = W.lj_fluid(N=256, rho=0.7, rc=3.5)
     vv = ms2.System.from_workload(wl)
     with pytest.raises(ms2.Ms2Error, match="EINVAL"):
