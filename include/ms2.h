@@ -297,11 +297,13 @@ typedef struct {
  * device memory; a scheduler thread admits eligible jobs in arrival order as
  * budget and slots free up, advances all resident jobs together chunk by chunk
  * (continuous batching), and retires finished ones.  max_slots <= 1024.  A job's
- * path is fixed at admission: with 8 or more jobs resident, jobs the batch
- * kernels take join the batch; otherwise a job steps with its own
- * single-system kernels.  All the server's systems share one stream.  Results
- * are reproducible for a given arrival sequence; the two paths agree within the
- * parity tolerances, not bit for bit. */
+ * path depends on the job alone: a job the batch kernels take (see
+ * ms2_batch_create) always steps in the server's batch, a batch of one when it
+ * is the only such job, and any other job with its own single-system kernels.
+ * So a job's results are bit for bit the same alone and in any mix of other
+ * jobs.  All the server's systems share one stream.  The admission estimate of a
+ * job's device memory includes the batch's candidate lists; a batch that cannot
+ * be built retires its jobs with the error. */
 /* (Serving has no counterpart in the paper; each job is one simulation as in
  * its Sec. "Introduction".)  opt: the defaults of the jobs' systems (NULL:
  * ms2_default_options); *out receives the server.  Errors: MS2_EINVAL, MS2_ECUDA. */

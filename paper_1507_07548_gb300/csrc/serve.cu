@@ -7,15 +7,16 @@
 //      not fit yet blocks the ones behind it, so admission is FIFO-fair),
 //   3. advances every resident job by one chunk.
 // Jobs that arrive while others run are admitted at the next chunk boundary
-// (continuous batching).  A job's path is fixed at admission: while at least
-// BATCH_MIN_RESIDENT jobs are resident, a job the batch kernels take goes into
-// the batch (the multi-system step kernels, ahead of stepping the systems one
-// by one from about 4 systems on); otherwise it steps with its own
-// single-system kernels (the fused step
-// where the system allows, each chunk on the whole GPU).  All systems of a
-// server share one stream, so cooperative fused launches never overlap each
-// other or the batch.  Results are reproducible for a given arrival sequence;
-// the two paths agree within the parity tolerances, not bit for bit.
+// (continuous batching).  A job's path is a function of the job alone: a job the
+// batch kernels take always steps in the batch (a batch of one when it is the
+// only such job), any other job with its own single-system kernels (the fused
+// step where the system allows, each chunk on the whole GPU).  A batched
+// system's results depend only on the system, so every job gives the same bits
+// alone and in any mix.  (A path chosen by the load would not: the batch and
+// the single-system kernels split the pair sums differently and agree only
+// within the parity tolerances, and trajectories amplify that difference.)
+// All systems of a server share one stream, so cooperative launches never
+// overlap each other or the batch.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -30,8 +31,6 @@
 bool ms2_batch_accepts(ms2_system s);  // batch.cu
 
 namespace {
-
-constexpr int BATCH_MIN_RESIDENT = 8;  // resident jobs from which new jobs join the batch
 
 struct JobSpec {
     long long id = 0;
@@ -64,6 +63,12 @@ size_t estimate_bytes(const JobSpec &j) {
     }
     const int nsp = ns <= 1 ? 1 : (ns <= 4 ? 4 : 8);  // padded slots (upper bound)
     size_t b = (size_t)N * (23 * 8 + 4 + 12 + 2 * 12 * nsp + 12 + 8 * 12 * 4 + 4 + 8);
+    // in a batch: reduction-unit partials and candidate lists (16-bit slots,
+    // 1.3 x the ideal-gas count within 1.3 r_c + 32 per molecule; an upper bound
+    // of the batch's allocation, which takes lists only where they are short)
+    const double V = N / std::max(j.rho, 1e-300), rl = 1.3 * j.cutoff;
+    const double frac = std::min(1.0, 4.18879020478639098 * rl * rl * rl / V);
+    b += (size_t)N * (8 * 32 + 16) + (size_t)N * 2 * (size_t)(1.3 * frac * N + 64);
     if (j.elec == MS2_ELEC_EWALD) {
         const size_t M = (size_t)N * nsp;
         b += M * (12 + 4 + 3 * 9 * 8 + 17 * 3 * 4) + 17 * 17 * 9 * 8 * 2;
@@ -181,7 +186,7 @@ static void admit(ms2_server S) {
         }
         S->resident += j.bytes;
         sl.remaining = j.steps;
-        sl.batched = (int)S->slots.size() + 1 >= BATCH_MIN_RESIDENT && ms2_batch_accepts(sl.sys);
+        sl.batched = ms2_batch_accepts(sl.sys);  // the job's own property, never the load
         S->slots.push_back(sl);
         S->batch_dirty = true;
     }
@@ -197,12 +202,17 @@ static void advance(ms2_server S) {
     if (S->batch_dirty) {
         if (S->batch) ms2_batch_destroy(S->batch);
         S->batch = nullptr;
-        if (!bs.empty() && ms2_batch_create(bs.data(), (int)bs.size(), &S->batch) != MS2_OK) {
-            // fall back to stepping those jobs on their own streams
-            for (Slot &sl : S->slots) sl.batched = false;
-            bs.clear();
-        }
+        ms2_status st = MS2_OK;
+        if (!bs.empty()) st = ms2_batch_create(bs.data(), (int)bs.size(), &S->batch);
         S->batch_dirty = false;
+        if (st != MS2_OK) {
+            // no silent change of path (it would change the jobs' results):
+            // the batched jobs retire with the failure
+            S->batch = nullptr;
+            for (Slot &sl : S->slots)
+                if (sl.batched) sl.remaining = -1 - (long long)st;
+            return;
+        }
     }
     // unbatched jobs first (they run on their own streams), then the batch
     for (Slot &sl : S->slots)

@@ -2,8 +2,9 @@
 together between chunks, retired with averages and RDF.
 
 A job's result must be the same whether it runs alone or arrives while other
-jobs are resident (continuous batching), budget admission must bind, and Ewald
-jobs (stepped on their own streams beside the batch) must complete too.
+jobs are resident (continuous batching: it joins the running batch), budget
+admission must bind, and Ewald jobs (batched with the other kinds) must
+complete too.
 """
 import time
 
@@ -50,22 +51,41 @@ def test_serve_completes_jobs_with_outputs():
         assert r["t_arrive"] <= r["t_admit"] <= r["t_done"]
 
 
+def wait_for(server, got, jid, timeout=120.0):
+    t0 = time.time()
+    while jid not in got:
+        for r in server.poll(64):
+            got[r["job_id"]] = r
+        if time.time() - t0 > timeout:
+            raise TimeoutError("job %d did not finish" % jid)
+        time.sleep(0.01)
+    return got[jid]
+
+
 def test_result_is_the_same_alone_and_in_the_mix():
+    """The target job alone (a batch of one) and the same job joining a running
+    batch of nine other jobs (water, Stockmayer, argon, an Ewald ionic solution)
+    mid-stream: its averages and g(r) are bit for bit the same."""
     target = JOBS[0]
     alone = run([target], steps=300)[0]          # seed 100
-    # the same job (seed 100) arrives while two others are already resident,
-    # and a fourth arrives after it
+    ion = W.ionic_solution(n_water=200, n_ion_pairs=4, rc=8.0, seed=5)
+    others = [JOBS[1], JOBS[2], JOBS[3], JOBS[1], JOBS[3], JOBS[0], JOBS[3],
+              (ion.models, [200, 4, 4], 298.0, RHO_W, 8.0, ms2.ELEC_EWALD)]
     s = ms2.Server(1 << 30, 64)
-    for k, job in enumerate([JOBS[1], JOBS[2]]):
-        s.submit(*job, 300, arrival=0.0, seed=200 + k, rdf_bins=60)
-    jid = s.submit(*target, 300, arrival=0.05, seed=100, rdf_bins=60)
-    s.submit(*JOBS[3], 300, arrival=0.06, seed=203, rdf_bins=60)
-    s.drain(300.0)
-    got = {x["job_id"]: x for x in s.poll(64)}[jid]
-    s.close()
-    assert got["t_admit"] >= got["t_arrive"]
-    assert got["U"] == alone["U"] and got["P"] == alone["P"] and got["T"] == alone["T"]
-    assert np.array_equal(got["g"], alone["g"])
+    got = {}
+    oid = [s.submit(*job, 100000, seed=200 + k, rdf_bins=60) for k, job in enumerate(others)]
+    # a short job among them: once it is done, the batch has been running
+    first = s.submit(*JOBS[2], 200, seed=300, rdf_bins=60)
+    wait_for(s, got, first)
+    jid = s.submit(*target, 300, arrival=0.0, seed=100, rdf_bins=60)
+    mine = wait_for(s, got, jid)
+    assert not any(i in got for i in oid)         # the long jobs ran beside it throughout
+    s.close()                                    # (and retire unfinished here)
+    assert got[first]["status"] == 0 and got[first]["t_done"] <= mine["t_admit"]
+    assert mine["status"] == 0
+    assert mine["U"] == alone["U"] and mine["P"] == alone["P"] and mine["T"] == alone["T"]
+    assert mine["U_err"] == alone["U_err"] and mine["P_err"] == alone["P_err"]
+    assert np.array_equal(mine["g"], alone["g"])
 
 
 def test_budget_admission_binds_and_rejects_oversized_jobs():
@@ -73,9 +93,10 @@ def test_budget_admission_binds_and_rejects_oversized_jobs():
     with pytest.raises(ms2.Ms2Error, match="EBUDGET"):
         small.submit([W.water()], [4000], 298.0, RHO_W, 14.0, ms2.ELEC_RF, 100)
     small.close()
-    # room for two of these jobs at a time (~1.15 MB each by the admission estimate)
+    # room for two of these jobs at a time (~1.34 MiB each by the admission
+    # estimate, which counts the batch's candidate lists)
     job = ([W.water()], [216], 298.0, RHO_W, 9.0, ms2.ELEC_RF)
-    s = ms2.Server(int(2.6 * (1 << 20)), 64)
+    s = ms2.Server(int(3.0 * (1 << 20)), 64)
     for k in range(4):
         s.submit(*job, 400, seed=10 + k)
     s.drain(300.0)
@@ -86,7 +107,7 @@ def test_budget_admission_binds_and_rejects_oversized_jobs():
     assert res[2]["t_admit"] >= min(res[0]["t_done"], res[1]["t_done"]) - 1e-6
 
 
-def test_ewald_job_runs_beside_the_batch():
+def test_ewald_job_runs_in_the_batch():
     ion = W.ionic_solution(n_water=200, n_ion_pairs=4, rc=8.0, seed=5)
     res = run([JOBS[0], (ion.models, [200, 4, 4], 298.0, RHO_W, 8.0, ms2.ELEC_EWALD)], steps=100)
     assert all(r["status"] == 0 for r in res)
