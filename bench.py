@@ -66,8 +66,11 @@ def parse():
     ap.add_argument("--impl", default="ms2", choices=["ms2", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle CPU-baseline sample length")
     ap.add_argument("--no-extra", action="store_true", help="skip the Ewald sub-benchmark")
-    ap.add_argument("--only", choices=["ewald", "massieu", "thermal", "batch"], default=None,
+    ap.add_argument("--only", choices=["ewald", "massieu", "thermal", "batch", "serve"], default=None,
                     help="run one sub-benchmark alone and print its JSON object")
+    ap.add_argument("--batch-steps", type=int, default=BATCH_STEPS,
+                    help="steps of the batch leg (the production length, 10000 in chunks of 100, is opt-in: "
+                         "--only batch --batch-steps 10000)")
     ap.add_argument("--batch-kinds", default=None, metavar="K[,K]",
                     help="batch leg: only the systems of these model kinds of the mix (lj, stockmayer, water)")
     ap.add_argument("--uniform-batch", type=int, default=0, metavar="S",
@@ -307,7 +310,7 @@ def gpu_arm(args, rank, world, local_rank):
         extra["massieu"] = massieu_sub(args, stream, flush)
         extra["thermal"] = thermal_sub(args, stream, flush)
         extra["batch"] = batch_sub(args, flush)
-        extra["serve"] = serve_sub(args, extra["batch"]["batched"]["value"])
+        extra["serve"] = serve_sub(args)
 
     if rank != 0:
         return 0
@@ -358,12 +361,17 @@ def gpu_arm(args, rank, world, local_rank):
 
 
 BATCH_SYSTEMS, BATCH_STEPS = 512, 200      # many-system mix (production runs: 1e4 steps in chunks of 100)
-SERVE_JOBS, SERVE_STEPS = 48, (100, 1000)  # job stream (production: 256 jobs of 1e4 - 1e5 steps)
+# the served job stream: 256 jobs with steps 1/100 of production (1e4 - 1e5) and
+# arrivals 100x as fast as production's 50/s, so that the offered load in
+# molecule-steps/s is the production stream's (several times one GPU's capacity)
+SERVE_JOBS, SERVE_RATE, SERVE_STEPS = 256, 5000.0, (100, 1000)
+SWEEP_JOBS, SWEEP_STEPS = 48, (100, 1000)   # load-sweep point at ~0.7 of the served capacity
+SERVE_RDF_BINS = 100
 
 
 def batch_sub(args, flush):
     """The same work -- BATCH_SYSTEMS independent systems of the LJ / Stockmayer /
-    water mix, BATCH_STEPS steps each -- run one system at a time on one stream
+    water mix, --batch-steps steps each (200 by default) -- run one system at a time on one stream
     (each on its best single-system path: the fused step kernel) and as one
     batch (one cooperative multi-system step kernel per model kind).  Host wall time between
     device synchronisations (each run is far longer than a launch), L2 flushed
@@ -381,7 +389,8 @@ def batch_sub(args, flush):
                            seed=sp["seed"], dt=2.0, **kw) for sp in specs]
 
     plain, batched = make(stream=one.cuda_stream), make()
-    work = sum(sp["counts"][0] for sp in specs) * BATCH_STEPS
+    steps = args.batch_steps
+    work = sum(sp["counts"][0] for sp in specs) * steps
     b = ms2.Batch(batched)
     for s in plain:       # warm-up: one chunk-sized step each, both sets
         s.step(1)
@@ -391,13 +400,13 @@ def batch_sub(args, flush):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for s in plain:
-        s.step(BATCH_STEPS)
+        s.step(steps)
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - t0
     flush.zero_()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    b.step(BATCH_STEPS)
+    b.step(steps)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
     fused = sum(s.fused_step() for s in plain)
@@ -407,7 +416,7 @@ def batch_sub(args, flush):
     kinds = {k: sum(1 for sp in specs if sp["name"] == k) for k in W.MIX_STATES}
     return {"workload": "%d independent systems (%s), N ~ U[256, 2048], T ~ U[0.7, 1.3] T0, rho ~ U[0.5, 1.0] rho0; "
                         "%d steps each (production: 1e4)" % (BATCH_SYSTEMS, ", ".join("%d %s" % (v, k) for k, v in
-                                                                                      kinds.items()), BATCH_STEPS),
+                                                                                      kinds.items()), steps),
             "unit": "molecule-steps/s",
             "plain": {"value": work / t_plain, "seconds": t_plain, "path": "one system at a time, %d of %d fused"
                       % (fused, len(plain))},
@@ -415,33 +424,96 @@ def batch_sub(args, flush):
             "speedup": t_plain / t_batch}
 
 
-def serve_sub(args, capacity):
-    """Job stream through the server (ms2_serve_*): SERVE_JOBS jobs, Poisson
-    arrivals at ~0.7 of the batch capacity measured above, 20 % ionic (Ewald),
-    a 2 GiB admission budget.  Latency = result on the host minus arrival."""
-    import numpy as np
+def run_served(jobs, budget, slots=256):
+    """The jobs through the server (ms2_serve_*); arrival times on the server's
+    clock.  Returns the results and the span from the first arrival to the last
+    result."""
     import paper_1507_07548_gb300.ms2 as ms2
-    from paper_1507_07548_gb300 import workloads as W
-    probe = W.job_stream(SERVE_JOBS, 1.0, seed=5, steps=SERVE_STEPS)
-    mean_work = np.mean([sum(j["counts"]) * j["steps"] for j in probe])
-    rate = 0.7 * capacity / mean_work
-    jobs = W.job_stream(SERVE_JOBS, rate, seed=5, steps=SERVE_STEPS)
-    srv = ms2.Server(2 << 30, 256)
+    srv = ms2.Server(budget, slots)
     for j in jobs:
         srv.submit(j["models"], j["counts"], j["T"], j["rho"], j["cutoff"], j["elec"], j["steps"],
-                   arrival=j["arrival"], seed=j["seed"], rdf_bins=100)
-    srv.drain(600.0)
-    res = srv.poll(SERVE_JOBS)
+                   arrival=j["arrival"], seed=j["seed"], rdf_bins=SERVE_RDF_BINS)
+    srv.drain(1800.0)
+    res = srv.poll(len(jobs) + 8)
     srv.close()
-    lat = np.array([r["t_done"] - r["t_arrive"] for r in res])
     span = max(r["t_done"] for r in res) - min(r["t_arrive"] for r in res)
+    return res, span
+
+
+def run_one_at_a_time(jobs):
+    """The same jobs, one after the other, each on its own single-system path
+    (the fused step kernel where the system allows): create the system as the
+    server does, sample the RDF, step, read the averages and g(r).  Returns the
+    total time and the latencies of a FIFO queue served this way (each job
+    starts at max(its arrival, the previous job's end))."""
+    import torch
+    import paper_1507_07548_gb300.ms2 as ms2
+    total, clock, lat = 0.0, 0.0, []
+    for j in jobs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = ms2.System(j["models"], j["counts"], j["T"], j["cutoff"], j["elec"], rho=j["rho"], seed=j["seed"])
+        s.rdf_setup(min(s.rc, 0.5 * s.L), SERVE_RDF_BINS, every=10)
+        s.reset_averages()
+        s.step(j["steps"])
+        s.averages()
+        s.rdf()
+        s.close()
+        dt = time.perf_counter() - t0
+        total += dt
+        clock = max(clock, j["arrival"]) + dt
+        lat.append(clock - j["arrival"])
+    return total, lat
+
+
+def serve_sub(args):
+    """Serving, two measurements.
+    (1) The job stream of the served workload, scaled in time: SERVE_JOBS jobs,
+    N ~ U[500, 4000], 80 % the LJ / Stockmayer / water mix and 20 % ionic
+    (Ewald), steps 1/100 of the production 10^4 - 10^5 (100 - 1000 in multiples
+    of 100) and Poisson arrivals 100 times as fast as the production 50/s, so the
+    offered load is the production stream's; energy/pressure averages and g(r)
+    out, a 2 GiB admission budget.  The same jobs then run one at a time on the
+    single-system path; served / one-at-a-time is the throughput ratio.
+    (2) A load sweep point: SWEEP_JOBS jobs of the same kinds arriving at ~0.7 of
+    the served capacity just measured, where p50/p99 reflect service time.
+    Latency = result on the host minus arrival."""
+    import numpy as np
+    from paper_1507_07548_gb300 import workloads as W
+    jobs = W.job_stream(SERVE_JOBS, SERVE_RATE, seed=5, steps=SERVE_STEPS)
     work = sum(sum(j["counts"]) * j["steps"] for j in jobs)
-    return {"workload": "%d jobs, N ~ U[500, 4000], %d-%d steps, 20%% ionic (Ewald), Poisson arrivals at %.1f/s "
-                        "(~0.7 of the measured batch capacity), 2 GiB budget" % (SERVE_JOBS, SERVE_STEPS[0],
-                                                                               SERVE_STEPS[1], rate),
-            "completed": int(sum(1 for r in res if r["status"] == 0)), "jobs": len(jobs),
-            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "value": work / span, "unit": "molecule-steps/s"}
+    res, span = run_served(jobs, 2 << 30)
+    lat = np.array([r["t_done"] - r["t_arrive"] for r in res])
+    served = work / span
+    t_one, lat_one = run_one_at_a_time(jobs)
+    one = work / t_one
+    stream = {"workload": "%d jobs, N ~ U[500, 4000], 80%% LJ/Stockmayer/water mix + 20%% ionic (Ewald), %d-%d "
+                          "steps and Poisson arrivals at %.0f/s (production 1e4-1e5 steps at 50/s, time-scaled by "
+                          "1/100: the same offered load), <U>, <P>, g(r) out, 2 GiB budget"
+                          % (SERVE_JOBS, SERVE_STEPS[0], SERVE_STEPS[1], SERVE_RATE),
+              "completed": int(sum(1 for r in res if r["status"] == 0)), "jobs": len(jobs),
+              "served": {"value": served, "seconds": span, "p50_latency_s": float(np.percentile(lat, 50)),
+                         "p99_latency_s": float(np.percentile(lat, 99))},
+              "one_at_a_time": {"value": one, "seconds": t_one,
+                                "p50_latency_s": float(np.percentile(lat_one, 50)),
+                                "p99_latency_s": float(np.percentile(lat_one, 99))},
+              "served_over_one_at_a_time": served / one, "unit": "molecule-steps/s"}
+    probe = W.job_stream(SWEEP_JOBS, 1.0, seed=7, steps=SWEEP_STEPS)
+    mean_work = np.mean([sum(j["counts"]) * j["steps"] for j in probe])
+    rate = 0.7 * served / mean_work
+    sweep = W.job_stream(SWEEP_JOBS, rate, seed=7, steps=SWEEP_STEPS)
+    res2, span2 = run_served(sweep, 2 << 30)
+    lat2 = np.array([r["t_done"] - r["t_arrive"] for r in res2])
+    work2 = sum(sum(j["counts"]) * j["steps"] for j in sweep)
+    load = {"workload": "%d jobs of the same kinds, %d-%d steps, Poisson arrivals at %.1f/s (~0.7 of the served "
+                        "capacity above)" % (SWEEP_JOBS, SWEEP_STEPS[0], SWEEP_STEPS[1], rate),
+            "completed": int(sum(1 for r in res2 if r["status"] == 0)), "jobs": len(sweep),
+            "p50_latency_s": float(np.percentile(lat2, 50)), "p99_latency_s": float(np.percentile(lat2, 99)),
+            "value": work2 / span2, "unit": "molecule-steps/s"}
+    return {"stream": stream, "load_sweep": load,
+            # headline figures of the served leg
+            "value": served, "unit": "molecule-steps/s", "p50_latency_s": stream["served"]["p50_latency_s"],
+            "p99_latency_s": stream["served"]["p99_latency_s"]}
 
 
 MASSIEU_STEPS = 1000
@@ -599,7 +671,8 @@ def only_sub(args):
     torch.cuda.set_stream(stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     fn = {"ewald": lambda: ewald_sub(args, stream), "massieu": lambda: massieu_sub(args, stream, flush),
-          "thermal": lambda: thermal_sub(args, stream, flush), "batch": lambda: batch_sub(args, flush)}[args.only]
+          "thermal": lambda: thermal_sub(args, stream, flush), "batch": lambda: batch_sub(args, flush),
+          "serve": lambda: serve_sub(args)}[args.only]
     print(json.dumps({args.only: fn()}), flush=True)
     return 0
 

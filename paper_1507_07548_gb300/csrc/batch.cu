@@ -373,6 +373,7 @@ struct ms2_batch_s {
     unsigned *dbar = nullptr;  // [K_COUNT][2]: barrier counter, timeout flag
     int *dnflag[K_COUNT] = {nullptr};  // candidate-list rebuild flags, one per system of the kind
     int chunk = 100;
+    bool tune_shapes = true;  // false: cached shape or the default, no trial launches
 };
 
 // trial = autotuner run: no RDF samples, no step counters
@@ -567,7 +568,7 @@ static ms2_status tune(ms2_batch b) {
         if (it != cache.end() && set_shape(b, k, it->second) == MS2_OK) continue;
         need = true;
     }
-    if (!need) return MS2_OK;
+    if (!need || !b->tune_shapes) return MS2_OK;  // (untuned kinds keep the default shape)
     std::vector<void *> saved;
     ms2_status st = snapshot_state(b, saved, true);
     if (st != MS2_OK) return st;
@@ -616,6 +617,17 @@ static ms2_status tune(ms2_batch b) {
     return MS2_OK;
 }
 
+// dynamic shared memory a block of kind k's kernel can have at most on this
+// device: the opt-in per-block limit less the kernel's static shared memory
+static size_t batch_smem_limit(int kind, int threads) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, (const void *)kernel_of(kind, threads)) != cudaSuccess) return 0;
+    return optin > (int)fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+}
+
 // whether the batch kernels take this system (used by the server)
 bool ms2_batch_accepts(ms2_system s) {
     if (!s || s->hp.integrator != MS2_INT_LEAPFROG_Q || s->fp64 || s->hp.massieu || s->d.gk || s->res_every > 0 ||
@@ -625,13 +637,22 @@ bool ms2_batch_accepts(ms2_system s) {
     if (kind < 0) return false;
     const int rdf = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
     if (rdf > RDF_SMEM_MAX) return false;
-    return std::max(batch_smem(kind, (s->N + 3) & ~3, 256, rdf), ewald_smem(s, 256)) <= 227 * 1024;
+    return std::max(batch_smem(kind, (s->N + 3) & ~3, 256, rdf), ewald_smem(s, 256)) <= batch_smem_limit(kind, 256);
 }
 
-extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_batch *out) {
+// Batch creation with options (the server's batches): tune = false takes the
+// cached block shape or the default without trial launches; fa/ff/ctx, if set,
+// allocate the batch's device memory (a server's block cache, so that the
+// batches it rebuilds as jobs come and go do not call cudaMalloc/cudaFree).
+ms2_status ms2_batch_create_opt(const ms2_system *systems, int n, ms2_batch *out, bool tune_shapes,
+                                void *(*fa)(size_t, void *), void (*ff)(void *, void *), void *ctx) {
     if (!out || !systems || n < 1) return ms2_fail(MS2_EINVAL, "need n >= 1 systems and an output handle");
     *out = nullptr;
     ms2_batch b = new ms2_batch_s();
+    b->al.fa = fa;
+    b->al.ff = ff;
+    b->al.ctx = ctx;
+    b->tune_shapes = tune_shapes;
     // the batch owns its stream: it must outlive none of the systems' streams
     for (int k = 0; k < n; ++k) {
         ms2_system s = systems[k];
@@ -650,7 +671,7 @@ extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_bat
         }
         const int rdf = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
         if (rdf > RDF_SMEM_MAX) { delete b; return ms2_fail(MS2_EINVAL, "system %d: RDF histogram too large for a batch", k); }
-        if (std::max(batch_smem(kind, (s->N + 3) & ~3, 256, rdf), ewald_smem(s, 256)) > 227 * 1024) {
+        if (std::max(batch_smem(kind, (s->N + 3) & ~3, 256, rdf), ewald_smem(s, 256)) > batch_smem_limit(kind, 256)) {
             delete b;
             return ms2_fail(MS2_EINVAL, "system %d: %d molecules do not fit one block's shared memory", k, s->N);
         }
@@ -765,6 +786,10 @@ extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_bat
     if (st != MS2_OK) return fail(st);
     *out = b;
     return MS2_OK;
+}
+
+extern "C" ms2_status ms2_batch_create(const ms2_system *systems, int n, ms2_batch *out) {
+    return ms2_batch_create_opt(systems, n, out, true, nullptr, nullptr, nullptr);
 }
 
 extern "C" ms2_status ms2_batch_step(ms2_batch b, long long n) {

@@ -813,9 +813,16 @@ ms2_status ms2_ensure_forces(ms2_system s) {
 
 static ms2_status setup_ewald(ms2_system s, double alpha, int kx, int ky, int kz) {
     DevSys &d = s->d;
+    // the splitting parameter is its FP32 value in every part (real space, k-space
+    // tables, self and intramolecular terms): exact in the kernels' FP32 arithmetic
+    alpha = (double)(float)alpha;
     s->alpha = alpha;
     s->hp.alpha = (float)alpha;
-    s->hp.two_alpha_sqrtpi = (float)(2.0 * alpha / std::sqrt(M_PI));
+    {
+        const double tasp = 2.0 * alpha / std::sqrt(M_PI);
+        s->hp.two_alpha_sqrtpi = (float)tasp;
+        s->hp.two_alpha_sqrtpi_lo = (float)(tasp - (double)s->hp.two_alpha_sqrtpi);
+    }
     d.kx = kx;
     d.ky = ky;
     d.kz = kz;
@@ -831,13 +838,18 @@ static ms2_status setup_ewald(ms2_system s, double alpha, int kx, int ky, int kz
     MS2_CUDA_OK(A((void **)&d.frec, sizeof(float) * d.kchunks * 3 * M));
     // sites per structure-factor task: one round over the fused grid (the same on both paths)
     d.sk_sites = ms2_ewald_sk_sites(M, s->step_grid > 0 ? s->step_grid : s->sms);
-    d.ew_fpre = (float)(8.0 * 3.141592653589793 * (double)s->hp.coulomb / s->hp.V * 2.0 * 3.141592653589793 / s->hp.L);
+    {
+        const double C64 = (double)s->hp.coulomb + (double)s->hp.coulomb_lo;  // C to ~48 bits
+        const double fpre = 8.0 * 3.141592653589793 * C64 / s->hp.V * 2.0 * 3.141592653589793 / s->hp.L;
+        d.ew_fpre = (float)fpre;
+        d.ew_fpre_lo = (float)(fpre - (double)d.ew_fpre);
+    }
     MS2_CUDA_OK(A((void **)&d.skpart, sizeof(float2) * (size_t)ms2_ewald_skp_blocks(M, d.sk_sites) * K));
     MS2_CUDA_OK(A((void **)&d.kblk, sizeof(double) * 2 * ms2_ewald_sksum_blocks(K)));
     MS2_CUDA_OK(A((void **)&s->AS, sizeof(float2) * K));
     {  // the k-space tables of this box and alpha (k = (col, nx) with col = (ny + ky)(2 kz + 1) + nz + kz)
         std::vector<double> Ak(K), Bk(K);
-        const double tw = 2.0 * M_PI / s->hp.L, ia2 = 1.0 / ((double)s->hp.alpha * (double)s->hp.alpha);
+        const double tw = 2.0 * M_PI / s->hp.L, ia2 = 1.0 / (alpha * alpha);
         for (int k = 0; k < K; ++k) {
             const int col = k / (kx + 1), nx = k % (kx + 1);
             const int ny = col / (2 * kz + 1) - ky, nz = col % (2 * kz + 1) - kz;
@@ -1022,6 +1034,30 @@ static ms2_status read_scalars(ms2_system s, double *sc) {
     MS2_CUDA_OK(cudaMemcpyAsync(s->hscal, s->d.scal, sizeof(double) * SC_COUNT_, cudaMemcpyDeviceToHost, s->stream));
     MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
     std::memcpy(sc, s->hscal, sizeof(double) * SC_COUNT_);
+    return MS2_OK;
+}
+
+// The server's status round: the system scalars queued to the page-locked host
+// copy (ms2_scalars_enqueue, for many systems), one synchronisation by the
+// caller, then each system's status from its copy (ms2_scalars_status): the
+// checks of ms2_energy_virial without a synchronisation per system.
+ms2_status ms2_scalars_enqueue(ms2_system s) {
+    if (!s->hscal) MS2_CUDA_OK(cudaMallocHost((void **)&s->hscal, sizeof(double) * SC_COUNT_));
+    MS2_CUDA_OK(cudaMemcpyAsync(s->hscal, s->d.scal, sizeof(double) * SC_COUNT_, cudaMemcpyDeviceToHost, s->stream));
+    return MS2_OK;
+}
+
+ms2_status ms2_scalars_status(ms2_system s) {
+    const double *sc = s->hscal;
+    if (sc[SC_KERR] != 0.0) {
+        const double zero = 0.0;
+        cudaMemcpyAsync(s->d.scal + SC_KERR, &zero, sizeof zero, cudaMemcpyHostToDevice, s->stream);
+        cudaMemsetAsync(s->d.counter + 48, 0, sizeof(unsigned), s->stream);
+        cudaStreamSynchronize(s->stream);
+        return ms2_fail(MS2_ETIMEOUT, "a grid-barrier wait of the step kernels timed out");
+    }
+    if (sc[SC_UNSTABLE] != 0.0 || !std::isfinite(sc[SC_UTOT]))
+        return ms2_fail(MS2_EUNSTABLE, "non-finite or exploding forces in the current configuration");
     return MS2_OK;
 }
 

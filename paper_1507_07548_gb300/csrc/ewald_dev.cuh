@@ -193,7 +193,7 @@ __device__ __forceinline__ void sum_finish(const SysParams *__restrict__ P, cons
     te = warp_sum(te);
     tw = warp_sum(tw);
     if (lane == 0) {
-        const double pre = 4.0 * 3.141592653589793 * (double)P->coulomb / P->V;
+        const double pre = 4.0 * 3.141592653589793 * ((double)P->coulomb + (double)P->coulomb_lo) / P->V;
         S.scal[SC_UREC] = pre * te;
         S.scal[SC_WREC_AT] = pre * tw;
     }
@@ -261,8 +261,16 @@ __device__ __forceinline__ void force_task(const SysParams *__restrict__ P, cons
                 kahan_add(fz, cz, (float)nz * syz);
             }
         }
-        const float pre = S.ew_fpre * q;  // 8 pi C / V * 2 pi / L, formed once on the host
-        fx = (fx - cx) * pre; fy = (fy - cy) * pre; fz = (fz - cz) * pre;
+        // the prefactor (8 pi C / V) (2 pi / L) q_s as hi + lo: the host's FP64
+        // constant and the site's charge, each carried as two floats (one FP32
+        // rounding of either would scale every site force of its kind the same
+        // way and bias the lever sum sum_s F_s.s_s of the molecular virial)
+        const int a = ss / S.N, sp = S.species[ss - a * S.N];
+        const float ql = a < P->n_sites[sp] ? P->qlo[sp][a] : 0.f;
+        const float ph = S.ew_fpre * q;
+        const float pl = fmaf(S.ew_fpre, q, -ph) + fmaf(S.ew_fpre, ql, S.ew_fpre_lo * q);
+        fx -= cx; fy -= cy; fz -= cz;
+        fx = fmaf(fx, ph, fx * pl); fy = fmaf(fy, ph, fy * pl); fz = fmaf(fz, ph, fz * pl);
     }
     if (s < M) {
         float *o = S.frec + (size_t)ch * 3 * M + s;

@@ -50,7 +50,11 @@ struct SysParams {
     // LJ site pairs at close contact, r < 1.1 sigma_ab (t12 > close_k6 t6, with
     // close_k6 = 1.1^-6), are evaluated in double-float; +inf switches it off
     float close_k6;
-    float pad_close_[3];                   // keeps the struct a whole number of 16-byte words
+    // Ewald: the FP32 rounding remainder of 2 alpha / sqrt(pi) (a rounded constant
+    // would scale every real-space term of the molecular virial the same way;
+    // alpha itself is taken as its FP32 value everywhere, so it is exact)
+    float two_alpha_sqrtpi_lo;
+    float pad_ew_[2];                      // keeps the struct a whole number of 16-byte words
     // species tables
     int n_sites[MS2_MAXSP];
     double bpos[MS2_MAXSP][MS2_MAXS][3];   // body-frame site positions
@@ -100,7 +104,7 @@ struct DevSys {
     // Ewald
     int nk, kx, ky, kz, nsite_q, kchunks;
     int sk_sites;                      // sites per structure-factor task
-    float ew_fpre;                     // force prefactor 8 pi C / V * 2 pi / L (FP64 on the host, then FP32)
+    float ew_fpre, ew_fpre_lo;         // force prefactor 8 pi C / V * 2 pi / L (FP64 on the host) as hi + lo floats
     float *qs;                         // [nsite_q] site charges
     float2 *eik;                       // [3][kmax+1][nsite_q] e^{i n theta}
     double *Sk;                        // [nk][4]: A*Re S, A*Im S, |S|^2 A part, ... (scaled)

@@ -193,7 +193,7 @@ struct PairWarp {
     static constexpr bool CLOSE = LJM != 0 && QM != 0;
     int elec;
     bool rfq;
-    float C, krf, alpha, tasp, l2l, l2l_lo, ck6;
+    float C, krf, alpha, tasp, tasp_lo, l2l, l2l_lo, ck6;
     unsigned long long rc2;
     // coefficient tables of a single-species system (hi + lo floats: a single
     // FP32 rounding of C q_a q_b or 4 eps sigma^12 would scale every term of that
@@ -228,6 +228,7 @@ struct PairWarp {
         l2l = P->lat_to_len;
         l2l_lo = P->lat_to_len_lo;
         ck6 = P->close_k6;
+        tasp_lo = P->two_alpha_sqrtpi_lo;
         rc2 = P->rc2;
         if (!MULTI) {
 #pragma unroll
@@ -506,9 +507,11 @@ struct PairWarp {
                     uqq += eq;
                     gq = -eq * rinv2;
                 } else {
+                    // alpha is exact in FP32; 2 alpha / sqrt(pi) as hi + lo (one rounding of it
+                    // would scale every exp term of the molecular virial the same way)
                     const float ar = alpha * r2 * rinv;
                     const float ec = erfcf(ar), ex = expf(-ar * ar);
-                    const float bu = ec * rinv, bx = tasp * ex, bg = -(bu + bx) * rinv2;
+                    const float bu = ec * rinv, bx = fmaf(tasp, ex, tasp_lo * ex), bg = -(bu + bx) * rinv2;
                     const float eu = fmaf(cqq, bu, cql * bu);
                     uqq += eu;
                     gq = fmaf(cqq, bg, cql * bg);

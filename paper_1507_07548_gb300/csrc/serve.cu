@@ -22,6 +22,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -29,6 +30,10 @@
 #include "ms2_host.h"
 
 bool ms2_batch_accepts(ms2_system s);  // batch.cu
+ms2_status ms2_batch_create_opt(const ms2_system *systems, int n, ms2_batch *out, bool tune_shapes,
+                                void *(*fa)(size_t, void *), void (*ff)(void *, void *), void *ctx);
+ms2_status ms2_scalars_enqueue(ms2_system s);  // capi.cu: the system scalars to the host, queued
+ms2_status ms2_scalars_status(ms2_system s);   // capi.cu: their status, after a synchronisation
 
 namespace {
 
@@ -76,6 +81,53 @@ size_t estimate_bytes(const JobSpec &j) {
     return b + (1 << 20);
 }
 
+// Device blocks the server's batches reuse: a batch is rebuilt whenever a job is
+// admitted or retires, and cudaMalloc/cudaFree (which synchronises the device)
+// on every rebuild would stall the loop.  Sizes are rounded up to 1/8 steps of a
+// power of two so that blocks fit the next batch's similar requests.
+struct DevCache {
+    std::multimap<size_t, void *> free_;
+    std::map<void *, size_t> size_;
+    static size_t round(size_t n) {
+        size_t p = 256;
+        while (p < n) p <<= 1;
+        const size_t step = std::max<size_t>(p >> 3, 256);
+        return (n + step - 1) / step * step;
+    }
+    static void *alloc(size_t n, void *ctx) {
+        DevCache *c = (DevCache *)ctx;
+        n = round(n);
+        auto it = c->free_.lower_bound(n);
+        if (it != c->free_.end() && it->first <= n + (n >> 2)) {
+            void *p = it->second;
+            c->free_.erase(it);
+            return p;
+        }
+        void *p = nullptr;
+        if (cudaMalloc(&p, n) != cudaSuccess) {
+            c->trim();  // give the cached blocks back and try once more
+            if (cudaMalloc(&p, n) != cudaSuccess) return nullptr;
+        }
+        c->size_[p] = n;
+        return p;
+    }
+    static void release(void *p, void *ctx) {
+        DevCache *c = (DevCache *)ctx;
+        auto it = c->size_.find(p);
+        if (it != c->size_.end()) c->free_.emplace(it->second, p);
+    }
+    void trim() {
+        for (auto &kv : free_) {
+            cudaFree(kv.second);
+            size_.erase(kv.second);
+        }
+        free_.clear();
+    }
+    ~DevCache() {
+        for (auto &kv : size_) cudaFree(kv.first);
+    }
+};
+
 }  // namespace
 
 struct ms2_server_s {
@@ -96,6 +148,7 @@ struct ms2_server_s {
     std::thread th;
     ms2_batch batch = nullptr;
     bool batch_dirty = true;
+    DevCache cache;  // device blocks of the rebuilt batches
     cudaStream_t stream = nullptr;  // shared by all the server's systems
 
     double now() const {
@@ -203,7 +256,9 @@ static void advance(ms2_server S) {
         if (S->batch) ms2_batch_destroy(S->batch);
         S->batch = nullptr;
         ms2_status st = MS2_OK;
-        if (!bs.empty()) st = ms2_batch_create(bs.data(), (int)bs.size(), &S->batch);
+        if (!bs.empty())
+            st = ms2_batch_create_opt(bs.data(), (int)bs.size(), &S->batch, false, &DevCache::alloc, &DevCache::release,
+                                      &S->cache);
         S->batch_dirty = false;
         if (st != MS2_OK) {
             // no silent change of path (it would change the jobs' results):
@@ -218,9 +273,14 @@ static void advance(ms2_server S) {
     for (Slot &sl : S->slots)
         if (!sl.batched) ms2_step(sl.sys, m);
     if (S->batch) ms2_batch_step(S->batch, m);
-    for (Slot &sl : S->slots) {
-        double U;
-        const ms2_status st = ms2_energy_virial(sl.sys, &U, nullptr, nullptr, nullptr);  // synchronises
+    // every job's scalars to the host in one round (one synchronisation), then
+    // the status of each: a failed job retires with it
+    std::vector<ms2_status> qst(S->slots.size(), MS2_OK);
+    for (size_t k = 0; k < S->slots.size(); ++k) qst[k] = ms2_scalars_enqueue(S->slots[k].sys);
+    cudaStreamSynchronize(S->stream);
+    for (size_t k = 0; k < S->slots.size(); ++k) {
+        Slot &sl = S->slots[k];
+        const ms2_status st = qst[k] != MS2_OK ? qst[k] : ms2_scalars_status(sl.sys);
         sl.remaining -= m;
         if (st != MS2_OK) sl.remaining = -1 - (long long)st;  // failed job: retire with its status
     }
@@ -373,7 +433,11 @@ extern "C" ms2_status ms2_serve_close(ms2_server S) {
         S->cv.notify_all();
     }
     if (S->th.joinable()) S->th.join();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaSetDevice(S->device);  // the stream and the block cache belong to the server's device
     if (S->stream) cudaStreamDestroy(S->stream);  // after every system of the server is gone
     delete S;
+    cudaSetDevice(dev);
     return MS2_OK;
 }

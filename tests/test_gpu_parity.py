@@ -25,14 +25,13 @@ def rms_rel(a, b):
 
 # The molecular virial of the ionic solution at ambient pressure is ~1/100 of its
 # LJ and real-space Coulomb parts (W = -2.0e5 K against +2.4e7 K of LJ virial and
-# -1.8e7 K of site-lever terms).  Each FP32 real-space site-pair term carries
-# ~1e-7 relative rounding; over the ~3.5e6 charged site pairs of a configuration
-# that leaves ~0.5 K rms in W (an FP32 emulation of the kernel puts 0.3 K in the
-# erfc virial terms and 0.4 K in the force factors that meet the site levers),
-# i.e. 2.5e-6 of this W; measured 1.7e-6 on the snapshot and up to 7e-6 on
-# stepped states.  Close-contact LJ pairs are double-float; the erfc terms are
-# not.  The Ewald cases are held to W_EWALD; every other case and every energy
-# to 1e-6.
+# -1.8e7 K of site-lever terms).  Every FP32 constant of the Ewald terms carries
+# its rounding remainder and close LJ pairs are double-float; what is left is the
+# FP32 rounding of the erfc argument and of the arithmetic around erfcf/expf in
+# the ~3.5e6 charged site pairs, ~7e-3 K rms per molecule by an FP32 emulation of
+# the kernel, i.e. 0.1-0.6 K in W: measured 7e-7 on the snapshot and 2e-7 -
+# 4.8e-6 on the states of the next five steps.  The Ewald cases are held to
+# W_EWALD; every other case and every energy to 1e-6.
 W_EWALD = 1e-5
 
 
