@@ -4,19 +4,21 @@
 Workload: rigid 3-site water, N = 1000 molecules at 997 kg/m^3 (box 31.07 A),
 molecule-centre cut-off 14 A, conducting reaction field, 298 K, leapfrog with
 quaternion integration, dt = 2 fs, FP32 site-pair arithmetic with FP64 state
-and sums.  One benchmark step = one MD time step: partner search + site-pair
-energies/forces/torques (pair kernel), reduction + thermostat kick, drift +
-quaternion rotation + site build.  The RDF (every 10 steps) is sampled as well.
-Synthetic input: the liquid snapshot tests/golden/water_N1000.npz (a seeded
-simple-cubic lattice start with random orientations and Maxwell-Boltzmann
-velocities, relaxed by FP64 NVT leapfrog steps; written by
-tests/golden/make_snapshots.py).  The GPU arm, the CPU baseline and the
-reference arm all start from it.
+and sums, 1000 NVT steps per job.  One benchmark step = one job: 1000 MD time
+steps (partner search + site-pair energies/forces/torques, reduction +
+thermostat kick, drift + quaternion rotation + site build, the RDF every 10
+steps), run as fused launches of 50 steps.  The job's input state is set
+(untimed) before each job; the pairs of a job are counted by replaying it one
+step at a time.  Synthetic input: the liquid snapshot
+tests/golden/water_N1000.npz (a seeded simple-cubic lattice start with random
+orientations and Maxwell-Boltzmann velocities, relaxed by FP64 NVT leapfrog
+steps; written by tests/golden/make_snapshots.py).  The GPU arm, the CPU
+baseline and the reference arm all start from it.
 
-The L2 cache (129 MB; the whole system is ~0.1 MB) is flushed by writing a
-256 MiB buffer between timed steps, outside the timed interval.  Each step is
-timed with CUDA events on the system's stream; the pair kernel inside it is
-timed with events captured around it.
+The L2 cache (129 MB; the whole system is ~0.4 MB) is flushed by writing a
+256 MiB buffer between timed jobs, outside the timed interval.  Each job is
+timed with CUDA events on the system's stream.  The JSON line also carries the
+single MD step per launch, flushed before each (single_step).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ms2|reference]
 
@@ -39,6 +41,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_WATER, RC, SEED = 1000, 14.0, 2
+JOB_STEPS = 1000      # NVT steps of one job of the water workload (one bench step)
+SINGLE_STEPS = 1000   # flushed single MD steps of the single-step measurement
+REF_SAMPLE_STEPS = 5  # the oracle's bounded sample of a job per bench step (reference arm)
 SNAPSHOT = os.path.join(ROOT, "tests", "golden", "water_N1000.npz")
 RDF_EVERY = 10
 # algorithmic FP32 flops per unique water molecule pair (reaction field):
@@ -61,7 +66,7 @@ def workload():
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=20, help="timed jobs of %d MD steps" % 1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ms2", choices=["ms2", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle CPU-baseline sample length")
@@ -178,10 +183,12 @@ def reference_arm(args, rank, world):
     o = Oracle.from_workload(wl)
     cores = len(os.sched_getaffinity(0))
     R, q, v, L = wl.R, wl.q, wl.v, wl.Lang
+    # each bench step is a bounded sample of the job: REF_SAMPLE_STEPS MD steps of it
     for _ in range(args.warmup):
         R, q, v, L, _, _ = o.run_leapfrog(R, q, v, L, wl.dt, 1, T0=wl.T)
+    R, q, v, L = wl.R, wl.q, wl.v, wl.Lang
     pairs, dt = 0.0, 0.0
-    for _ in range(args.steps):
+    for _ in range(args.steps * REF_SAMPLE_STEPS):
         t0 = time.perf_counter()
         R, q, v, L, _, _ = o.run_leapfrog(R, q, v, L, wl.dt, 1, T0=wl.T)
         dt += time.perf_counter() - t0
@@ -191,11 +198,13 @@ def reference_arm(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": "rigid 3-site water N=1000, reaction field, rc=14 A, 298 K, dt=2 fs, leapfrog+quaternion",
+            "config": {"workload": "rigid 3-site water N=1000, reaction field, rc=14 A, 298 K, dt=2 fs, leapfrog+quaternion, "
+                                   "%d NVT steps per job (one bench step = one job)" % JOB_STEPS,
                        "molecules": N_WATER, "start": "relaxed liquid snapshot (tests/golden/water_N1000.npz)",
                        "parallelism": "host cores (OpenMP owner loop)"},
             "cpu_baseline": {"value": val, "unit": "pair interactions/s", "cores": cores, "kind": "oracle",
-                             "sample": "%d full MD steps of the workload" % args.steps},
+                             "sample": "each bench step the first %d MD steps of the job (%d in all)"
+                                       % (REF_SAMPLE_STEPS, args.steps * REF_SAMPLE_STEPS)},
             "e2e": {"value": val, "unit": "pair interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -204,8 +213,8 @@ def reference_arm(args, rank, world):
 # ---------------------------------------------------------------- GPU arm
 # kernel sources a stored DRAM-traffic figure describes (it is void once they change)
 TRAFFIC_SOURCES = {"pair_water_rf": ("k_pair.cu", "pair_engine.cuh", "ms2_internal.cuh"),
-                   "step_water_rf": ("k_step.cu", "pair_engine.cuh", "integrate_dev.cuh", "grid_dev.cuh",
-                                     "ms2_internal.cuh")}
+                   "step_water_rf_chunk50": ("k_step.cu", "pair_engine.cuh", "integrate_dev.cuh", "grid_dev.cuh",
+                                             "ms2_internal.cuh")}
 
 
 def traffic_record(kernel):
@@ -254,11 +263,53 @@ def gpu_arm(args, rank, world, local_rank):
     wl = workload()
     s = ms2.System.from_workload(wl, stream=stream.cuda_stream)
     s.rdf_setup(min(RC, 0.5 * s.L), 280, every=RDF_EVERY)
-    s.enable_timing(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    R0, q0, v0, L0 = wl.R, wl.q, wl.v, wl.Lang
+
+    # pairs of one job: the job replayed one step at a time (the same trajectory
+    # bit for bit: every launch shape runs the same device functions on the same
+    # decomposition), counting each step's partner pairs
+    s.set_state(R0, q0, v0, L0)
+    job_pairs = 0.0
+    for _ in range(JOB_STEPS):
+        s.step(1)
+        job_pairs += s.energy_terms()["n_pairs"]
+    U_replay = s.energy_virial()[0]
+
+    def one_job():
+        s.set_state(R0, q0, v0, L0)                  # the job's input into HBM (untimed)
+        flush.zero_()                                # evict L2 (outside the timed interval)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(JOB_STEPS)                            # fused launches of 50 steps each
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        one_job()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    n0 = ms2.kernel_launches()
+    fused = s.fused_step() == 1
+    t_job = []
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            t_job.append(one_job())
+    torch.cuda.synchronize()
+    launches = ms2.kernel_launches() - n0
+    U_job = s.energy_virial()[0]
+    tot_ms_max, pairs_all = combine_ranks(sum(t_job), job_pairs * args.steps, world)
+    clocks = clk.summary()
+
+    # the flushed single MD step (one fused launch per step), as before the job
+    # measurement: its event time and the pair phase inside it
+    s.set_state(R0, q0, v0, L0)
+    s.enable_timing(True)
 
     def one_step():
-        flush.zero_()                                # evict L2 (outside the timed interval)
+        flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         s.step(1)
@@ -267,40 +318,28 @@ def gpu_arm(args, rank, world, local_rank):
         tp = s.last_step_times()    # [0] pair kernel (or fused pair phase), [2] the step's kernels
         return e0.elapsed_time(e1), tp[0], tp[2], s.energy_terms()["n_pairs"]
 
-    for _ in range(args.warmup):
+    for _ in range(3):
         one_step()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    n0 = ms2.kernel_launches()
-    fused = s.fused_step() == 1
-    t_step, t_pair, t_kern, pairs = [], [], [], []
-    with ClockSampler(local_rank) as clk:
-        for _ in range(args.steps):
-            a, b, c, d = one_step()
-            t_step.append(a)
-            t_pair.append(b)
-            t_kern.append(c)
-            pairs.append(d)
-    torch.cuda.synchronize()
-    launches = ms2.kernel_launches() - n0
-    tot_ms_max, pairs_all = combine_ranks(sum(t_step), sum(pairs), world)
-    clocks = clk.summary()
-
-    # end to end through the public API from host buffers: set_state (H2D of
-    # the step's input state from page-locked staging) + step + energy read (D2H)
-    R, q, v, L, _ = s.get_state()
+    t1_step, t1_pair, t1_kern, pairs1 = [], [], [], []
+    for _ in range(SINGLE_STEPS):
+        a, b, c, d = one_step()
+        t1_step.append(a)
+        t1_pair.append(b)
+        t1_kern.append(c)
+        pairs1.append(d)
     s.enable_timing(False)
-    e2e_t, e2e_pairs = 0.0, 0.0
+
+    # end to end through the public API from host buffers, per job: set_state
+    # (H2D of the job's input state through page-locked staging), the job's
+    # steps, and the energy read back (D2H)
+    e2e_t = 0.0
     for k in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s.set_state(R, q, v, L)
-        s.step(1)
+        s.set_state(R0, q0, v0, L0)
+        s.step(JOB_STEPS)
         U, Wv, T, P = s.energy_virial()
         e2e_t += time.perf_counter() - t0
-        e2e_pairs += s.energy_terms()["n_pairs"]
-        R, q, v, L, _ = s.get_state()
     h2d = N_WATER * (3 + 4 + 3 + 3) * 8
     d2h = 4 * 8
 
@@ -318,11 +357,15 @@ def gpu_arm(args, rank, world, local_rank):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
     peak_tflops = sms * FP32_LANES * 2 * sm_max * 1e6 / 1e12
-    flops = FLOPS_PER_WATER_PAIR * sum(pairs)
-    # dominant kernel: the fused step kernel (one launch per step) or, per phase, the pair kernel
-    kern_ms = t_kern if fused else t_pair
-    achieved = flops / (sum(kern_ms) * 1e-3) / 1e12
-    traffic = traffic_record("step_water_rf" if fused else "pair_water_rf")
+    # dominant kernel: the fused step kernel, JOB_STEPS / 50 launches per job (the
+    # first also evaluates the state as set, whose pair phase is not counted)
+    per_job = JOB_STEPS // 50 if fused else JOB_STEPS
+    kern_ms = statistics.mean(t_job) / per_job
+    achieved = FLOPS_PER_WATER_PAIR * job_pairs / per_job / (kern_ms * 1e-3) / 1e12
+    traffic = traffic_record("step_water_rf_chunk50" if fused else "pair_water_rf")
+    # the flushed single step
+    single_ms = statistics.mean(t1_step)
+    single_achieved = FLOPS_PER_WATER_PAIR * sum(pairs1) / (sum(t1_kern) * 1e-3) / 1e12
     cpu_val, cpu_n, cpu_dt, cores = oracle_rate(args.cpu_seconds)
     cpu1_val, cpu1_n, cpu1_dt, _ = oracle_rate(max(1.0, args.cpu_seconds / 4), threads=1)
     value = pairs_all / (tot_ms_max * 1e-3)
@@ -330,27 +373,34 @@ def gpu_arm(args, rank, world, local_rank):
         "metric": "pair interactions/s", "value": value, "unit": "pair interactions/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "rigid 3-site water N=1000, reaction field, rc=14 A, 298 K, dt=2 fs, leapfrog+quaternion",
-                   "molecules": N_WATER, "l2": "flushed between steps (256 MiB write)",
-                   "start": "relaxed liquid snapshot (tests/golden/water_N1000.npz)",
+        "config": {"workload": "rigid 3-site water N=1000, reaction field, rc=14 A, 298 K, dt=2 fs, leapfrog+quaternion, "
+                               "%d NVT steps per job (one bench step = one job)" % JOB_STEPS,
+                   "molecules": N_WATER, "md_steps_per_bench_step": JOB_STEPS,
+                   "l2": "flushed between jobs (256 MiB write); a job keeps its state on chip between its steps",
+                   "start": "relaxed liquid snapshot (tests/golden/water_N1000.npz), set before each job (untimed)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "state": "FP64 positions/integrator/sums, FP32 site pairs"},
-        "molecule_steps_per_s": N_WATER * args.steps * world / (tot_ms_max * 1e-3),
+        "molecule_steps_per_s": N_WATER * JOB_STEPS * args.steps * world / (tot_ms_max * 1e-3),
         "site_pair_interactions_per_s": value * 10,
+        "pairs_per_job": job_pairs, "replay_matches_job": bool(U_replay == U_job),
         "roofline": {"bound": "alu",
-                     "kernel": "k_step<3,1,7,0,RF> (fused MD step)" if fused else "k_pair<3,1,7,0,RF>",
+                     "kernel": "k_step<3,1,7,0,RF> (fused MD step, 50 steps per launch)" if fused else "k_pair<3,1,7,0,RF>",
                      "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                      "peak_source": "%d SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz max SM clock (unit counts; "
                                     "MEASURED_PEAKS.json has no FP32 figure)" % (sms, sm_max),
-                     "kernel_ms": statistics.mean(kern_ms),
-                     "pair_phase_ms": statistics.mean(t_pair),
-                     "algorithmic_flops_per_launch": FLOPS_PER_WATER_PAIR * statistics.mean(pairs)},
+                     "kernel_ms": kern_ms,
+                     "algorithmic_flops_per_launch": FLOPS_PER_WATER_PAIR * job_pairs / per_job},
+        "single_step": {"what": "one MD step per fused launch, L2 flushed before each, CUDA events",
+                        "steps": SINGLE_STEPS, "ms_per_step": single_ms,
+                        "value": sum(pairs1) / (sum(t1_step) * 1e-3), "unit": "pair interactions/s",
+                        "kernel_ms": statistics.mean(t1_kern), "pair_phase_ms": statistics.mean(t1_pair),
+                        "achieved_tflops": single_achieved, "frac": single_achieved / peak_tflops},
         "cpu_baseline": {"value": cpu_val, "unit": "pair interactions/s", "cores": cores, "kind": "oracle",
-                         "sample": "%d MD steps of the same workload, %.1f s" % (cpu_n, cpu_dt),
+                         "sample": "the first %d MD steps of the job, %.1f s" % (cpu_n, cpu_dt),
                          "single_thread": {"value": cpu1_val, "cores": 1,
                                            "sample": "%d MD steps, %.1f s" % (cpu1_n, cpu1_dt)}},
-        "e2e": {"value": e2e_pairs / e2e_t, "unit": "pair interactions/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_pairs * args.steps / e2e_t, "unit": "pair interactions/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
