@@ -110,8 +110,8 @@ __global__ void __launch_bounds__(BT, 1) k_mstep(MsArgs A) {
     __shared__ double wtot[BT / 32][MS2_NRED];
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * nw + warp, W = gridDim.x * nw;
-    const Smem sm = carve<NS, Eng::DMU, MULTI>(smem_raw, A.Np, nw);
-    unsigned *hist = (unsigned *)(smem_raw + al16(pair_engine::smem_bytes(NS, Eng::DMU, MULTI, A.Np, nw)));
+    const Smem sm = carve<NS, Eng::TILE, MULTI>(smem_raw, A.Np, nw);
+    unsigned *hist = (unsigned *)(smem_raw + al16(pair_engine::smem_bytes(NS, Eng::TILE, MULTI, A.Np, nw)));
     int *wq = sm.queue + warp * QSTRIDE;
     unsigned target = 0;
     auto on_timeout = [&]() {
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(BT, 1) k_mstep(MsArgs A) {
             e.setup(P);
             __syncthreads();  // the previous segment's tile is no longer read
             load_tables<MULTI>(P, sm);
-            stage_tile<NS, Eng::DMU, MULTI>(sm, S, 0, N, A.Np, Eng::MOLD && e.rfq);
+            stage_tile<NS, DM, Eng::MOLD, MULTI>(sm, S, 0, N, A.Np, Eng::MOLD && e.rfq);
             if (rdf)
                 for (int c = threadIdx.x; c < S.rdf_rows * S.rdf_bins; c += blockDim.x) hist[c] = 0u;
             __syncthreads();
@@ -271,8 +271,19 @@ const BatchFn kBatchFnWide[K_COUNT] = {&k_mstep<1, 1u, 0u, 0u, ELEC_NONE, false,
                                        nullptr, nullptr, nullptr};
 BatchFn kernel_of(int kind, int threads) { return threads > MS_THREADS ? kBatchFnWide[kind] : kBatchFn[kind]; }
 const int kKindNS[K_COUNT] = {1, 3, 3, 4, 4, 3};
-const bool kKindDMU[K_COUNT] = {false, false, true, false, true, false};
+// tile layout of each kind's kernel (dipole slots kept, molecular dipoles kept)
+const int kKindTile[K_COUNT] = {pair_engine::tile_code(0, false), pair_engine::tile_code(0, true),
+                                 pair_engine::tile_code(1, false), pair_engine::tile_code(0, true),
+                                 pair_engine::tile_code(4, true), pair_engine::tile_code(0, false)};
 const bool kKindMulti[K_COUNT] = {false, false, false, true, true, true};
+
+static_assert(PairWarp<1, 1u, 0u, 0u, ELEC_NONE, false>::TILE == tile_code(0, false) &&
+                  PairWarp<3, 1u, 7u, 0u, ELEC_RF, false>::TILE == tile_code(0, true) &&
+                  PairWarp<3, 3u, 0u, 4u, ELEC_RF, false>::TILE == tile_code(1, false) &&
+                  PairWarp<4, 0xFu, 0xFu, 0u, -1, true>::TILE == tile_code(0, true) &&
+                  PairWarp<4, 0xFu, 0xFu, 0xFu, -1, true>::TILE == tile_code(4, true) &&
+                  PairWarp<3, 1u, 7u, 0u, ELEC_EWALD, true>::TILE == tile_code(0, false),
+              "kKindTile matches the kinds' kernels");
 
 int kind_of(ms2_system s) {
     const SysParams &P = s->hp;
@@ -286,7 +297,7 @@ int kind_of(ms2_system s) {
 }
 
 size_t batch_smem(int kind, int Np, int threads, int rdf_cells) {
-    return al16(pair_engine::smem_bytes(kKindNS[kind], kKindDMU[kind], kKindMulti[kind], Np, threads / 32)) +
+    return al16(pair_engine::smem_bytes(kKindNS[kind], kKindTile[kind], kKindMulti[kind], Np, threads / 32)) +
            sizeof(unsigned) * (size_t)std::max(rdf_cells, 1);
 }
 

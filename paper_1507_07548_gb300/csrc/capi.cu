@@ -56,10 +56,10 @@ int ms2_ewald_sksum_blocks(int K);
 size_t ms2_ewald_force_smem(int kx, int kz, int ny_per_chunk);
 __global__ void k_rdf(const SysParams *, DevSys);
 __global__ void k_terms(const SysParams *, DevSys, double *);
-size_t ms2_pair_smem_bytes(int NS, bool dmu, bool multi, int TJ, int wpb);
+size_t ms2_pair_smem_bytes(int NS, int tile, bool multi, int TJ, int wpb);
 size_t ms2_pair64_smem_bytes(int TJ, int wpb);
 void *ms2_pick_pair_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, int *ns_used,
-                           bool *dmu, bool *mult_used, bool mass);
+                           int *tile, bool *mult_used, bool mass);
 void *ms2_pick_heat_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, const void *pair_fn);
 
 
@@ -445,10 +445,10 @@ static ms2_status setup_pair(ms2_system s) {
     if (s->fp64) {
         s->ns = 1;
         s->pair_fn = (void *)&k_pair_lj64;
-        s->dmu = false;
+        s->tile = 0;
         s->multi_used = false;
     } else {
-        s->pair_fn = ms2_pick_pair_kernel(P.ns, ljm, qm, dm, P.elec, P.multi != 0, &s->ns, &s->dmu, &s->multi_used,
+        s->pair_fn = ms2_pick_pair_kernel(P.ns, ljm, qm, dm, P.elec, P.multi != 0, &s->ns, &s->tile, &s->multi_used,
                                           P.massieu != 0);
     }
     s->hp.ns = s->ns;
@@ -461,7 +461,7 @@ static ms2_status size_pair_tiles(ms2_system s) {
     const size_t cap = 96 * 1024;
     int TJ = std::max(32, range);
     auto bytes = [&](int tj) {
-        return s->fp64 ? ms2_pair64_smem_bytes(tj, s->wpb) : ms2_pair_smem_bytes(s->ns, s->dmu, s->multi_used, tj, s->wpb);
+        return s->fp64 ? ms2_pair64_smem_bytes(tj, s->wpb) : ms2_pair_smem_bytes(s->ns, s->tile, s->multi_used, tj, s->wpb);
     };
     while (bytes(TJ) > cap && TJ > 64) TJ = (TJ + 1) / 2;
     s->TJ = TJ;
@@ -505,7 +505,7 @@ static void setup_fused(ms2_system s, const ms2_options &o) {
     // Ewald: the reciprocal-space scratch of the default |n| <= 8 (ms2_ewald_params may change it later;
     // a launch that then does not fit takes the per-phase kernels)
     const size_t ews = s->hp.elec == ELEC_EWALD ? ms2_step_ewald_scratch(8, 8, 8, 1, ms2_ewald_sk_sites(s->N * s->ns, sms)) : 0;
-    const size_t base = ms2_step_smem_bytes(s->ns, s->dmu, s->multi_used, Np, mcap, js, 0, ews);
+    const size_t base = ms2_step_smem_bytes(s->ns, s->tile, s->multi_used, Np, mcap, js, 0, ews);
     int nb = 0;
     if (base > maxdyn || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxdyn) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ms2_step_threads(), base) != cudaSuccess || nb < 1) {
@@ -1021,7 +1021,7 @@ extern "C" ms2_status ms2_step_kernel(ms2_system s, int *fused) {
     if (!s || !fused) return ms2_fail(MS2_EINVAL, "null argument");
     const int cells = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
     *fused = s->step_fn && s->res_every == 0 && (s->hf_every == 0 || s->step_heat_fn) &&
-                     ms2_step_smem_bytes(s->ns, s->dmu, s->multi_used, s->Np, s->mcap, s->jsplit, cells, step_ews(s)) <=
+                     ms2_step_smem_bytes(s->ns, s->tile, s->multi_used, s->Np, s->mcap, s->jsplit, cells, step_ews(s)) <=
                          s->step_smem_max
                  ? 1 : 0;
     return MS2_OK;
@@ -1132,7 +1132,7 @@ static bool run_fused(ms2_system s, long long m, long long s0) {
     void *fn = s->hf_every > 0 ? s->step_heat_fn : s->step_fn;
     if (!fn) return false;
     const int cells = s->d.rdf ? s->d.rdf_rows * s->d.rdf_bins : 0;
-    const size_t smem = ms2_step_smem_bytes(s->ns, s->dmu, s->multi_used, s->Np, s->mcap, s->jsplit, cells, step_ews(s));
+    const size_t smem = ms2_step_smem_bytes(s->ns, s->tile, s->multi_used, s->Np, s->mcap, s->jsplit, cells, step_ews(s));
     if (smem > s->step_smem_max) return false;
     unsigned *cnt = s->d.counter;
     StepArgs A;
@@ -1720,7 +1720,7 @@ extern "C" ms2_status ms2_heat_setup(ms2_system s, int every, int n_lags, const 
     if (s->fuse_fn && s->step_fn) {
         void *fn = ms2_pick_step_kernel(s->ns, s->ljm, s->qm, s->dm, s->hp.elec, false, s->hp.massieu != 0, true);
         int nb = 0;
-        const size_t base = ms2_step_smem_bytes(s->ns, s->dmu, s->multi_used, s->Np, s->mcap, s->jsplit, 0, 0);
+        const size_t base = ms2_step_smem_bytes(s->ns, s->tile, s->multi_used, s->Np, s->mcap, s->jsplit, 0, 0);
         if (fn && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->step_smem_max) == cudaSuccess &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ms2_step_threads(), base) == cudaSuccess && nb >= 1)
             s->step_heat_fn = fn;

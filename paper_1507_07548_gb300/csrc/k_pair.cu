@@ -29,8 +29,8 @@
 using namespace pair_engine;
 
 // bytes of dynamic shared memory the pair kernel needs
-size_t ms2_pair_smem_bytes(int NS, bool dmu, bool multi, int TJ, int wpb) {
-    return pair_engine::smem_bytes(NS, dmu, multi, TJ, wpb);
+size_t ms2_pair_smem_bytes(int NS, int tile, bool multi, int TJ, int wpb) {
+    return pair_engine::smem_bytes(NS, tile, multi, TJ, wpb);
 }
 
 // grid: x = blocks of wpb molecules (one warp each), y = j-range; one FP32
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) k_pair(const SysParams *__restrict__ P, D
     const int i = blockIdx.x * wpb + warp;
     const int JS = gridDim.y, p = blockIdx.y;
     const int j0 = (int)(((long long)N * p) / JS), j1 = (int)(((long long)N * (p + 1)) / JS);
-    Smem sm = carve<NS, Eng::DMU, MULTI>(smem_raw, TJ, wpb);
+    Smem sm = carve<NS, Eng::TILE, MULTI>(smem_raw, TJ, wpb);
     int *wq = sm.queue + warp * QSTRIDE;
     load_tables<MULTI>(P, sm);
     Eng e;
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) k_pair(const SysParams *__restrict__ P, D
     for (int t0 = j0; t0 < j1; t0 += TJ) {
         const int tn = min(TJ, j1 - t0);
         __syncthreads();
-        stage_tile<NS, Eng::DMU, MULTI>(sm, S, t0, tn, TJ, Eng::MOLD && e.rfq);
+        stage_tile<NS, DM, Eng::MOLD, MULTI>(sm, S, t0, tn, TJ, Eng::MOLD && e.rfq);
         __syncthreads();
         if (active) e.scan(sm, TJ, t0, tn, wq, lane);
     }
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256) k_heat(const SysParams *__restrict__ P, D
     const int i = blockIdx.x * wpb + warp;
     const int JS = gridDim.y, p = blockIdx.y;
     const int j0 = (int)(((long long)N * p) / JS), j1 = (int)(((long long)N * (p + 1)) / JS);
-    Smem sm = carve<NS, Eng::DMU, MULTI>(smem_raw, TJ, wpb);
+    Smem sm = carve<NS, Eng::TILE, MULTI>(smem_raw, TJ, wpb);
     int *wq = sm.queue + warp * QSTRIDE;
     load_tables<MULTI>(P, sm);
     Eng e;
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) k_heat(const SysParams *__restrict__ P, D
     for (int t0 = j0; t0 < j1; t0 += TJ) {
         const int tn = min(TJ, j1 - t0);
         __syncthreads();
-        stage_tile<NS, Eng::DMU, MULTI>(sm, S, t0, tn, TJ, Eng::MOLD && e.rfq);
+        stage_tile<NS, DM, Eng::MOLD, MULTI>(sm, S, t0, tn, TJ, Eng::MOLD && e.rfq);
         __syncthreads();
         if (active) e.template scan<true>(sm, TJ, t0, tn, wq, lane);
     }
@@ -250,12 +250,12 @@ void *ms2_pick_heat_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int e
 // With mass, the variant that also sums the second volume derivative (null where
 // none is built: dipoles, Ewald, 8 site slots).
 void *ms2_pick_pair_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, int *ns_used,
-                           bool *dmu, bool *mult_used, bool mass) {
+                           int *tile, bool *mult_used, bool mass) {
     for (const PairVariant &v : kVariants) {
         if (v.ns == ns && v.ljm == ljm && v.qm == qm && v.dm == dm && v.elec == elec && v.multi == multi &&
             (!mass || v.mass)) {
             *ns_used = ns;
-            *dmu = dm != 0;
+            *tile = pair_engine::tile_code(pair_engine::popc_c(v.dm), v.qm != 0 && v.elec == ELEC_RF);
             *mult_used = multi;
             return (void *)(mass ? v.mass : v.fn);
         }
@@ -268,7 +268,7 @@ void *ms2_pick_pair_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int e
                     exact_single = true;
             if (!exact_single) {
                 *ns_used = ns;
-                *dmu = dm != 0;
+                *tile = pair_engine::tile_code(pair_engine::popc_c(v.dm), v.qm != 0 && v.elec == ELEC_RF);
                 *mult_used = true;
                 return (void *)v.fn;
             }
@@ -276,7 +276,9 @@ void *ms2_pick_pair_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int e
     }
     const int g = ns <= 4 ? 0 : 1;
     *ns_used = g ? 8 : 4;
-    *dmu = dm != 0;
+    // the generic kernels keep every slot's dipole (when they take dipoles) and the
+    // molecular dipoles (their electrostatics are chosen at run time)
+    *tile = pair_engine::tile_code(dm != 0 ? *ns_used : 0, true);
     *mult_used = true;
     if (mass) return (g == 0 && dm == 0 && elec != ELEC_EWALD) ? (void *)kGenericMass : nullptr;
     return (void *)kGeneric[g][dm != 0];

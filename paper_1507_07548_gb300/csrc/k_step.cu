@@ -117,8 +117,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lo = (int)((long long)N * b / G), hi = (int)((long long)N * (b + 1) / G), nm = hi - lo;
     if (A.timing && b == 0 && threadIdx.x == 0) tph[5] = global_ns();  // kernel entry
-    Smem sm = carve<NS, Eng::DMU, MULTI>(smem_raw, A.Np, STEP_WARPS);
-    unsigned char *own = smem_raw + al16(smem_bytes(NS, Eng::DMU, MULTI, A.Np, STEP_WARPS));
+    Smem sm = carve<NS, Eng::TILE, MULTI>(smem_raw, A.Np, STEP_WARPS);
+    unsigned char *own = smem_raw + al16(smem_bytes(NS, Eng::TILE, MULTI, A.Np, STEP_WARPS));
     // the own region's arrays, rebuilt where needed (short live ranges: the
     // pair loop keeps its registers)
     auto view = [&]() {
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         grid_sync(A.bar, A.err, target, on_timeout, A.wait_ns);
         if (tm) tph[1] = global_ns();
         // ---- stage the whole system; pair items of the own molecules; RDF
-        stage_tile<NS, Eng::DMU, MULTI>(sm, S, 0, N, A.Np, rfq);
+        stage_tile<NS, DM, Eng::MOLD, MULTI>(sm, S, 0, N, A.Np, rfq);
         __syncthreads();
         // the previous step's record (U, W, T, P, averages, a conductivity
         // sample), off the critical path: block 0's last warp, which has no pair
@@ -379,9 +379,9 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
 // shared memory of the fused step: the staged system, the partner queues of 16
 // warps, the parameter tables, then the own region (state and partials of at
 // most mcap molecules, j-split js) and an RDF histogram of rdf_cells counters
-size_t ms2_step_smem_bytes(int NS, bool dmu, bool multi, int Np, int mcap, int js, int rdf_cells, size_t ews) {
+size_t ms2_step_smem_bytes(int NS, int tile, bool multi, int Np, int mcap, int js, int rdf_cells, size_t ews) {
     const size_t own = own_layout(mcap, js, ews).hist;
-    return al16(pair_engine::smem_bytes(NS, dmu, multi, Np, STEP_WARPS)) + own + sizeof(unsigned) * (size_t)rdf_cells;
+    return al16(pair_engine::smem_bytes(NS, tile, multi, Np, STEP_WARPS)) + own + sizeof(unsigned) * (size_t)rdf_cells;
 }
 
 int ms2_step_threads() { return STEP_THREADS; }

@@ -38,7 +38,8 @@ struct ms2_system_s {
     double rc = 0;
     bool lrc = true, reduced = false, fp64 = false;
     unsigned ljm = 0, qm = 0, dm = 0;
-    bool dmu = false, multi_used = false;
+    int tile = 0;  // tile layout of the pair kernel: dipole slots kept + 256 x (molecular dipoles kept)
+    bool multi_used = false;
     void *pair_fn = nullptr;
     int wpb = 8, jsplit = 1, TJ = 32;
     size_t pair_smem = 0;
@@ -102,7 +103,7 @@ ms2_status ms2_validate_models(const ms2_model *models, int n_models, ms2_elec e
 void ms2_launch_residence(cudaStream_t st, const SysParams *P, const DevSys &S, const ResArgs &a);
 size_t ms2_residence_state_doubles(int M);
 // fused step kernel (k_step.cu)
-size_t ms2_step_smem_bytes(int NS, bool dmu, bool multi, int Np, int mcap, int js, int rdf_cells, size_t ews);
+size_t ms2_step_smem_bytes(int NS, int tile, bool multi, int Np, int mcap, int js, int rdf_cells, size_t ews);
 size_t ms2_step_ewald_scratch(int kx, int ky, int kz, int ny_per_chunk, int skc);
 int ms2_step_threads();
 void *ms2_pick_step_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, bool mass, bool heat);

@@ -57,9 +57,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 __global__ void k_build(const SysParams *, DevSys);
 __global__ void k_reduce(const SysParams *, DevSys, int);
 __global__ void k_aos3(const double *src, double *dst, int N);
-size_t ms2_pair_smem_bytes(int NS, bool dmu, bool multi, int TJ, int wpb);
+size_t ms2_pair_smem_bytes(int NS, int tile, bool multi, int TJ, int wpb);
 void *ms2_pick_pair_kernel(int ns, unsigned ljm, unsigned qm, unsigned dm, int elec, bool multi, int *ns_used,
-                           bool *dmu, bool *mult_used, bool mass);
+                           int *tile, bool *mult_used, bool mass);
 ms2_status ms2_validate_models(const ms2_model *models, int n_models, ms2_elec elec);
 void ms2_fill_params(SysParams &P, const ms2_model *models, int n_models, const std::vector<int> &species, double L,
                      double rc, ms2_elec elec, const ms2_options &o, double T0);
@@ -191,8 +191,9 @@ extern "C" ms2_status ms2_forces_noalloc(const ms2_model *models, const int *N_p
             if (hp.bdip[m][a][0] != 0 || hp.bdip[m][a][1] != 0 || hp.bdip[m][a][2] != 0) dm |= 1u << a;
         }
     int ns = 1;
-    bool dmu = false, multi = false;
-    void *fn = ms2_pick_pair_kernel(hp.ns, ljm, qm, dm, hp.elec, hp.multi != 0, &ns, &dmu, &multi, false);
+    int tile = 0;
+    bool multi = false;
+    void *fn = ms2_pick_pair_kernel(hp.ns, ljm, qm, dm, hp.elec, hp.multi != 0, &ns, &tile, &multi, false);
     if (ns > NA_NS) return ms2_fail(MS2_EINVAL, "ms2_forces_noalloc: at most %d site slots", NA_NS);
     hp.ns = ns;
     double coulomb, kconv, uconst, wbg, ulrc, plrc;
@@ -245,8 +246,8 @@ extern "C" ms2_status ms2_forces_noalloc(const ms2_model *models, const int *N_p
 
     const int range = (N + d.jsplit - 1) / d.jsplit;
     int TJ = std::max(32, range);
-    while (ms2_pair_smem_bytes(ns, dmu, multi, TJ, wpb) > 96 * 1024 && TJ > 64) TJ = (TJ + 1) / 2;
-    const size_t smem = ms2_pair_smem_bytes(ns, dmu, multi, TJ, wpb);
+    while (ms2_pair_smem_bytes(ns, tile, multi, TJ, wpb) > 96 * 1024 && TJ > 64) TJ = (TJ + 1) / 2;
+    const size_t smem = ms2_pair_smem_bytes(ns, tile, multi, TJ, wpb);
 
     k_noalloc_setup<<<(N + 127) / 128, 128, 0, sm>>>(hp, c, d, (SysParams *)(base + O_PARAMS), R_dev, q_dev);
     k_build<<<(4 * N + 127) / 128, 128, 0, sm>>>(dP, d);

@@ -21,8 +21,10 @@ constexpr int CQCAP = 64;
 constexpr int QSTRIDE = QCAP + CQCAP;
 
 // Tile arrays: tP[j] = (lattice centre X, Y, Z, species) of tile molecule j
-// (one 16-byte load), site offsets ts[(k NS + b) TJ + j], point dipoles tmu (same
-// layout) and molecular dipoles tmd[k TJ + j].
+// (one 16-byte load), site offsets ts[(k NS + b) TJ + j], the point dipoles of
+// the ND dipole slots tmu[(k ND + d) TJ + j] (d: the slot's rank among them) and,
+// for the reaction field with point charges (MD), molecular dipoles tmd[k TJ + j].
+// A tile layout is coded as ND + 256 MD.
 struct Smem {
     uint4 *tP;
     float *ts, *tmu, *tmd;
@@ -31,15 +33,22 @@ struct Smem {
     int *sljt;
 };
 
+__host__ __device__ constexpr int popc_c(unsigned x) { return x ? (int)(x & 1u) + popc_c(x >> 1) : 0; }
+// rank of slot b among the dipole slots of mask DM
+__host__ __device__ constexpr int dip_rank(unsigned DM, int b) { return popc_c(DM & ((1u << b) - 1u)); }
+__host__ __device__ constexpr int tile_code(int nd, bool md) { return nd + (md ? 256 : 0); }
+
 // tile arrays of TJ molecules, the per-warp queues and the parameter tables
-template <int NS, bool DMU, bool MULTI>
+template <int NS, int TILE, bool MULTI>
 __device__ __forceinline__ Smem carve(unsigned char *base, int TJ, int wpb) {
+    constexpr int ND = TILE & 255;
+    constexpr bool MD = (TILE >> 8) != 0;
     Smem m;
     m.tP = (uint4 *)base;
     m.ts = (float *)(m.tP + TJ);
     m.tmu = m.ts + 3 * NS * TJ;
-    m.tmd = m.tmu + (DMU ? 3 * NS * TJ : 0);
-    m.queue = (int *)(m.tmd + 3 * TJ);
+    m.tmd = m.tmu + 3 * ND * TJ;
+    m.queue = (int *)(m.tmd + (MD ? 3 * TJ : 0));
     m.sq = (float *)(m.queue + wpb * QSTRIDE);
     m.sql = m.sq + MS2_MAXSP * MS2_MAXS;
     m.sljt = (int *)(m.sql + MS2_MAXSP * MS2_MAXS);
@@ -50,18 +59,21 @@ __device__ __forceinline__ Smem carve(unsigned char *base, int TJ, int wpb) {
     return m;
 }
 
-__host__ __device__ inline size_t smem_bytes(int NS, bool dmu, bool multi, int TJ, int wpb) {
+// bytes of carve's arrays (tile: the layout code ND + 256 MD)
+__host__ __device__ inline size_t smem_bytes(int NS, int tile, bool multi, int TJ, int wpb) {
     (void)multi;
+    const int nd = tile & 255;
+    const bool md = (tile >> 8) != 0;
     size_t n = sizeof(uint4) * TJ + sizeof(float) * 3 * NS * TJ;
-    if (dmu) n += sizeof(float) * 3 * NS * TJ;
-    n += sizeof(float) * 3 * TJ;  // molecular dipoles (reaction field; reserved always)
+    n += sizeof(float) * 3 * nd * TJ;
+    if (md) n += sizeof(float) * 3 * TJ;
     n += sizeof(int) * wpb * QSTRIDE;
     n += 2 * sizeof(float) * MS2_MAXSP * MS2_MAXS + sizeof(int) * MS2_MAXSP * MS2_MAXS;
     n += 4 * sizeof(float) * MS2_MAXT * MS2_MAXT;
     return n;
 }
 
-// block-level: multi-species parameter tables into shared memory
+// block-level: tables of several species into shared memory
 template <bool MULTI>
 __device__ __forceinline__ void load_tables(const SysParams *__restrict__ P, const Smem &sm) {
     if constexpr (MULTI) {
@@ -79,9 +91,11 @@ __device__ __forceinline__ void load_tables(const SysParams *__restrict__ P, con
     }
 }
 
-// block-level: molecules [t0, t0+tn) of S into tile slots [0, tn)
-template <int NS, bool DMU, bool MULTI>
+// block-level: molecules [t0, t0+tn) of S into tile slots [0, tn); DM: the
+// dipole slots of the kernel, MD: molecular dipoles kept (read when rfq)
+template <int NS, unsigned DM, bool MD, bool MULTI>
 __device__ __forceinline__ void stage_tile(const Smem &sm, const DevSys &S, int t0, int tn, int TJ, bool rfq) {
+    constexpr int ND = popc_c(DM);
     const int N = S.N;
     for (int k = threadIdx.x; k < tn; k += blockDim.x) {
         const int j = t0 + k;
@@ -90,11 +104,15 @@ __device__ __forceinline__ void stage_tile(const Smem &sm, const DevSys &S, int 
                               MULTI ? (uint32_t)S.species[j] : 0u);
 #pragma unroll
         for (int c = 0; c < 3 * NS; ++c) sm.ts[c * TJ + k] = __ldcg(S.s + c * N + j);
-        if (DMU) {
+        if constexpr (ND > 0) {
 #pragma unroll
-            for (int c = 0; c < 3 * NS; ++c) sm.tmu[c * TJ + k] = __ldcg(S.mu + c * N + j);
+            for (int b = 0; b < NS; ++b)
+                if ((DM >> b) & 1u)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        sm.tmu[(c * ND + dip_rank(DM, b)) * TJ + k] = __ldcg(S.mu + (c * NS + b) * N + j);
         }
-        if (rfq) {
+        if (MD && rfq) {
             sm.tmd[k] = __ldcg(S.mum + j);
             sm.tmd[TJ + k] = __ldcg(S.mum + N + j);
             sm.tmd[2 * TJ + k] = __ldcg(S.mum + 2 * N + j);
@@ -172,6 +190,8 @@ struct PairWarp {
     static_assert(!MASS || (DM == 0 && ELEC != ELEC_EWALD), "volume derivatives: LJ and point charges, no Ewald");
     static constexpr bool DMU = DM != 0;
     static constexpr bool MOLD = QM != 0 && (ELEC == ELEC_RF || ELEC < 0);  // molecular-dipole RF term
+    static constexpr int ND = popc_c(DM);                 // dipole slots kept in the tile
+    static constexpr int TILE = tile_code(ND, MOLD);      // the tile layout of this variant
     // First site PA of an adjacent pair (PA, PA + 1) that meets every partner site
     // with the same kinds of term (LJ and/or charge, no point dipole), or -1.  In
     // the force pass of a single-species LJ / reaction-field kernel the two rows of
@@ -293,7 +313,7 @@ struct PairWarp {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 si[a][k] = sm.ts[(k * NS + a) * TJ + i];
-                mui[a][k] = DMU && ((DM >> a) & 1) ? sm.tmu[(k * NS + a) * TJ + i] : 0.f;
+                mui[a][k] = DMU && ((DM >> a) & 1) ? sm.tmu[(k * ND + dip_rank(DM, a)) * TJ + i] : 0.f;
             }
         spi = MULTI ? (int)p.w : 0;
 #pragma unroll
@@ -371,7 +391,7 @@ struct PairWarp {
         pj[b][2] = dz + sm.ts[(2 * NS + b) * TJ + jl];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-            muj[b][k] = DMU && ((DM >> b) & 1) ? sm.tmu[(k * NS + b) * TJ + jl] : 0.f;
+            muj[b][k] = DMU && ((DM >> b) & 1) ? sm.tmu[(k * ND + dip_rank(DM, b)) * TJ + jl] : 0.f;
     }
     // Molecular virial, owner share: the site-pair part -sum_ab f_ab.r_ab here
     // (short levers, no FP32 force sum meets the long lever d), the
