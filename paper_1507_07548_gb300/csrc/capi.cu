@@ -477,10 +477,11 @@ static size_t step_ews(ms2_system s) {
 }
 
 // fused step: a system is fusable where a variant exists, the device launches
-// cooperative kernels, every block owns at most 16 molecules (one pair item per
-// warp for j-split >= 1) and the whole system plus the own region fits one
-// SM's shared memory.  A fusable system gets the fused decomposition (reduction
-// units = the grid's block ranges, j-split 16 / molecules per block) on both
+// cooperative kernels, every block owns at most 32 molecules (above 16 a block's
+// warps take two pair items each, j-split 1) and the whole system plus the own
+// region fits one SM's shared memory.  A fusable system gets the fused
+// decomposition (reduction units = the grid's block ranges, j-split 16 /
+// molecules per block, at least 1) on both
 // paths, so fused and per-phase chunks agree bit for bit; ms2_options.fused_step
 // only chooses which path runs.
 static void setup_fused(ms2_system s, const ms2_options &o) {
@@ -493,7 +494,7 @@ static void setup_fused(ms2_system s, const ms2_options &o) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
     const int mcap = (s->N + sms - 1) / std::max(sms, 1);
-    if (sms < 1 || mcap > 16) return;
+    if (sms < 1 || mcap > 32) return;  // (the whole-system tile must fit one block as well)
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
         cudaGetLastError();

@@ -34,6 +34,12 @@ def water_ragged():
     return wl
 
 
+def water_large():
+    wl = W.water_box(N=2744, rc=14.0, seed=22)  # 19 molecules per block; unrelaxed lattice start
+    wl.dt = 0.5
+    return wl
+
+
 def stock():
     return snapshot(W.stockmayer_fluid(N=500, seed=4), "stockmayer_N500")
 
@@ -49,8 +55,8 @@ def ionic():
     return snapshot(W.ionic_solution(seed=3), "ionic_N1040")
 
 
-CASES = [water1000, water_ragged, stock, lj32, ionic]
-IDS = ["water1000", "water1003", "stockmayer", "lj", "ionic_ewald"]
+CASES = [water1000, water_ragged, water_large, stock, lj32, ionic]
+IDS = ["water1000", "water1003", "water2744", "stockmayer", "lj", "ionic_ewald"]
 
 
 def rms_rel(a, b):
