@@ -285,6 +285,16 @@ static_assert(PairWarp<1, 1u, 0u, 0u, ELEC_NONE, false>::TILE == tile_code(0, fa
                   PairWarp<3, 1u, 7u, 0u, ELEC_EWALD, true>::TILE == tile_code(0, false),
               "kKindTile matches the kinds' kernels");
 
+// A batch launches one kernel per group: the systems of one model kind and one
+// size class (up to BIG_N molecules, or more).  A kind's block shape and
+// shared memory follow its largest system; the class split keeps a few large
+// systems from setting them for all the small ones.  Which group runs a system
+// never changes its results (they depend on the system alone).
+constexpr int BIG_N = 2048;
+constexpr int G_COUNT = 2 * K_COUNT;
+inline int kind_of_group(int g) { return g >> 1; }
+inline int group_of(int kind, int N) { return 2 * kind + (N > BIG_N ? 1 : 0); }
+
 int kind_of(ms2_system s) {
     const SysParams &P = s->hp;
     if (P.ns == 1 && s->ljm == 1u && s->qm == 0 && s->dm == 0 && P.elec == ELEC_NONE && !P.multi) return K_LJ1;
@@ -368,21 +378,21 @@ struct ms2_batch_s {
     std::vector<ms2_system> sys;
     cudaStream_t stream = nullptr;
     DevAlloc al;
-    std::vector<int> order[K_COUNT];       // member systems of each kind, in creation order
-    std::vector<BatchEntry> htab[K_COUNT];
-    BatchEntry *dtab[K_COUNT] = {nullptr};
-    int2 *ddrift[K_COUNT] = {nullptr}, *dunit[K_COUNT] = {nullptr};
-    int n_drift[K_COUNT] = {0}, n_unit[K_COUNT] = {0};
-    int4 *dseg[K_COUNT] = {nullptr};
-    int *dsegoff[K_COUNT] = {nullptr};
-    int Np[K_COUNT] = {0}, rdf_cells[K_COUNT] = {0};
+    std::vector<int> order[G_COUNT];       // member systems of each group, in creation order
+    std::vector<BatchEntry> htab[G_COUNT];
+    BatchEntry *dtab[G_COUNT] = {nullptr};
+    int2 *ddrift[G_COUNT] = {nullptr}, *dunit[G_COUNT] = {nullptr};
+    int n_drift[G_COUNT] = {0}, n_unit[G_COUNT] = {0};
+    int4 *dseg[G_COUNT] = {nullptr};
+    int *dsegoff[G_COUNT] = {nullptr};
+    int Np[G_COUNT] = {0}, rdf_cells[G_COUNT] = {0};
     // Ewald kinds: reciprocal-space task tables
-    int2 *dew_sk[K_COUNT] = {nullptr}, *dew_sum[K_COUNT] = {nullptr}, *dew_force[K_COUNT] = {nullptr};
-    int n_ew_sk[K_COUNT] = {0}, n_ew_sum[K_COUNT] = {0}, n_ew_force[K_COUNT] = {0};
-    int threads[K_COUNT] = {0}, grid[K_COUNT] = {0};
-    size_t smem[K_COUNT] = {0};
-    unsigned *dbar = nullptr;  // [K_COUNT][2]: barrier counter, timeout flag
-    int *dnflag[K_COUNT] = {nullptr};  // candidate-list rebuild flags, one per system of the kind
+    int2 *dew_sk[G_COUNT] = {nullptr}, *dew_sum[G_COUNT] = {nullptr}, *dew_force[G_COUNT] = {nullptr};
+    int n_ew_sk[G_COUNT] = {0}, n_ew_sum[G_COUNT] = {0}, n_ew_force[G_COUNT] = {0};
+    int threads[G_COUNT] = {0}, grid[G_COUNT] = {0};
+    size_t smem[G_COUNT] = {0};
+    unsigned *dbar = nullptr;  // [G_COUNT][2]: barrier counter, timeout flag
+    int *dnflag[G_COUNT] = {nullptr};  // candidate-list rebuild flags, one per system of the kind
     int chunk = 100;
     bool tune_shapes = true;  // false: cached shape or the default, no trial launches
 };
@@ -391,7 +401,7 @@ struct ms2_batch_s {
 static ms2_status set_shape(ms2_batch b, int k, int threads);
 
 static ms2_status batch_launch(ms2_batch b, int nsteps, bool trial = false) {
-    for (int k = 0; k < K_COUNT; ++k) {
+    for (int k = 0; k < G_COUNT; ++k) {
         if (b->order[k].empty()) continue;
         std::vector<BatchEntry> &t = b->htab[k];
         int cells = b->rdf_cells[k];
@@ -440,7 +450,7 @@ static ms2_status batch_launch(ms2_batch b, int nsteps, bool trial = false) {
         A.n_sum = b->n_ew_sum[k];
         A.n_force = b->n_ew_force[k];
         void *args[] = {(void *)&A};
-        MS2_CUDA_OK(cudaLaunchCooperativeKernel((const void *)kernel_of(k, b->threads[k]), b->grid[k], b->threads[k], args, b->smem[k],
+        MS2_CUDA_OK(cudaLaunchCooperativeKernel((const void *)kernel_of(kind_of_group(k), b->threads[k]), b->grid[k], b->threads[k], args, b->smem[k],
                                                 b->stream));
         ms2_count_launches(1);
     }
@@ -456,10 +466,11 @@ static ms2_status batch_launch(ms2_batch b, int nsteps, bool trial = false) {
 // block shape of kind k and the pair segments of each block: the kind's items
 // (molecules, system by system) cut into grid ranges of equal estimated cost
 static ms2_status set_shape(ms2_batch b, int k, int threads) {
-    const BatchFn fn = kernel_of(k, threads);
-    if (!fn) return ms2_fail(MS2_EINVAL, "batch kind %s has no %d-thread shape", kKindName[k], threads);
+    const int kind = kind_of_group(k);
+    const BatchFn fn = kernel_of(kind, threads);
+    if (!fn) return ms2_fail(MS2_EINVAL, "batch kind %s has no %d-thread shape", kKindName[kind], threads);
     b->threads[k] = threads;
-    b->smem[k] = batch_smem(k, b->Np[k], threads, b->rdf_cells[k]);
+    b->smem[k] = batch_smem(kind, b->Np[k], threads, b->rdf_cells[k]);
     for (int idx : b->order[k]) b->smem[k] = std::max(b->smem[k], ewald_smem(b->sys[idx], threads));
     MS2_CUDA_OK(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)std::max<size_t>(b->smem[k], 48 * 1024)));
@@ -470,7 +481,7 @@ static ms2_status set_shape(ms2_batch b, int k, int threads) {
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (per_sm < 1 || !coop)
         return ms2_fail(MS2_EINVAL, "batch kind %s: %d threads with %zu B of shared memory do not fit one SM",
-                        kKindName[k], threads, b->smem[k]);
+                        kKindName[kind], threads, b->smem[k]);
     const int G = per_sm * sms;
     b->grid[k] = G;
     double total = 0;
@@ -561,9 +572,9 @@ static ms2_status snapshot_state(ms2_batch b, std::vector<void *> &buf, bool sav
 static ms2_status tune(ms2_batch b) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     std::map<std::string, int> cache = load_tune();
-    std::string key[K_COUNT];
+    std::string key[G_COUNT];
     bool need = false;
-    for (int k = 0; k < K_COUNT; ++k) {
+    for (int k = 0; k < G_COUNT; ++k) {
         if (b->order[k].empty()) continue;
         std::vector<int> ns;
         for (int idx : b->order[k]) ns.push_back(b->sys[idx]->N);
@@ -573,7 +584,7 @@ static ms2_status tune(ms2_batch b) {
         int cnt = 1;
         while (cnt < (int)ns.size()) cnt <<= 1;
         std::ostringstream os;
-        os << "v3/" << kKindName[k] << "/N" << bucket << "/S" << cnt;
+        os << "v4/" << kKindName[kind_of_group(k)] << "/C" << (k & 1) << "/N" << bucket << "/S" << cnt;
         key[k] = os.str();
         auto it = cache.find(key[k]);
         if (it != cache.end() && set_shape(b, k, it->second) == MS2_OK) continue;
@@ -586,15 +597,15 @@ static ms2_status tune(ms2_batch b) {
     cudaEvent_t e0, e1;
     MS2_CUDA_OK(cudaEventCreate(&e0));
     MS2_CUDA_OK(cudaEventCreate(&e1));
-    for (int k = 0; k < K_COUNT; ++k) {
+    for (int k = 0; k < G_COUNT; ++k) {
         if (b->order[k].empty() || cache.count(key[k])) continue;
         float best = 1e30f;
         int best_t = MS_THREADS;
         for (int t : {256, MS_THREADS, 2 * MS_THREADS}) {
-            if (!kernel_of(k, t) || set_shape(b, k, t) != MS2_OK) continue;
-            // only kind k runs in a trial
-            std::vector<int> keep[K_COUNT];
-            for (int j = 0; j < K_COUNT; ++j)
+            if (!kernel_of(kind_of_group(k), t) || set_shape(b, k, t) != MS2_OK) continue;
+            // only group k runs in a trial
+            std::vector<int> keep[G_COUNT];
+            for (int j = 0; j < G_COUNT; ++j)
                 if (j != k) std::swap(keep[j], b->order[j]);
             // an untimed launch first (module loading, cold caches), then the state back
             st = batch_launch(b, 1, true);
@@ -604,7 +615,7 @@ static ms2_status tune(ms2_batch b) {
                 st = batch_launch(b, 1, true);
                 MS2_CUDA_OK(cudaEventRecord(e1, b->stream));
             }
-            for (int j = 0; j < K_COUNT; ++j)
+            for (int j = 0; j < G_COUNT; ++j)
                 if (j != k) std::swap(keep[j], b->order[j]);
             if (st != MS2_OK) return st;
             MS2_CUDA_OK(cudaEventSynchronize(e1));
@@ -687,7 +698,7 @@ ms2_status ms2_batch_create_opt(const ms2_system *systems, int n, ms2_batch *out
             return ms2_fail(MS2_EINVAL, "system %d: %d molecules do not fit one block's shared memory", k, s->N);
         }
         b->sys.push_back(s);
-        b->order[kind].push_back(k);
+        b->order[group_of(kind, s->N)].push_back(k);
     }
     ms2_status st = MS2_OK;
     auto fail = [&](ms2_status s2) { ms2_batch_destroy(b); return s2; };
@@ -695,8 +706,8 @@ ms2_status ms2_batch_create_opt(const ms2_system *systems, int n, ms2_batch *out
         cudaError_t e0 = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
         if (e0 != cudaSuccess) return fail(ms2_fail_cuda(e0, "batch stream", __FILE__, __LINE__));
     }
-    cudaError_t ce = b->al.alloc((void **)&b->dbar, sizeof(unsigned) * 2 * K_COUNT);
-    for (int k = 0; k < K_COUNT && ce == cudaSuccess; ++k) {
+    cudaError_t ce = b->al.alloc((void **)&b->dbar, sizeof(unsigned) * 2 * G_COUNT);
+    for (int k = 0; k < G_COUNT && ce == cudaSuccess; ++k) {
         if (b->order[k].empty()) continue;
         std::vector<int2> drift, unit, ew_sk, ew_sum, ew_force;
         ce = b->al.alloc((void **)&b->dnflag[k], sizeof(int) * b->order[k].size());
@@ -785,7 +796,7 @@ ms2_status ms2_batch_create_opt(const ms2_system *systems, int n, ms2_batch *out
         b->n_ew_force[k] = (int)ew_force.size();
     }
     if (ce != cudaSuccess) return fail(ms2_fail_cuda(ce, "batch set-up", __FILE__, __LINE__));
-    for (int k = 0; k < K_COUNT; ++k)
+    for (int k = 0; k < G_COUNT; ++k)
         if (!b->order[k].empty() && set_shape(b, k, MS_THREADS) != MS2_OK && (st = set_shape(b, k, 256)) != MS2_OK)
             return fail(st);
     // the systems' own queued work comes first
