@@ -51,6 +51,7 @@ const char *kKindName[K_COUNT] = {"lj1", "water3_rf", "stockmayer3_rf", "generic
 
 constexpr int MS_THREADS = 512;   // largest block shape (the autotuner may take 256)
 constexpr int UNIT = 8;           // molecules per reduction unit (one quad pass of a warp)
+constexpr int VB_PER_BLOCK = 4;   // pair-phase pieces per block of the grid (drawn dynamically)
 constexpr int RDF_SMEM_MAX = 4096;  // histogram cells staged in shared memory
 // candidate-list skin, in units of the cut-off (measured on the bench mix, which
 // starts from lattices: 0.1 -> 2.74, 0.15 -> 2.55, 0.22 -> 2.42, 0.3 -> 2.32,
@@ -86,12 +87,14 @@ struct MsArgs {
     const int2 *drift;     // drift groups (entry, first molecule), 8 molecules each
     int n_drift;
     const int4 *seg;       // pair segments (entry, first molecule, end, 0) ...
-    const int *seg_off;    // ... of block b: seg[seg_off[b] .. seg_off[b + 1])
+    const int *seg_off;    // ... of virtual block v: seg[seg_off[v] .. seg_off[v + 1])
+    int n_vb;              // virtual blocks (pieces of equal estimated cost, in system order)
     const int2 *unit;      // reduction units (entry, unit)
     int n_unit;
     int Np;                // stride of the staged tile (largest N of the kind, multiple of 4)
     int nsteps;
     unsigned *bar, *err;   // barrier counter (zero at entry) and sticky timeout flag
+    unsigned *work;        // pair-phase work counter (zero at entry): n_vb + grid draws a step
     // Ewald kinds: reciprocal-space tasks (entry, task): structure-factor tasks,
     // sum tasks, force tasks (one k chunk of a system, all its site groups)
     const int2 *ew_sk, *ew_sum, *ew_force;
@@ -113,7 +116,8 @@ __global__ void __launch_bounds__(BT, 1) k_mstep(MsArgs A) {
     const Smem sm = carve<NS, Eng::TILE, MULTI>(smem_raw, A.Np, nw);
     unsigned *hist = (unsigned *)(smem_raw + al16(pair_engine::smem_bytes(NS, Eng::TILE, MULTI, A.Np, nw)));
     int *wq = sm.queue + warp * QSTRIDE;
-    unsigned target = 0;
+    unsigned target = 0, work_base = 0;
+    __shared__ int s_vb;
     auto on_timeout = [&]() {
         for (int e = 0; e < A.n_sys; ++e) A.tab[e].S.scal[SC_KERR] = 1.0;
     };
@@ -140,8 +144,18 @@ __global__ void __launch_bounds__(BT, 1) k_mstep(MsArgs A) {
             }
         }
         grid_sync(A.bar, A.err, target, on_timeout);
-        // ---- pair items of this block, system by system (and RDF samples)
-        for (int sg = A.seg_off[blockIdx.x]; sg < A.seg_off[blockIdx.x + 1]; ++sg) {
+        // ---- pair items (and RDF samples): the virtual blocks, drawn one at a
+        // time from the work counter, so that a block that finishes early takes
+        // the next piece; every block stops at its first draw past the end, so a
+        // step takes exactly n_vb + grid draws.  Which block runs an item does
+        // not change its result.
+        for (;;) {
+            if (threadIdx.x == 0) s_vb = (int)(atomicAdd(A.work, 1u) - work_base);
+            __syncthreads();
+            const int vb = s_vb;
+            __syncthreads();  // read by all before thread 0 draws again
+            if (vb >= A.n_vb) break;
+        for (int sg = A.seg_off[vb]; sg < A.seg_off[vb + 1]; ++sg) {
             const int4 g = A.seg[sg];
             const BatchEntry &en = A.tab[g.x];
             const SysParams *P = en.P;
@@ -193,6 +207,8 @@ __global__ void __launch_bounds__(BT, 1) k_mstep(MsArgs A) {
                     if (hist[c]) atomicAdd(&S.rdf[c], (unsigned long long)hist[c]);
             }
         }
+        }
+        work_base += (unsigned)(A.n_vb + gridDim.x);
         grid_sync(A.bar, A.err, target, on_timeout);
         // ---- Ewald reciprocal space of every system of the kind: the tasks of
         // the single-system path (structure factor, sums, forces), each a function
@@ -391,7 +407,8 @@ struct ms2_batch_s {
     int n_ew_sk[G_COUNT] = {0}, n_ew_sum[G_COUNT] = {0}, n_ew_force[G_COUNT] = {0};
     int threads[G_COUNT] = {0}, grid[G_COUNT] = {0};
     size_t smem[G_COUNT] = {0};
-    unsigned *dbar = nullptr;  // [G_COUNT][2]: barrier counter, timeout flag
+    unsigned *dbar = nullptr;  // [G_COUNT][3]: barrier counter, timeout flag, pair-phase work counter
+    int nvb[G_COUNT] = {0};    // virtual blocks of each group's pair phase
     int *dnflag[G_COUNT] = {nullptr};  // candidate-list rebuild flags, one per system of the kind
     int chunk = 100;
     bool tune_shapes = true;  // false: cached shape or the default, no trial launches
@@ -427,7 +444,7 @@ static ms2_status batch_launch(ms2_batch b, int nsteps, bool trial = false) {
         }
         MS2_CUDA_OK(cudaMemcpyAsync(b->dtab[k], t.data(), sizeof(BatchEntry) * t.size(), cudaMemcpyHostToDevice,
                                     b->stream));
-        MS2_CUDA_OK(cudaMemsetAsync(b->dbar + 2 * k, 0, 2 * sizeof(unsigned), b->stream));
+        MS2_CUDA_OK(cudaMemsetAsync(b->dbar + 3 * k, 0, 3 * sizeof(unsigned), b->stream));
         // the lists are rebuilt at the start of every launch (the states may have been set or stepped since)
         MS2_CUDA_OK(cudaMemsetAsync(b->dnflag[k], 1, sizeof(int) * t.size(), b->stream));
         MsArgs A;
@@ -437,12 +454,14 @@ static ms2_status batch_launch(ms2_batch b, int nsteps, bool trial = false) {
         A.n_drift = b->n_drift[k];
         A.seg = b->dseg[k];
         A.seg_off = b->dsegoff[k];
+        A.n_vb = b->nvb[k];
         A.unit = b->dunit[k];
         A.n_unit = b->n_unit[k];
         A.Np = b->Np[k];
         A.nsteps = nsteps;
-        A.bar = b->dbar + 2 * k;
-        A.err = b->dbar + 2 * k + 1;
+        A.bar = b->dbar + 3 * k;
+        A.err = b->dbar + 3 * k + 1;
+        A.work = b->dbar + 3 * k + 2;
         A.ew_sk = b->dew_sk[k];
         A.ew_sum = b->dew_sum[k];
         A.ew_force = b->dew_force[k];
@@ -491,8 +510,12 @@ static ms2_status set_shape(ms2_batch b, int k, int threads) {
         cost.push_back(item_cost(b->sys[idx], b->htab[k][e].lcap > 0));
         total += cost.back() * b->sys[idx]->N;
     }
+    // VB_PER_BLOCK virtual blocks of equal estimated cost per block of the grid,
+    // drawn dynamically by the blocks (the estimate need not be exact)
+    const int GV = VB_PER_BLOCK * G;
+    b->nvb[k] = GV;
     std::vector<int4> seg;
-    std::vector<int> off(G + 1, 0);
+    std::vector<int> off(GV + 1, 0);
     double acc = 0;
     int blk = 0;
     for (size_t e = 0; e < b->order[k].size(); ++e) {
@@ -500,7 +523,7 @@ static ms2_status set_shape(ms2_batch b, int k, int threads) {
         int first = 0;
         for (int i = 0; i < N; ++i) {
             const double mid = acc + (i + 0.5) * cost[e];
-            const int bi = std::min(G - 1, (int)(mid * G / total));
+            const int bi = std::min(GV - 1, (int)(mid * GV / total));
             if (bi != blk) {
                 if (i > first) seg.push_back(make_int4((int)e, first, i, 0));
                 for (int q = blk + 1; q <= bi; ++q) off[q] = (int)seg.size();
@@ -511,11 +534,11 @@ static ms2_status set_shape(ms2_batch b, int k, int threads) {
         if (N > first) seg.push_back(make_int4((int)e, first, N, 0));
         acc += cost[e] * N;
     }
-    for (int q = blk + 1; q <= G; ++q) off[q] = (int)seg.size();
+    for (int q = blk + 1; q <= GV; ++q) off[q] = (int)seg.size();
     MS2_CUDA_OK(b->al.alloc((void **)&b->dseg[k], sizeof(int4) * std::max<size_t>(seg.size(), 1)));
-    MS2_CUDA_OK(b->al.alloc((void **)&b->dsegoff[k], sizeof(int) * (G + 1)));
+    MS2_CUDA_OK(b->al.alloc((void **)&b->dsegoff[k], sizeof(int) * (GV + 1)));
     MS2_CUDA_OK(cudaMemcpyAsync(b->dseg[k], seg.data(), sizeof(int4) * seg.size(), cudaMemcpyHostToDevice, b->stream));
-    MS2_CUDA_OK(cudaMemcpyAsync(b->dsegoff[k], off.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, b->stream));
+    MS2_CUDA_OK(cudaMemcpyAsync(b->dsegoff[k], off.data(), sizeof(int) * (GV + 1), cudaMemcpyHostToDevice, b->stream));
     MS2_CUDA_OK(cudaStreamSynchronize(b->stream));  // the host vectors go out of scope
     return MS2_OK;
 }
@@ -706,7 +729,7 @@ ms2_status ms2_batch_create_opt(const ms2_system *systems, int n, ms2_batch *out
         cudaError_t e0 = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
         if (e0 != cudaSuccess) return fail(ms2_fail_cuda(e0, "batch stream", __FILE__, __LINE__));
     }
-    cudaError_t ce = b->al.alloc((void **)&b->dbar, sizeof(unsigned) * 2 * G_COUNT);
+    cudaError_t ce = b->al.alloc((void **)&b->dbar, sizeof(unsigned) * 3 * G_COUNT);
     for (int k = 0; k < G_COUNT && ce == cudaSuccess; ++k) {
         if (b->order[k].empty()) continue;
         std::vector<int2> drift, unit, ew_sk, ew_sum, ew_force;
