@@ -51,7 +51,7 @@ const char *kKindName[K_COUNT] = {"lj1", "water3_rf", "stockmayer3_rf", "generic
 
 constexpr int MS_THREADS = 512;   // largest block shape (the autotuner may take 256)
 constexpr int UNIT = 8;           // molecules per reduction unit (one quad pass of a warp)
-constexpr int VB_PER_BLOCK = 4;   // pair-phase pieces per block of the grid (drawn dynamically)
+constexpr int VB_PER_BLOCK = 4;   // pair-phase pieces per block of the grid (drawn dynamically), by default
 constexpr int RDF_SMEM_MAX = 4096;  // histogram cells staged in shared memory
 // candidate-list skin, in units of the cut-off (measured on the bench mix, which
 // starts from lattices: 0.1 -> 2.74, 0.15 -> 2.55, 0.22 -> 2.42, 0.3 -> 2.32,
@@ -409,13 +409,14 @@ struct ms2_batch_s {
     size_t smem[G_COUNT] = {0};
     unsigned *dbar = nullptr;  // [G_COUNT][3]: barrier counter, timeout flag, pair-phase work counter
     int nvb[G_COUNT] = {0};    // virtual blocks of each group's pair phase
+    int vbpb[G_COUNT] = {0};   // ... per block of the grid (the tuned piece size)
     int *dnflag[G_COUNT] = {nullptr};  // candidate-list rebuild flags, one per system of the kind
     int chunk = 100;
     bool tune_shapes = true;  // false: cached shape or the default, no trial launches
 };
 
 // trial = autotuner run: no RDF samples, no step counters
-static ms2_status set_shape(ms2_batch b, int k, int threads);
+static ms2_status set_shape(ms2_batch b, int k, int threads, int vb = VB_PER_BLOCK);
 
 static ms2_status batch_launch(ms2_batch b, int nsteps, bool trial = false) {
     for (int k = 0; k < G_COUNT; ++k) {
@@ -438,8 +439,8 @@ static ms2_status batch_launch(ms2_batch b, int nsteps, bool trial = false) {
         if (cells > b->rdf_cells[k]) {  // a larger histogram than the shape reserves
             if (cells > RDF_SMEM_MAX) return ms2_fail(MS2_EINVAL, "RDF histogram too large for a batch");
             b->rdf_cells[k] = cells;
-            ms2_status st = set_shape(b, k, b->threads[k]);
-            if (st != MS2_OK) st = set_shape(b, k, 256);
+            ms2_status st = set_shape(b, k, b->threads[k], b->vbpb[k]);
+            if (st != MS2_OK) st = set_shape(b, k, 256, b->vbpb[k]);
             if (st != MS2_OK) return st;
         }
         MS2_CUDA_OK(cudaMemcpyAsync(b->dtab[k], t.data(), sizeof(BatchEntry) * t.size(), cudaMemcpyHostToDevice,
@@ -484,7 +485,7 @@ static ms2_status batch_launch(ms2_batch b, int nsteps, bool trial = false) {
 
 // block shape of kind k and the pair segments of each block: the kind's items
 // (molecules, system by system) cut into grid ranges of equal estimated cost
-static ms2_status set_shape(ms2_batch b, int k, int threads) {
+static ms2_status set_shape(ms2_batch b, int k, int threads, int vb) {
     const int kind = kind_of_group(k);
     const BatchFn fn = kernel_of(kind, threads);
     if (!fn) return ms2_fail(MS2_EINVAL, "batch kind %s has no %d-thread shape", kKindName[kind], threads);
@@ -510,9 +511,10 @@ static ms2_status set_shape(ms2_batch b, int k, int threads) {
         cost.push_back(item_cost(b->sys[idx], b->htab[k][e].lcap > 0));
         total += cost.back() * b->sys[idx]->N;
     }
-    // VB_PER_BLOCK virtual blocks of equal estimated cost per block of the grid,
-    // drawn dynamically by the blocks (the estimate need not be exact)
-    const int GV = VB_PER_BLOCK * G;
+    // vb virtual blocks of equal estimated cost per block of the grid, drawn
+    // dynamically by the blocks (the estimate need not be exact)
+    const int GV = vb * G;
+    b->vbpb[k] = vb;
     b->nvb[k] = GV;
     std::vector<int4> seg;
     std::vector<int> off(GV + 1, 0);
@@ -588,10 +590,14 @@ static ms2_status snapshot_state(ms2_batch b, std::vector<void *> &buf, bool sav
     return MS2_OK;
 }
 
-// Autotuner: per model kind, the block shape (256 threads, two blocks per SM
-// where they fit, or 512 threads, one block per SM) that runs one step of this
-// batch fastest; results cached on disk by (kind, size bucket, count bucket).
-// The shape changes only the work split, never a system's results.
+// Autotuner: per group (model kind and size class), the decomposition that runs
+// this batch fastest over a list build and two steps on the lists: the block
+// shape (256 threads, two blocks per SM where they fit; 512 threads, one block
+// per SM; 1024 threads with 64 registers where the kind has that kernel) times
+// the size of the pair-phase pieces (1, 4 or 16 pieces per block of the grid:
+// larger pieces stage fewer systems, smaller ones balance better); results
+// cached on disk by (kind, size class, size bucket, count bucket).  The shape
+// changes only the work split, never a system's results.
 static ms2_status tune(ms2_batch b) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     std::map<std::string, int> cache = load_tune();
@@ -607,10 +613,10 @@ static ms2_status tune(ms2_batch b) {
         int cnt = 1;
         while (cnt < (int)ns.size()) cnt <<= 1;
         std::ostringstream os;
-        os << "v4/" << kKindName[kind_of_group(k)] << "/C" << (k & 1) << "/N" << bucket << "/S" << cnt;
+        os << "v5/" << kKindName[kind_of_group(k)] << "/C" << (k & 1) << "/N" << bucket << "/S" << cnt;
         key[k] = os.str();
-        auto it = cache.find(key[k]);
-        if (it != cache.end() && set_shape(b, k, it->second) == MS2_OK) continue;
+        auto it = cache.find(key[k]);  // shape code: threads x 64 + pieces per block
+        if (it != cache.end() && set_shape(b, k, it->second / 64, it->second % 64) == MS2_OK) continue;
         need = true;
     }
     if (!need || !b->tune_shapes) return MS2_OK;  // (untuned kinds keep the default shape)
@@ -623,9 +629,11 @@ static ms2_status tune(ms2_batch b) {
     for (int k = 0; k < G_COUNT; ++k) {
         if (b->order[k].empty() || cache.count(key[k])) continue;
         float best = 1e30f;
-        int best_t = MS_THREADS;
-        for (int t : {256, MS_THREADS, 2 * MS_THREADS}) {
-            if (!kernel_of(kind_of_group(k), t) || set_shape(b, k, t) != MS2_OK) continue;
+        int best_t = MS_THREADS, best_vb = VB_PER_BLOCK;
+        for (int trial = 0; trial < 9; ++trial) {
+            const int t = (trial / 3 == 0) ? 256 : (trial / 3 == 1 ? MS_THREADS : 2 * MS_THREADS);
+            const int vb = trial % 3 == 0 ? 1 : (trial % 3 == 1 ? 4 : 16);
+            if (!kernel_of(kind_of_group(k), t) || set_shape(b, k, t, vb) != MS2_OK) continue;
             // only group k runs in a trial
             std::vector<int> keep[G_COUNT];
             for (int j = 0; j < G_COUNT; ++j)
@@ -633,9 +641,9 @@ static ms2_status tune(ms2_batch b) {
             // an untimed launch first (module loading, cold caches), then the state back
             st = batch_launch(b, 1, true);
             if (st == MS2_OK) st = snapshot_state(b, saved, false);
-            if (st == MS2_OK) {
+            if (st == MS2_OK) {  // a list build and two steps on the lists
                 MS2_CUDA_OK(cudaEventRecord(e0, b->stream));
-                st = batch_launch(b, 1, true);
+                st = batch_launch(b, 3, true);
                 MS2_CUDA_OK(cudaEventRecord(e1, b->stream));
             }
             for (int j = 0; j < G_COUNT; ++j)
@@ -647,14 +655,15 @@ static ms2_status tune(ms2_batch b) {
             if (ms < best) {
                 best = ms;
                 best_t = t;
+                best_vb = vb;
             }
             st = snapshot_state(b, saved, false);
             if (st != MS2_OK) return st;
         }
         MS2_CUDA_OK(cudaStreamSynchronize(b->stream));
-        st = set_shape(b, k, best_t);
+        st = set_shape(b, k, best_t, best_vb);
         if (st != MS2_OK) return st;
-        store_tune(key[k], best_t);
+        store_tune(key[k], best_t * 64 + best_vb);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -745,8 +754,12 @@ ms2_status ms2_batch_create_opt(const ms2_system *systems, int n, ms2_batch *out
             const int N = s->N;
             const double L = s->hp.L, rc = s->rc, skin = kSkin * rc;
             const double frac = std::min(1.0, 4.18879020478639098 * std::pow(rc + skin, 3.0) / (L * L * L));  // 4 pi / 3
-            const int lcap = ((int)std::ceil(1.3 * frac * N + 32.0) + 31) & ~31;
-            if (N <= 65535 && lcap < (3 * N) / 4) {
+            const int lexp = (int)std::ceil(1.3 * frac * N + 32.0);  // the expected list, with a margin
+            // capacity MS2_LIST_CAP x the ideal-gas count (dilute systems condense into
+            // droplets over long runs: a molecule there has 2-3 x the average
+            // neighbours; an owner whose list overflows scans in full)
+            const int lcap = std::min(((N + 31) & ~31), ((int)std::ceil(MS2_LIST_CAP * frac * N + 64.0) + 31) & ~31);
+            if (N <= 65535 && lexp < (3 * N) / 4) {
                 lcaps[e] = lcap;
                 nl_off[e] = nl_bytes;
                 nl_bytes += al16(sizeof(uint16_t) * (size_t)N * lcap) + al16(sizeof(int) * N) + al16(sizeof(uint32_t) * 3 * N);

@@ -93,6 +93,11 @@ struct ms2_system_s {
     size_t mu_bytes() const { return d.mu ? 3 * sizeof(float) * (size_t)ns * N : 0; }
 };
 
+// Candidate lists of the batch kernels: capacity per molecule = MS2_LIST_CAP x
+// the ideal-gas count within r_c + skin, + 64, at most the system (batch.cu; the
+// server's admission estimate uses the same bound)
+constexpr double MS2_LIST_CAP = 2.5;
+
 ms2_status ms2_fail(ms2_status st, const char *fmt, ...);
 ms2_status ms2_fail_cuda(cudaError_t e, const char *what, const char *file, int line);
 void ms2_unit_constants(bool reduced, double *coulomb, double *kconv);

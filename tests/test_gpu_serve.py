@@ -93,7 +93,7 @@ def test_budget_admission_binds_and_rejects_oversized_jobs():
     with pytest.raises(ms2.Ms2Error, match="EBUDGET"):
         small.submit([W.water()], [4000], 298.0, RHO_W, 14.0, ms2.ELEC_RF, 100)
     small.close()
-    # room for two of these jobs at a time (~1.34 MiB each by the admission
+    # room for two of these jobs at a time (~1.30 MiB each by the admission
     # estimate, which counts the batch's candidate lists)
     job = ([W.water()], [216], 298.0, RHO_W, 9.0, ms2.ELEC_RF)
     s = ms2.Server(int(3.0 * (1 << 20)), 64)
