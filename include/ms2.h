@@ -249,8 +249,8 @@ MS2_API ms2_status ms2_reset_averages(ms2_system sys);
  * summation") run over all its systems between grid barriers after the pair
  * phase.  The block shape comes from the autotuner cache.  Where it pays
  * (a list shorter than 3N/4), a system also gets device memory for candidate
- * lists: 2 bytes x N x (2.5 x the molecules within 1.3 r_c + 64, at most N), rebuilt at
- * the start of every chunk of steps and whenever a molecule has moved 0.15 r_c;
+ * lists: 2 bytes x N x (2.5 x the molecules within 1.2 r_c + 64, at most N), rebuilt at
+ * the start of every chunk of steps and whenever a molecule has moved 0.1 r_c;
  * the partners found are those of the full search.  A barrier wait
  * that runs out (2 s) marks every system of the kind so that its next
  * ms2_energy_virial returns MS2_ETIMEOUT.  The systems stay

@@ -53,10 +53,12 @@ constexpr int MS_THREADS = 512;   // largest block shape (the autotuner may take
 constexpr int UNIT = 8;           // molecules per reduction unit (one quad pass of a warp)
 constexpr int VB_PER_BLOCK = 4;   // pair-phase pieces per block of the grid (drawn dynamically), by default
 constexpr int RDF_SMEM_MAX = 4096;  // histogram cells staged in shared memory
-// candidate-list skin, in units of the cut-off (measured on the bench mix, which
-// starts from lattices: 0.1 -> 2.74, 0.15 -> 2.55, 0.22 -> 2.42, 0.3 -> 2.32,
-// 0.4 -> 2.48 ms per step; the small skins rebuild often while the lattices relax)
-constexpr double kSkin = 0.3;
+// candidate-list skin, in units of the cut-off.  Measured on the bench mix over
+// 10^4 steps from lattices (ms per step in the first and last 2000 steps):
+// 0.15 -> 2.45 / 2.67, 0.2 -> 2.45 / 2.63, 0.25 -> 2.50 / 2.73, 0.3 -> 2.52 / 2.76,
+// 0.45 -> 2.65 / 2.87.  Small skins rebuild often while the lattices relax; large
+// ones scan long lists once the dilute systems condense.
+constexpr double kSkin = 0.2;
 
 struct BatchEntry {
     const SysParams *P;
@@ -492,8 +494,7 @@ static ms2_status set_shape(ms2_batch b, int k, int threads, int vb) {
     b->threads[k] = threads;
     b->smem[k] = batch_smem(kind, b->Np[k], threads, b->rdf_cells[k]);
     for (int idx : b->order[k]) b->smem[k] = std::max(b->smem[k], ewald_smem(b->sys[idx], threads));
-    MS2_CUDA_OK(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)std::max<size_t>(b->smem[k], 48 * 1024)));
+    MS2_CUDA_OK(ms2_allow_smem((const void *)fn, b->smem[k]));
     int per_sm = 0, sms = 0, dev = 0, coop = 0;
     MS2_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, b->smem[k]));
     cudaGetDevice(&dev);
@@ -744,8 +745,8 @@ ms2_status ms2_batch_create_opt(const ms2_system *systems, int n, ms2_batch *out
         std::vector<int2> drift, unit, ew_sk, ew_sum, ew_force;
         ce = b->al.alloc((void **)&b->dnflag[k], sizeof(int) * b->order[k].size());
         // candidate lists of the kind's systems in one allocation (a server re-creates
-        // batches as jobs come and go): skin kSkin r_c, capacity 1.3 x the ideal-gas
-        // count within r_c + skin; only where the list is shorter than 3N/4
+        // batches as jobs come and go): skin kSkin r_c; only where the expected list
+        // (1.3 x the ideal-gas count within r_c + skin) is shorter than 3N/4
         std::vector<int> lcaps(b->order[k].size(), 0);
         std::vector<size_t> nl_off(b->order[k].size(), 0);
         size_t nl_bytes = 0;

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -34,6 +35,49 @@ ms2_status ms2_fail_cuda(cudaError_t e, const char *what, const char *file, int 
     cudaGetLastError();
     return ms2_fail(e == cudaErrorMemoryAllocation ? MS2_ENOMEM : MS2_ECUDA, "%s failed: %s (%s:%d)", what,
                     cudaGetErrorString(e), file, line);
+}
+
+// Dynamic shared memory of a kernel: the limit is one setting per kernel and
+// device, shared by every system and batch that launches the kernel, so it only
+// ever rises (a small system created after a large one must not lower the limit
+// the large one launches with).  A fixed table, no host allocation; if it is
+// ever full, the kernel gets the largest amount the device allows.
+namespace {
+struct SmemMark {
+    int dev;
+    const void *fn;
+    size_t bytes;
+};
+constexpr int kSmemMarks = 1024;
+SmemMark g_smem_mark[kSmemMarks];
+int g_smem_marks = 0;
+std::mutex g_smem_mu;
+}  // namespace
+
+cudaError_t ms2_allow_smem(const void *fn, size_t bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const size_t want = std::max<size_t>(bytes, 48 * 1024);
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    SmemMark *m = nullptr;
+    for (int k = 0; k < g_smem_marks && !m; ++k)
+        if (g_smem_mark[k].fn == fn && g_smem_mark[k].dev == dev) m = &g_smem_mark[k];
+    if (m && want <= m->bytes) return cudaSuccess;
+    size_t set = want;
+    if (!m && g_smem_marks == kSmemMarks) {  // untracked from here on: the device maximum
+        int optin = 0;
+        cudaFuncAttributes fa;
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+        if (e != cudaSuccess) return e;
+        set = std::max(want, (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0);
+    }
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)set);
+    if (e != cudaSuccess) return e;
+    if (m) m->bytes = set;
+    else if (g_smem_marks < kSmemMarks) g_smem_mark[g_smem_marks++] = SmemMark{dev, fn, set};
+    return cudaSuccess;
 }
 
 extern "C" const char *ms2_last_error(void) { return g_err.c_str(); }
@@ -466,8 +510,7 @@ static ms2_status size_pair_tiles(ms2_system s) {
     while (bytes(TJ) > cap && TJ > 64) TJ = (TJ + 1) / 2;
     s->TJ = TJ;
     s->pair_smem = bytes(TJ);
-    MS2_CUDA_OK(cudaFuncSetAttribute((const void *)s->pair_fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)std::max<size_t>(s->pair_smem, 48 * 1024)));
+    MS2_CUDA_OK(ms2_allow_smem((const void *)s->pair_fn, s->pair_smem));
     return MS2_OK;
 }
 
@@ -508,7 +551,7 @@ static void setup_fused(ms2_system s, const ms2_options &o) {
     const size_t ews = s->hp.elec == ELEC_EWALD ? ms2_step_ewald_scratch(8, 8, 8, 1, ms2_ewald_sk_sites(s->N * s->ns, sms)) : 0;
     const size_t base = ms2_step_smem_bytes(s->ns, s->tile, s->multi_used, Np, mcap, js, 0, ews);
     int nb = 0;
-    if (base > maxdyn || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxdyn) != cudaSuccess ||
+    if (base > maxdyn || ms2_allow_smem(fn, maxdyn) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ms2_step_threads(), base) != cudaSuccess || nb < 1) {
         cudaGetLastError();
         return;
@@ -867,10 +910,8 @@ static ms2_status setup_ewald(ms2_system s, double alpha, int kx, int ky, int kz
     }
     {
         const size_t sm = ms2_ewald_skp_smem(kx, ky, kz, d.sk_sites), fm = ms2_ewald_force_smem(kx, kz, s->ny_per_chunk);
-        MS2_CUDA_OK(cudaFuncSetAttribute((const void *)k_ewald_skp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)std::max<size_t>(sm, 48 * 1024)));
-        MS2_CUDA_OK(cudaFuncSetAttribute(ms2_ewald_force_kernel(kx, kz), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)std::max<size_t>(fm, 48 * 1024)));
+        MS2_CUDA_OK(ms2_allow_smem((const void *)k_ewald_skp, sm));
+        MS2_CUDA_OK(ms2_allow_smem(ms2_ewald_force_kernel(kx, kz), fm));
     }
     double coulomb, kconv;
     ms2_unit_constants(s->reduced, &coulomb, &kconv);
@@ -1704,8 +1745,7 @@ extern "C" ms2_status ms2_heat_setup(ms2_system s, int every, int n_lags, const 
     for (int m = 0; h && m < s->hp.n_species; ++m)
         if (!std::isfinite(h[m])) return ms2_fail(MS2_EINVAL, "partial molar enthalpy %d is not finite", m);
     MS2_CUDA_OK(cudaStreamSynchronize(s->stream));
-    MS2_CUDA_OK(cudaFuncSetAttribute((const void *)hfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)std::max<size_t>(s->pair_smem, 48 * 1024)));
+    MS2_CUDA_OK(ms2_allow_smem((const void *)hfn, s->pair_smem));
     if (!s->d.hpart) MS2_CUDA_OK(s->al.alloc((void **)&s->d.hpart, sizeof(float) * 3 * (size_t)s->jsplit * s->N));
     if (!s->d.hf || s->d.hf_lags != n_lags) {
         double *g = nullptr;
@@ -1722,7 +1762,7 @@ extern "C" ms2_status ms2_heat_setup(ms2_system s, int every, int n_lags, const 
         void *fn = ms2_pick_step_kernel(s->ns, s->ljm, s->qm, s->dm, s->hp.elec, false, s->hp.massieu != 0, true);
         int nb = 0;
         const size_t base = ms2_step_smem_bytes(s->ns, s->tile, s->multi_used, s->Np, s->mcap, s->jsplit, 0, 0);
-        if (fn && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s->step_smem_max) == cudaSuccess &&
+        if (fn && ms2_allow_smem(fn, s->step_smem_max) == cudaSuccess &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ms2_step_threads(), base) == cudaSuccess && nb >= 1)
             s->step_heat_fn = fn;
         cudaGetLastError();

@@ -141,7 +141,7 @@ ms2_status scratch_base(unsigned char **out, int *sms, const void *fn) {
     bool set = false;
     for (int k = 0; k < d.n_attr; ++k) set = set || d.attr_set[k] == fn;
     if (!set) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        e = ms2_allow_smem(fn, 96 * 1024);
         if (e != cudaSuccess) return ms2_fail_cuda(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
         if (d.n_attr < 16) d.attr_set[d.n_attr++] = fn;
     }

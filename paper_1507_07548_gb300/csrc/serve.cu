@@ -69,10 +69,10 @@ size_t estimate_bytes(const JobSpec &j) {
     const int nsp = ns <= 1 ? 1 : (ns <= 4 ? 4 : 8);  // padded slots (upper bound)
     size_t b = (size_t)N * (23 * 8 + 4 + 12 + 2 * 12 * nsp + 12 + 8 * 12 * 4 + 4 + 8);
     // in a batch: reduction-unit partials and candidate lists (16-bit slots,
-    // MS2_LIST_CAP x the ideal-gas count within 1.3 r_c + 64 per molecule, at most
+    // MS2_LIST_CAP x the ideal-gas count within 1.2 r_c + 64 per molecule, at most
     // the system; an upper bound of the batch's allocation, which takes lists
     // only where they are short)
-    const double V = N / std::max(j.rho, 1e-300), rl = 1.3 * j.cutoff;
+    const double V = N / std::max(j.rho, 1e-300), rl = 1.2 * j.cutoff;
     const double frac = std::min(1.0, 4.18879020478639098 * rl * rl * rl / V);
     const double lcap = std::min(MS2_LIST_CAP * frac * N + 64.0, (double)N + 32.0);
     b += (size_t)N * (8 * 32 + 16) + (size_t)N * 2 * (size_t)lcap;

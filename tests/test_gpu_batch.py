@@ -116,6 +116,28 @@ def test_system_alone_and_in_a_mixed_batch_is_bitwise_identical():
     assert alone.energy_virial() == mix[1].energy_virial()
 
 
+def test_large_system_alone_and_beside_small_ones_is_bitwise_identical():
+    """A system above 2048 molecules runs in its kind's large-size group, with
+    its own block shape: alone, beside small systems of its kind, and stepped in
+    two chunks, its state comes out the same bit for bit."""
+    def big():
+        wl = W.water_box(N=2744, rc=12.0, seed=31)   # unrelaxed lattice start: a short time step
+        wl.dt = 0.5
+        return wl
+    alone = ms2.System.from_workload(big())
+    b1 = ms2.Batch([alone])
+    b1.step(24)
+    ref = alone.get_state()[:4]
+    mix = [ms2.System.from_workload(w) for w in (water(), big(), ljf(), water())]
+    b2 = ms2.Batch(mix)
+    b2.step(10)
+    b2.step(14)
+    got = mix[1].get_state()[:4]
+    for a, c in zip(got, ref):
+        assert np.array_equal(a, c)
+    assert alone.energy_virial() == mix[1].energy_virial()
+
+
 def test_batch_matches_single_system_stepping_closely():
     a = ms2.System.from_workload(water())
     b = ms2.System.from_workload(water())

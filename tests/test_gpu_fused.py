@@ -92,6 +92,23 @@ def test_fused_chunks_equal_per_phase_kernels_bitwise(make):
     assert np.array_equal(a.molecule_energies(), b.molecule_energies())
 
 
+def test_smaller_system_created_later_leaves_the_larger_one_launchable():
+    """A kernel's dynamic shared-memory limit is one setting shared by every
+    system that launches it: a small system of the same model, created after a
+    large one, must not lower the limit the large one's pair tile needs."""
+    big = ms2.System.from_workload(water_large(), fused_step=0)
+    small = ms2.System.from_workload(W.water_box(N=216, rc=9.0, seed=9), fused_step=0)
+    F, tau = big.forces_torques()  # the per-phase pair kernel with the large tile
+    big.step(2)
+    small.step(2)
+    ref = ms2.System.from_workload(water_large(), fused_step=0)
+    Fr, taur = ref.forces_torques()
+    ref.step(2)
+    assert np.array_equal(F, Fr) and np.array_equal(tau, taur)
+    for x, y in zip(big.get_state(), ref.get_state()):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
 def test_fused_step_matches_oracle():
     wl = water1000()
     s = ms2.System.from_workload(wl)
