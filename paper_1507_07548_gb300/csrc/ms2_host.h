@@ -100,6 +100,8 @@ constexpr double MS2_LIST_CAP = 2.5;
 
 ms2_status ms2_fail(ms2_status st, const char *fmt, ...);
 ms2_status ms2_fail_cuda(cudaError_t e, const char *what, const char *file, int line);
+// raises (never lowers) a kernel's dynamic shared-memory limit on the current device
+cudaError_t ms2_allow_smem(const void *fn, size_t bytes);
 void ms2_unit_constants(bool reduced, double *coulomb, double *kconv);
 ms2_status ms2_eval_forces(ms2_system s);
 ms2_status ms2_ensure_forces(ms2_system s);  // evaluates after ms2_set_state, else nothing

@@ -251,8 +251,6 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 // host-side launch accounting (one increment per kernel launch or graph node replay)
 void ms2_count_launches(long long n);
-// raises (never lowers) a kernel's dynamic shared-memory limit on the current device
-cudaError_t ms2_allow_smem(const void *fn, size_t bytes);
 
 #define MS2_CUDA_OK(call)                                                                     \
     do {                                                                                      \

@@ -138,6 +138,55 @@ def test_large_system_alone_and_beside_small_ones_is_bitwise_identical():
     assert alone.energy_virial() == mix[1].energy_virial()
 
 
+def test_full_size_mix_sampled_systems_match_oracle():
+    """The batch benchmark's workload at full size, launched as the benchmark
+    launches it: the 512-system mix (point LJ, Stockmayer, water; N ~ U[256,
+    2048], seeded lattice starts) in one batch, one step.  Sampled systems -- the
+    smallest and the largest of each kind -- against the oracle's step from the
+    same state, at the single-system tolerances, and their partner counts
+    bit-exact against a full evaluation of the stepped state."""
+    specs = W.system_mix(512, seed=4)
+    systems = [ms2.System(sp["models"], sp["counts"], sp["T"], sp["cutoff"], sp["elec"], rho=sp["rho"],
+                          seed=sp["seed"], dt=2.0) for sp in specs]
+    pick = []
+    for kind in W.MIX_STATES:
+        idx = sorted((k for k, sp in enumerate(specs) if sp["name"] == kind), key=lambda k: specs[k]["counts"][0])
+        pick += [idx[0], idx[-1]]
+    start = {k: systems[k].get_state() for k in pick}
+    b = ms2.Batch(systems)
+    b.step(1)
+    for k in pick:
+        sp, s = specs[k], systems[k]
+        R0, q0, v0, L0, _ = start[k]
+        R, q, v, L, st = s.get_state()
+        assert st == 1
+        o = Oracle(sp["models"], np.zeros(s.N, np.int32), s.L, s.rc, elec=sp["elec"])
+        Ro, qo, vo, Lo, th, _ = o.run_leapfrog(R0, q0, v0, L0, 2.0, 1, T0=sp["T"])
+        dR = Ro - R0
+        assert np.abs((R - R0) - dR).max() <= 1e-6 * np.abs(dR).max(), sp["name"]
+        assert rms_rel(v, vo) <= 1e-6, sp["name"]
+        if np.linalg.norm(Lo) > 0:
+            sgn = np.sign((q * qo).sum(1))[:, None]
+            assert np.abs(q * sgn - qo).max() <= 1e-7, sp["name"]
+            assert rms_rel(L, Lo) <= 1e-5, sp["name"]
+        U, Wv, T, P = s.energy_virial()
+        assert abs(U - th[0, 0]) <= 1e-6 * abs(th[0, 0]), sp["name"]
+        F, tau = s.forces_torques()
+        Fo, To, to = o.forces(R, q)  # the identical (stepped) configuration
+        assert abs(Wv - to["W_total"]) <= 1e-6 * abs(to["W_total"]), sp["name"]
+        assert rms_rel(F, Fo) <= 1e-5, sp["name"]
+        if np.linalg.norm(To) > 0:
+            assert rms_rel(tau, To) <= 1e-5, sp["name"]
+        c = ms2.System(sp["models"], sp["counts"], sp["T"], sp["cutoff"], sp["elec"], rho=sp["rho"],
+                       seed=sp["seed"], dt=2.0)
+        c.set_state(R, q, v, L)
+        assert np.array_equal(np.asarray(s.partner_counts()), np.asarray(c.partner_counts())), sp["name"]
+        c.close()
+    b.close()
+    for s in systems:
+        s.close()
+
+
 def test_batch_matches_single_system_stepping_closely():
     a = ms2.System.from_workload(water())
     b = ms2.System.from_workload(water())

@@ -120,3 +120,38 @@ def test_noalloc_rejects_sizes_beyond_its_maximum():
     wl = W.water_box(N=4913, rc=14.0, seed=3)
     with pytest.raises(ms2.Ms2Error, match="EINVAL"):
         noalloc(wl)
+
+
+def test_noalloc_call_captured_in_a_cuda_graph():
+    """After a first call on the device (its set-up), a call queues only kernels
+    and a device-to-device copy: it can be captured in a CUDA graph under the
+    global capture mode, where allocations and pageable copies are refused, and
+    every replay gives the system's forces, energy and virial."""
+    wl = snapshot(W.water_box(N=216, rc=9.0, seed=9), "water_N216")
+    ref = reference(wl)
+    noalloc(wl)  # set-up call (scratch address, kernel attributes)
+    models, keep = ms2.make_models(wl.models)
+    cnt = (C.c_int * 1)(wl.N)
+    opts = ms2.default_options(reduced=int(wl.reduced), lrc=wl.lrc, eps_rf=wl.eps_rf)
+    dev = torch.device("cuda")
+    R = torch.tensor(wl.R, dtype=torch.float64, device=dev)
+    q = torch.tensor(wl.q, dtype=torch.float64, device=dev)
+    F = torch.empty((wl.N, 3), dtype=torch.float64, device=dev)
+    tau = torch.empty((wl.N, 3), dtype=torch.float64, device=dev)
+    UW = torch.empty((2,), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=side, capture_error_mode="global"):
+        st = ms2.lib().ms2_forces_noalloc(models, cnt, 1, wl.L, wl.rc, wl.elec, C.byref(opts), R.data_ptr(),
+                                          q.data_ptr(), F.data_ptr(), tau.data_ptr(), UW.data_ptr(),
+                                          torch.cuda.current_stream().cuda_stream)
+    ms2.check(st)
+    for _ in range(2):
+        F.fill_(float("nan"))
+        tau.fill_(float("nan"))
+        UW.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        uw = UW.cpu().numpy()
+        check_same((F.cpu().numpy(), tau.cpu().numpy(), uw[0], uw[1]), ref)
