@@ -418,9 +418,12 @@ MS2_API ms2_status ms2_enable_timing(ms2_system sys, int on);
  * shared memory sends the chunk to the per-phase kernels), else 0. */
 MS2_API ms2_status ms2_step_kernel(ms2_system sys, int *fused);
 /* Diagnostic of the fused step with timing on: device-timer durations (ms) of
- * the last step of the last chunk: [0] drift and site build, [2] staging, pair
- * and RDF, [3] unit reduction (each until the slowest block is done), [1] and
- * [4] the grid barriers after [0] and [3], [5] totals and thermostat factor,
+ * the last step of the last chunk: [0] drift and site build, with the thermostat
+ * factor the drifting warps form first from the previous step's totals, [2]
+ * staging, pair and RDF, [3] unit reduction (each until the slowest block is
+ * done), [1] and [4] the grid barriers after [0] and [3], [5] the rest of the
+ * step on block 0's first warp (the totals of its record run on other warps,
+ * beside the next drift),
  * [6] kernel entry to that last step, [7] the whole last step, [8] its end to
  * the kernel's exit (write-back of the block-held state); Ewald systems (whose
  * reciprocal-space tasks run between [2] and the reduction, inside [3]):

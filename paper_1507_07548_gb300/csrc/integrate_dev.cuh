@@ -568,8 +568,19 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
 // total of per-unit scalar k over units [0, nvb) by one warp, in reduce_totals'
 // order (lane l sums units l, l + 32, ... in order, then the fixed tree); every lane
 __device__ __forceinline__ double unit_total(const DevSys &S, int nvb, int k, int lane) {
+    // the lane's first 8 values are all loaded before the first add (one L2
+    // round trip, not one per value), then added in unit order as the loop below
+    double v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int b = lane + 32 * t;
+        v[t] = b < nvb ? __ldcg(S.blk + (size_t)b * MS2_NRED + k) : 0.0;
+    }
     double x = 0;
-    for (int b = lane; b < nvb; b += 32) x += __ldcg(S.blk + (size_t)b * MS2_NRED + k);
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+        if (lane + 32 * t < nvb) x += v[t];
+    for (int b = lane + 256; b < nvb; b += 32) x += __ldcg(S.blk + (size_t)b * MS2_NRED + k);
     return warp_sum(x);
 }
 
@@ -706,9 +717,13 @@ __device__ __forceinline__ void heat_record(const DevSys &S, int nvb, int lane) 
 }
 
 // isokinetic factor sqrt(T0 / T') from the kicked kinetic energy (as finish_step_warp)
-__device__ __forceinline__ double lambda_of(const SysParams *__restrict__ P, const double *tot) {
-    const double x = P->lam_c * tot[Q_K1];  // T' / T0
+__device__ __forceinline__ double lambda_k1(const SysParams *__restrict__ P, double k1) {
+    const double x = P->lam_c * k1;  // T' / T0
     return (P->thermostat && x > 0) ? rsqrt_fp64(x) : 1.0;
+}
+
+__device__ __forceinline__ double lambda_of(const SysParams *__restrict__ P, const double *tot) {
+    return lambda_k1(P, tot[Q_K1]);
 }
 
 }  // namespace integ

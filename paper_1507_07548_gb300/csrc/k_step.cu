@@ -186,6 +186,9 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     };
     if (threadIdx.x == 0) lam_s = lam0;
     __syncthreads();
+    // the thermostat factor of the next drift, per thread: the drift warps form
+    // it themselves after each step's reduction (no block barrier on it)
+    double lam_r = lam_s;
     // k = -1 (after ms2_set_state): the state as set is evaluated first -- site
     // build instead of the drift, then partner search, forces, unit reduction,
     // totals and the configuration's scalars (ms2_eval_forces' k_build, k_pair
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
             for (int m0 = 8 * (warp - 1); m0 < nm; m0 += 8 * (STEP_WARPS - 1)) {
                 const int m = m0 + (lane >> 2), c = lane & 3;
                 if (!ev) {
-                    drift_quad<true>(Ps, S, view(), m, lo + m, m < nm, c, false, lam_s);
+                    drift_quad<true>(Ps, S, view(), m, lo + m, m < nm, c, false, lam_r);
                 } else if (m < nm && c < 3) {
                     const StateView sv = view();
                     const double q[4] = {sv.q[m], sv.q[MC + m], sv.q[2 * MC + m], sv.q[3 * MC + m]};
@@ -283,14 +286,25 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         mark(k, 2);
         grid_sync(A.bar, A.err, target, on_timeout, A.wait_ns);
         if (tm) tph[3] = global_ns();
-        // ---- totals in every block; thermostat factor for the next drift
-        reduce_totals(S, G, tot, !ev && gk_step(A, k) ? Q_N + 3 : Q_N);
-        __syncthreads();
-        if (warp == 0) {
-            if (lane == 0) lam_s = lambda_of(Ps, tot);
-            if (ev && b == 0) finish_step_warp(Ps, S, RED_SUM | RED_LAMBDA | EWM, tot, lane, acc_s, kc_s);  // the scalars of the state as set
+        // ---- totals.  The warps that drift the block's molecules form the
+        // kinetic energy after the kick and from it the thermostat factor of
+        // their next drift (the same fixed-order sum in each); block 0 forms
+        // every step scalar for its record on the last warps, which the drift
+        // leaves idle (its molecules take warps 1-4 at most), beside the next
+        // drift.  The next grid barrier orders them before the record reads them.
+        {
+            const int nq = !ev && gk_step(A, k) ? Q_N + 3 : Q_N;
+            if (warp >= 1 && 8 * (warp - 1) < nm) lam_r = lambda_k1(Ps, unit_total(S, G, Q_K1, lane));
+            if (b == 0 && warp >= STEP_WARPS - nq) {
+                const int q = warp - (STEP_WARPS - nq);
+                const double x = unit_total(S, G, q, lane);
+                if (lane == 0) tot[q] = x;
+            }
+            if (ev && b == 0) {  // the scalars of the state as set, at once
+                __syncthreads();
+                if (warp == 0) finish_step_warp(Ps, S, RED_SUM | RED_LAMBDA | EWM, tot, lane, acc_s, kc_s);
+            }
         }
-        __syncthreads();
         // ---- heat flux of this configuration (sampled steps): power pass over
         // the staged system, then heat unit b
         if constexpr (HEAT) {
@@ -335,7 +349,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         }
     }
     // ---- the last step's record; own state, forces and per-molecule results
-    // back to global memory
+    // back to global memory (after block 0's last totals are written)
+    __syncthreads();
     if (A.nsteps > 0 && b == 0 && warp == 0) {
         const int gk = gk_step(A, A.nsteps - 1) ? RED_GK : 0;
         finish_step_warp(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA | EWM | gk, tot, lane, acc_s, kc_s);
