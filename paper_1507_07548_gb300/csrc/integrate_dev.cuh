@@ -411,6 +411,32 @@ __device__ __forceinline__ RedIO global_io(const DevSys &S) {
     return RedIO{S.part, S.part64, S.N, global_view(S), S.Ui, S.npart, S.N, 0};
 }
 
+// The kinetic terms of the stored state of the molecule in slot m, for lane c of
+// its quad (they need no forces): column cc of A(q), the body component lb of L,
+// and the translational and rotational kinetic energies of component c (0 in
+// lane 3).  reduce_unit forms them inline, or takes what kin_pre formed earlier
+// with the same arithmetic.
+template <bool SH>
+__device__ __forceinline__ void kin_terms(const SysParams *__restrict__ P, const StateView &sv, int m, int sp, int c,
+                                          int cc, bool anyrot, double col[3], double &lb, double &ktr, double &krot) {
+    const int ld = sv.ld;
+    const double hM = P->half_mass[sp], hI = P->half_Iinv[sp][cc];
+    col[0] = col[1] = col[2] = 0.0;
+    lb = 0.0;
+    if (anyrot) {
+        const double q[4] = {ldv<SH>(sv.q + m), ldv<SH>(sv.q + ld + m), ldv<SH>(sv.q + 2 * ld + m),
+                             ldv<SH>(sv.q + 3 * ld + m)};
+        double L[3];
+        rot_column(q, cc, col);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) L[k] = ldv<SH>(sv.L + k * ld + m);
+        lb = col[0] * L[0] + col[1] * L[1] + col[2] * L[2];
+    }
+    const double v = ldv<SH>(sv.v + cc * ld + m);
+    ktr = c < 3 ? hM * v * v : 0.0;
+    krot = (c < 3 && anyrot) ? hI * lb * lb : 0.0;
+}
+
 // Reduction unit u of U: molecules [N u / U, N (u+1) / U), one warp, a quad per
 // molecule, passes of 8 molecules.  With RED_SUM the quad sums the pair partials
 // over the j-ranges (lane c takes the partial values c, c+4, c+8 in j-range
@@ -421,7 +447,7 @@ __device__ __forceinline__ RedIO global_io(const DevSys &S) {
 // in order; the warp's totals of the Q_N step scalars go to blk[u][*].
 template <bool SH>
 __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, const DevSys &S, const RedIO &io, int mode,
-                                            int u, int U, int lane) {
+                                            int u, int U, int lane, const double *pre = nullptr) {
     const unsigned F = 0xffffffffu, qb = lane & 28;
     const int N = S.N, c = lane & 3, cc = c < 3 ? c : 2;
     const int i_lo = (int)((long long)N * u / U), i_hi = (int)((long long)N * (u + 1) / U);
@@ -510,23 +536,22 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
         {
             const double hM = P->half_mass[sp], hI = P->half_Iinv[sp][cc];
             const bool anyrot = __any_sync(F, P->rot[sp] != 0);
-            double col[3] = {0, 0, 0}, tq[3];
-            double lb = 0.0;
+            double col[3], tq[3], lb, ktr, krot;
 #pragma unroll
             for (int k = 0; k < 3; ++k) tq[k] = __shfl_sync(F, Tc, qb | k);
-            if (anyrot) {
-                const double q[4] = {ldv<SH>(sv.q + m), ldv<SH>(sv.q + ld + m), ldv<SH>(sv.q + 2 * ld + m),
-                                     ldv<SH>(sv.q + 3 * ld + m)};
-                double L[3];
-                rot_column(q, cc, col);
+            if (pre) {  // formed earlier by kin_pre (one pass)
 #pragma unroll
-                for (int k = 0; k < 3; ++k) L[k] = ldv<SH>(sv.L + k * ld + m);
-                lb = col[0] * L[0] + col[1] * L[1] + col[2] * L[2];
+                for (int k = 0; k < 3; ++k) col[k] = pre[k * 32 + lane];
+                lb = pre[3 * 32 + lane];
+                ktr = pre[4 * 32 + lane];
+                krot = pre[5 * 32 + lane];
+            } else {
+                kin_terms<SH>(P, sv, m, sp, c, cc, anyrot, col, lb, ktr, krot);
             }
             double v = ldv<SH>(sv.v + cc * ld + m);
             if (c < 3) {
-                x[Q_KTR] = hM * v * v;
-                x[Q_KROT] = anyrot ? hI * lb * lb : 0.0;
+                x[Q_KTR] = ktr;
+                x[Q_KROT] = krot;
             }
             if (mode & RED_HALFKICK) {  // Verlet: velocities at t + dt, recorded
                 v += 0.5 * P->kick[sp] * Fc;
@@ -563,6 +588,27 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
         const int kj = (lane >> 3) & 3;
         if ((lane & 7) == 0 && kj < 3) S.blk[(size_t)u * MS2_NRED + Q_N + kj] = tj;
     }
+}
+
+// The kinetic terms of reduction unit u of U (at most 8 molecules: one pass of
+// reduce_unit) into pre[6][32], as reduce_unit would form them: a warp with no
+// other work forms them before the forces are known.  Every lane calls it.
+template <bool SH>
+__device__ __forceinline__ void kin_pre(const SysParams *__restrict__ P, const DevSys &S, const RedIO &io, int u, int U,
+                                        int lane, double *pre) {
+    const int N = S.N, c = lane & 3, cc = c < 3 ? c : 2;
+    const int i_lo = (int)((long long)N * u / U), i_hi = (int)((long long)N * (u + 1) / U);
+    const int i = i_lo + (lane >> 2);
+    const int ii = i < i_hi ? i : i_lo, m = ii - io.i0;
+    const int sp = io.sv.spc[m];
+    const bool anyrot = __any_sync(0xffffffffu, P->rot[sp] != 0);
+    double col[3], lb, ktr, krot;
+    kin_terms<SH>(P, io.sv, m, sp, c, cc, anyrot, col, lb, ktr, krot);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) pre[k * 32 + lane] = col[k];
+    pre[3 * 32 + lane] = lb;
+    pre[4 * 32 + lane] = ktr;
+    pre[5 * 32 + lane] = krot;
 }
 
 // total of per-unit scalar k over units [0, nvb) by one warp, in reduce_totals'

@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     constexpr int EWM = ELEC == ELEC_EWALD ? RED_EWALD : 0;  // reduction mode bit of the reciprocal space
     __shared__ double tot[MS2_NRED];
     __shared__ double lam_s;                    // thermostat factor for the next drift
+    __shared__ double kin_s[6 * 32];            // kinetic terms of the reduction unit (kin_pre)
     __shared__ unsigned long long tph[6];       // timing: entry, then the phase marks of the last step
     const int N = S.N, G = gridDim.x, b = blockIdx.x, JS = S.jsplit, MC = A.mcap;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -189,6 +190,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     // the thermostat factor of the next drift, per thread: the drift warps form
     // it themselves after each step's reduction (no block barrier on it)
     double lam_r = lam_s;
+    // one reduction pass (at most 8 molecules) and a warp left without a pair item
+    const bool kin_early = nm <= 8 && nm * JS <= STEP_WARPS - 2;
     // k = -1 (after ms2_set_state): the state as set is evaluated first -- site
     // build instead of the drift, then partner search, forces, unit reduction,
     // totals and the configuration's scalars (ms2_eval_forces' k_build, k_pair
@@ -223,6 +226,13 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
             finish_step_warp(Ps, S, RED_SUM | RED_RECORD | RED_LAMBDA | EWM | gk, tot, lane, acc_s, kc_s);
             if (gk) gk_update(S, tot, lane);
             if (HEAT && hf_step(A, k - 1)) heat_record(S, G, lane);
+        }
+        // the kinetic terms of the reduction unit need no forces: a warp without
+        // a pair item (nor block 0's record) forms them beside the pair phase
+        if (kin_early && warp == STEP_WARPS - 2) {
+            const OwnLayout ol = own_layout(MC, JS, (size_t)A.ews);
+            const RedIO io{part_at(), nullptr, MC, view(), (double *)(own + ol.ui), (int *)(own + ol.np), MC, lo};
+            kin_pre<true>(Ps, S, io, b, G, lane, kin_s);
         }
         for (int t = warp; t < nm * JS; t += STEP_WARPS) {
             const int m = t % nm, p = t / nm, i = lo + m;
@@ -281,7 +291,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         if (warp == 0) {
             const OwnLayout ol = own_layout(MC, JS, (size_t)A.ews);
             const RedIO io{part_at(), nullptr, MC, view(), (double *)(own + ol.ui), (int *)(own + ol.np), MC, lo};
-            reduce_unit<true>(Ps, S, io, RED_SUM | RED_LAMBDA | EWM | (!ev && gk_step(A, k) ? RED_GK : 0), b, G, lane);
+            reduce_unit<true>(Ps, S, io, RED_SUM | RED_LAMBDA | EWM | (!ev && gk_step(A, k) ? RED_GK : 0), b, G, lane,
+                              kin_early ? kin_s : nullptr);
         }
         mark(k, 2);
         grid_sync(A.bar, A.err, target, on_timeout, A.wait_ns);
