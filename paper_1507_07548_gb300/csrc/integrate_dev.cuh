@@ -590,9 +590,10 @@ __device__ __forceinline__ void reduce_unit(const SysParams *__restrict__ P, con
     }
 }
 
-// The kinetic terms of reduction unit u of U (at most 8 molecules: one pass of
-// reduce_unit) into pre[6][32], as reduce_unit would form them: a warp with no
-// other work forms them before the forces are known.  Every lane calls it.
+// The kinetic terms of reduction unit u of U (1 to 8 molecules: one pass of
+// reduce_unit; the caller checks) into pre[6][32], as reduce_unit would form
+// them: a warp with no other work forms them before the forces are known.
+// Every lane calls it.
 template <bool SH>
 __device__ __forceinline__ void kin_pre(const SysParams *__restrict__ P, const DevSys &S, const RedIO &io, int u, int U,
                                         int lane, double *pre) {

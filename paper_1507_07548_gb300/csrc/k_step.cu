@@ -190,8 +190,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     // the thermostat factor of the next drift, per thread: the drift warps form
     // it themselves after each step's reduction (no block barrier on it)
     double lam_r = lam_s;
-    // one reduction pass (at most 8 molecules) and a warp left without a pair item
-    const bool kin_early = nm <= 8 && nm * JS <= STEP_WARPS - 2;
+    // one reduction pass (1 to 8 molecules) and a warp left without a pair item
+    const bool kin_early = nm >= 1 && nm <= 8 && nm * JS <= STEP_WARPS - 2;
     // k = -1 (after ms2_set_state): the state as set is evaluated first -- site
     // build instead of the drift, then partner search, forces, unit reduction,
     // totals and the configuration's scalars (ms2_eval_forces' k_build, k_pair

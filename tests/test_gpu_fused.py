@@ -40,6 +40,12 @@ def water_large():
     return wl
 
 
+def water_tiny():
+    wl = W.water_box(N=100, rc=7.0, seed=23)  # fewer molecules than blocks: blocks that own none
+    wl.dt = 0.5
+    return wl
+
+
 def stock():
     return snapshot(W.stockmayer_fluid(N=500, seed=4), "stockmayer_N500")
 
@@ -55,8 +61,8 @@ def ionic():
     return snapshot(W.ionic_solution(seed=3), "ionic_N1040")
 
 
-CASES = [water1000, water_ragged, water_large, stock, lj32, ionic]
-IDS = ["water1000", "water1003", "water2744", "stockmayer", "lj", "ionic_ewald"]
+CASES = [water1000, water_ragged, water_large, water_tiny, stock, lj32, ionic]
+IDS = ["water1000", "water1003", "water2744", "water100", "stockmayer", "lj", "ionic_ewald"]
 
 
 def rms_rel(a, b):
