@@ -50,6 +50,8 @@ namespace {
 
 constexpr int STEP_THREADS = 512;
 constexpr int STEP_WARPS = STEP_THREADS / 32;
+// warps of block 0's record totals (quantity q on kTotWarp[q]; up to Q_N + 3)
+__device__ constexpr int kTotWarp[10] = {6, 7, 8, 10, 11, 12, 14, 15, 9, 13};
 // site-site RDF of the staged configuration (the k_rdf arithmetic, reading
 // the shared-memory tile): molecules i = block, block + grid, ...; threads over j > i
 template <int NS, bool MULTI>
@@ -300,16 +302,24 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         // ---- totals.  The warps that drift the block's molecules form the
         // kinetic energy after the kick and from it the thermostat factor of
         // their next drift (the same fixed-order sum in each); block 0 forms
-        // every step scalar for its record on the last warps, which the drift
+        // every step scalar for its record on warps 6-15, which the drift
         // leaves idle (its molecules take warps 1-4 at most), beside the next
         // drift.  The next grid barrier orders them before the record reads them.
         {
             const int nq = !ev && gk_step(A, k) ? Q_N + 3 : Q_N;
             if (warp >= 1 && 8 * (warp - 1) < nm) lam_r = lambda_k1(Ps, unit_total(S, G, Q_K1, lane));
-            if (b == 0 && warp >= STEP_WARPS - nq) {
-                const int q = warp - (STEP_WARPS - nq);
-                const double x = unit_total(S, G, q, lane);
-                if (lane == 0) tot[q] = x;
+            // quantity q on warp kTotWarp[q]: warps 6-15, those that share no
+            // scheduler (warp % 4) with warp 1, which drifts up to 8 molecules,
+            // first (the FP64 unit is per scheduler)
+            if (b == 0) {
+                int q = -1;
+#pragma unroll
+                for (int t = 0; t < 10; ++t)
+                    if (kTotWarp[t] == warp && t < nq) q = t;
+                if (q >= 0) {
+                    const double x = unit_total(S, G, q, lane);
+                    if (lane == 0) tot[q] = x;
+                }
             }
             if (ev && b == 0) {  // the scalars of the state as set, at once
                 __syncthreads();
