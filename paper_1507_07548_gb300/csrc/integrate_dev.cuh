@@ -13,22 +13,42 @@ __device__ __forceinline__ double rsqrt_fp64(double x) {  // FP32 seed + two New
 }
 
 // ------------------------------------------------------------ site build
+// row c of A(q) for the cyclic order (c, c1, c2), with v = (x, y, z):
+//   A[c][c] = 1 - 2 (v_c1^2 + v_c2^2), A[c][c1] = 2 (v_c v_c1 - w v_c2),
+//   A[c][c2] = 2 (v_c v_c2 + w v_c1)
+// (one instruction stream for the three lanes: no branch on c)
+__device__ __forceinline__ void rot_row(const double q[4], int c, double &acc, double &ac1, double &ac2) {
+    const double w = q[0];
+    const double vc = c == 0 ? q[1] : (c == 1 ? q[2] : q[3]);
+    const double v1 = c == 0 ? q[2] : (c == 1 ? q[3] : q[1]);
+    const double v2 = c == 0 ? q[3] : (c == 1 ? q[1] : q[2]);
+    acc = 1.0 - 2.0 * (v1 * v1 + v2 * v2);
+    ac1 = 2.0 * (vc * v1 - w * v2);
+    ac2 = 2.0 * (vc * v2 + w * v1);
+}
+
+// component c of the space-frame offset o and dipole m of site a of species sp
+// (0 where a is not one of its sites), from row c of A(q)
+__device__ __forceinline__ void site_row(const SysParams *__restrict__ P, int sp, int a, int c, double acc, double ac1,
+                                         double ac2, bool dip, double &o, double &m) {
+    const int c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
+    o = 0.0;
+    m = 0.0;
+    if (a < P->n_sites[sp]) {
+        const double *b = P->bpos[sp][a], *u = P->bdip[sp][a];
+        o = acc * b[c] + ac1 * b[c1] + ac2 * b[c2];
+        if (dip) m = acc * u[c] + ac1 * u[c1] + ac2 * u[c2];
+    }
+}
+
 // lattice centre coordinate of component c; row c of the space-frame site
 // offsets, dipoles and molecular charge dipole (lane c of a quad)
 __device__ __forceinline__ void build_row(const SysParams *__restrict__ P, const DevSys &S, int i, int c,
                                           const double q[4], double Rc, int sp) {
     const int N = S.N, NS = S.ns;
     S.X[c * N + i] = lattice_coord(Rc, P->lat_scale);
-    // row c of A(q) for the cyclic order (c, c1, c2), with v = (x, y, z):
-    //   A[c][c] = 1 - 2 (v_c1^2 + v_c2^2), A[c][c1] = 2 (v_c v_c1 - w v_c2),
-    //   A[c][c2] = 2 (v_c v_c2 + w v_c1)
-    // (one instruction stream for the three lanes: no branch on c)
-    const double w = q[0];
-    const double vc = c == 0 ? q[1] : (c == 1 ? q[2] : q[3]);
-    const double v1 = c == 0 ? q[2] : (c == 1 ? q[3] : q[1]);
-    const double v2 = c == 0 ? q[3] : (c == 1 ? q[1] : q[2]);
-    const int c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
-    const double acc = 1.0 - 2.0 * (v1 * v1 + v2 * v2), ac1 = 2.0 * (vc * v1 - w * v2), ac2 = 2.0 * (vc * v2 + w * v1);
+    double acc, ac1, ac2;
+    rot_row(q, c, acc, ac1, ac2);
     const int nsp = P->n_sites[sp];
     if (P->point[sp]) {  // sites and dipoles at the centre: the offsets are zero in every orientation
         for (int a = 0; a < NS; ++a) {
@@ -40,17 +60,41 @@ __device__ __forceinline__ void build_row(const SysParams *__restrict__ P, const
     }
     double md = 0.0;
     for (int a = 0; a < NS; ++a) {
-        double o = 0.0, m = 0.0;
-        if (a < nsp) {
-            const double *b = P->bpos[sp][a], *u = P->bdip[sp][a];
-            o = acc * b[c] + ac1 * b[c1] + ac2 * b[c2];
-            if (S.mu) m = acc * u[c] + ac1 * u[c1] + ac2 * u[c2];
-            md += P->qd[sp][a] * o;
-        }
+        double o, m;
+        site_row(P, sp, a, c, acc, ac1, ac2, S.mu != nullptr, o, m);
+        if (a < nsp) md += P->qd[sp][a] * o;
         S.s[(c * NS + a) * N + i] = d2f(o);
         if (S.mu) S.mu[(c * NS + a) * N + i] = d2f(m);
     }
     if (S.mum) S.mum[c * N + i] = d2f(md);
+}
+
+// build_row split by site, for a warp per site: site a's offset and dipole rows
+// (returns the offset for build_md); the lattice coordinate is left to the caller
+__device__ __forceinline__ double build_site(const SysParams *__restrict__ P, const DevSys &S, int i, int c,
+                                             const double q[4], int sp, int a) {
+    const int N = S.N, NS = S.ns;
+    double o = 0.0, m = 0.0;
+    if (!P->point[sp]) {
+        double acc, ac1, ac2;
+        rot_row(q, c, acc, ac1, ac2);
+        site_row(P, sp, a, c, acc, ac1, ac2, S.mu != nullptr, o, m);
+    }
+    S.s[(c * NS + a) * N + i] = d2f(o);
+    if (S.mu) S.mu[(c * NS + a) * N + i] = d2f(m);
+    return o;
+}
+
+// the molecular charge dipole of build_row from the site offsets od[a] of build_site
+__device__ __forceinline__ void build_md(const SysParams *__restrict__ P, const DevSys &S, int i, int c, int sp,
+                                         const double *od, int ostride) {
+    if (!S.mum) return;
+    const int N = S.N, NS = S.ns, nsp = P->n_sites[sp];
+    double md = 0.0;
+    if (!P->point[sp])
+        for (int a = 0; a < NS; ++a)
+            if (a < nsp) md += P->qd[sp][a] * od[a * ostride];
+    S.mum[c * N + i] = d2f(md);
 }
 
 // ------------------------------------------------------- rigid rotation
@@ -301,7 +345,7 @@ __device__ __forceinline__ StateView global_view(const DevSys &S) {
 // `on` is false for padding quads: they compute on slot/molecule 0 and store
 // nothing.  F and tau come through L2 loads (another block may have written
 // them in a persistent kernel).
-template <bool SH>
+template <bool SH, bool BUILD = true>
 __device__ __forceinline__ void drift_quad(const SysParams *__restrict__ P, const DevSys &S, const StateView &sv, int m,
                                            int i, bool on, int c, bool verlet, double lam) {
     const int ld = sv.ld, mm = on ? m : 0, cc = c < 3 ? c : 2;
@@ -345,7 +389,7 @@ __device__ __forceinline__ void drift_quad(const SysParams *__restrict__ P, cons
             }
         }
     }
-    if (c < 3 && on) build_row(P, S, i, c, q, Rc, sp);
+    if (BUILD && c < 3 && on) build_row(P, S, i, c, q, Rc, sp);
 }
 
 // Fixed-tree sum of 8 values over a warp: 9 FP64 adds instead of 8 x 5.  On

@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     __shared__ double tot[MS2_NRED];
     __shared__ double lam_s;                    // thermostat factor for the next drift
     __shared__ double kin_s[6 * 32];            // kinetic terms of the reduction unit (kin_pre)
+    __shared__ double od_s[4 * 32];             // site offsets of the split site build (build_site)
     __shared__ unsigned long long tph[6];       // timing: entry, then the phase marks of the last step
     const int N = S.N, G = gridDim.x, b = blockIdx.x, JS = S.jsplit, MC = A.mcap;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -194,6 +195,9 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
     double lam_r = lam_s;
     // one reduction pass (1 to 8 molecules) and a warp left without a pair item
     const bool kin_early = nm >= 1 && nm <= 8 && nm * JS <= STEP_WARPS - 2;
+    // one drift pass (1 to 8 molecules, warp 1) and 2 to 4 site slots: the site
+    // build runs a warp per site
+    const bool site_split = NS >= 2 && NS <= 4 && nm >= 1 && nm <= 8;
     // k = -1 (after ms2_set_state): the state as set is evaluated first -- site
     // build instead of the drift, then partner search, forces, unit reduction,
     // totals and the configuration's scalars (ms2_eval_forces' k_build, k_pair
@@ -207,13 +211,33 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
             for (int m0 = 8 * (warp - 1); m0 < nm; m0 += 8 * (STEP_WARPS - 1)) {
                 const int m = m0 + (lane >> 2), c = lane & 3;
                 if (!ev) {
-                    drift_quad<true>(Ps, S, view(), m, lo + m, m < nm, c, false, lam_r);
+                    if (site_split)
+                        drift_quad<true, false>(Ps, S, view(), m, lo + m, m < nm, c, false, lam_r);
+                    else
+                        drift_quad<true>(Ps, S, view(), m, lo + m, m < nm, c, false, lam_r);
                 } else if (m < nm && c < 3) {
                     const StateView sv = view();
                     const double q[4] = {sv.q[m], sv.q[MC + m], sv.q[2 * MC + m], sv.q[3 * MC + m]};
                     build_row(Ps, S, lo + m, c, q, sv.R[c * MC + m], sv.spc[m]);
                 }
             }
+        if (!ev && site_split) {
+            // the site build of the drifted molecules split by site: warp 1 + a
+            // builds site a's rows (and warp 1 the lattice centres), each FP64
+            // chain on a scheduler of its own; then warp 1 sums the molecular
+            // dipole from their offsets in site order (build_row's arithmetic)
+            __syncthreads();
+            const int m = lane >> 2, c = lane & 3;
+            if (warp >= 1 && warp <= NS && m < nm && c < 3) {
+                const StateView sv = view();
+                const double q[4] = {sv.q[m], sv.q[MC + m], sv.q[2 * MC + m], sv.q[3 * MC + m]};
+                const int a = warp - 1;
+                if (a == 0) S.X[c * N + lo + m] = lattice_coord(sv.R[c * MC + m], Ps->lat_scale);
+                od_s[a * 32 + lane] = build_site(Ps, S, lo + m, c, q, sv.spc[m], a);
+            }
+            __syncthreads();
+            if (warp == 1 && m < nm && c < 3) build_md(Ps, S, lo + m, c, view().spc[m], od_s + lane, 32);
+        }
         mark(k, 0);
         grid_sync(A.bar, A.err, target, on_timeout, A.wait_ns);
         if (tm) tph[1] = global_ns();
