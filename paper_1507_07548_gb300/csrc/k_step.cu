@@ -50,8 +50,25 @@ namespace {
 
 constexpr int STEP_THREADS = 512;
 constexpr int STEP_WARPS = STEP_THREADS / 32;
-// warps of block 0's record totals (quantity q on kTotWarp[q]; up to Q_N + 3)
-__device__ constexpr int kTotWarp[10] = {6, 7, 8, 10, 11, 12, 14, 15, 9, 13};
+// the quantity of block 0's record totals that warp w forms (-1: none), up to
+// Q_N + 3 of them: warps 6-15, those that share no scheduler (warp % 4) with
+// warp 1 first (a switch: no table in memory, which a step after an L2 flush
+// would read from DRAM)
+__device__ __forceinline__ int tot_quantity(int w) {
+    switch (w) {
+        case 6: return 0;
+        case 7: return 1;
+        case 8: return 2;
+        case 10: return 3;
+        case 11: return 4;
+        case 12: return 5;
+        case 14: return 6;
+        case 15: return 7;
+        case 9: return 8;
+        case 13: return 9;
+        default: return -1;
+    }
+}
 // site-site RDF of the staged configuration (the k_rdf arithmetic, reading
 // the shared-memory tile): molecules i = block, block + grid, ...; threads over j > i
 template <int NS, bool MULTI>
@@ -331,16 +348,15 @@ __global__ void __launch_bounds__(STEP_THREADS, 1) k_step(const SysParams *__res
         // drift.  The next grid barrier orders them before the record reads them.
         {
             const int nq = !ev && gk_step(A, k) ? Q_N + 3 : Q_N;
-            if (warp >= 1 && 8 * (warp - 1) < nm) lam_r = lambda_k1(Ps, unit_total(S, G, Q_K1, lane));
-            // quantity q on warp kTotWarp[q]: warps 6-15, those that share no
-            // scheduler (warp % 4) with warp 1, which drifts up to 8 molecules,
-            // first (the FP64 unit is per scheduler)
+            // (none after the launch's last step: the next launch takes the factor
+            // from block 0's record)
+            if (k < A.nsteps - 1 && warp >= 1 && 8 * (warp - 1) < nm) lam_r = lambda_k1(Ps, unit_total(S, G, Q_K1, lane));
+            // quantity q on warp tot_quantity^-1(q): warps 6-15, those that
+            // share no scheduler (warp % 4) with warp 1, which drifts up to 8
+            // molecules, first (the FP64 unit is per scheduler)
             if (b == 0) {
-                int q = -1;
-#pragma unroll
-                for (int t = 0; t < 10; ++t)
-                    if (kTotWarp[t] == warp && t < nq) q = t;
-                if (q >= 0) {
+                const int q = tot_quantity(warp);
+                if (q >= 0 && q < nq) {
                     const double x = unit_total(S, G, q, lane);
                     if (lane == 0) tot[q] = x;
                 }
